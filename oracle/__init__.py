@@ -1,0 +1,20 @@
+"""CPU FP64 oracle for the space-time IgA monodomain / Rogers-McCulloch solver.
+
+TEST INFRASTRUCTURE ONLY.  This package is the plain, slow, independent
+definition of what the CUDA path computes: it assembles the sparse space-time
+matrices element by element with Gauss quadrature and solves them with a direct
+sparse solver (Sec. 2-3 of the paper).  It shares no code with the CUDA path;
+only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
+it.
+
+Pins (tests/test_oracle_*.py) tie it to what the paper and the mathematics fix:
+partition of unity and linear precision of the B-splines, textbook 1D mass and
+stiffness rows, the W_t + W_t^T identity, the Kronecker structure of A and
+A-hat, the tau invariant, the w elimination, the rest state, the low-rank
+tolerance, convergence rates against closed-form solutions and the spatially
+uniform ODE limit.  Parity is unpinned for the full nonlinear Spline-Upwind
+wave runs, which only the oracle itself defines.
+"""
+
+from .solve import Oracle  # noqa: F401
+from .spacetime import SpaceTime  # noqa: F401
