@@ -1,0 +1,10 @@
+"""GB300-native space-time isogeometric solver for the monodomain equation
+with the Rogers-McCulloch ionic model (Spline Upwind stabilization).
+
+The compute path is libst.so (include/st.h): CUDA kernels for sm_103a behind
+a C ABI.  This package holds the in-tree build script and a thin ctypes
+binding; it has no CPU fallback.
+"""
+
+from ._lib import (Solver, footprint, load, make_desc, StError,  # noqa: F401
+                   ST_FP64, ST_MIXED, ST_PICARD, ST_NEWTON, EXPORTS)

@@ -1,0 +1,794 @@
+// C ABI of libst.so: set-up, operator, preconditioner, Krylov solver and the
+// nonlinear loop of the space-time IgA monodomain solver (include/st.h).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+#include "st_internal.h"
+
+void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, int M, int N, int K,
+                   long long sam, long long sak, long long sbk, long long sbc, long long scm, long long scc,
+                   double alpha, double beta);
+
+namespace {
+
+struct Sizes {
+  int d, p, nq, B;
+  int n[3], nel[3], Q[3];
+  int Nt, nel_t, Qt;
+  long long Ns, Ndof, Qs, Nel_s, NtQs;
+  int m, nmax, cap;
+  size_t bytes;
+};
+
+st_status validate(const st_problem_desc *d) {
+  if (!d) return ST_ERR_ARG;
+  if (d->d < 1 || d->d > 3 || d->p < 1 || d->p > ST_MAXP) return ST_ERR_ARG;
+  for (int l = 0; l < d->d; ++l)
+    if (d->n_el[l] < 1 || d->n_el[l] > (1 << 16) || !(d->D[l] > 0)) return ST_ERR_ARG;
+  if (d->n_el_t < 1 || d->n_el_t > (1 << 16)) return ST_ERR_ARG;
+  if (!(d->T > 0) || !(d->C_m > 0)) return ST_ERR_ARG;
+  if (d->source_kind < ST_SRC_ZERO || d->source_kind > ST_SRC_E1_MMS) return ST_ERR_ARG;
+  if (d->source_kind == ST_SRC_E1_MMS && d->d != 1) return ST_ERR_ARG;
+  if (d->n_stim < 0 || d->n_stim > ST_MAX_STIM) return ST_ERR_ARG;
+  if (d->stabilization != ST_GALERKIN && d->stabilization != ST_SU) return ST_ERR_ARG;
+  if (d->suppext != ST_SUPPEXT_LITERAL && d->suppext != ST_SUPPEXT_SYMMETRIC) return ST_ERR_ARG;
+  if (d->nonlinear != ST_PICARD && d->nonlinear != ST_NEWTON) return ST_ERR_ARG;
+  if (d->precision != ST_FP64 && d->precision != ST_MIXED) return ST_ERR_ARG;
+  if (d->gmres_m < 1 || d->gmres_m > 500 || !(d->rtol > 0) || d->max_it < 1) return ST_ERR_ARG;
+  if (!(d->eps_theta >= 0) || !(d->alpha > 0) || d->alpha > 1 || !(d->delta >= 0) || d->max_fp < 1)
+    return ST_ERR_ARG;
+  return ST_OK;
+}
+
+Sizes plan(const st_problem_desc &D) {
+  Sizes z;
+  z.d = D.d; z.p = D.p; z.nq = D.p + 1; z.B = 2 * D.p + 1;
+  z.Ns = 1; z.Qs = 1; z.Nel_s = 1;
+  for (int l = 0; l < 3; ++l) {
+    if (l < D.d) { z.nel[l] = D.n_el[l]; z.n[l] = D.n_el[l] + D.p; z.Q[l] = D.n_el[l] * z.nq; }
+    else { z.nel[l] = 1; z.n[l] = 1; z.Q[l] = 1; }
+    z.Ns *= z.n[l]; z.Qs *= z.Q[l]; z.Nel_s *= z.nel[l];
+  }
+  z.nel_t = D.n_el_t;
+  z.Nt = D.n_el_t + D.p - 1;
+  z.Qt = D.n_el_t * z.nq;
+  z.Ndof = z.Ns * z.Nt;
+  z.NtQs = (long long)z.Nt * z.Qs;
+  z.m = D.gmres_m;
+  z.nmax = z.Nt;
+  for (int l = 0; l < D.d; ++l) z.nmax = std::max(z.nmax, z.n[l]);
+  z.cap = (int)std::min<long long>(z.Nt, z.Ns);
+  size_t b = 0;
+  size_t d8 = sizeof(double), f4 = sizeof(float);
+  // 1D data (generous)
+  b += (size_t)(6 * z.nmax * z.B + 4 * z.nmax * z.nmax) * (d8 + f4) + (size_t)z.Qt * (z.p + 2) * z.nq * d8 * 4;
+  b += (size_t)(3 * z.nmax * z.nq * z.nq * 4) * d8;
+  b += (size_t)z.Ns * d8;                                          // mu
+  b += (size_t)z.Nt * z.B * z.Ns * (d8 + f4);                      // LU per eigen-index
+  b += (size_t)(z.p + 1) * z.NtQs * (d8 + f4);                     // bands
+  b += (size_t)z.Ndof * d8 * 9;                                    // f, theta, FP64 vectors
+  b += (size_t)z.Ndof * f4 * 4;                                    // FP32 vectors
+  b += (size_t)z.nel_t * z.Nel_s * 8;                              // element maxima
+  b += (size_t)z.Nt * z.Nt * d8 * 2 + (size_t)z.nmax * z.nmax * (12 * d8 + 2 * f4);
+  b += (size_t)z.cap * (z.Nt + z.Ns + 1 + z.Qt + (z.p + 1) * z.Nt) * d8;
+  b += (size_t)z.NtQs * d8 * 5;                                    // two work buffers + ionic fields
+  b += (size_t)z.NtQs * f4 * 2;
+  b += (size_t)z.Ndof * (d8 + f4) * 7;                             // Kronecker temporaries
+  if (D.precision == ST_FP64) b += (size_t)(z.m + 1) * z.Ndof * d8;
+  else b += (size_t)(z.m + 1) * z.Ndof * f4;
+  b += (size_t)(304 * (z.m + 40) + 4096) * d8;
+  z.bytes = b;
+  return z;
+}
+
+template <typename T>
+T *dalloc(st_handle *h, size_t count, st_status *err) {
+  return (T *)st_alloc(h, count * sizeof(T), err);
+}
+
+template <typename T>
+st_status upload(st_handle *h, T **dst, const std::vector<double> &src) {
+  st_status e = ST_OK;
+  *dst = dalloc<T>(h, std::max<size_t>(src.size(), 1), &e);
+  if (e != ST_OK) return e;
+  std::vector<T> tmp(src.begin(), src.end());
+  if (!tmp.empty()) ST_CUDA(cudaMemcpyAsync(*dst, tmp.data(), tmp.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  ST_CUDA(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+template <typename T>
+st_status upload_i(st_handle *h, int **dst, const std::vector<int> &src) {
+  st_status e = ST_OK;
+  *dst = dalloc<int>(h, std::max<size_t>(src.size(), 1), &e);
+  if (e != ST_OK) return e;
+  if (!src.empty()) ST_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream));
+  ST_CUDA(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
+// left node and weight of the linear interpolation on `grid` at each point
+void hat_data(const std::vector<double> &grid, const std::vector<double> &pts, std::vector<int> &idx,
+              std::vector<double> &lam) {
+  int n = (int)grid.size();
+  idx.assign(pts.size(), 0);
+  lam.assign(pts.size(), 0.0);
+  if (n < 2) return;
+  for (size_t k = 0; k < pts.size(); ++k) {
+    double x = pts[k];
+    int i = (int)(std::upper_bound(grid.begin(), grid.end(), x) - grid.begin()) - 1;
+    i = std::max(0, std::min(n - 2, i));
+    double l = (x - grid[i]) / (grid[i + 1] - grid[i]);
+    idx[k] = i;
+    lam[k] = std::max(0.0, std::min(1.0, l));
+  }
+}
+
+double host_scalar(st_handle *h, const double *dptr) {
+  double v = 0.0;
+  cudaMemcpyAsync(&v, dptr, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  return v;
+}
+
+double norm2_64(st_handle *h, const double *x) {
+  launch_norm2_64(h->stream, h->red + 4000, x, h->Ndof, h->red + 4096);
+  return std::sqrt(host_scalar(h, h->red + 4000));
+}
+
+double absmax_diff(st_handle *h, const double *x, const double *y) {
+  launch_absmax64(h->stream, h->red + 4000, x, y, h->Ndof, h->red + 4096);
+  return host_scalar(h, h->red + 4000);
+}
+
+// Krylov basis accessors
+template <typename T> T *basis(st_handle *h);
+template <> double *basis<double>(st_handle *h) { return h->V64; }
+template <> float *basis<float>(st_handle *h) { return h->V32; }
+template <typename T> T *ztmp(st_handle *h);
+template <> double *ztmp<double>(st_handle *h) { return h->z64; }
+template <> float *ztmp<float>(st_handle *h) { return h->t32a; }
+
+// Right-preconditioned GMRES(m) on A_T d = b from d = 0, one cycle of at most
+// `maxit` (<= m) iterations; stops when the Arnoldi residual estimate drops to
+// tol * ||b||.  Gram-Schmidt: classical with one reorthogonalization, inner
+// products accumulated in FP64 in a fixed order.  Hessenberg and Givens in FP64.
+template <typename T>
+st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int *its, double *est) {
+  cudaStream_t s = h->stream;
+  long long N = h->Ndof;
+  T *V = basis<T>(h);
+  T *z = ztmp<T>(h);
+  int m = std::min(maxit, h->m);
+  double *hd = h->hcol;           // device: h1 [0..m], h2 [m+1 ..]
+  double *scratch = h->red + 4096;
+  launch_multi_dot<T>(s, hd, b, N, 1, b, N, scratch);
+  double beta = std::sqrt(host_scalar(h, hd));
+  *its = 0;
+  if (!(beta > 0.0) || !std::isfinite(beta)) {
+    ST_CUDA(cudaMemsetAsync(d, 0, N * sizeof(T), s));
+    *est = std::isfinite(beta) ? 0.0 : INFINITY;
+    return std::isfinite(beta) ? ST_OK : ST_ERR_NAN;
+  }
+  launch_scale_copy<T>(s, V, b, 1.0 / beta, N);
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
+  std::vector<double> hh(2 * (m + 1) + 1);
+  g[0] = beta;
+  int j = 0;
+  double res = beta;
+  for (; j < m; ++j) {
+    T *vj = V + (long long)j * N, *w = V + (long long)(j + 1) * N;
+    ST_TRY(precond_T<T>(h, vj, z));
+    ST_TRY(apply_T<T>(h, z, w));
+    double *h1 = hd, *h2 = hd + (m + 1), *hn = hd + 2 * (m + 1);
+    launch_multi_dot<T>(s, h1, V, N, j + 1, w, N, scratch);
+    launch_multi_axpy<T>(s, w, V, N, j + 1, h1, N);
+    launch_multi_dot<T>(s, h2, V, N, j + 1, w, N, scratch);
+    launch_multi_axpy<T>(s, w, V, N, j + 1, h2, N);
+    launch_multi_dot<T>(s, hn, w, N, 1, w, N, scratch);
+    ST_CUDA(cudaMemcpyAsync(hh.data(), hd, (2 * (m + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaStreamSynchronize(s));
+    double hnorm = std::sqrt(std::max(hh[2 * (m + 1)], 0.0));
+    if (!std::isfinite(hnorm)) return ST_ERR_NAN;
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[(m + 1) + i];
+    H[(size_t)(j + 1) * m + j] = hnorm;
+    if (hnorm > 0.0) launch_scale_copy<T>(s, w, w, 1.0 / hnorm, N);
+    // apply the previous Givens rotations to the new column, then a new one
+    for (int i = 0; i < j; ++i) {
+      double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+      H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
+      H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+    }
+    double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+    double r = std::hypot(a, c);
+    cs[j] = r > 0 ? a / r : 1.0;
+    sn[j] = r > 0 ? c / r : 0.0;
+    H[(size_t)j * m + j] = r;
+    H[(size_t)(j + 1) * m + j] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    res = std::fabs(g[j + 1]);
+    if (res <= tol * beta || hnorm == 0.0) { ++j; break; }
+  }
+  int k = j;   // columns used
+  // back substitution H(0:k,0:k) y = g(0:k)
+  std::vector<double> y(k, 0.0);
+  for (int i = k - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int l = i + 1; l < k; ++l) t -= H[(size_t)i * m + l] * y[l];
+    double piv = H[(size_t)i * m + i];
+    y[i] = piv != 0.0 ? t / piv : 0.0;
+  }
+  // d = M^{-1} (V y): accumulate V y into z with the multi-axpy (z -= sum (-y_i) V_i)
+  for (int i = 0; i < k; ++i) y[i] = -y[i];
+  ST_CUDA(cudaMemcpyAsync(hd, y.data(), std::max(k, 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+  ST_CUDA(cudaMemsetAsync(z, 0, N * sizeof(T), s));
+  if (k > 0) launch_multi_axpy<T>(s, z, V, N, k, hd, N);
+  ST_TRY(precond_T<T>(h, z, d));
+  *its = k;
+  *est = res / beta;
+  ST_CUDA(cudaStreamSynchronize(s));
+  return ST_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- internals
+void *st_alloc(st_handle *h, size_t bytes, st_status *err) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    cudaGetLastError();
+    *err = ST_ERR_OOM;
+    return nullptr;
+  }
+  h->allocs.push_back(p);
+  return p;
+}
+
+template <typename T> struct Prec;
+template <> struct Prec<double> {
+  static const double *Mb(st_handle *h, int l) { return h->Mb[l]; }
+  static const double *Kb(st_handle *h, int l) { return h->Kb[l]; }
+  static const double *Mt(st_handle *h) { return h->Mtb; }
+  static const double *Wt(st_handle *h) { return h->Wtb; }
+  static const double *Bq(st_handle *h, int l) { return h->Bq[l]; }
+  static double *W(st_handle *h, int i) { return h->W64[i]; }
+  static double *K(st_handle *h, int i) { return h->K64[i]; }
+  static const double *band(st_handle *h) { return h->band64; }
+  static const double *UT(st_handle *h, int l) { return h->UT64[l]; }
+  static const double *U(st_handle *h, int l) { return h->U64[l]; }
+  static const double *lu(st_handle *h) { return h->lu64; }
+};
+template <> struct Prec<float> {
+  static const float *Mb(st_handle *h, int l) { return h->Mb32[l]; }
+  static const float *Kb(st_handle *h, int l) { return h->Kb32[l]; }
+  static const float *Mt(st_handle *h) { return h->Mtb32; }
+  static const float *Wt(st_handle *h) { return h->Wtb32; }
+  static const float *Bq(st_handle *h, int l) { return h->Bq32[l]; }
+  static float *W(st_handle *h, int i) { return h->W32[i]; }
+  static float *K(st_handle *h, int i) { return h->K32[i]; }
+  static const float *band(st_handle *h) { return h->band32; }
+  static const float *UT(st_handle *h, int l) { return h->UT32[l]; }
+  static const float *U(st_handle *h, int l) { return h->U32[l]; }
+  static const float *lu(st_handle *h) { return h->lu32; }
+};
+
+// y = A x (Eq. lin_sys_A): Kronecker part C_m W_t (x) M_s + M_t (x) K_s by
+// banded passes, then the reaction + SU part (I (x) B_s^T) band (I (x) B_s)
+// by sum factorization in space and one banded product along time per
+// spatial Gauss point.
+template <typename T>
+st_status apply_T(st_handle *h, const T *x, T *y) {
+  typedef Prec<T> P;
+  cudaStream_t s = h->stream;
+  const st_problem_desc &D = h->desc;
+  int p = h->p;
+  long long nx = h->n[0], ny = h->n[1], nz = h->n[2], Nt = h->Nt, Ns = h->Ns;
+  // --- Kronecker part
+  const T *bands[3];
+  const T *ins[3];
+  double cf[3];
+  T *m = nullptr, *sK = nullptr;
+  if (h->d == 1) {
+    m = P::K(h, 0); sK = P::K(h, 1);
+    bands[0] = P::Mb(h, 0); ins[0] = x; cf[0] = 1.0;
+    launch_band_pass<T>(s, m, 1, bands, ins, cf, (int)nx, 1, Nt, p, false);
+    bands[0] = P::Kb(h, 0); cf[0] = D.D[0];
+    launch_band_pass<T>(s, sK, 1, bands, ins, cf, (int)nx, 1, Nt, p, false);
+  } else if (h->d == 2) {
+    T *a = P::K(h, 0), *b = P::K(h, 1);
+    m = P::K(h, 2); sK = P::K(h, 3);
+    bands[0] = P::Mb(h, 0); ins[0] = x; cf[0] = 1.0;
+    launch_band_pass<T>(s, a, 1, bands, ins, cf, (int)nx, 1, Nt * ny, p, false);
+    bands[0] = P::Kb(h, 0);
+    launch_band_pass<T>(s, b, 1, bands, ins, cf, (int)nx, 1, Nt * ny, p, false);
+    bands[0] = P::Mb(h, 1); ins[0] = a;
+    launch_band_pass<T>(s, m, 1, bands, ins, cf, (int)ny, nx, Nt, p, false);
+    bands[0] = P::Mb(h, 1); ins[0] = b; cf[0] = D.D[0];
+    bands[1] = P::Kb(h, 1); ins[1] = a; cf[1] = D.D[1];
+    launch_band_pass<T>(s, sK, 2, bands, ins, cf, (int)ny, nx, Nt, p, false);
+  } else {
+    T *a = P::K(h, 0), *b = P::K(h, 1), *c = P::K(h, 2), *e = P::K(h, 3), *g = P::K(h, 4);
+    m = P::K(h, 5); sK = P::K(h, 6);
+    cf[0] = 1.0;
+    bands[0] = P::Mb(h, 0); ins[0] = x;
+    launch_band_pass<T>(s, a, 1, bands, ins, cf, (int)nx, 1, Nt * ny * nz, p, false);
+    bands[0] = P::Kb(h, 0);
+    launch_band_pass<T>(s, b, 1, bands, ins, cf, (int)nx, 1, Nt * ny * nz, p, false);
+    bands[0] = P::Mb(h, 1); ins[0] = a;
+    launch_band_pass<T>(s, c, 1, bands, ins, cf, (int)ny, nx, Nt * nz, p, false);
+    ins[0] = b;
+    launch_band_pass<T>(s, e, 1, bands, ins, cf, (int)ny, nx, Nt * nz, p, false);
+    bands[0] = P::Kb(h, 1); ins[0] = a;
+    launch_band_pass<T>(s, g, 1, bands, ins, cf, (int)ny, nx, Nt * nz, p, false);
+    bands[0] = P::Mb(h, 2); ins[0] = c;
+    launch_band_pass<T>(s, m, 1, bands, ins, cf, (int)nz, nx * ny, Nt, p, false);
+    bands[0] = P::Mb(h, 2); ins[0] = e; cf[0] = D.D[0];
+    bands[1] = P::Mb(h, 2); ins[1] = g; cf[1] = D.D[1];
+    bands[2] = P::Kb(h, 2); ins[2] = c; cf[2] = D.D[2];
+    launch_band_pass<T>(s, sK, 3, bands, ins, cf, (int)nz, nx * ny, Nt, p, false);
+  }
+  bands[0] = P::Wt(h); ins[0] = m; cf[0] = D.C_m;
+  bands[1] = P::Mt(h); ins[1] = sK; cf[1] = 1.0;
+  launch_band_pass<T>(s, y, 2, bands, ins, cf, (int)Nt, Ns, 1, p, false);
+  // --- reaction + SU part
+  long long qd[3] = {h->Q[0], h->Q[1], h->Q[2]};
+  long long nd[3] = {h->n[0], h->n[1], h->n[2]};
+  const T *cur = x;
+  int ping = 0;
+  for (int l = 0; l < h->d; ++l) {
+    long long inner = 1, outer = Nt;
+    for (int k = 0; k < l; ++k) inner *= qd[k];
+    for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
+    T *out = P::W(h, ping);
+    launch_interp_fwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer);
+    cur = out;
+    ping ^= 1;
+  }
+  T *zq = P::W(h, ping);
+  launch_qband_apply<T>(s, zq, cur, P::band(h), h->Nt, h->Qs, p);
+  cur = zq;
+  ping ^= 1;
+  for (int l = h->d - 1; l >= 0; --l) {
+    long long inner = 1, outer = Nt;
+    for (int k = 0; k < l; ++k) inner *= qd[k];
+    for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
+    T *out = (l == 0) ? y : P::W(h, ping);
+    launch_interp_bwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer, l == 0);
+    cur = out;
+    ping ^= 1;
+  }
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+// z = A-hat^{-1} r by fast diagonalization (Eq. factorized): transforms with
+// U_l^T along each spatial axis, one banded LU solve along time per spatial
+// eigen-index, transforms with U_l.
+template <typename T>
+st_status precond_T(st_handle *h, const T *r, T *z) {
+  typedef Prec<T> P;
+  cudaStream_t s = h->stream;
+  long long nd[3] = {h->n[0], h->n[1], h->n[2]};
+  const T *cur = r;
+  T *bufs[2] = {P::K(h, 0), P::K(h, 1)};
+  int ping = 0;
+  for (int l = 0; l < h->d; ++l) {
+    long long inner = 1, outer = h->Nt;
+    for (int k = 0; k < l; ++k) inner *= nd[k];
+    for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
+    launch_mode_gemm<T>(s, bufs[ping], cur, P::UT(h, l), h->n[l], inner, outer);
+    cur = bufs[ping];
+    ping ^= 1;
+  }
+  launch_tline_lu_solve<T>(s, bufs[ping], cur, P::lu(h), h->Nt, h->Ns, h->p);
+  cur = bufs[ping];
+  ping ^= 1;
+  for (int l = 0; l < h->d; ++l) {
+    long long inner = 1, outer = h->Nt;
+    for (int k = 0; k < l; ++k) inner *= nd[k];
+    for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
+    T *out = (l == h->d - 1) ? z : bufs[ping];
+    launch_mode_gemm<T>(s, out, cur, P::U(h, l), h->n[l], inner, outer);
+    cur = out;
+    ping ^= 1;
+  }
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+template st_status apply_T<double>(st_handle *, const double *, double *);
+template st_status apply_T<float>(st_handle *, const float *, float *);
+template st_status precond_T<double>(st_handle *, const double *, double *);
+template st_status precond_T<float>(st_handle *, const float *, float *);
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+const char *st_error_string(st_status s) {
+  switch (s) {
+    case ST_OK: return "ok";
+    case ST_ERR_ARG: return "invalid argument";
+    case ST_ERR_OOM: return "device out of memory";
+    case ST_ERR_CUDA: return "CUDA error";
+    case ST_ERR_NOT_CONVERGED: return "not converged";
+    case ST_ERR_BREAKDOWN: return "breakdown (zero pivot)";
+    case ST_ERR_NAN: return "NaN or Inf detected";
+    case ST_ERR_TIMEOUT: return "device wait timed out";
+    case ST_ERR_STATE: return "invalid call order";
+  }
+  return "unknown status";
+}
+
+st_status st_footprint(const st_problem_desc *desc, size_t *bytes) {
+  ST_TRY(validate(desc));
+  if (!bytes) return ST_ERR_ARG;
+  *bytes = plan(*desc).bytes;
+  return ST_OK;
+}
+
+st_status st_destroy(st_handle *h) {
+  if (!h) return ST_OK;
+  cudaSetDevice(h->dev);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (void *p : h->allocs) cudaFree(p);
+  if (h->red_host) cudaFreeHost(h->red_host);
+  delete h;
+  return ST_OK;
+}
+
+st_status st_get_dims(const st_handle *h, st_dims *out) {
+  if (!h || !out) return ST_ERR_ARG;
+  out->N_s = h->Ns; out->N_t = h->Nt; out->N_dof = h->Ndof; out->Q_s = h->Qs;
+  for (int l = 0; l < 3; ++l) out->n[l] = h->n[l];
+  return ST_OK;
+}
+
+static st_status setup_impl(st_handle *h) {
+  const st_problem_desc &D = h->desc;
+  Sizes z = plan(D);
+  h->d = z.d; h->p = z.p; h->nq = z.nq; h->B = z.B;
+  for (int l = 0; l < 3; ++l) { h->n[l] = z.n[l]; h->nel[l] = z.nel[l]; h->Q[l] = z.Q[l]; }
+  h->Nt = z.Nt; h->nel_t = z.nel_t; h->Qt = z.Qt;
+  h->Ns = z.Ns; h->Ndof = z.Ndof; h->Qs = z.Qs; h->Nel_s = z.Nel_s; h->NtQs = z.NtQs;
+  h->m = z.m;
+  h->rank_cap = z.cap;
+  ST_TRY(host_setup(D, h->hs));
+  HostSetup &hs = h->hs;
+  st_status e = ST_OK;
+  // ---- 1D data
+  for (int l = 0; l < h->d; ++l) {
+    const Dir1D &dr = hs.sdir[l];
+    ST_TRY(upload<double>(h, &h->Mb[l], hs.M[l]));
+    ST_TRY(upload<double>(h, &h->Kb[l], hs.K[l]));
+    ST_TRY(upload<float>(h, &h->Mb32[l], hs.M[l]));
+    ST_TRY(upload<float>(h, &h->Kb32[l], hs.K[l]));
+    size_t per = (size_t)dr.n_el * dr.nq * (dr.p + 1);
+    std::vector<double> b0(dr.tab.begin(), dr.tab.begin() + per);
+    std::vector<double> b2(per, 0.0);
+    if (dr.kmax >= 2) b2.assign(dr.tab.begin() + 2 * per, dr.tab.begin() + 3 * per);
+    ST_TRY(upload<double>(h, &h->Bq[l], b0));
+    ST_TRY(upload<double>(h, &h->B2q[l], b2));
+    ST_TRY(upload<float>(h, &h->Bq32[l], b0));
+    ST_TRY(upload<double>(h, &h->wqs[l], dr.wq));
+    ST_TRY(upload<double>(h, &h->xs[l], dr.xq));
+  }
+  ST_TRY(upload<double>(h, &h->Mtb, hs.Mt));
+  ST_TRY(upload<double>(h, &h->Wtb, hs.Wt));
+  ST_TRY(upload<float>(h, &h->Mtb32, hs.Mt));
+  ST_TRY(upload<float>(h, &h->Wtb32, hs.Wt));
+  ST_TRY(upload<double>(h, &h->bt, hs.tdir.tab));
+  ST_TRY(upload<double>(h, &h->wt, hs.tdir.wq));
+  ST_TRY(upload<double>(h, &h->xt, hs.tdir.xq));
+  ST_TRY(upload<double>(h, &h->tauq, hs.tau_q));
+  ST_TRY(upload<double>(h, &h->wlu, hs.wlu));
+  {
+    std::vector<double> gt(hs.tdir.greville.begin() + 1, hs.tdir.greville.end());
+    std::vector<int> ii;
+    std::vector<double> ll;
+    hat_data(gt, hs.tdir.xq, ii, ll);
+    ST_TRY(upload_i<int>(h, &h->hat_i_t, ii));
+    ST_TRY(upload<double>(h, &h->hat_l_t, ll));
+    for (int l = 0; l < h->d; ++l) {
+      hat_data(hs.sdir[l].greville, hs.sdir[l].xq, ii, ll);
+      ST_TRY(upload_i<int>(h, &h->hat_i_s[l], ii));
+      ST_TRY(upload<double>(h, &h->hat_l_s[l], ll));
+    }
+  }
+  // ---- buffers
+  int nmax = z.nmax;
+  for (int l = 0; l < h->d; ++l) {
+    size_t nn = (size_t)h->n[l] * h->n[l];
+    h->U64[l] = dalloc<double>(h, nn, &e); h->UT64[l] = dalloc<double>(h, nn, &e);
+    h->U32[l] = dalloc<float>(h, nn, &e); h->UT32[l] = dalloc<float>(h, nn, &e);
+    h->lam[l] = dalloc<double>(h, h->n[l], &e);
+  }
+  h->mu = dalloc<double>(h, h->Ns, &e);
+  h->lu64 = dalloc<double>(h, (size_t)h->Nt * h->B * h->Ns, &e);
+  h->lu32 = dalloc<float>(h, (size_t)h->Nt * h->B * h->Ns, &e);
+  h->band64 = dalloc<double>(h, (size_t)(h->p + 1) * h->NtQs, &e);
+  h->band32 = dalloc<float>(h, (size_t)(h->p + 1) * h->NtQs, &e);
+  h->f64 = dalloc<double>(h, h->Ndof, &e);
+  h->emax = dalloc<unsigned long long>(h, (size_t)h->nel_t * h->Nel_s, &e);
+  h->stats = dalloc<double>(h, 8, &e);
+  h->theta = dalloc<double>(h, h->Ndof, &e);
+  h->gram = dalloc<double>(h, (size_t)h->Nt * h->Nt, &e);
+  h->evec = dalloc<double>(h, (size_t)h->Nt * h->Nt, &e);
+  h->eval = dalloc<double>(h, h->Nt, &e);
+  h->eig_work = dalloc<double>(h, (size_t)12 * nmax * nmax + 16 * (size_t)nmax + 64, &e);
+  h->eig32 = dalloc<float>(h, (size_t)2 * nmax * nmax, &e);
+  int cap = h->rank_cap;
+  h->Ur = dalloc<double>(h, (size_t)h->Nt * cap, &e);
+  h->sr = dalloc<double>(h, cap, &e);
+  h->Vr = dalloc<double>(h, (size_t)h->Ns * cap, &e);
+  h->th_t = dalloc<double>(h, (size_t)cap * h->Qt, &e);
+  h->Tr = dalloc<double>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
+  for (int i = 0; i < 2; ++i) {
+    h->W64[i] = dalloc<double>(h, h->NtQs, &e);
+    h->W32[i] = dalloc<float>(h, h->NtQs, &e);
+  }
+  for (int i = 0; i < 7; ++i) {
+    h->K64[i] = dalloc<double>(h, h->Ndof, &e);
+    h->K32[i] = dalloc<float>(h, h->Ndof, &e);
+  }
+  h->U0 = dalloc<double>(h, h->NtQs, &e);
+  h->L0 = dalloc<double>(h, h->NtQs, &e);
+  h->Wq0 = dalloc<double>(h, h->NtQs, &e);
+  h->red = dalloc<double>(h, 4096 + 304 * (size_t)(h->m + 40), &e);
+  if (D.precision == ST_FP64) h->V64 = dalloc<double>(h, (size_t)(h->m + 1) * h->Ndof, &e);
+  else h->V32 = dalloc<float>(h, (size_t)(h->m + 1) * h->Ndof, &e);
+  h->r64 = dalloc<double>(h, h->Ndof, &e);
+  h->x64 = dalloc<double>(h, h->Ndof, &e);
+  h->t64a = dalloc<double>(h, h->Ndof, &e);
+  h->t64b = dalloc<double>(h, h->Ndof, &e);
+  h->z64 = dalloc<double>(h, h->Ndof, &e);
+  h->b64 = dalloc<double>(h, h->Ndof, &e);
+  h->r32 = dalloc<float>(h, h->Ndof, &e);
+  h->t32a = dalloc<float>(h, h->Ndof, &e);
+  h->t32b = dalloc<float>(h, h->Ndof, &e);
+  h->d32 = dalloc<float>(h, h->Ndof, &e);
+  h->hcol = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
+  if (e != ST_OK) return e;
+  // ---- device set-up: fast diagonalization, right-hand side
+  ST_TRY(fd_setup(h));
+  ST_TRY(source_assemble(h));
+  ST_CUDA(cudaStreamSynchronize(h->stream));
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status st_setup(const st_problem_desc *desc, void *cuda_stream, st_handle **out) {
+  if (!out) return ST_ERR_ARG;
+  *out = nullptr;
+  ST_TRY(validate(desc));
+  st_handle *h = new st_handle();
+  h->desc = *desc;
+  h->stream = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&h->dev);
+  st_status s = setup_impl(h);
+  if (s != ST_OK) {
+    st_destroy(h);
+    return s;
+  }
+  *out = h;
+  return ST_OK;
+}
+
+st_status st_linearize(st_handle *h, const double *u, const double *w, int kind, int keep_theta,
+                       st_ionic_info *info) {
+  if (!h || !u || !w) return ST_ERR_ARG;
+  if (kind != ST_PICARD && kind != ST_NEWTON) return ST_ERR_ARG;
+  bool su = h->desc.stabilization == ST_SU;
+  bool stats = !keep_theta;
+  ST_TRY(ionic_run(h, u, w, kind, stats));
+  if (stats) {
+    if (su) {
+      ST_TRY(theta_and_lowrank(h, info));
+    } else {
+      double st[4];
+      ST_CUDA(cudaMemcpyAsync(st, h->stats, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      ST_CUDA(cudaStreamSynchronize(h->stream));
+      h->rank = 0;
+      if (info) {
+        info->u_max = st[0]; info->ut_max = st[1]; info->r_max = st[2];
+        info->den = h->desc.C_m * (st[0] / h->desc.T + st[1]);
+        info->rank = 0; info->theta_fro = 0.0;
+      }
+      if (!std::isfinite(st[0]) || !std::isfinite(st[1])) return ST_ERR_NAN;
+    }
+  } else if (info) {
+    info->rank = h->rank;
+    info->theta_fro = h->theta_fro;
+  }
+  ST_TRY(su_band_add(h));
+  launch_band_to_f32(h->stream, h->band32, h->band64, (long long)(h->p + 1) * h->NtQs);
+  ST_CUDA(cudaStreamSynchronize(h->stream));
+  ST_CUDA(cudaGetLastError());
+  h->have_lin = true;
+  return ST_OK;
+}
+
+st_status st_ionic(st_handle *h, const double *u, const double *w, st_ionic_info *info) {
+  if (!h) return ST_ERR_ARG;
+  return st_linearize(h, u, w, h->desc.nonlinear, 0, info);
+}
+
+st_status st_apply(st_handle *h, int prec, const void *x, void *y) {
+  if (!h || !x || !y || x == y) return ST_ERR_ARG;
+  if (!h->have_lin) return ST_ERR_STATE;
+  if (prec == ST_FP64) return apply_T<double>(h, (const double *)x, (double *)y);
+  if (prec == ST_MIXED) return apply_T<float>(h, (const float *)x, (float *)y);
+  return ST_ERR_ARG;
+}
+
+st_status st_precond(st_handle *h, int prec, const void *r, void *z) {
+  if (!h || !r || !z) return ST_ERR_ARG;
+  if (prec == ST_FP64) return precond_T<double>(h, (const double *)r, (double *)z);
+  if (prec == ST_MIXED) return precond_T<float>(h, (const float *)r, (float *)z);
+  return ST_ERR_ARG;
+}
+
+st_status st_rhs(st_handle *h, double *f) {
+  if (!h || !f) return ST_ERR_ARG;
+  ST_CUDA(cudaMemcpyAsync(f, h->f64, h->Ndof * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  return ST_OK;
+}
+
+st_status st_wupdate(st_handle *h, const double *u, double *w) {
+  if (!h || !u || !w || u == w) return ST_ERR_ARG;
+  return wupdate_run(h, u, w);
+}
+
+st_status st_linsolve(st_handle *h, const double *b, double *x, st_stats *stats) {
+  if (!h || !b || !x) return ST_ERR_ARG;
+  if (!h->have_lin) return ST_ERR_STATE;
+  cudaStream_t s = h->stream;
+  const st_problem_desc &D = h->desc;
+  long long N = h->Ndof;
+  double bn = norm2_64(h, b);
+  if (!std::isfinite(bn)) return ST_ERR_NAN;
+  if (stats) { stats->gmres_iters = 0; stats->outer_iters = 0; stats->rel_res = 0.0; stats->rank = h->rank; }
+  if (bn == 0.0) {
+    ST_CUDA(cudaMemsetAsync(x, 0, N * sizeof(double), s));
+    ST_CUDA(cudaStreamSynchronize(s));
+    return ST_OK;
+  }
+  int total = 0, outer = 0;
+  double rel = INFINITY;
+  st_status status = ST_ERR_NOT_CONVERGED;
+  while (true) {
+    ST_TRY(apply_T<double>(h, x, h->t64a));
+    launch_sub64(s, h->r64, b, h->t64a, N);
+    double rn = norm2_64(h, h->r64);
+    if (!std::isfinite(rn)) return ST_ERR_NAN;
+    rel = rn / bn;
+    if (rel <= D.rtol) { status = ST_OK; break; }
+    if (total >= D.max_it) break;
+    int its = 0;
+    double est = 0.0;
+    double tol_in = D.rtol * bn / rn;
+    int maxit = std::min(h->m, D.max_it - total);
+    if (D.precision == ST_FP64) {
+      ST_TRY(gmres_cycle<double>(h, h->r64, h->t64a, 0.5 * tol_in, maxit, &its, &est));
+      launch_axpby64(s, x, h->t64a, 1.0, 1.0, N);
+    } else {
+      // FP32 inner solve on the scaled residual, FP64 update
+      launch_d2f(s, h->r32, h->r64, 1.0 / rn, N);
+      double tin = std::max(0.5 * tol_in, 1e-6);
+      ST_TRY(gmres_cycle<float>(h, h->r32, h->d32, tin, maxit, &its, &est));
+      launch_f2d_axpy(s, x, h->d32, rn, N);
+    }
+    total += its;
+    ++outer;
+    if (its == 0) break;
+  }
+  ST_CUDA(cudaStreamSynchronize(s));
+  if (stats) { stats->gmres_iters = total; stats->outer_iters = outer; stats->rel_res = rel; stats->rank = h->rank; }
+  return status;
+}
+
+st_status st_solve(st_handle *h, double *u, double *w, st_stats *stats) {
+  if (!h || !u || !w) return ST_ERR_ARG;
+  cudaStream_t s = h->stream;
+  const st_problem_desc &D = h->desc;
+  long long N = h->Ndof;
+  double *unew = h->x64, *wnew = h->t64b;
+  st_stats ls;
+  int total = 0;
+  double diff = INFINITY;
+  int k = 0;
+  st_status status = ST_ERR_NOT_CONVERGED;
+  for (; k < D.max_fp; ++k) {
+    st_ionic_info info;
+    if (D.nonlinear == ST_NEWTON) {
+      // rhs = f - A_P(u^k) u^k, then J du = rhs with theta frozen
+      ST_TRY(st_linearize(h, u, w, ST_PICARD, 0, &info));
+      ST_TRY(apply_T<double>(h, u, h->t64a));
+      launch_sub64(s, h->b64, h->f64, h->t64a, N);
+      ST_TRY(st_linearize(h, u, w, ST_NEWTON, 1, &info));
+      ST_CUDA(cudaMemsetAsync(unew, 0, N * sizeof(double), s));
+      st_status ls_s = st_linsolve(h, h->b64, unew, &ls);
+      if (ls_s != ST_OK && ls_s != ST_ERR_NOT_CONVERGED) return ls_s;
+      total += ls.gmres_iters;
+      diff = absmax_diff(h, unew, nullptr);
+      launch_axpby64(s, unew, u, 1.0, 1.0, N);   // u + du
+      if (D.fix_w_zero) ST_CUDA(cudaMemsetAsync(wnew, 0, N * sizeof(double), s));
+      else ST_TRY(wupdate_run(h, u, wnew));
+    } else {
+      ST_TRY(st_linearize(h, u, w, ST_PICARD, 0, &info));
+      ST_CUDA(cudaMemcpyAsync(unew, u, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      st_status ls_s = st_linsolve(h, h->f64, unew, &ls);
+      if (ls_s != ST_OK && ls_s != ST_ERR_NOT_CONVERGED) return ls_s;
+      total += ls.gmres_iters;
+      if (D.fix_w_zero) ST_CUDA(cudaMemsetAsync(wnew, 0, N * sizeof(double), s));
+      else ST_TRY(wupdate_run(h, u, wnew));
+      // relaxation
+      launch_axpby64(s, unew, u, 1.0 - D.alpha, D.alpha, N);   // unew = alpha unew + (1-alpha) u
+      launch_axpby64(s, wnew, w, 1.0 - D.alpha, D.alpha, N);
+      diff = absmax_diff(h, unew, u);
+    }
+    ST_CUDA(cudaMemcpyAsync(u, unew, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    ST_CUDA(cudaMemcpyAsync(w, wnew, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (!std::isfinite(diff)) { status = ST_ERR_NAN; ++k; break; }
+    if (diff <= D.delta) { status = ST_OK; ++k; break; }
+  }
+  ST_CUDA(cudaStreamSynchronize(s));
+  if (stats) {
+    *stats = ls;
+    stats->fp_iters = k;
+    stats->total_gmres = total;
+    stats->last_diff = diff;
+    stats->rank = h->rank;
+  }
+  return status;
+}
+
+st_status st_get(st_handle *h, int what, void *dst, size_t bytes) {
+  if (!h || !dst) return ST_ERR_ARG;
+  cudaStream_t s = h->stream;
+  size_t need = 0;
+  const void *src = nullptr;
+  std::vector<double> tmp;
+  switch (what) {
+    case ST_GET_THETA_HAT: need = h->Ndof * sizeof(double); src = h->theta; break;
+    case ST_GET_LOWRANK_S: need = h->rank * sizeof(double); src = h->sr; break;
+    case ST_GET_LOWRANK_U: need = (size_t)h->Nt * h->rank * sizeof(double); src = h->Ur; break;
+    case ST_GET_LOWRANK_V: need = (size_t)h->Ns * h->rank * sizeof(double); src = h->Vr; break;
+    case ST_GET_TAU_Q: tmp = h->hs.tau_q; break;
+    case ST_GET_FD_EIG: {
+      size_t tot = 0;
+      for (int l = 0; l < h->d; ++l) tot += h->n[l];
+      need = tot * sizeof(double);
+      if (bytes != need) return ST_ERR_ARG;
+      size_t off = 0;
+      for (int l = 0; l < h->d; ++l) {
+        ST_CUDA(cudaMemcpyAsync((double *)dst + off, h->lam[l], h->n[l] * sizeof(double), cudaMemcpyDeviceToHost, s));
+        off += h->n[l];
+      }
+      ST_CUDA(cudaStreamSynchronize(s));
+      return ST_OK;
+    }
+    case ST_GET_BANDS_1D:
+      for (int l = 0; l < h->d; ++l) {
+        tmp.insert(tmp.end(), h->hs.M[l].begin(), h->hs.M[l].end());
+        tmp.insert(tmp.end(), h->hs.K[l].begin(), h->hs.K[l].end());
+      }
+      tmp.insert(tmp.end(), h->hs.Mt.begin(), h->hs.Mt.end());
+      tmp.insert(tmp.end(), h->hs.Wt.begin(), h->hs.Wt.end());
+      break;
+    default: return ST_ERR_ARG;
+  }
+  if (!src) {
+    need = tmp.size() * sizeof(double);
+    if (bytes != need) return ST_ERR_ARG;
+    std::memcpy(dst, tmp.data(), need);
+    return ST_OK;
+  }
+  if (bytes != need) return ST_ERR_ARG;
+  if (need) ST_CUDA(cudaMemcpyAsync(dst, src, need, cudaMemcpyDeviceToHost, s));
+  ST_CUDA(cudaStreamSynchronize(s));
+  return ST_OK;
+}
+
+}  // extern "C"

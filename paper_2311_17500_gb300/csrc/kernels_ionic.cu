@@ -1,0 +1,652 @@
+// Ionic quadrature, Theta-hat, the low-rank theta, the SU and reaction time
+// bands, the right-hand side and the w-update (Sec. 3 and Sec. 3.1).
+#include <algorithm>
+#include <cmath>
+#include "st_internal.h"
+
+void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, int M, int N, int K,
+                   long long sam, long long sak, long long sbk, long long sbc, long long scm, long long scc,
+                   double alpha, double beta);
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// f of eq. 3.1 at one point (stimulus boxes, or the manufactured sources).
+__device__ double source_at(const st_problem_desc &D, const double *x, double t) {
+  if (D.source_kind == ST_SRC_STIM) {
+    double f = 0.0;
+    for (int b = 0; b < D.n_stim; ++b) {
+      const st_stim &s = D.stim[b];
+      bool in = (t >= s.t0) && (t < s.t1);
+      for (int l = 0; l < D.d; ++l) in = in && (x[l] >= s.lo[l]) && (x[l] <= s.hi[l]);
+      if (in) f += s.amp;
+    }
+    return f;
+  }
+  if (D.source_kind == ST_SRC_HEAT_MMS) {
+    // u = prod cos(pi x_l) sin t, w = 0
+    double c = 1.0, lapc = 0.0;
+    for (int l = 0; l < D.d; ++l) { c *= cos(kPi * x[l]); lapc += D.D[l]; }
+    double u = c * sin(t);
+    return D.C_m * c * cos(t) + kPi * kPi * lapc * u + D.c1 * u * (u - D.a) * (u - 1.0);
+  }
+  if (D.source_kind == ST_SRC_E1_MMS) {
+    // u = 10 g(x) h(t), g = sin(pi x)(1-e^-x)(1-e^(x-1)), h = sin(pi t)(1-e^(t-1)), w = 0
+    double xx = x[0];
+    double s0 = sin(kPi * xx), s1 = kPi * cos(kPi * xx), s2 = -kPi * kPi * sin(kPi * xx);
+    double em = exp(-xx), ep = exp(xx - 1.0);
+    double A0 = 1.0 - em, A1 = em, A2 = -em;
+    double B0 = 1.0 - ep, B1 = -ep, B2 = -ep;
+    double g = s0 * A0 * B0;
+    double g2 = s2 * A0 * B0 + s0 * A2 * B0 + s0 * A0 * B2 + 2.0 * (s1 * A1 * B0 + s1 * A0 * B1 + s0 * A1 * B1);
+    double et = exp(t - 1.0);
+    double h = sin(kPi * t) * (1.0 - et);
+    double h1 = kPi * cos(kPi * t) * (1.0 - et) - sin(kPi * t) * et;
+    double u = 10.0 * g * h;
+    return D.C_m * 10.0 * g * h1 - D.D[0] * 10.0 * g2 * h + D.c1 * u * (u - D.a) * (u - 1.0);
+  }
+  return 0.0;
+}
+
+struct SpatialPoint {
+  double ws;        // product of the 1D weights
+  double x[3];      // coordinates
+  long long es;     // spatial element (colexicographic)
+};
+
+struct GeomArgs {
+  int d, nq;
+  int Q[3], nel[3];
+  const double *wqs[3];
+  const double *xs[3];
+};
+
+__device__ SpatialPoint spatial_point(const GeomArgs &g, long long q) {
+  SpatialPoint sp;
+  sp.ws = 1.0;
+  sp.es = 0;
+  long long stride = 1, rem = q;
+  for (int l = 0; l < 3; ++l) sp.x[l] = 0.0;
+  for (int l = 0; l < g.d; ++l) {
+    int ql = (int)(rem % g.Q[l]);
+    rem /= g.Q[l];
+    sp.ws *= g.wqs[l][ql];
+    sp.x[l] = g.xs[l][ql];
+    sp.es += (long long)(ql / g.nq) * stride;
+    stride *= g.nel[l];
+  }
+  return sp;
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double v) {
+  // non-negative doubles order like their bit patterns; NaN maps to +inf
+  if (v != v) v = INFINITY;
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+struct IonicArgs {
+  st_problem_desc D;
+  GeomArgs g;
+  const double *U0, *L0, *W0;   // [Nt][Qs]: u, sum D_l d_ll u, w at spatial Gauss points
+  const double *bt, *wt, *xt;   // time tables
+  int Nt, nel_t;
+  long long Qs, Nel_s;
+  int kind;                     // ST_PICARD: C_r, ST_NEWTON: C_J
+  int want_stats;
+  double *band;                 // [k][it][q]
+  unsigned long long *emax;     // [et][es]
+  unsigned long long *stats;    // max|u|, max|d_t u|, max|R|
+};
+
+// One thread per spatial Gauss point sweeps the time elements: evaluates u,
+// d_t u, the Laplacian and w at the time Gauss points from the time
+// coefficients, forms the residual R (Eq. theta_ce_u numerator) and the
+// reaction coefficient, keeps max |R| per space-time element, and assembles
+// the time band sum_qt w C b_i b_j of the reaction mass term at this spatial
+// point (multiplied by its spatial weight).  Rows are written once complete.
+template <int P>
+__global__ void ionic_tline_kernel(IonicArgs a) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  __shared__ double red[3][32];
+  double mu = 0.0, mut = 0.0, mr = 0.0;
+  if (q < a.Qs) {
+    const int nq = P + 1;
+    const double *D1 = a.D.D;
+    (void)D1;
+    SpatialPoint sp = spatial_point(a.g, q);
+    const long long plane = (long long)a.Nt * a.Qs;
+    double acc[P + 1][P + 1];
+#pragma unroll
+    for (int r = 0; r <= P; ++r)
+#pragma unroll
+      for (int k = 0; k <= P; ++k) acc[r][k] = 0.0;
+    for (int e = 0; e < a.nel_t; ++e) {
+      double cu[P + 1], cl[P + 1], cw[P + 1];
+#pragma unroll
+      for (int j = 0; j <= P; ++j) {
+        int it = e + j - 1;
+        bool ok = it >= 0;
+        long long off = (long long)it * a.Qs + q;
+        cu[j] = ok ? a.U0[off] : 0.0;
+        cl[j] = ok ? a.L0[off] : 0.0;
+        cw[j] = ok ? a.W0[off] : 0.0;
+      }
+      double rloc = 0.0;
+      for (int qt = 0; qt < nq; ++qt) {
+        const double *b0 = a.bt + ((size_t)(0 * a.nel_t + e) * nq + qt) * (P + 1);
+        const double *b1 = a.bt + ((size_t)(1 * a.nel_t + e) * nq + qt) * (P + 1);
+        double u = 0.0, ut = 0.0, lap = 0.0, w = 0.0;
+#pragma unroll
+        for (int j = 0; j <= P; ++j) {
+          u += b0[j] * cu[j];
+          ut += b1[j] * cu[j];
+          lap += b0[j] * cl[j];
+          w += b0[j] * cw[j];
+        }
+        double t = a.xt[e * nq + qt];
+        double f = source_at(a.D, sp.x, t);
+        double R = a.D.C_m * ut - lap + a.D.c1 * u * (u - a.D.a) * (u - 1.0) + a.D.c2 * u * w - f;
+        double C;
+        if (a.kind == ST_NEWTON)
+          C = a.D.c1 * (3.0 * u * u - 2.0 * (1.0 + a.D.a) * u + a.D.a) + a.D.c2 * w;
+        else
+          C = a.D.c1 * (u - a.D.a) * (u - 1.0) + a.D.c2 * w;
+        double aR = fabs(R);
+        rloc = fmax(rloc, aR != aR ? INFINITY : aR);
+        mu = fmax(mu, fabs(u));
+        mut = fmax(mut, fabs(ut));
+        double wc = a.wt[e * nq + qt] * sp.ws * C;
+#pragma unroll
+        for (int i = 0; i <= P; ++i)
+#pragma unroll
+          for (int k = 0; k <= P - i; ++k) acc[i][k] += wc * b0[i] * b0[i + k];
+      }
+      mr = fmax(mr, rloc);
+      if (a.want_stats) atomic_max_pos(&a.emax[(long long)e * a.Nel_s + sp.es], rloc);
+      // row e-1 is complete
+      int row = e - 1;
+      if (row >= 0)
+#pragma unroll
+        for (int k = 0; k <= P; ++k) a.band[k * plane + (long long)row * a.Qs + q] = acc[0][k];
+#pragma unroll
+      for (int r = 0; r < P; ++r)
+#pragma unroll
+        for (int k = 0; k <= P; ++k) acc[r][k] = acc[r + 1][k];
+#pragma unroll
+      for (int k = 0; k <= P; ++k) acc[P][k] = 0.0;
+    }
+    for (int r = 0; r < P; ++r) {
+      int row = a.nel_t - 1 + r;
+      if (row < a.Nt)
+        for (int k = 0; k <= P; ++k) a.band[k * plane + (long long)row * a.Qs + q] = acc[r][k];
+    }
+  }
+  if (a.want_stats) {
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      mu = fmax(mu, __shfl_down_sync(0xffffffffu, mu, off));
+      mut = fmax(mut, __shfl_down_sync(0xffffffffu, mut, off));
+      mr = fmax(mr, __shfl_down_sync(0xffffffffu, mr, off));
+    }
+    if (lane == 0) { red[0][warp] = mu; red[1][warp] = mut; red[2][warp] = mr; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double m0 = 0, m1 = 0, m2 = 0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+        m0 = fmax(m0, red[0][i]); m1 = fmax(m1, red[1][i]); m2 = fmax(m2, red[2][i]);
+      }
+      atomic_max_pos(&a.stats[0], m0);
+      atomic_max_pos(&a.stats[1], m1);
+      atomic_max_pos(&a.stats[2], m2);
+    }
+  }
+}
+
+// Right-hand side of Eq. (rhsfun), first stage: for each spatial Gauss point,
+// Fq[it][q] = ws(q) sum over time Gauss points of wt f(x_q, t) b_it(t).
+template <int P>
+__global__ void source_tline_kernel(st_problem_desc D, GeomArgs g, const double *bt, const double *wt,
+                                    const double *xt, int Nt, int nel_t, long long Qs, double *Fq) {
+  long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= Qs) return;
+  const int nq = P + 1;
+  SpatialPoint sp = spatial_point(g, q);
+  double acc[P + 1];
+#pragma unroll
+  for (int r = 0; r <= P; ++r) acc[r] = 0.0;
+  for (int e = 0; e < nel_t; ++e) {
+    for (int qt = 0; qt < nq; ++qt) {
+      const double *b0 = bt + ((size_t)e * nq + qt) * (P + 1);
+      double v = wt[e * nq + qt] * sp.ws * source_at(D, sp.x, xt[e * nq + qt]);
+#pragma unroll
+      for (int j = 0; j <= P; ++j) acc[j] += v * b0[j];
+    }
+    if (e - 1 >= 0) Fq[(long long)(e - 1) * Qs + q] = acc[0];
+#pragma unroll
+    for (int r = 0; r < P; ++r) acc[r] = acc[r + 1];
+    acc[P] = 0.0;
+  }
+  for (int r = 0; r < P; ++r) {
+    int row = nel_t - 1 + r;
+    if (row < Nt) Fq[(long long)row * Qs + q] = acc[r];
+  }
+}
+
+// Support-extension maximum along one axis (Eq. suppext), separable over the
+// axes of the box: out[o][i][c] = max_{e in window(i)} in[o][e][c] with
+// window(i) = [i+shift-2p, i+shift] (literal) or [i+shift-2p, i+shift+p]
+// (symmetric), clamped to the spans; shift = 1 for the time axis (X_t index
+// i is the (i+1)-th B-spline).
+__global__ void window_max_kernel(double *__restrict__ out, const double *__restrict__ in, int nel, int nout,
+                                  int p, int shift, int symmetric, long long inner, long long outer) {
+  long long total = outer * nout * inner;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long c = idx % inner;
+    long long r = idx / inner;
+    int i = (int)(r % nout);
+    long long o = r / nout;
+    int lo = max(0, i + shift - 2 * p);
+    int hi = min(nel - 1, i + shift + (symmetric ? p : 0));
+    double m = 0.0;
+    for (int e = lo; e <= hi; ++e) m = fmax(m, in[(o * nel + e) * inner + c]);
+    out[idx] = m;
+  }
+}
+
+// Theta-hat = min(num / den, 1), with 1 for num > 0 = den and 0 for num = 0 = den.
+__global__ void theta_kernel(double *__restrict__ th, const double *__restrict__ num, double den, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = num[e];
+    th[e] = den > 0.0 ? fmin(v / den, 1.0) : (v > 0.0 ? 1.0 : 0.0);
+  }
+}
+
+// theta_{t,r} at the time Gauss points: linear interpolation of U[:, r] on
+// the time Greville grid, constant before the first node.  thq[r][qt].
+__global__ void theta_t_kernel(double *__restrict__ thq, const double *__restrict__ U, int R, int Qt,
+                               const int *hi, const double *hl) {
+  int total = Qt * R;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int qt = idx % Qt, r = idx / Qt;
+    int i = hi[qt];
+    double l = hl[qt];
+    double v = (1.0 - l) * U[(long long)i * R + r];
+    if (l != 0.0) v += l * U[(long long)(i + 1) * R + r];
+    thq[idx] = v;
+  }
+}
+
+// SU time bands per rank (Eq. tildeS, matrices S^t_{r,l} summed over l):
+// Tr[r][k][it] = sum_l int tau_l theta_{t,r} d^l b_it d^l b_{it+k} dt.
+__global__ void su_time_band_kernel(double *__restrict__ Tr, const double *__restrict__ tht,
+                                    const double *__restrict__ tauq, const double *__restrict__ bt,
+                                    const double *__restrict__ wt, int R, int Nt, int nel_t, int p) {
+  int nq = p + 1;
+  int total = R * (p + 1) * Nt;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int it = idx % Nt;
+    int k = (idx / Nt) % (p + 1);
+    int r = idx / (Nt * (p + 1));
+    double s = 0.0;
+    if (it + k < Nt) {
+      int e0 = max(0, it + k + 1 - p), e1 = min(nel_t - 1, it + 1);
+      for (int e = e0; e <= e1; ++e) {
+        int ai = it + 1 - e, ci = it + k + 1 - e;
+        for (int qt = 0; qt < nq; ++qt) {
+          double w = wt[e * nq + qt] * tht[(long long)r * nel_t * nq + e * nq + qt];
+          double acc = 0.0;
+          for (int l = 1; l <= p; ++l) {
+            const double *bl = bt + (((size_t)l * nel_t + e) * nq + qt) * (p + 1);
+            acc += tauq[((size_t)(l - 1) * nel_t + e) * nq + qt] * bl[ai] * bl[ci];
+          }
+          s += w * acc;
+        }
+      }
+    }
+    Tr[idx] = s;
+  }
+}
+
+struct HatArgs {
+  const int *idx[3];
+  const double *lam[3];
+  int n[3];
+};
+
+// Cq[r][q] = C_m sigma_r ws(q) theta_{s,r}(x_q): the spatial factors of the SU
+// ranks, with theta_{s,r} the d-linear interpolation of V[:, r] on the
+// spatial Greville grid (Sec. 3.1) evaluated at the spatial Gauss point x_q.
+__global__ void su_space_coef_kernel(double *__restrict__ Cq, const double *__restrict__ V,
+                                     const double *__restrict__ sig, GeomArgs g, HatArgs hat, double Cm, int R,
+                                     long long Qs) {
+  long long total = Qs * R;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long q = idx % Qs;
+    int r = (int)(idx / Qs);
+    SpatialPoint sp = spatial_point(g, q);
+    int il[3] = {0, 0, 0};
+    double ll[3] = {0.0, 0.0, 0.0};
+    long long rem = q;
+    for (int l = 0; l < g.d; ++l) {
+      int ql = (int)(rem % g.Q[l]);
+      rem /= g.Q[l];
+      il[l] = hat.idx[l][ql];
+      ll[l] = hat.lam[l][ql];
+    }
+    double s = 0.0;
+    int nc = 1 << g.d;
+    for (int c = 0; c < nc; ++c) {
+      double w = 1.0;
+      long long j = 0, stride = 1;
+      for (int l = 0; l < g.d; ++l) {
+        int cl = (c >> l) & 1;
+        w *= cl ? ll[l] : 1.0 - ll[l];
+        j += (long long)(il[l] + cl) * stride;
+        stride *= hat.n[l];
+      }
+      if (w != 0.0) s += w * V[j * R + r];
+    }
+    Cq[idx] = Cm * sig[r] * sp.ws * s;
+  }
+}
+
+// w-update (Sec. 3.2): w[:, j] = b (W_t + b d_e M_t)^{-1} M_t u[:, j] for every
+// spatial index j; the LU factors of the time matrix are shared by all columns.
+template <int P>
+__global__ void wupdate_kernel(double *__restrict__ w, const double *__restrict__ u, const double *__restrict__ Mt,
+                               const double *__restrict__ lu, double bcoef, int Nt, long long Ns) {
+  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= Ns) return;
+  constexpr int B = 2 * P + 1;
+  double uw[2 * P + 1];
+#pragma unroll
+  for (int i = 0; i < 2 * P + 1; ++i) uw[i] = 0.0;
+#pragma unroll
+  for (int k = 0; k < P; ++k) uw[P + 1 + k] = (k < Nt) ? u[(long long)k * Ns + j] : 0.0;
+  double yw[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) yw[k] = 0.0;
+  for (int it = 0; it < Nt; ++it) {
+#pragma unroll
+    for (int i = 0; i < 2 * P; ++i) uw[i] = uw[i + 1];
+    uw[2 * P] = (it + P < Nt) ? u[(long long)(it + P) * Ns + j] : 0.0;
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      int c = it - P + k;
+      if (c >= 0 && c < Nt) v += Mt[(size_t)it * B + k] * uw[k];
+    }
+    double s = bcoef * v;
+#pragma unroll
+    for (int k = 1; k <= P; ++k)
+      if (it - k >= 0) s -= lu[(size_t)it * B + (P - k)] * yw[P - k];
+#pragma unroll
+    for (int k = 0; k < P - 1; ++k) yw[k] = yw[k + 1];
+    yw[P - 1] = s;
+    w[(long long)it * Ns + j] = s;
+  }
+  double zw[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) zw[k] = 0.0;
+  for (int it = Nt - 1; it >= 0; --it) {
+    double s = w[(long long)it * Ns + j];
+#pragma unroll
+    for (int k = 1; k <= P; ++k)
+      if (it + k < Nt) s -= lu[(size_t)it * B + (P + k)] * zw[k - 1];
+    s *= lu[(size_t)it * B + P];
+#pragma unroll
+    for (int k = P - 1; k > 0; --k) zw[k] = zw[k - 1];
+    zw[0] = s;
+    w[(long long)it * Ns + j] = s;
+  }
+}
+
+__global__ void zero_ull_kernel(unsigned long long *p, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    p[e] = 0ull;
+}
+
+__global__ void scale_cols_kernel(double *V, const double *sig, int R, long long n) {
+  long long total = n * R;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e % R);
+    V[e] = sig[r] > 0.0 ? V[e] / sig[r] : 0.0;
+  }
+}
+
+inline int grid_for(long long total, int threads = 256) {
+  long long g = (total + threads - 1) / threads;
+  if (g > 152LL * 64) g = 152LL * 64;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+GeomArgs geom(st_handle *h) {
+  GeomArgs g;
+  g.d = h->d;
+  g.nq = h->nq;
+  for (int l = 0; l < 3; ++l) {
+    g.Q[l] = h->Q[l];
+    g.nel[l] = h->nel[l];
+    g.wqs[l] = h->wqs[l];
+    g.xs[l] = h->xs[l];
+  }
+  return g;
+}
+
+// coefficient tensor [N_t][n_z][n_y][n_x] -> values at spatial Gauss points
+// [N_t][Q_z][Q_y][Q_x]; `deriv_dir` selects the direction that uses the second
+// derivative table (-1: values only).  Uses both FP64 work buffers.
+double *spatial_to_qpts(st_handle *h, const double *x, int deriv_dir, double *dst) {
+  cudaStream_t s = h->stream;
+  const double *cur = x;
+  long long dims[3] = {h->n[0], h->n[1], h->n[2]};
+  int ping = 0;
+  for (int l = 0; l < h->d; ++l) {
+    long long inner = 1, outer = h->Nt;
+    for (int m = 0; m < l; ++m) inner *= h->Q[m];
+    for (int m = l + 1; m < h->d; ++m) outer *= dims[m];
+    double *out = (l == h->d - 1) ? dst : h->W64[ping];
+    const double *tab = (l == deriv_dir) ? h->B2q[l] : h->Bq[l];
+    launch_interp_fwd<double>(s, out, cur, tab, h->nel[l], h->p, h->nq, inner, outer);
+    cur = out;
+    ping ^= 1;
+  }
+  return dst;
+}
+
+}  // namespace
+
+st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bool want_stats) {
+  cudaStream_t s = h->stream;
+  // fields at spatial Gauss points: u, sum_l D_ll d_ll u, w
+  spatial_to_qpts(h, u, -1, h->U0);
+  for (int l = 0; l < h->d; ++l) {
+    spatial_to_qpts(h, u, l, h->Wq0);   // temporarily the second-derivative field
+    launch_axpby64(s, h->L0, h->Wq0, h->desc.D[l], l == 0 ? 0.0 : 1.0, h->NtQs);
+  }
+  spatial_to_qpts(h, w, -1, h->Wq0);
+  if (want_stats) {
+    zero_ull_kernel<<<grid_for((long long)h->nel_t * h->Nel_s), 256, 0, s>>>(h->emax, (long long)h->nel_t * h->Nel_s);
+    zero_ull_kernel<<<1, 32, 0, s>>>((unsigned long long *)h->stats, 4);
+  }
+  IonicArgs a;
+  a.D = h->desc;
+  a.g = geom(h);
+  a.U0 = h->U0; a.L0 = h->L0; a.W0 = h->Wq0;
+  a.bt = h->bt; a.wt = h->wt; a.xt = h->xt;
+  a.Nt = h->Nt; a.nel_t = h->nel_t;
+  a.Qs = h->Qs; a.Nel_s = h->Nel_s;
+  a.kind = kind;
+  a.want_stats = want_stats ? 1 : 0;
+  a.band = h->band64;
+  a.emax = h->emax;
+  a.stats = (unsigned long long *)h->stats;
+  unsigned blocks = (unsigned)((h->Qs + 127) / 128);
+  switch (h->p) {
+    case 1: ionic_tline_kernel<1><<<blocks, 128, 0, s>>>(a); break;
+    case 2: ionic_tline_kernel<2><<<blocks, 128, 0, s>>>(a); break;
+    case 3: ionic_tline_kernel<3><<<blocks, 128, 0, s>>>(a); break;
+    default: ionic_tline_kernel<4><<<blocks, 128, 0, s>>>(a); break;
+  }
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
+  cudaStream_t s = h->stream;
+  const st_problem_desc &D = h->desc;
+  double st[4];
+  ST_CUDA(cudaMemcpyAsync(st, h->stats, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  ST_CUDA(cudaStreamSynchronize(s));
+  double umax = st[0], utmax = st[1], rmax = st[2];
+  double den = D.C_m * (umax / D.T + utmax);
+  if (info) {
+    info->u_max = umax; info->ut_max = utmax; info->den = den; info->r_max = rmax;
+  }
+  if (!std::isfinite(umax) || !std::isfinite(utmax) || !std::isfinite(rmax)) return ST_ERR_NAN;
+  // numerators: window maxima of the element maxima, axis by axis
+  const double *cur = (const double *)h->emax;
+  long long dimsE[4] = {h->nel[0], h->nel[1], h->nel[2], h->nel_t};
+  long long dimsB[4] = {h->n[0], h->n[1], h->n[2], h->Nt};
+  long long cdims[4];
+  for (int l = 0; l < 3; ++l) cdims[l] = l < h->d ? dimsE[l] : 1;
+  cdims[3] = h->nel_t;
+  int ping = 0;
+  int axes[4];
+  int na = 0;
+  for (int l = 0; l < h->d; ++l) axes[na++] = l;
+  axes[na++] = 3;
+  for (int ai = 0; ai < na; ++ai) {
+    int l = axes[ai];
+    long long inner = 1, outer = 1;
+    for (int m = 0; m < l; ++m) inner *= cdims[m];
+    for (int m = l + 1; m < 4; ++m) outer *= cdims[m];
+    int nel = (int)dimsE[l], nout = (int)dimsB[l];
+    double *out = h->W64[ping];
+    long long total = outer * nout * inner;
+    window_max_kernel<<<grid_for(total), 256, 0, s>>>(out, cur, nel, nout, h->p, l == 3 ? 1 : 0,
+                                                       D.suppext == ST_SUPPEXT_SYMMETRIC, inner, outer);
+    cdims[l] = nout;
+    cur = out;
+    ping ^= 1;
+  }
+  long long NtNs = h->Ndof;
+  theta_kernel<<<grid_for(NtNs), 256, 0, s>>>(h->theta, cur, den, NtNs);
+  // Gram matrix G = Theta Theta^T (N_t x N_t, FP64)
+  int Nt = h->Nt;
+  launch_gemm64(s, h->gram, h->theta, h->theta, Nt, Nt, (int)h->Ns, h->Ns, 1, 1, h->Ns, Nt, 1, 1.0, 0.0);
+  std::vector<double> G((size_t)Nt * Nt);
+  // trace = ||Theta||_F^2
+  ST_CUDA(cudaMemcpyAsync(G.data(), h->gram, G.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  ST_CUDA(cudaStreamSynchronize(s));
+  double tr = 0.0;
+  for (int i = 0; i < Nt; ++i) tr += G[(size_t)i * Nt + i];
+  h->theta_fro = std::sqrt(tr);
+  if (info) info->theta_fro = h->theta_fro;
+  h->rank = 0;
+  if (!(tr > 0.0)) {
+    if (info) info->rank = 0;
+    return ST_OK;
+  }
+  // eigen-decomposition of G on the device (eigenvalues descending)
+  ST_TRY(sym_eig_desc(h, h->gram, Nt, h->evec, h->eval));
+  std::vector<double> lam(Nt);
+  ST_CUDA(cudaMemcpyAsync(lam.data(), h->eval, Nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+  ST_CUDA(cudaStreamSynchronize(s));
+  // smallest R with ||Theta - U S V^T||_F^2 = tr - sum_{i<R} lam_i <= eps^2 tr (Eq. tol)
+  double eps = D.eps_theta;
+  double kept = 0.0;
+  int R = Nt;
+  for (int r = 1; r <= Nt; ++r) {
+    kept += std::max(lam[r - 1], 0.0);
+    if (tr - kept <= eps * eps * tr) { R = r; break; }
+  }
+  if (R > h->rank_cap) R = h->rank_cap;
+  h->rank = R;
+  if (info) info->rank = R;
+  // U_R (N_t x R) = first R columns of evec (evec[i][c], c sorted descending)
+  std::vector<double> sig(R);
+  for (int r = 0; r < R; ++r) sig[r] = std::sqrt(std::max(lam[r], 0.0));
+  ST_CUDA(cudaMemcpyAsync(h->sr, sig.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+  ST_CUDA(cudaMemcpy2DAsync(h->Ur, R * sizeof(double), h->evec, Nt * sizeof(double), R * sizeof(double), Nt,
+                            cudaMemcpyDeviceToDevice, s));
+  // V = Theta^T U_R diag(1/sigma): (N_s x R)
+  launch_gemm64(s, h->Vr, h->theta, h->Ur, (int)h->Ns, R, Nt, 1, h->Ns, R, 1, R, 1, 1.0, 0.0);
+  scale_cols_kernel<<<grid_for(h->Ns * R), 256, 0, s>>>(h->Vr, h->sr, R, h->Ns);
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status su_band_add(st_handle *h) {
+  if (h->desc.stabilization != ST_SU || h->rank == 0) return ST_OK;
+  cudaStream_t s = h->stream;
+  int R = h->rank, p = h->p;
+  theta_t_kernel<<<grid_for((long long)h->Qt * R), 256, 0, s>>>(h->th_t, h->Ur, R, h->Qt, h->hat_i_t, h->hat_l_t);
+  su_time_band_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tr, h->th_t, h->tauq, h->bt,
+                                                                              h->wt, R, h->Nt, h->nel_t, p);
+  // Cq = C_m sigma_r ws theta_s (into the first work buffer, R x Q_s <= N_t x Q_s)
+  double *Cq = h->W64[0];
+  HatArgs hat;
+  for (int l = 0; l < 3; ++l) {
+    hat.idx[l] = h->hat_i_s[l];
+    hat.lam[l] = h->hat_l_s[l];
+    hat.n[l] = h->n[l];
+  }
+  su_space_coef_kernel<<<grid_for(h->Qs * R), 256, 0, s>>>(Cq, h->Vr, h->sr, geom(h), hat, h->desc.C_m, R, h->Qs);
+  // band[(k,it)][q] += sum_r Tr[r][(k,it)] Cq[r][q]
+  int Mrows = (p + 1) * h->Nt;
+  launch_gemm64(s, h->band64, h->Tr, Cq, Mrows, (int)h->Qs, R, 1, Mrows, h->Qs, 1, h->Qs, 1, 1.0, 1.0);
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status source_assemble(st_handle *h) {
+  cudaStream_t s = h->stream;
+  double *Fq = h->U0;   // [Nt][Qs]
+  unsigned blocks = (unsigned)((h->Qs + 127) / 128);
+  GeomArgs g = geom(h);
+  switch (h->p) {
+    case 1: source_tline_kernel<1><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
+    case 2: source_tline_kernel<2><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
+    case 3: source_tline_kernel<3><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
+    default: source_tline_kernel<4><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
+  }
+  // spatial test functions: Gauss points -> coefficients, last axis first
+  const double *cur = Fq;
+  long long qd[3] = {h->Q[0], h->Q[1], h->Q[2]};
+  long long nd[3] = {h->n[0], h->n[1], h->n[2]};
+  int ping = 0;
+  for (int l = h->d - 1; l >= 0; --l) {
+    long long inner = 1, outer = h->Nt;
+    for (int m = 0; m < l; ++m) inner *= qd[m];
+    for (int m = l + 1; m < h->d; ++m) outer *= nd[m];
+    double *out = (l == 0) ? h->f64 : h->W64[ping];
+    launch_interp_bwd<double>(s, out, cur, h->Bq[l], h->nel[l], h->p, h->nq, inner, outer, false);
+    cur = out;
+    ping ^= 1;
+  }
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status wupdate_run(st_handle *h, const double *u, double *w) {
+  cudaStream_t s = h->stream;
+  double bcoef = h->desc.b;
+  unsigned blocks = (unsigned)((h->Ns + 127) / 128);
+  switch (h->p) {
+    case 1: wupdate_kernel<1><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
+    case 2: wupdate_kernel<2><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
+    case 3: wupdate_kernel<3><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
+    default: wupdate_kernel<4><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
+  }
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}

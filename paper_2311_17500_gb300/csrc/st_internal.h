@@ -1,0 +1,178 @@
+// Internal declarations shared by the translation units of libst.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include "st.h"
+
+#define ST_MAXP 4
+#define ST_MAXB (2 * ST_MAXP + 1)
+
+// ---------------------------------------------------------------- host 1D data
+// One parametric direction (space, or time with `scale` = T).  Tables are per
+// knot span e (n_el spans, nq = p+1 Gauss points each); the local functions on
+// span e are the global B-splines e .. e+p (open knots, maximal regularity).
+struct Dir1D {
+  int n_el = 0, p = 0, n = 0, nq = 0, kmax = 0;
+  double scale = 1.0;
+  std::vector<double> knots;      // parametric, n + p + 1
+  std::vector<double> xq, wq;     // physical points / weights, [e*nq + q]
+  std::vector<double> tab;        // [k][e][q][a]: k-th physical derivative of local fn a
+  std::vector<double> greville;   // physical, n
+  double at(int k, int e, int q, int a) const {
+    return tab[(((size_t)k * n_el + e) * nq + q) * (p + 1) + a];
+  }
+};
+
+struct HostSetup {
+  Dir1D sdir[3];
+  Dir1D tdir;
+  // banded (n x (2p+1)), entry (i, i-p+k) at [i*(2p+1)+k]
+  std::vector<double> M[3], K[3];   // spatial mass, stiffness (unscaled by D)
+  std::vector<double> Mt, Wt;       // time, X_t indexing
+  std::vector<double> tau_q;        // [l-1][e][q]
+  std::vector<double> wlu;          // banded LU of W_t + b d_e M_t, no pivoting
+};
+
+st_status host_setup(const st_problem_desc &d, HostSetup &hs);
+// Banded LU without pivoting in place (n x (2p+1)); stores 1/u_ii on the diagonal.
+int band_lu_inplace(double *a, int n, int p);
+
+// ---------------------------------------------------------------- handle
+struct st_handle {
+  st_problem_desc desc;
+  cudaStream_t stream = nullptr;
+  int dev = 0;
+  int d = 0, p = 0, nq = 0, B = 0;       // B = 2p+1
+  int n[3] = {1, 1, 1}, nel[3] = {1, 1, 1}, Q[3] = {1, 1, 1};
+  int Nt = 0, nel_t = 0, Qt = 0;
+  long long Ns = 0, Ndof = 0, Qs = 0, Nel_s = 0, NtQs = 0, maxStage = 0;
+  HostSetup hs;
+
+  // 1D device data (FP64 and FP32 copies of the bands)
+  double *Mb[3] = {}, *Kb[3] = {}, *Mtb = nullptr, *Wtb = nullptr;
+  float *Mb32[3] = {}, *Kb32[3] = {}, *Mtb32 = nullptr, *Wtb32 = nullptr;
+  double *Bq[3] = {}, *B2q[3] = {}, *wqs[3] = {};   // spatial tables [e][q][a], weights [e*nq+q]
+  float *Bq32[3] = {};
+  double *bt = nullptr;       // time tables [k][e][q][a], k = 0..p
+  double *wt = nullptr;       // time weights [e*nq+q]
+  double *xt = nullptr;       // time points [e*nq+q]
+  double *xs[3] = {};         // spatial points per direction [e*nq+q]
+  double *tauq = nullptr;     // [l-1][e][q]
+  double *wlu = nullptr;      // LU of W_t + b d_e M_t
+  // hat-function data of the Greville interpolation, per 1D Gauss point
+  int *hat_i_t = nullptr, *hat_i_s[3] = {};
+  double *hat_l_t = nullptr, *hat_l_s[3] = {};
+
+  // fast diagonalization
+  double *U64[3] = {}, *UT64[3] = {}, *lam[3] = {};
+  float *U32[3] = {}, *UT32[3] = {};
+  double *mu = nullptr;       // spatial eigenvalues mu_j, j over N_s
+  double *lu64 = nullptr;     // [it][k][j], k = 0..2p
+  float *lu32 = nullptr;
+
+  // linearization: symmetric time band per spatial Gauss point, [k][it][q], k = 0..p
+  double *band64 = nullptr;
+  float *band32 = nullptr;
+  bool have_lin = false;
+  double *f64 = nullptr;
+
+  // ionic / low rank
+  unsigned long long *emax = nullptr;   // [et][es] bit pattern of max |R| (non-negative double)
+  double *stats = nullptr;              // [0] max|u| [1] max|d_t u| [2] max|R| (bit patterns)
+  double *theta = nullptr;              // [Nt][Ns]
+  double *gram = nullptr;               // [Nt][Nt]
+  double *evec = nullptr, *eval = nullptr;
+  double *eig_work = nullptr;
+  float *eig32 = nullptr;
+  int rank = 0;
+  double *Ur = nullptr, *sr = nullptr, *Vr = nullptr;   // [Nt][R], [R], [Ns][R]
+  double *th_t = nullptr;   // theta_{t,r} at time Gauss points [r][Qt]
+  double *Tr = nullptr;     // SU time bands [r][k][it]
+  int rank_cap = 0;
+  double theta_fro = 0.0;
+
+  // workspaces
+  double *W64[2] = {};
+  float *W32[2] = {};
+  double *K64[7] = {};
+  float *K32[7] = {};
+  double *U0 = nullptr, *L0 = nullptr, *Wq0 = nullptr;   // ionic fields at spatial qpts [Nt][Qs]
+  double *red = nullptr;       // reduction scratch (device)
+  double *red_host = nullptr;  // pinned host mirror
+  // Krylov
+  int m = 0;
+  double *V64 = nullptr; float *V32 = nullptr;
+  double *r64 = nullptr, *x64 = nullptr, *t64a = nullptr, *t64b = nullptr;
+  double *z64 = nullptr, *b64 = nullptr;   // GMRES preconditioner output, Newton right-hand side
+  float *r32 = nullptr, *t32a = nullptr, *t32b = nullptr, *d32 = nullptr;
+  double *hcol = nullptr;      // device [2*(m+2)] Arnoldi coefficients
+  std::vector<void *> allocs;
+};
+
+// ---------------------------------------------------------------- helpers
+#define ST_CUDA(call)                                                  \
+  do {                                                                 \
+    cudaError_t _e = (call);                                           \
+    if (_e != cudaSuccess) return _e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA; \
+  } while (0)
+
+#define ST_TRY(call)                    \
+  do {                                  \
+    st_status _s = (call);              \
+    if (_s != ST_OK) return _s;         \
+  } while (0)
+
+// ---------------------------------------------------------------- kernels (launchers)
+// generic tensor views: [outer][n][inner]
+template <typename T>
+void launch_band_pass(cudaStream_t s, T *out, int nterms, const T *const *bands, const T *const *ins,
+                      const double *coefs, int n, long long inner, long long outer, int p, bool accumulate);
+template <typename T>
+void launch_interp_fwd(cudaStream_t s, T *out, const T *in, const T *tab, int nel, int p, int nq,
+                       long long inner, long long outer);
+template <typename T>
+void launch_interp_bwd(cudaStream_t s, T *out, const T *in, const T *tab, int nel, int p, int nq,
+                       long long inner, long long outer, bool accumulate);
+template <typename T>
+void launch_qband_apply(cudaStream_t s, T *z, const T *x, const T *band, int Nt, long long Qs, int p);
+template <typename T>
+void launch_mode_gemm(cudaStream_t s, T *out, const T *in, const T *A, int n, long long inner, long long outer);
+template <typename T>
+void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p);
+template <typename T>
+void launch_multi_dot(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *w,
+                      long long n, double *scratch);
+template <typename T>
+void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, const double *h,
+                       long long n);
+template <typename T>
+void launch_scale_copy(cudaStream_t s, T *y, const T *x, double alpha, long long n);
+void launch_axpby64(cudaStream_t s, double *y, const double *x, double a, double b, long long n);
+void launch_sub64(cudaStream_t s, double *r, const double *b, const double *ax, long long n);
+void launch_d2f(cudaStream_t s, float *y, const double *x, double scale, long long n);
+void launch_f2d_axpy(cudaStream_t s, double *y, const float *x, double scale, long long n);
+void launch_absmax64(cudaStream_t s, double *out, const double *x, const double *y, long long n, double *scratch);
+void launch_norm2_64(cudaStream_t s, double *out, const double *x, long long n, double *scratch);
+void launch_band_to_f32(cudaStream_t s, float *out, const double *in, long long n);
+
+// ionic / stabilization
+st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bool want_stats);
+st_status theta_and_lowrank(st_handle *h, st_ionic_info *info);
+st_status su_band_add(st_handle *h);
+st_status source_assemble(st_handle *h);
+st_status wupdate_run(st_handle *h, const double *u, double *w);
+
+// eigen / FD
+st_status fd_setup(st_handle *h);
+st_status sym_eig_desc(st_handle *h, const double *A, int n, double *evec, double *eval);
+
+// apply / precond
+template <typename T>
+st_status apply_T(st_handle *h, const T *x, T *y);
+template <typename T>
+st_status precond_T(st_handle *h, const T *r, T *z);
+
+void *st_alloc(st_handle *h, size_t bytes, st_status *err);
