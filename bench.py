@@ -1,0 +1,353 @@
+#!/usr/bin/env python
+"""Benchmark of the space-time IgA monodomain solver on GB300.
+
+One step = one pass of the whole hot path: one fixed-point iteration of
+Sec. 3.1 (ionic quadrature, Theta-hat, low rank, reaction + SU bands, the
+preconditioned GMRES solve of A u = f to true relative residual 1e-8, the
+w-update, relaxation and the stopping norm), on the 2D anisotropic workload
+(p = 3, 128 x 128 spatial x 256 time elements, 4,427,538 unknowns), starting
+every step from the same saved iterate k = 2.  The set-up (1D data,
+eigendecompositions, LU factors) runs once per problem and is reported apart.
+
+Output: one JSON line (rank 0).  `value` is unknowns per second of the mixed
+FP32/FP64 path with inputs resident on the device; `fp64` gives the FP64 path
+on the same step; `e2e` measures the same step through the C ABI from pinned
+host buffers, copies included; `roofline` reports the stage with the largest
+share of device time against the measured HBM bandwidth; `cpu_baseline` times
+the CPU oracle on a bounded sample of the same workload.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "c2_aniso_2d"
+CPU_SAMPLE = dict(n_el=[12, 12], n_el_t=24)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--scale", default=None, help="nx,ny,nt element counts (smaller case, e.g. for profiling)")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.path is None or not os.path.exists(self.path):
+            return None
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_oracle_step(desc_sample):
+    """One fixed-point step of the oracle from u = w = 0 (runs in a child process
+    pinned to one thread so that `cores` is exact)."""
+    code = (
+        "import json, sys, time; sys.path.insert(0, %r)\n"
+        "import workloads as W\n"
+        "from oracle import Oracle\n"
+        "desc = json.loads(%r)\n"
+        "t = time.perf_counter(); o = Oracle(desc); u, w, h = o.solve(max_fp=1); dt = time.perf_counter() - t\n"
+        "print(json.dumps(dict(seconds=dt, n_dof=o.st.N_dof)))\n" % (ROOT, json.dumps(desc_sample)))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def cpu_sample_desc():
+    import workloads as W
+    d = W.config(WORKLOAD, scale=CPU_SAMPLE)
+    d["max_fp"] = 1
+    return d
+
+
+def cpu_baseline():
+    out = cpu_oracle_step(cpu_sample_desc())
+    return {"value": out["n_dof"] / out["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
+            "sample": f"one fixed-point step from u=w=0 of the same physics on {CPU_SAMPLE['n_el'][0]}x"
+                      f"{CPU_SAMPLE['n_el'][1]}x{CPU_SAMPLE['n_el_t']} elements ({out['n_dof']} DoF): "
+                      f"sparse space-time assembly + SuperLU direct solve, {out['seconds']:.1f} s"}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    desc = cpu_sample_desc()
+    times = []
+    n_dof = None
+    for k in range(args.warmup + args.steps):
+        out = cpu_oracle_step(desc)
+        n_dof = out["n_dof"]
+        if k >= args.warmup:
+            times.append(out["seconds"])
+    ms = 1000.0 * sum(times) / len(times)
+    value = n_dof / (ms / 1000.0)
+    line = {"impl": "reference", "metric": "space-time solve throughput (one fixed-point step incl. linear "
+                                           "solve at rel.res 1e-8)",
+            "value": value, "unit": "DoF/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} physics on a bounded sample "
+                                   f"({CPU_SAMPLE['n_el']} x {CPU_SAMPLE['n_el_t']} elements, {n_dof} DoF)"},
+            "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
+                             "sample": "CPU FP64 oracle: sparse assembly + SuperLU, one fixed-point step"},
+            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import workloads as W
+    from paper_2311_17500_gb300 import build as B
+    B.build()
+    import paper_2311_17500_gb300 as P
+    P.load()
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    desc = W.config(WORKLOAD)
+    if args.scale:
+        nx, ny, nt = (int(v) for v in args.scale.split(","))
+        desc["n_el"] = [nx, ny]
+        desc["n_el_t"] = nt
+    desc["max_fp"] = 1
+    desc["rtol"] = 1e-8
+    desc["gmres_m"] = 150
+    desc["max_it"] = 3000
+
+    def make(precision):
+        d = dict(desc, precision=precision)
+        t0 = time.perf_counter()
+        s = P.Solver(d, sptr)
+        torch.cuda.synchronize()
+        return s, time.perf_counter() - t0
+
+    s, setup_s = make("mixed")
+    N = s.dims["N_dof"]
+    u = torch.zeros(N, dtype=torch.float64, device="cuda")
+    w = torch.zeros_like(u)
+    for _ in range(2):                       # iterate k = 2 of the nonlinear loop
+        s.solve(u.data_ptr(), w.data_ptr(), allow_unconverged=True)
+    u2, w2 = u.clone(), w.clone()
+
+    def step(solver):
+        u.copy_(u2)
+        w.copy_(w2)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        st = solver.solve(u.data_ptr(), w.data_ptr(), allow_unconverged=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1), st
+
+    for _ in range(args.warmup):
+        step(s)
+    lib = P.load()
+    n0 = lib.st_launch_count()
+    barrier()
+    s.profile(True)
+    times, stats = [], []
+    peaks = measured_peaks()
+    with Clocks(local) as clk:
+        for _ in range(args.steps):
+            ms, st = step(s)
+            times.append(ms)
+            stats.append(st)
+    barrier()
+    prof = s.profile_read()
+    s.profile(False)
+    launches = lib.st_launch_count() - n0
+    clocks = clk.summary()
+    ms_local = sum(times) / len(times)
+    t = torch.tensor([ms_local], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item())
+    value = ws * N / (ms_step / 1000.0)
+    st_last = stats[-1]
+
+    # roofline of the stage with the largest device time (HBM-bound kernels)
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    name, rec = top
+    achieved = rec["bytes"] / (rec["ms"] / 1000.0) / 1e9 if rec["ms"] > 0 else 0.0
+    hbm, bf16, src = peaks
+    roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": None, "peak_source": src,
+            "share_of_step": rec["ms"] / sum(times), "launch_groups": rec["launches"],
+            "stages_ms_per_step": {k: v["ms"] / len(times) for k, v in prof.items()}}
+
+    # e2e: pinned host inputs, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        hu = u2.cpu().pin_memory()
+        hw = w2.cpu().pin_memory()
+        ou = torch.empty_like(hu).pin_memory()
+        ow = torch.empty_like(hw).pin_memory()
+        e_ms = []
+        for k in range(max(2, args.steps // 2)):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            u.copy_(hu, non_blocking=True)
+            w.copy_(hw, non_blocking=True)
+            s.solve(u.data_ptr(), w.data_ptr(), allow_unconverged=True)
+            ou.copy_(u, non_blocking=True)
+            ow.copy_(w, non_blocking=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            e_ms.append(ev0.elapsed_time(ev1))
+        em = sum(e_ms) / len(e_ms)
+        e2e = {"value": ws * N / (em / 1000.0), "unit": "DoF/s", "h2d_bytes_per_step": 2 * 8 * N,
+               "d2h_bytes_per_step": 2 * 8 * N}
+    s.close()
+
+    fp64 = None
+    if not args.no_fp64:
+        s64, setup64 = make("fp64")
+        u.copy_(u2); w.copy_(w2)
+        step(s64)                                   # warm-up
+        f_ms = []
+        f_st = None
+        for _ in range(max(1, args.fp64_steps)):
+            ms, f_st = step(s64)
+            f_ms.append(ms)
+        fm = sum(f_ms) / len(f_ms)
+        fp64 = {"value": N / (fm / 1000.0), "ms_per_step": fm, "gmres_iters": f_st["gmres_iters"],
+                "rel_res": f_st["rel_res"], "setup_s": setup64, "speedup_mixed_vs_fp64": fm / ms_step}
+        s64.close()
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline()
+
+    srt = sorted(times)
+    line = {
+        "metric": "space-time solve throughput (one fixed-point step incl. linear solve at rel.res 1e-8), "
+                  "mixed vs FP64",
+        "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{WORKLOAD}: 2D unit square, p=3, {desc['n_el'][0]}x{desc['n_el'][1]} x "
+                               f"{desc['n_el_t']} elements, D=diag(1e-3,2.5e-4), seeded corner stimulus, SU, "
+                               f"Picard step from saved iterate k=2",
+                   "N_dof": N, "precision": "mixed: FP32 inner GMRES(150) + FP64 refinement",
+                   "l2": "inputs larger than L2 (time bands alone 1.08 GB FP32)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "setup_s": setup_s},
+        "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+        "solve": {"gmres_iters": st_last["gmres_iters"], "outer_iters": st_last["outer_iters"],
+                  "rel_res": st_last["rel_res"], "rank": st_last["rank"]},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "fp64": fp64,
+        "e2e": e2e,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -205,6 +205,29 @@ enum {
 };
 st_status st_get(st_handle *h, int what, void *dst_host, size_t bytes);
 
+/* Optional per-stage timing, for measurement only (no part of the method):
+ * st_profile(h, 1) clears the record and brackets every later launch group
+ * of a stage with CUDA events on the handle's stream; st_profile(h, 0) stops.
+ * st_profile_read sums, for one stage, the event-timed milliseconds, the
+ * algorithmic bytes moved (the compulsory HBM traffic of the launch group:
+ * each input read once, each output written once), the flops, and the number
+ * of launch groups.  Stages: */
+enum {
+  ST_STAGE_KRON = 0,     /* banded Kronecker passes of A */
+  ST_STAGE_INTERP = 1,   /* sum-factorization passes between coefficients and Gauss points */
+  ST_STAGE_QBAND = 2,    /* time band per spatial Gauss point (reaction + SU terms) */
+  ST_STAGE_FD_GEMM = 3,  /* preconditioner spatial transforms */
+  ST_STAGE_FD_LU = 4,    /* preconditioner banded time solves */
+  ST_STAGE_ARNOLDI = 5,  /* Gram-Schmidt inner products, updates and norms */
+  ST_STAGE_IONIC = 6,    /* ionic quadrature and reaction band assembly */
+  ST_STAGE_LOWRANK = 7,  /* Theta-hat, Gram matrix, eigen-decomposition, SU bands */
+  ST_STAGE_COUNT = 9
+};
+st_status st_profile(st_handle *h, int enable);
+/* Number of kernel launches this library has issued in the process so far. */
+long long st_launch_count(void);
+st_status st_profile_read(st_handle *h, int stage, double *ms, double *bytes, double *flops, long long *launches);
+
 #ifdef __cplusplus
 }
 #endif

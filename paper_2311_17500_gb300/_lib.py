@@ -24,7 +24,8 @@ GET = dict(theta_hat=0, lowrank_s=1, lowrank_u=2, lowrank_v=3, tau_q=4, fd_eig=5
 
 EXPORTS = ["st_footprint", "st_setup", "st_destroy", "st_error_string", "st_get_dims", "st_ionic",
            "st_linearize", "st_apply", "st_precond", "st_linsolve", "st_wupdate", "st_rhs", "st_solve",
-           "st_get"]
+           "st_get", "st_profile", "st_profile_read", "st_launch_count"]
+STAGES = ["kron", "interp", "qband", "fd_gemm", "fd_lu", "arnoldi", "ionic", "lowrank"]
 
 
 class StStim(ctypes.Structure):
@@ -96,8 +97,13 @@ def load(path=None):
     lib.st_rhs.argtypes = [vp, vp]
     lib.st_solve.argtypes = [vp, vp, vp, P(StStats)]
     lib.st_get.argtypes = [vp, i, vp, sz]
+    lib.st_profile.argtypes = [vp, i]
+    d = ctypes.c_double
+    lib.st_profile_read.argtypes = [vp, i, P(d), P(d), P(d), P(ctypes.c_longlong)]
+    lib.st_launch_count.argtypes = []
+    lib.st_launch_count.restype = ctypes.c_longlong
     for name in EXPORTS:
-        if name != "st_error_string":
+        if name not in ("st_error_string", "st_launch_count"):
             getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -219,6 +225,19 @@ class Solver:
             _check(code, "st_solve")
         out = _struct_dict(st)
         out["status"] = code
+        return out
+
+    def profile(self, enable):
+        _check(self.lib.st_profile(self.h, 1 if enable else 0), "st_profile")
+
+    def profile_read(self):
+        """{stage: dict(ms, bytes, flops, launches)} of the recorded launches."""
+        out = {}
+        for k, name in enumerate(STAGES):
+            ms, b, f, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+            _check(self.lib.st_profile_read(self.h, k, ctypes.byref(ms), ctypes.byref(b), ctypes.byref(f),
+                                            ctypes.byref(n)), "st_profile_read")
+            out[name] = dict(ms=ms.value, bytes=b.value, flops=f.value, launches=n.value)
         return out
 
     def get(self, what, count):

@@ -1,6 +1,7 @@
 // C ABI of libst.so: set-up, operator, preconditioner, Krylov solver and the
 // nonlinear loop of the space-time IgA monodomain solver (include/st.h).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -182,11 +183,16 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
     ST_TRY(precond_T<T>(h, vj, z));
     ST_TRY(apply_T<T>(h, z, w));
     double *h1 = hd, *h2 = hd + (m + 1), *hn = hd + 2 * (m + 1);
-    launch_multi_dot<T>(s, h1, V, N, j + 1, w, N, scratch);
-    launch_multi_axpy<T>(s, w, V, N, j + 1, h1, N);
-    launch_multi_dot<T>(s, h2, V, N, j + 1, w, N, scratch);
-    launch_multi_axpy<T>(s, w, V, N, j + 1, h2, N);
-    launch_multi_dot<T>(s, hn, w, N, 1, w, N, scratch);
+    {
+      // CGS2: two projections (each reads j+1 basis vectors and w twice, writes w) and a norm
+      double vb = (double)N * sizeof(T);
+      ProfScope ps(h, PROF_ARNOLDI, vb * (2.0 * (2 * (j + 1) + 3) + 1.0), 8.0 * (j + 1) * (double)N + 2.0 * N);
+      launch_multi_dot<T>(s, h1, V, N, j + 1, w, N, scratch);
+      launch_multi_axpy<T>(s, w, V, N, j + 1, h1, N);
+      launch_multi_dot<T>(s, h2, V, N, j + 1, w, N, scratch);
+      launch_multi_axpy<T>(s, w, V, N, j + 1, h2, N);
+      launch_multi_dot<T>(s, hn, w, N, 1, w, N, scratch);
+    }
     ST_CUDA(cudaMemcpyAsync(hh.data(), hd, (2 * (m + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
     ST_CUDA(cudaStreamSynchronize(s));
     double hnorm = std::sqrt(std::max(hh[2 * (m + 1)], 0.0));
@@ -235,6 +241,34 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
 }  // namespace
 
 // ---------------------------------------------------------------- internals
+static std::atomic<long long> g_launches{0};
+void st_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static cudaEvent_t prof_event(st_handle *h) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    h->ev_pool.push_back(e);
+  }
+  return h->ev_pool[h->ev_used++];
+}
+
+ProfScope::ProfScope(st_handle *hh, int cat, double bytes, double flops) : h(hh), idx((size_t)-1) {
+  if (!h->prof_on) return;
+  st_handle::ProfRec r;
+  r.cat = cat;
+  r.a = prof_event(h);
+  r.b = prof_event(h);
+  r.bytes = bytes;
+  r.flops = flops;
+  cudaEventRecord(r.a, h->stream);
+  idx = h->prof.size();
+  h->prof.push_back(r);
+}
+
+ProfScope::~ProfScope() {
+  if (idx != (size_t)-1) cudaEventRecord(h->prof[idx].b, h->stream);
+}
+
 void *st_alloc(st_handle *h, size_t bytes, st_status *err) {
   void *p = nullptr;
   if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
@@ -285,7 +319,10 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   const st_problem_desc &D = h->desc;
   int p = h->p;
   long long nx = h->n[0], ny = h->n[1], nz = h->n[2], Nt = h->Nt, Ns = h->Ns;
+  const double sz = sizeof(T);
+  const double vec = (double)h->Ndof * sz;
   // --- Kronecker part
+  ProfScope *pk = new ProfScope(h, PROF_KRON, vec * (h->d == 1 ? 7 : h->d == 2 ? 12 : 19));
   const T *bands[3];
   const T *ins[3];
   double cf[3];
@@ -332,6 +369,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   bands[0] = P::Wt(h); ins[0] = m; cf[0] = D.C_m;
   bands[1] = P::Mt(h); ins[1] = sK; cf[1] = 1.0;
   launch_band_pass<T>(s, y, 2, bands, ins, cf, (int)Nt, Ns, 1, p, false);
+  delete pk;
   // --- reaction + SU part
   long long qd[3] = {h->Q[0], h->Q[1], h->Q[2]};
   long long nd[3] = {h->n[0], h->n[1], h->n[2]};
@@ -342,12 +380,16 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
     for (int k = 0; k < l; ++k) inner *= qd[k];
     for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
     T *out = P::W(h, ping);
+    ProfScope ps(h, PROF_INTERP, sz * (double)outer * inner * (h->n[l] + (double)h->Q[l]));
     launch_interp_fwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer);
     cur = out;
     ping ^= 1;
   }
   T *zq = P::W(h, ping);
-  launch_qband_apply<T>(s, zq, cur, P::band(h), h->Nt, h->Qs, p);
+  {
+    ProfScope ps(h, PROF_QBAND, sz * (double)h->NtQs * (p + 3));
+    launch_qband_apply<T>(s, zq, cur, P::band(h), h->Nt, h->Qs, p);
+  }
   cur = zq;
   ping ^= 1;
   for (int l = h->d - 1; l >= 0; --l) {
@@ -355,6 +397,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
     for (int k = 0; k < l; ++k) inner *= qd[k];
     for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
     T *out = (l == 0) ? y : P::W(h, ping);
+    ProfScope ps(h, PROF_INTERP, sz * (double)outer * inner * (h->n[l] * (l == 0 ? 2.0 : 1.0) + (double)h->Q[l]));
     launch_interp_bwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer, l == 0);
     cur = out;
     ping ^= 1;
@@ -374,15 +417,20 @@ st_status precond_T(st_handle *h, const T *r, T *z) {
   const T *cur = r;
   T *bufs[2] = {P::K(h, 0), P::K(h, 1)};
   int ping = 0;
+  const double vec = (double)h->Ndof * sizeof(T);
   for (int l = 0; l < h->d; ++l) {
     long long inner = 1, outer = h->Nt;
     for (int k = 0; k < l; ++k) inner *= nd[k];
     for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
+    ProfScope ps(h, PROF_FD_GEMM, 2 * vec, 2.0 * h->n[l] * (double)h->Ndof);
     launch_mode_gemm<T>(s, bufs[ping], cur, P::UT(h, l), h->n[l], inner, outer);
     cur = bufs[ping];
     ping ^= 1;
   }
-  launch_tline_lu_solve<T>(s, bufs[ping], cur, P::lu(h), h->Nt, h->Ns, h->p);
+  {
+    ProfScope ps(h, PROF_FD_LU, vec * (2 + h->B));
+    launch_tline_lu_solve<T>(s, bufs[ping], cur, P::lu(h), h->Nt, h->Ns, h->p);
+  }
   cur = bufs[ping];
   ping ^= 1;
   for (int l = 0; l < h->d; ++l) {
@@ -390,6 +438,7 @@ st_status precond_T(st_handle *h, const T *r, T *z) {
     for (int k = 0; k < l; ++k) inner *= nd[k];
     for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
     T *out = (l == h->d - 1) ? z : bufs[ping];
+    ProfScope ps(h, PROF_FD_GEMM, 2 * vec, 2.0 * h->n[l] * (double)h->Ndof);
     launch_mode_gemm<T>(s, out, cur, P::U(h, l), h->n[l], inner, outer);
     cur = out;
     ping ^= 1;
@@ -433,6 +482,7 @@ st_status st_destroy(st_handle *h) {
   cudaSetDevice(h->dev);
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void *p : h->allocs) cudaFree(p);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->red_host) cudaFreeHost(h->red_host);
   delete h;
   return ST_OK;
@@ -581,7 +631,11 @@ st_status st_linearize(st_handle *h, const double *u, const double *w, int kind,
   if (kind != ST_PICARD && kind != ST_NEWTON) return ST_ERR_ARG;
   bool su = h->desc.stabilization == ST_SU;
   bool stats = !keep_theta;
-  ST_TRY(ionic_run(h, u, w, kind, stats));
+  {
+    ProfScope ps(h, PROF_IONIC, 8.0 * (double)h->NtQs * (3 + h->p + 1));
+    ST_TRY(ionic_run(h, u, w, kind, stats));
+  }
+  ProfScope plr(h, PROF_LOWRANK, 0.0);
   if (stats) {
     if (su) {
       ST_TRY(theta_and_lowrank(h, info));
@@ -742,6 +796,32 @@ st_status st_solve(st_handle *h, double *u, double *w, st_stats *stats) {
     stats->rank = h->rank;
   }
   return status;
+}
+
+long long st_launch_count(void) { return g_launches.load(); }
+
+st_status st_profile(st_handle *h, int enable) {
+  if (!h) return ST_ERR_ARG;
+  ST_CUDA(cudaStreamSynchronize(h->stream));
+  h->prof.clear();
+  h->ev_used = 0;
+  h->prof_on = enable != 0;
+  return ST_OK;
+}
+
+st_status st_profile_read(st_handle *h, int cat, double *ms, double *bytes, double *flops, long long *launches) {
+  if (!h || cat < 0 || cat >= PROF_NCAT || !ms || !bytes || !flops || !launches) return ST_ERR_ARG;
+  ST_CUDA(cudaStreamSynchronize(h->stream));
+  double t = 0.0, b = 0.0, f = 0.0;
+  long long n = 0;
+  for (const auto &r : h->prof) {
+    if (r.cat != cat) continue;
+    float e = 0.0f;
+    if (cudaEventElapsedTime(&e, r.a, r.b) != cudaSuccess) { cudaGetLastError(); continue; }
+    t += e; b += r.bytes; f += r.flops; ++n;
+  }
+  *ms = t; *bytes = b; *flops = f; *launches = n;
+  return ST_OK;
 }
 
 st_status st_get(st_handle *h, int what, void *dst, size_t bytes) {

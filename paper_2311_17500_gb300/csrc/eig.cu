@@ -352,10 +352,10 @@ st_status refine(st_handle *h, const Op &A, const Op &B, int n, double normA, do
     // S = X^T AX, Rm = X^T BX
     launch_gemm64(s, S, X, AX, n, n, n, 1, n, n, 1, n, 1, 1.0, 0.0);
     launch_gemm64(s, Rm, X, BX, n, n, n, 1, n, n, 1, n, 1, 1.0, 0.0);
-    refine_norms_kernel<<<1, 1024, 0, s>>>(norms, S, Rm, n);
-    refine_E_kernel<<<grid_for(nn), 256, 0, s>>>(E, S, Rm, lam, n, norms, normA);
+    st_count_launch(); refine_norms_kernel<<<1, 1024, 0, s>>>(norms, S, Rm, n);
+    st_count_launch(); refine_E_kernel<<<grid_for(nn), 256, 0, s>>>(E, S, Rm, lam, n, norms, normA);
     launch_gemm64(s, XE, X, E, n, n, n, n, 1, n, 1, n, 1, 1.0, 0.0);
-    add_kernel<<<grid_for(nn), 256, 0, s>>>(X, XE, nn);
+    st_count_launch(); add_kernel<<<grid_for(nn), 256, 0, s>>>(X, XE, nn);
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;
@@ -365,11 +365,11 @@ st_status jacobi32(st_handle *h, const double *A64, int n, double *X64) {
   cudaStream_t s = h->stream;
   size_t nn = (size_t)n * n;
   float *A32 = h->eig32, *V32 = h->eig32 + nn;
-  d2f_kernel<<<grid_for(nn), 256, 0, s>>>(A32, A64, nn);
+  st_count_launch(); d2f_kernel<<<grid_for(nn), 256, 0, s>>>(A32, A64, nn);
   int m = n + (n & 1);
   size_t sh = (size_t)(m / 2) * (2 * sizeof(float) + 2 * sizeof(int));
-  jacobi_kernel<float><<<1, kJacThreads, sh, s>>>(A32, V32, n, 30, 2e-7, nullptr);
-  f2d_kernel<<<grid_for(nn), 256, 0, s>>>(X64, V32, nn);
+  st_count_launch(); jacobi_kernel<float><<<1, kJacThreads, sh, s>>>(A32, V32, n, 30, 2e-7, nullptr);
+  st_count_launch(); f2d_kernel<<<grid_for(nn), 256, 0, s>>>(X64, V32, nn);
   ST_CUDA(cudaGetLastError());
   return ST_OK;
 }
@@ -396,7 +396,7 @@ st_status sym_eig_desc(st_handle *h, const double *A, int n, double *evec, doubl
   opA.dense = A;
   double normA = host_fro(s, A, nn);
   ST_TRY(refine(h, opA, opB, n, normA, X, lam, 3, work));
-  sort_desc_kernel<<<grid_for(n), 256, 0, s>>>(eval, evec, lam, X, n);
+  st_count_launch(); sort_desc_kernel<<<grid_for(n), 256, 0, s>>>(eval, evec, lam, X, n);
   ST_CUDA(cudaGetLastError());
   return ST_OK;
 }
@@ -416,13 +416,13 @@ st_status fd_setup(st_handle *h) {
     double *L = h->eig_work;                      // n x (p+1)
     double *Kd = L + (size_t)n * (p + 1);         // dense D K
     double *T1 = Kd + nn, *C = T1 + nn, *X = C + nn, *lam = X + nn, *work = lam + n;
-    chol_band_kernel<<<1, 1, 0, s>>>(L, h->Mb[l], n, p, fail);
-    band_to_dense_kernel<<<grid_for(nn), 256, 0, s>>>(Kd, h->Kb[l], n, p, D.D[l]);
-    lower_solve_cols_kernel<<<(n + 127) / 128, 128, 0, s>>>(T1, Kd, L, n, p, 0);   // T1 = L^-1 DK
-    lower_solve_cols_kernel<<<(n + 127) / 128, 128, 0, s>>>(C, T1, L, n, p, 1);    // C = L^-1 T1^T
-    symmetrize_kernel<<<grid_for(nn), 256, 0, s>>>(C, n);
+    st_count_launch(); chol_band_kernel<<<1, 1, 0, s>>>(L, h->Mb[l], n, p, fail);
+    st_count_launch(); band_to_dense_kernel<<<grid_for(nn), 256, 0, s>>>(Kd, h->Kb[l], n, p, D.D[l]);
+    st_count_launch(); lower_solve_cols_kernel<<<(n + 127) / 128, 128, 0, s>>>(T1, Kd, L, n, p, 0);   // T1 = L^-1 DK
+    st_count_launch(); lower_solve_cols_kernel<<<(n + 127) / 128, 128, 0, s>>>(C, T1, L, n, p, 1);    // C = L^-1 T1^T
+    st_count_launch(); symmetrize_kernel<<<grid_for(nn), 256, 0, s>>>(C, n);
     ST_TRY(jacobi32(h, C, n, T1));                                                   // T1 = Z
-    upper_solve_cols_kernel<<<(n + 127) / 128, 128, 0, s>>>(X, T1, L, n, p);        // X = L^-T Z
+    st_count_launch(); upper_solve_cols_kernel<<<(n + 127) / 128, 128, 0, s>>>(X, T1, L, n, p);        // X = L^-T Z
     Op opA, opB;
     opA.band = h->Kb[l];
     opA.scale = D.D[l];
@@ -431,18 +431,18 @@ st_status fd_setup(st_handle *h) {
     ST_TRY(refine(h, opA, opB, n, normA, X, lam, 3, work));
     ST_CUDA(cudaMemcpyAsync(h->U64[l], X, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
     ST_CUDA(cudaMemcpyAsync(h->lam[l], lam, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    transpose_kernel<<<grid_for(nn), 256, 0, s>>>(h->UT64[l], h->U64[l], n);
+    st_count_launch(); transpose_kernel<<<grid_for(nn), 256, 0, s>>>(h->UT64[l], h->U64[l], n);
     launch_band_to_f32(s, h->U32[l], h->U64[l], nn);
     launch_band_to_f32(s, h->UT32[l], h->UT64[l], nn);
   }
-  mu_kernel<<<grid_for(h->Ns), 256, 0, s>>>(h->mu, h->lam[0], h->lam[1], h->lam[2], h->n[0], h->n[1], h->d, h->Ns);
+  st_count_launch(); mu_kernel<<<grid_for(h->Ns), 256, 0, s>>>(h->mu, h->lam[0], h->lam[1], h->lam[2], h->n[0], h->n[1], h->d, h->Ns);
   unsigned blocks = (unsigned)((h->Ns + 127) / 128);
   double shift = D.a * D.c1;
   switch (p) {
-    case 1: fd_lu_kernel<1><<<blocks, 128, 0, s>>>(h->lu64, h->Wtb, h->Mtb, h->mu, D.C_m, shift, h->Nt, h->Ns, fail); break;
-    case 2: fd_lu_kernel<2><<<blocks, 128, 0, s>>>(h->lu64, h->Wtb, h->Mtb, h->mu, D.C_m, shift, h->Nt, h->Ns, fail); break;
-    case 3: fd_lu_kernel<3><<<blocks, 128, 0, s>>>(h->lu64, h->Wtb, h->Mtb, h->mu, D.C_m, shift, h->Nt, h->Ns, fail); break;
-    default: fd_lu_kernel<4><<<blocks, 128, 0, s>>>(h->lu64, h->Wtb, h->Mtb, h->mu, D.C_m, shift, h->Nt, h->Ns, fail); break;
+    case 1: st_count_launch(); fd_lu_kernel<1><<<blocks, 128, 0, s>>>(h->lu64, h->Wtb, h->Mtb, h->mu, D.C_m, shift, h->Nt, h->Ns, fail); break;
+    case 2: st_count_launch(); fd_lu_kernel<2><<<blocks, 128, 0, s>>>(h->lu64, h->Wtb, h->Mtb, h->mu, D.C_m, shift, h->Nt, h->Ns, fail); break;
+    case 3: st_count_launch(); fd_lu_kernel<3><<<blocks, 128, 0, s>>>(h->lu64, h->Wtb, h->Mtb, h->mu, D.C_m, shift, h->Nt, h->Ns, fail); break;
+    default: st_count_launch(); fd_lu_kernel<4><<<blocks, 128, 0, s>>>(h->lu64, h->Wtb, h->Mtb, h->mu, D.C_m, shift, h->Nt, h->Ns, fail); break;
   }
   long long nlu = (long long)h->Nt * h->B * h->Ns;
   launch_band_to_f32(s, h->lu32, h->lu64, nlu);

@@ -474,8 +474,8 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   }
   spatial_to_qpts(h, w, -1, h->Wq0);
   if (want_stats) {
-    zero_ull_kernel<<<grid_for((long long)h->nel_t * h->Nel_s), 256, 0, s>>>(h->emax, (long long)h->nel_t * h->Nel_s);
-    zero_ull_kernel<<<1, 32, 0, s>>>((unsigned long long *)h->stats, 4);
+    st_count_launch(); zero_ull_kernel<<<grid_for((long long)h->nel_t * h->Nel_s), 256, 0, s>>>(h->emax, (long long)h->nel_t * h->Nel_s);
+    st_count_launch(); zero_ull_kernel<<<1, 32, 0, s>>>((unsigned long long *)h->stats, 4);
   }
   IonicArgs a;
   a.D = h->desc;
@@ -491,10 +491,10 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   a.stats = (unsigned long long *)h->stats;
   unsigned blocks = (unsigned)((h->Qs + 127) / 128);
   switch (h->p) {
-    case 1: ionic_tline_kernel<1><<<blocks, 128, 0, s>>>(a); break;
-    case 2: ionic_tline_kernel<2><<<blocks, 128, 0, s>>>(a); break;
-    case 3: ionic_tline_kernel<3><<<blocks, 128, 0, s>>>(a); break;
-    default: ionic_tline_kernel<4><<<blocks, 128, 0, s>>>(a); break;
+    case 1: st_count_launch(); ionic_tline_kernel<1><<<blocks, 128, 0, s>>>(a); break;
+    case 2: st_count_launch(); ionic_tline_kernel<2><<<blocks, 128, 0, s>>>(a); break;
+    case 3: st_count_launch(); ionic_tline_kernel<3><<<blocks, 128, 0, s>>>(a); break;
+    default: st_count_launch(); ionic_tline_kernel<4><<<blocks, 128, 0, s>>>(a); break;
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;
@@ -532,14 +532,14 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
     int nel = (int)dimsE[l], nout = (int)dimsB[l];
     double *out = h->W64[ping];
     long long total = outer * nout * inner;
-    window_max_kernel<<<grid_for(total), 256, 0, s>>>(out, cur, nel, nout, h->p, l == 3 ? 1 : 0,
+    st_count_launch(); window_max_kernel<<<grid_for(total), 256, 0, s>>>(out, cur, nel, nout, h->p, l == 3 ? 1 : 0,
                                                        D.suppext == ST_SUPPEXT_SYMMETRIC, inner, outer);
     cdims[l] = nout;
     cur = out;
     ping ^= 1;
   }
   long long NtNs = h->Ndof;
-  theta_kernel<<<grid_for(NtNs), 256, 0, s>>>(h->theta, cur, den, NtNs);
+  st_count_launch(); theta_kernel<<<grid_for(NtNs), 256, 0, s>>>(h->theta, cur, den, NtNs);
   // Gram matrix G = Theta Theta^T (N_t x N_t, FP64)
   int Nt = h->Nt;
   launch_gemm64(s, h->gram, h->theta, h->theta, Nt, Nt, (int)h->Ns, h->Ns, 1, 1, h->Ns, Nt, 1, 1.0, 0.0);
@@ -580,7 +580,7 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
                             cudaMemcpyDeviceToDevice, s));
   // V = Theta^T U_R diag(1/sigma): (N_s x R)
   launch_gemm64(s, h->Vr, h->theta, h->Ur, (int)h->Ns, R, Nt, 1, h->Ns, R, 1, R, 1, 1.0, 0.0);
-  scale_cols_kernel<<<grid_for(h->Ns * R), 256, 0, s>>>(h->Vr, h->sr, R, h->Ns);
+  st_count_launch(); scale_cols_kernel<<<grid_for(h->Ns * R), 256, 0, s>>>(h->Vr, h->sr, R, h->Ns);
   ST_CUDA(cudaGetLastError());
   return ST_OK;
 }
@@ -589,8 +589,8 @@ st_status su_band_add(st_handle *h) {
   if (h->desc.stabilization != ST_SU || h->rank == 0) return ST_OK;
   cudaStream_t s = h->stream;
   int R = h->rank, p = h->p;
-  theta_t_kernel<<<grid_for((long long)h->Qt * R), 256, 0, s>>>(h->th_t, h->Ur, R, h->Qt, h->hat_i_t, h->hat_l_t);
-  su_time_band_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tr, h->th_t, h->tauq, h->bt,
+  st_count_launch(); theta_t_kernel<<<grid_for((long long)h->Qt * R), 256, 0, s>>>(h->th_t, h->Ur, R, h->Qt, h->hat_i_t, h->hat_l_t);
+  st_count_launch(); su_time_band_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tr, h->th_t, h->tauq, h->bt,
                                                                               h->wt, R, h->Nt, h->nel_t, p);
   // Cq = C_m sigma_r ws theta_s (into the first work buffer, R x Q_s <= N_t x Q_s)
   double *Cq = h->W64[0];
@@ -600,7 +600,7 @@ st_status su_band_add(st_handle *h) {
     hat.lam[l] = h->hat_l_s[l];
     hat.n[l] = h->n[l];
   }
-  su_space_coef_kernel<<<grid_for(h->Qs * R), 256, 0, s>>>(Cq, h->Vr, h->sr, geom(h), hat, h->desc.C_m, R, h->Qs);
+  st_count_launch(); su_space_coef_kernel<<<grid_for(h->Qs * R), 256, 0, s>>>(Cq, h->Vr, h->sr, geom(h), hat, h->desc.C_m, R, h->Qs);
   // band[(k,it)][q] += sum_r Tr[r][(k,it)] Cq[r][q]
   int Mrows = (p + 1) * h->Nt;
   launch_gemm64(s, h->band64, h->Tr, Cq, Mrows, (int)h->Qs, R, 1, Mrows, h->Qs, 1, h->Qs, 1, 1.0, 1.0);
@@ -614,10 +614,10 @@ st_status source_assemble(st_handle *h) {
   unsigned blocks = (unsigned)((h->Qs + 127) / 128);
   GeomArgs g = geom(h);
   switch (h->p) {
-    case 1: source_tline_kernel<1><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
-    case 2: source_tline_kernel<2><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
-    case 3: source_tline_kernel<3><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
-    default: source_tline_kernel<4><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
+    case 1: st_count_launch(); source_tline_kernel<1><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
+    case 2: st_count_launch(); source_tline_kernel<2><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
+    case 3: st_count_launch(); source_tline_kernel<3><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
+    default: st_count_launch(); source_tline_kernel<4><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
   }
   // spatial test functions: Gauss points -> coefficients, last axis first
   const double *cur = Fq;
@@ -642,10 +642,10 @@ st_status wupdate_run(st_handle *h, const double *u, double *w) {
   double bcoef = h->desc.b;
   unsigned blocks = (unsigned)((h->Ns + 127) / 128);
   switch (h->p) {
-    case 1: wupdate_kernel<1><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
-    case 2: wupdate_kernel<2><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
-    case 3: wupdate_kernel<3><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
-    default: wupdate_kernel<4><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
+    case 1: st_count_launch(); wupdate_kernel<1><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
+    case 2: st_count_launch(); wupdate_kernel<2><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
+    case 3: st_count_launch(); wupdate_kernel<3><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
+    default: st_count_launch(); wupdate_kernel<4><<<blocks, 128, 0, s>>>(w, u, h->Mtb, h->wlu, bcoef, h->Nt, h->Ns); break;
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;

@@ -399,21 +399,21 @@ void launch_band_pass(cudaStream_t s, T *out, int nterms, const T *const *bands,
     bt.coef[t] = t < nterms ? (T)coefs[t] : T(0);
   }
   long long total = outer * n * inner;
-  band_pass_kernel<T><<<grid_for(total), kThreads, 0, s>>>(out, bt, n, inner, outer, p, accumulate ? 1 : 0);
+  st_count_launch(); band_pass_kernel<T><<<grid_for(total), kThreads, 0, s>>>(out, bt, n, inner, outer, p, accumulate ? 1 : 0);
 }
 
 template <typename T>
 void launch_interp_fwd(cudaStream_t s, T *out, const T *in, const T *tab, int nel, int p, int nq,
                        long long inner, long long outer) {
   long long total = outer * (long long)nel * nq * inner;
-  interp_fwd_kernel<T><<<grid_for(total), kThreads, 0, s>>>(out, in, tab, nel, p, nq, inner, outer);
+  st_count_launch(); interp_fwd_kernel<T><<<grid_for(total), kThreads, 0, s>>>(out, in, tab, nel, p, nq, inner, outer);
 }
 
 template <typename T>
 void launch_interp_bwd(cudaStream_t s, T *out, const T *in, const T *tab, int nel, int p, int nq,
                        long long inner, long long outer, bool accumulate) {
   long long total = outer * (long long)(nel + p) * inner;
-  interp_bwd_kernel<T><<<grid_for(total), kThreads, 0, s>>>(out, in, tab, nel, p, nq, inner, outer,
+  st_count_launch(); interp_bwd_kernel<T><<<grid_for(total), kThreads, 0, s>>>(out, in, tab, nel, p, nq, inner, outer,
                                                             accumulate ? 1 : 0);
 }
 
@@ -422,17 +422,17 @@ void launch_qband_apply(cudaStream_t s, T *z, const T *x, const T *band, int Nt,
   int threads = 128;
   long long blocks = (Qs + threads - 1) / threads;
   switch (p) {
-    case 1: qband_kernel<T, 1><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
-    case 2: qband_kernel<T, 2><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
-    case 3: qband_kernel<T, 3><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
-    default: qband_kernel<T, 4><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
+    case 1: st_count_launch(); qband_kernel<T, 1><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
+    case 2: st_count_launch(); qband_kernel<T, 2><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
+    case 3: st_count_launch(); qband_kernel<T, 3><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
+    default: st_count_launch(); qband_kernel<T, 4><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
   }
 }
 
 template <typename T>
 void launch_gemm(cudaStream_t s, T *C, const T *A, const T *X, const GemmDesc &g, double alpha, double beta) {
   dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.batch);
-  gemm_kernel<T><<<grid, 256, 0, s>>>(C, A, X, g, (T)alpha, (T)beta);
+  st_count_launch(); gemm_kernel<T><<<grid, 256, 0, s>>>(C, A, X, g, (T)alpha, (T)beta);
 }
 
 // out[o][j][c] = sum_k A[j*n + k] in[o][k][c]
@@ -465,10 +465,10 @@ void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt
   int threads = 128;
   unsigned blocks = (unsigned)((Ns + threads - 1) / threads);
   switch (p) {
-    case 1: tline_lu_kernel<T, 1><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
-    case 2: tline_lu_kernel<T, 2><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
-    case 3: tline_lu_kernel<T, 3><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
-    default: tline_lu_kernel<T, 4><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
+    case 1: st_count_launch(); tline_lu_kernel<T, 1><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
+    case 2: st_count_launch(); tline_lu_kernel<T, 2><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
+    case 3: st_count_launch(); tline_lu_kernel<T, 3><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
+    default: st_count_launch(); tline_lu_kernel<T, 4><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
   }
 }
 
@@ -476,42 +476,42 @@ template <typename T>
 void launch_multi_dot(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *w, long long n,
                       double *scratch) {
   int blocks = (int)std::min<long long>(kDotBlocks, std::max<long long>(1, (n + 1023) / 1024));
-  multi_dot_kernel<T><<<blocks, 256, 0, s>>>(scratch, V, ldv, nv, w, n);
-  reduce_blocks_kernel<<<(nv + 127) / 128, 128, 0, s>>>(out, scratch, blocks, nv);
+  st_count_launch(); multi_dot_kernel<T><<<blocks, 256, 0, s>>>(scratch, V, ldv, nv, w, n);
+  st_count_launch(); reduce_blocks_kernel<<<(nv + 127) / 128, 128, 0, s>>>(out, scratch, blocks, nv);
 }
 
 template <typename T>
 void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, const double *h, long long n) {
-  multi_axpy_kernel<T><<<grid_for(n), kThreads, 0, s>>>(w, V, ldv, nv, h, n);
+  st_count_launch(); multi_axpy_kernel<T><<<grid_for(n), kThreads, 0, s>>>(w, V, ldv, nv, h, n);
 }
 
 template <typename T>
 void launch_scale_copy(cudaStream_t s, T *y, const T *x, double alpha, long long n) {
-  scale_copy_kernel<T><<<grid_for(n), kThreads, 0, s>>>(y, x, alpha, n);
+  st_count_launch(); scale_copy_kernel<T><<<grid_for(n), kThreads, 0, s>>>(y, x, alpha, n);
 }
 
 void launch_axpby64(cudaStream_t s, double *y, const double *x, double a, double b, long long n) {
-  axpby64_kernel<<<grid_for(n), kThreads, 0, s>>>(y, x, a, b, n);
+  st_count_launch(); axpby64_kernel<<<grid_for(n), kThreads, 0, s>>>(y, x, a, b, n);
 }
 void launch_sub64(cudaStream_t s, double *r, const double *b, const double *ax, long long n) {
-  sub64_kernel<<<grid_for(n), kThreads, 0, s>>>(r, b, ax, n);
+  st_count_launch(); sub64_kernel<<<grid_for(n), kThreads, 0, s>>>(r, b, ax, n);
 }
 void launch_d2f(cudaStream_t s, float *y, const double *x, double scale, long long n) {
-  d2f_kernel<<<grid_for(n), kThreads, 0, s>>>(y, x, scale, n);
+  st_count_launch(); d2f_kernel<<<grid_for(n), kThreads, 0, s>>>(y, x, scale, n);
 }
 void launch_f2d_axpy(cudaStream_t s, double *y, const float *x, double scale, long long n) {
-  f2d_axpy_kernel<<<grid_for(n), kThreads, 0, s>>>(y, x, scale, n);
+  st_count_launch(); f2d_axpy_kernel<<<grid_for(n), kThreads, 0, s>>>(y, x, scale, n);
 }
 void launch_absmax64(cudaStream_t s, double *out, const double *x, const double *y, long long n, double *scratch) {
   int blocks = (int)std::min<long long>(kDotBlocks, std::max<long long>(1, (n + 1023) / 1024));
-  absmax_kernel<<<blocks, 256, 0, s>>>(scratch, x, y, n);
-  max_blocks_kernel<<<1, 32, 0, s>>>(out, scratch, blocks);
+  st_count_launch(); absmax_kernel<<<blocks, 256, 0, s>>>(scratch, x, y, n);
+  st_count_launch(); max_blocks_kernel<<<1, 32, 0, s>>>(out, scratch, blocks);
 }
 void launch_norm2_64(cudaStream_t s, double *out, const double *x, long long n, double *scratch) {
   launch_multi_dot<double>(s, out, x, n, 1, x, n, scratch);
 }
 void launch_band_to_f32(cudaStream_t s, float *out, const double *in, long long n) {
-  to_f32_kernel<<<grid_for(n), kThreads, 0, s>>>(out, in, n);
+  st_count_launch(); to_f32_kernel<<<grid_for(n), kThreads, 0, s>>>(out, in, n);
 }
 
 void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, int M, int N, int K,

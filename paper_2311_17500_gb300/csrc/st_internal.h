@@ -110,6 +110,34 @@ struct st_handle {
   float *r32 = nullptr, *t32a = nullptr, *t32b = nullptr, *d32 = nullptr;
   double *hcol = nullptr;      // device [2*(m+2)] Arnoldi coefficients
   std::vector<void *> allocs;
+  // optional per-stage timing (CUDA events on the handle's stream)
+  bool prof_on = false;
+  struct ProfRec { int cat; cudaEvent_t a, b; double bytes, flops; };
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+};
+
+// Stage categories of the optional per-stage timing.
+enum {
+  PROF_KRON = 0,      // banded Kronecker passes of the operator
+  PROF_INTERP = 1,    // sum-factorization passes (coefficients <-> Gauss points)
+  PROF_QBAND = 2,     // time band per spatial Gauss point (reaction + SU)
+  PROF_FD_GEMM = 3,   // preconditioner spatial transforms
+  PROF_FD_LU = 4,     // preconditioner banded time solves
+  PROF_ARNOLDI = 5,   // Gram-Schmidt inner products and updates, norms
+  PROF_IONIC = 6,     // ionic quadrature and band assembly
+  PROF_LOWRANK = 7,   // Theta-hat, Gram matrix, eigen-decomposition, SU band update
+  PROF_OTHER = 8,
+  PROF_NCAT = 9
+};
+
+// Records events around the enclosed launches when profiling is on.
+struct ProfScope {
+  st_handle *h;
+  size_t idx;
+  ProfScope(st_handle *hh, int cat, double bytes, double flops = 0.0);
+  ~ProfScope();
 };
 
 // ---------------------------------------------------------------- helpers
@@ -176,3 +204,5 @@ template <typename T>
 st_status precond_T(st_handle *h, const T *r, T *z);
 
 void *st_alloc(st_handle *h, size_t bytes, st_status *err);
+// Process-wide count of kernel launches issued by this library.
+void st_count_launch();
