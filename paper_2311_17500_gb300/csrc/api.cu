@@ -78,7 +78,7 @@ Sizes plan(const st_problem_desc &D) {
   b += (size_t)z.Ndof * (d8 + f4) * 7;                             // Kronecker temporaries
   if (D.precision == ST_FP64) b += (size_t)(z.m + 1) * z.Ndof * d8;
   else b += (size_t)(z.m + 1) * z.Ndof * f4;
-  b += (size_t)(304 * (z.m + 40) + 4096) * d8;
+  b += (size_t)(608 * (z.m + 48) + 4096) * d8;
   z.bytes = b;
   return z;
 }
@@ -158,11 +158,11 @@ template <> float *ztmp<float>(st_handle *h) { return h->t32a; }
 template <typename T>
 st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int *its, double *est) {
   cudaStream_t s = h->stream;
-  long long N = h->Ndof;
+  long long N = h->Ndof, ld = h->ldv;
   T *V = basis<T>(h);
   T *z = ztmp<T>(h);
   int m = std::min(maxit, h->m);
-  double *hd = h->hcol;           // device: h1 [0..m], h2 [m+1 ..]
+  double *hd = h->hcol;           // device: h1 [0..m+1], h2 [m+2 .. 2m+3]
   double *scratch = h->red + 4096;
   launch_multi_dot<T>(s, hd, b, N, 1, b, N, scratch);
   double beta = std::sqrt(host_scalar(h, hd));
@@ -174,32 +174,33 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
   }
   launch_scale_copy<T>(s, V, b, 1.0 / beta, N);
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
-  std::vector<double> hh(2 * (m + 1) + 1);
+  std::vector<double> hh(2 * (m + 2));
   g[0] = beta;
   int j = 0;
   double res = beta;
   for (; j < m; ++j) {
-    T *vj = V + (long long)j * N, *w = V + (long long)(j + 1) * N;
+    T *vj = V + (long long)j * ld, *w = V + (long long)(j + 1) * ld;
     ST_TRY(precond_T<T>(h, vj, z));
     ST_TRY(apply_T<T>(h, z, w));
-    double *h1 = hd, *h2 = hd + (m + 1), *hn = hd + 2 * (m + 1);
+    double *h1 = hd, *h2 = hd + (m + 2);
     {
-      // CGS2: two projections (each reads j+1 basis vectors and w twice, writes w) and a norm
+      // CGS2: <V_i, w> for i <= j+1 (the last one is |w|^2), update, again,
+      // then the second update fused with the normalization by Pythagoras
       double vb = (double)N * sizeof(T);
-      ProfScope ps(h, PROF_ARNOLDI, vb * (2.0 * (2 * (j + 1) + 3) + 1.0), 8.0 * (j + 1) * (double)N + 2.0 * N);
-      launch_multi_dot<T>(s, h1, V, N, j + 1, w, N, scratch);
-      launch_multi_axpy<T>(s, w, V, N, j + 1, h1, N);
-      launch_multi_dot<T>(s, h2, V, N, j + 1, w, N, scratch);
-      launch_multi_axpy<T>(s, w, V, N, j + 1, h2, N);
-      launch_multi_dot<T>(s, hn, w, N, 1, w, N, scratch);
+      ProfScope ps(h, PROF_ARNOLDI, vb * (4.0 * (j + 1) + 6.0), 8.0 * (j + 1) * (double)N);
+      launch_multi_dot<T>(s, h1, V, ld, j + 2, w, N, scratch);
+      launch_multi_axpy<T>(s, w, V, ld, j + 1, h1, N);
+      launch_multi_dot<T>(s, h2, V, ld, j + 2, w, N, scratch);
+      launch_multi_axpy<T>(s, w, V, ld, j + 1, h2, N, h2 + (j + 1));
     }
-    ST_CUDA(cudaMemcpyAsync(hh.data(), hd, (2 * (m + 1) + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaMemcpyAsync(hh.data(), hd, 2 * (m + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
     ST_CUDA(cudaStreamSynchronize(s));
-    double hnorm = std::sqrt(std::max(hh[2 * (m + 1)], 0.0));
-    if (!std::isfinite(hnorm)) return ST_ERR_NAN;
-    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[(m + 1) + i];
+    double q = hh[(m + 2) + (j + 1)];
+    for (int i = 0; i <= j; ++i) q -= hh[(m + 2) + i] * hh[(m + 2) + i];
+    double hnorm = q > 0.0 ? std::sqrt(q) : 0.0;
+    if (!std::isfinite(hnorm) || !std::isfinite(hh[j + 1])) return ST_ERR_NAN;
+    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[(m + 2) + i];
     H[(size_t)(j + 1) * m + j] = hnorm;
-    if (hnorm > 0.0) launch_scale_copy<T>(s, w, w, 1.0 / hnorm, N);
     // apply the previous Givens rotations to the new column, then a new one
     for (int i = 0; i < j; ++i) {
       double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
@@ -230,7 +231,7 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
   for (int i = 0; i < k; ++i) y[i] = -y[i];
   ST_CUDA(cudaMemcpyAsync(hd, y.data(), std::max(k, 1) * sizeof(double), cudaMemcpyHostToDevice, s));
   ST_CUDA(cudaMemsetAsync(z, 0, N * sizeof(T), s));
-  if (k > 0) launch_multi_axpy<T>(s, z, V, N, k, hd, N);
+  if (k > 0) launch_multi_axpy<T>(s, z, V, ld, k, hd, N);
   ST_TRY(precond_T<T>(h, z, d));
   *its = k;
   *est = res / beta;
@@ -503,6 +504,7 @@ static st_status setup_impl(st_handle *h) {
   h->Nt = z.Nt; h->nel_t = z.nel_t; h->Qt = z.Qt;
   h->Ns = z.Ns; h->Ndof = z.Ndof; h->Qs = z.Qs; h->Nel_s = z.Nel_s; h->NtQs = z.NtQs;
   h->m = z.m;
+  h->ldv = (z.Ndof + 63) / 64 * 64;
   h->rank_cap = z.cap;
   ST_TRY(host_setup(D, h->hs));
   HostSetup &hs = h->hs;
@@ -585,9 +587,9 @@ static st_status setup_impl(st_handle *h) {
   h->U0 = dalloc<double>(h, h->NtQs, &e);
   h->L0 = dalloc<double>(h, h->NtQs, &e);
   h->Wq0 = dalloc<double>(h, h->NtQs, &e);
-  h->red = dalloc<double>(h, 4096 + 304 * (size_t)(h->m + 40), &e);
-  if (D.precision == ST_FP64) h->V64 = dalloc<double>(h, (size_t)(h->m + 1) * h->Ndof, &e);
-  else h->V32 = dalloc<float>(h, (size_t)(h->m + 1) * h->Ndof, &e);
+  h->red = dalloc<double>(h, 4096 + 608 * (size_t)(h->m + 48), &e);
+  if (D.precision == ST_FP64) h->V64 = dalloc<double>(h, (size_t)(h->m + 1) * h->ldv, &e);
+  else h->V32 = dalloc<float>(h, (size_t)(h->m + 1) * h->ldv, &e);
   h->r64 = dalloc<double>(h, h->Ndof, &e);
   h->x64 = dalloc<double>(h, h->Ndof, &e);
   h->t64a = dalloc<double>(h, h->Ndof, &e);
@@ -655,8 +657,7 @@ st_status st_linearize(st_handle *h, const double *u, const double *w, int kind,
     info->rank = h->rank;
     info->theta_fro = h->theta_fro;
   }
-  ST_TRY(su_band_add(h));
-  launch_band_to_f32(h->stream, h->band32, h->band64, (long long)(h->p + 1) * h->NtQs);
+  ST_TRY(su_band_add(h));   // also writes the FP32 copy of the bands
   ST_CUDA(cudaStreamSynchronize(h->stream));
   ST_CUDA(cudaGetLastError());
   h->have_lin = true;

@@ -16,7 +16,10 @@
 #include <algorithm>
 #include <cmath>
 #include <vector>
+#include <cooperative_groups.h>
 #include "st_internal.h"
+
+namespace cg = cooperative_groups;
 
 void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, int M, int N, int K,
                    long long sam, long long sak, long long sbk, long long sbc, long long scm, long long scc,
@@ -106,6 +109,83 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(T *A, T *V, int n, 
     __syncthreads();
   }
   if (tid == 0 && sweeps_out) *sweeps_out = sweep;
+}
+
+// The same cyclic Jacobi spread over a thread-block cluster: every block
+// computes the rotations of a round redundantly (identical data, identical
+// results), then block r applies the row updates of the pairs i = r mod CL and
+// the column updates of its slice of rows, the matrix staying in global
+// memory (L2).  Three cluster barriers per round; the number of sweeps is
+// bounded by max_sweeps.  `thr` is the absolute skip threshold.
+template <typename T>
+__global__ void __launch_bounds__(kJacThreads) jacobi_cluster_kernel(T *A, T *V, int n, int max_sweeps, double thr) {
+  extern __shared__ unsigned char smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int CL = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int m = n + (n & 1);
+  const int half = m / 2;
+  T *cs = (T *)smem_raw;
+  T *sn = cs + half;
+  int *pp = (int *)(sn + half);
+  int *qq = pp + half;
+  __shared__ int rotated;
+  const int tid = threadIdx.x;
+  const int r0 = (int)((long long)n * rank / CL), r1 = (int)((long long)n * (rank + 1) / CL);
+  for (int i = r0 * n + tid; i < r1 * n; i += blockDim.x) V[i] = (i / n == i % n) ? T(1) : T(0);
+  cluster.sync();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (tid == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < m - 1; ++round) {
+      for (int i = tid; i < half; i += blockDim.x) {
+        int a = (i == 0) ? 0 : 1 + ((i - 1 + round) % (m - 1));
+        int b = 1 + ((m - 2 - i + round) % (m - 1));
+        int p = min(a, b), q = max(a, b);
+        T c = T(1), s = T(0);
+        if (q < n) {
+          T apq = A[p * n + q];
+          if (fabs((double)apq) > thr) {
+            T app = A[p * n + p], aqq = A[q * n + q];
+            T tau = (aqq - app) / (T(2) * apq);
+            T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            c = T(1) / sqrt(T(1) + t * t);
+            s = t * c;
+            rotated = 1;
+          }
+        }
+        pp[i] = p; qq[i] = q; cs[i] = c; sn[i] = s;
+      }
+      cluster.sync();   // everyone has read the pivots before rows change
+      for (int idx = tid; idx < half * n; idx += blockDim.x) {
+        int i = idx / n, k = idx % n;
+        if (i % CL != rank) continue;
+        int p = pp[i], q = qq[i];
+        if (q >= n || sn[i] == T(0)) continue;
+        T c = cs[i], s = sn[i];
+        T ap = A[p * n + k], aq = A[q * n + k];
+        A[p * n + k] = c * ap - s * aq;
+        A[q * n + k] = s * ap + c * aq;
+      }
+      cluster.sync();
+      int rows = r1 - r0;
+      for (int idx = tid; idx < half * rows; idx += blockDim.x) {
+        int i = idx / rows, k = r0 + idx % rows;
+        int p = pp[i], q = qq[i];
+        if (q >= n || sn[i] == T(0)) continue;
+        T c = cs[i], s = sn[i];
+        T ap = A[k * n + p], aq = A[k * n + q];
+        A[k * n + p] = c * ap - s * aq;
+        A[k * n + q] = s * ap + c * aq;
+        T vp = V[k * n + p], vq = V[k * n + q];
+        V[k * n + p] = c * vp - s * vq;
+        V[k * n + q] = s * vp + c * vq;
+      }
+      cluster.sync();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
 }
 
 __global__ void d2f_kernel(float *y, const double *x, long long n) {
@@ -361,19 +441,6 @@ st_status refine(st_handle *h, const Op &A, const Op &B, int n, double normA, do
   return ST_OK;
 }
 
-st_status jacobi32(st_handle *h, const double *A64, int n, double *X64) {
-  cudaStream_t s = h->stream;
-  size_t nn = (size_t)n * n;
-  float *A32 = h->eig32, *V32 = h->eig32 + nn;
-  st_count_launch(); d2f_kernel<<<grid_for(nn), 256, 0, s>>>(A32, A64, nn);
-  int m = n + (n & 1);
-  size_t sh = (size_t)(m / 2) * (2 * sizeof(float) + 2 * sizeof(int));
-  st_count_launch(); jacobi_kernel<float><<<1, kJacThreads, sh, s>>>(A32, V32, n, 30, 2e-7, nullptr);
-  st_count_launch(); f2d_kernel<<<grid_for(nn), 256, 0, s>>>(X64, V32, nn);
-  ST_CUDA(cudaGetLastError());
-  return ST_OK;
-}
-
 double host_fro(cudaStream_t s, const double *A, size_t nn) {
   std::vector<double> hA(nn);
   cudaMemcpyAsync(hA.data(), A, nn * sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -382,6 +449,38 @@ double host_fro(cudaStream_t s, const double *A, size_t nn) {
   for (double v : hA) f += v * v;
   return std::sqrt(f);
 }
+
+st_status jacobi32(st_handle *h, const double *A64, int n, double *X64) {
+  cudaStream_t s = h->stream;
+  size_t nn = (size_t)n * n;
+  float *A32 = h->eig32, *V32 = h->eig32 + nn;
+  st_count_launch(); d2f_kernel<<<grid_for(nn), 256, 0, s>>>(A32, A64, nn);
+  int m = n + (n & 1);
+  size_t sh = (size_t)(m / 2) * (2 * sizeof(float) + 2 * sizeof(int));
+  if (n < 96) {
+    st_count_launch(); jacobi_kernel<float><<<1, kJacThreads, sh, s>>>(A32, V32, n, 30, 2e-7, nullptr);
+  } else {
+    double thr = 2e-7 * host_fro(s, A64, nn);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 8;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(8, 1, 1);
+    cfg.blockDim = dim3(kJacThreads, 1, 1);
+    cfg.dynamicSmemBytes = sh;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    st_count_launch();
+    ST_CUDA(cudaLaunchKernelEx(&cfg, jacobi_cluster_kernel<float>, A32, V32, n, 30, thr));
+  }
+  st_count_launch(); f2d_kernel<<<grid_for(nn), 256, 0, s>>>(X64, V32, nn);
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
 
 }  // namespace
 

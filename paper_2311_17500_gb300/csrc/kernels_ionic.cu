@@ -406,6 +406,25 @@ __global__ void wupdate_kernel(double *__restrict__ w, const double *__restrict_
   }
 }
 
+// band64[m][q] += sum_r Tr[r][m] Cq[r][q] (the SU ranks of Eq. tildeS added to
+// the reaction band), and the FP32 copy band32 = band64, in one pass.
+template <int RMAX>
+__global__ void su_band_update_kernel(double *__restrict__ band64, float *__restrict__ band32,
+                                      const double *__restrict__ Tr, const double *__restrict__ Cq, int R,
+                                      long long Mrows, long long Qs) {
+  long long total = Mrows * Qs;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    long long m = idx / Qs, q = idx - m * Qs;
+    double v = band64[idx];
+#pragma unroll
+    for (int r = 0; r < RMAX; ++r)
+      if (r < R) v += Tr[(long long)r * Mrows + m] * Cq[(long long)r * Qs + q];
+    band64[idx] = v;
+    band32[idx] = (float)v;
+  }
+}
+
 __global__ void zero_ull_kernel(unsigned long long *p, long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
@@ -586,7 +605,10 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
 }
 
 st_status su_band_add(st_handle *h) {
-  if (h->desc.stabilization != ST_SU || h->rank == 0) return ST_OK;
+  if (h->desc.stabilization != ST_SU || h->rank == 0) {
+    launch_band_to_f32(h->stream, h->band32, h->band64, (long long)(h->p + 1) * h->NtQs);
+    return ST_OK;
+  }
   cudaStream_t s = h->stream;
   int R = h->rank, p = h->p;
   st_count_launch(); theta_t_kernel<<<grid_for((long long)h->Qt * R), 256, 0, s>>>(h->th_t, h->Ur, R, h->Qt, h->hat_i_t, h->hat_l_t);
@@ -601,9 +623,17 @@ st_status su_band_add(st_handle *h) {
     hat.n[l] = h->n[l];
   }
   st_count_launch(); su_space_coef_kernel<<<grid_for(h->Qs * R), 256, 0, s>>>(Cq, h->Vr, h->sr, geom(h), hat, h->desc.C_m, R, h->Qs);
-  // band[(k,it)][q] += sum_r Tr[r][(k,it)] Cq[r][q]
+  // band[(k,it)][q] += sum_r Tr[r][(k,it)] Cq[r][q], and the FP32 copy
   int Mrows = (p + 1) * h->Nt;
-  launch_gemm64(s, h->band64, h->Tr, Cq, Mrows, (int)h->Qs, R, 1, Mrows, h->Qs, 1, h->Qs, 1, 1.0, 1.0);
+  long long total = (long long)Mrows * h->Qs;
+  if (R <= 8) {
+    st_count_launch(); su_band_update_kernel<8><<<grid_for(total), 256, 0, s>>>(h->band64, h->band32, h->Tr, Cq, R, Mrows, h->Qs);
+  } else if (R <= 16) {
+    st_count_launch(); su_band_update_kernel<16><<<grid_for(total), 256, 0, s>>>(h->band64, h->band32, h->Tr, Cq, R, Mrows, h->Qs);
+  } else {
+    launch_gemm64(s, h->band64, h->Tr, Cq, Mrows, (int)h->Qs, R, 1, Mrows, h->Qs, 1, h->Qs, 1, 1.0, 1.0);
+    launch_band_to_f32(s, h->band32, h->band64, total);
+  }
   ST_CUDA(cudaGetLastError());
   return ST_OK;
 }

@@ -17,6 +17,46 @@ inline int grid_for(long long total, int threads = kThreads) {
   return (int)g;
 }
 
+// Division by a fixed d of 32-bit unsigned x < 2^31 as a multiply and a shift:
+// with s = ceil(log2 d) and m = floor(2^(32+s) / d) + 1, floor(x m / 2^(32+s))
+// equals floor(x / d) because m d - 2^(32+s) lies in (0, d].
+struct FastDiv {
+  unsigned d;
+  int s;
+  unsigned long long m;
+  FastDiv() : d(1), s(0), m((1ull << 32) + 1) {}
+  explicit FastDiv(long long dd) {
+    d = (unsigned)dd;
+    s = 0;
+    while ((1ull << s) < d) ++s;
+    m = ((1ull << (32 + s)) / d) + 1;
+  }
+  __device__ __forceinline__ unsigned div(unsigned x) const {
+    return (unsigned)(((unsigned long long)x * m) >> (32 + s));
+  }
+};
+
+// idx = (o * n + i) * inner + c  ->  (o, i, c)
+struct Split3 {
+  FastDiv inner, n;
+  Split3(long long ninner, long long nn) : inner(ninner), n(nn) {}
+  __device__ __forceinline__ void operator()(long long idx, long long &o, int &i, long long &c, bool small) const {
+    if (small) {
+      unsigned x = (unsigned)idx;
+      unsigned r = inner.div(x);
+      c = x - r * inner.d;
+      unsigned oo = n.div(r);
+      i = (int)(r - oo * n.d);
+      o = oo;
+    } else {
+      c = idx % (long long)inner.d;
+      long long r = idx / (long long)inner.d;
+      i = (int)(r % (long long)n.d);
+      o = r / (long long)n.d;
+    }
+  }
+};
+
 template <typename T>
 struct BandTerms {
   const T *band[3];
@@ -28,24 +68,29 @@ struct BandTerms {
 // out[o][i][c] (+)= sum_t coef_t sum_k band_t[i][k] in_t[o][i-p+k][c]
 // (banded 1D matrix n x (2p+1) applied along one axis: the Kronecker factors
 // of W_t (x) M_s + M_t (x) K_s, Sec. 3.1).
-template <typename T>
+template <typename T, int P>
 __global__ void band_pass_kernel(T *__restrict__ out, BandTerms<T> bt, int n, long long inner,
-                                 long long outer, int p, int accumulate) {
-  const int B = 2 * p + 1;
+                                 long long outer, int accumulate, Split3 sp) {
+  constexpr int p = P, B = 2 * P + 1;
   long long total = outer * n * inner;
+  const bool small = total < (1ll << 31);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    long long c = idx % inner;
-    long long r = idx / inner;
-    int i = (int)(r % n);
-    long long o = r / n;
+    long long c, o;
+    int i;
+    sp(idx, o, i, c, small);
     T acc = accumulate ? out[idx] : T(0);
     int k0 = max(0, p - i), k1 = min(B - 1, n - 1 - i + p);
     for (int t = 0; t < bt.nterms; ++t) {
       const T *bd = bt.band[t] + (size_t)i * B;
       const T *src = bt.in[t] + (o * n + (i - p)) * inner + c;
       T s = T(0);
-      for (int k = k0; k <= k1; ++k) s += __ldg(bd + k) * src[(long long)k * inner];
+      if (k0 == 0 && k1 == B - 1) {
+#pragma unroll
+        for (int k = 0; k < B; ++k) s += __ldg(bd + k) * src[(long long)k * inner];
+      } else {
+        for (int k = k0; k <= k1; ++k) s += __ldg(bd + k) * src[(long long)k * inner];
+      }
       acc += bt.coef[t] * s;
     }
     out[idx] = acc;
@@ -54,21 +99,23 @@ __global__ void band_pass_kernel(T *__restrict__ out, BandTerms<T> bt, int n, lo
 
 // Coefficients -> Gauss points along one axis (sum factorization, Sec. 3.1):
 // out[o][e*nq+q][c] = sum_a tab[e][q][a] in[o][e+a][c].
-template <typename T>
+template <typename T, int P>
 __global__ void interp_fwd_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab,
-                                  int nel, int p, int nq, long long inner, long long outer) {
+                                  int nel, long long inner, long long outer, Split3 sp) {
+  constexpr int p = P, nq = P + 1;
   int nout = nel * nq, nin = nel + p;
   long long total = outer * nout * inner;
+  const bool small = total < (1ll << 31);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    long long c = idx % inner;
-    long long r = idx / inner;
-    int eq = (int)(r % nout);
-    long long o = r / nout;
+    long long c, o;
+    int eq;
+    sp(idx, o, eq, c, small);
     int e = eq / nq;
     const T *tb = tab + (size_t)eq * (p + 1);
     const T *src = in + (o * nin + e) * inner + c;
     T s = T(0);
+#pragma unroll
     for (int a = 0; a <= p; ++a) s += __ldg(tb + a) * src[(long long)a * inner];
     out[idx] = s;
   }
@@ -76,22 +123,26 @@ __global__ void interp_fwd_kernel(T *__restrict__ out, const T *__restrict__ in,
 
 // Gauss points -> coefficients (transpose of interp_fwd):
 // out[o][i][c] (+)= sum_{e=i-p..i} sum_q tab[e][q][i-e] in[o][e*nq+q][c].
-template <typename T>
+template <typename T, int P>
 __global__ void interp_bwd_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab,
-                                  int nel, int p, int nq, long long inner, long long outer, int accumulate) {
+                                  int nel, long long inner, long long outer, int accumulate, Split3 sp) {
+  constexpr int p = P, nq = P + 1;
   int nin = nel * nq, nout = nel + p;
   long long total = outer * nout * inner;
+  const bool small = total < (1ll << 31);
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    long long c = idx % inner;
-    long long r = idx / inner;
-    int i = (int)(r % nout);
-    long long o = r / nout;
+    long long c, o;
+    int i;
+    sp(idx, o, i, c, small);
     T s = T(0);
-    int e0 = max(0, i - p), e1 = min(nel - 1, i);
-    for (int e = e0; e <= e1; ++e) {
+#pragma unroll
+    for (int a = 0; a <= p; ++a) {
+      int e = i - a;
+      if (e < 0 || e >= nel) continue;
       const T *src = in + (o * nin + (long long)e * nq) * inner + c;
-      const T *tb = tab + (size_t)e * nq * (p + 1) + (i - e);
+      const T *tb = tab + (size_t)e * nq * (p + 1) + a;
+#pragma unroll
       for (int q = 0; q < nq; ++q) s += __ldg(tb + q * (p + 1)) * src[(long long)q * inner];
     }
     out[idx] = accumulate ? out[idx] + s : s;
@@ -219,32 +270,61 @@ __global__ void tline_lu_kernel(T *__restrict__ z, const T *__restrict__ r, cons
   long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (j >= Ns) return;
   constexpr int B = 2 * P + 1;
+  constexpr int U = 8;     // time steps whose operands are loaded ahead of the recurrence
   T yw[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) yw[k] = T(0);
-  for (int it = 0; it < Nt; ++it) {
-    T s = r[(long long)it * Ns + j];
+  // forward substitution with the unit lower factor
+  for (int it0 = 0; it0 < Nt; it0 += U) {
+    T rv[U], lv[U][P];
 #pragma unroll
-    for (int k = 1; k <= P; ++k)
-      if (it - k >= 0) s -= lu[((long long)it * B + (P - k)) * Ns + j] * yw[P - k];
+    for (int u = 0; u < U; ++u) {
+      int it = it0 + u;
+      bool ok = it < Nt;
+      rv[u] = ok ? r[(long long)it * Ns + j] : T(0);
 #pragma unroll
-    for (int k = 0; k < P - 1; ++k) yw[k] = yw[k + 1];
-    yw[P - 1] = s;
-    z[(long long)it * Ns + j] = s;
+      for (int k = 1; k <= P; ++k) lv[u][k - 1] = (ok && it - k >= 0) ? lu[((long long)it * B + (P - k)) * Ns + j] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int it = it0 + u;
+      if (it >= Nt) break;
+      T s = rv[u];
+#pragma unroll
+      for (int k = 1; k <= P; ++k) s -= lv[u][k - 1] * yw[P - k];
+#pragma unroll
+      for (int k = 0; k < P - 1; ++k) yw[k] = yw[k + 1];
+      yw[P - 1] = s;
+      z[(long long)it * Ns + j] = s;
+    }
   }
+  // backward substitution with the upper factor (1/u_ii stored on the diagonal)
   T zw[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) zw[k] = T(0);
-  for (int it = Nt - 1; it >= 0; --it) {
-    T s = z[(long long)it * Ns + j];
+  for (int it0 = Nt - 1; it0 >= 0; it0 -= U) {
+    T yv[U], uv[U][P + 1];
 #pragma unroll
-    for (int k = 1; k <= P; ++k)
-      if (it + k < Nt) s -= lu[((long long)it * B + (P + k)) * Ns + j] * zw[k - 1];
-    s *= lu[((long long)it * B + P) * Ns + j];
+    for (int u = 0; u < U; ++u) {
+      int it = it0 - u;
+      bool ok = it >= 0;
+      yv[u] = ok ? z[(long long)it * Ns + j] : T(0);
 #pragma unroll
-    for (int k = P - 1; k > 0; --k) zw[k] = zw[k - 1];
-    zw[0] = s;
-    z[(long long)it * Ns + j] = s;
+      for (int k = 0; k <= P; ++k) uv[u][k] = (ok && it + k < Nt) ? lu[((long long)it * B + (P + k)) * Ns + j] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      int it = it0 - u;
+      if (it < 0) break;
+      T s = yv[u];
+#pragma unroll
+      for (int k = 1; k <= P; ++k) s -= uv[u][k] * zw[k - 1];
+      s *= uv[u][0];
+#pragma unroll
+      for (int k = P - 1; k > 0; --k) zw[k] = zw[k - 1];
+      zw[0] = s;
+      z[(long long)it * Ns + j] = s;
+    }
   }
 }
 
@@ -252,65 +332,153 @@ template <typename T> struct Acc;
 template <> struct Acc<float> { typedef float type; };
 template <> struct Acc<double> { typedef double type; };
 
-// Partial inner products <V_i, w> for i < nv: each thread accumulates its
-// elements in the storage precision (FP32 for FP32 vectors: short chains of at
-// most `per_thread` products), then the partial is widened to FP64 and reduced
-// by warp shuffles and shared memory in a fixed order; scratch[block][i].
+// 16-byte vector type of the Krylov kernels
+template <typename T> struct V16;
+template <> struct V16<float> {
+  typedef float4 type;
+  static constexpr int W = 4;
+  __device__ static float dot(const float4 &a, const float4 &b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+  __device__ static float4 fma(float h, const float4 &v, float4 acc) {
+    acc.x += h * v.x; acc.y += h * v.y; acc.z += h * v.z; acc.w += h * v.w; return acc;
+  }
+  __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  __device__ static float4 upd(const float4 &w, const float4 &a, float s) {
+    return make_float4((w.x - a.x) * s, (w.y - a.y) * s, (w.z - a.z) * s, (w.w - a.w) * s);
+  }
+};
+template <> struct V16<double> {
+  typedef double2 type;
+  static constexpr int W = 2;
+  __device__ static double dot(const double2 &a, const double2 &b) { return a.x * b.x + a.y * b.y; }
+  __device__ static double2 fma(double h, const double2 &v, double2 acc) {
+    acc.x += h * v.x; acc.y += h * v.y; return acc;
+  }
+  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __device__ static double2 upd(const double2 &w, const double2 &a, double s) {
+    return make_double2((w.x - a.x) * s, (w.y - a.y) * s);
+  }
+};
+
+// Partial inner products <V_i, w>, i in [G*blockIdx.y, G*blockIdx.y + G) ∩ [0, nv),
+// over the block's contiguous chunk of elements: 16-byte loads of G basis
+// vectors per step, accumulation in the storage precision over short chains
+// (8 steps), widened to FP64 and reduced in a fixed order by warp shuffles and
+// shared memory; partial[i][block].  V rows (stride ldv) and w are 16-byte aligned.
+// Compensated (Kahan) accumulation in the storage precision: FP32 vectors
+// get close to FP64-accurate sums without FP64 instructions in the loop.
 template <typename T>
-__global__ void multi_dot_kernel(double *__restrict__ scratch, const T *__restrict__ V, long long ldv, int nv,
-                                 const T *__restrict__ w, long long n) {
-  __shared__ double red[32][8];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  long long chunk = (n + gridDim.x - 1) / gridDim.x;
-  long long beg = (long long)blockIdx.x * chunk, end = min(n, beg + chunk);
-  for (int i0 = 0; i0 < nv; i0 += 32) {
-    int cnt = min(32, nv - i0);
-    for (int ii = 0; ii < cnt; ++ii) {
-      const T *v = V + (long long)(i0 + ii) * ldv;
-      double tot = 0.0;
-      typename Acc<T>::type s = 0;
-      int c = 0;
-      for (long long e = beg + threadIdx.x; e < end; e += blockDim.x) {
-        s += v[e] * w[e];
-        if (++c == 16) { tot += (double)s; s = 0; c = 0; }
-      }
-      tot += (double)s;
+struct KahanAcc {
+  T s, c;
+  __device__ __forceinline__ void zero() { s = T(0); c = T(0); }
+  __device__ __forceinline__ void add(T x) {
+    T y = x - c;
+    T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Partial inner products <V_i, w>, i in [G*blockIdx.y, G*blockIdx.y + G) ∩ [0, nv),
+// over the block's contiguous chunk of elements: 16-byte loads of G basis
+// vectors per step, compensated accumulation per thread, FP64 block reduction
+// in a fixed order (warp shuffles, shared memory); partial[i][block].
+// V rows (stride ldv) and w are 16-byte aligned.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) mdot_kernel(double *__restrict__ partial, const T *__restrict__ V,
+                                                   long long ldv, int nv, const T *__restrict__ w, long long n) {
+  typedef V16<T> X;
+  typedef typename X::type VT;
+  constexpr int W = X::W;
+  __shared__ double red[G][8];
+  const int i0 = blockIdx.y * G;
+  const int cnt = min(G, nv - i0);
+  const long long nvec = n / W;
+  const long long chunk = (nvec + gridDim.x - 1) / gridDim.x;
+  const long long beg = (long long)blockIdx.x * chunk, end = min(nvec, beg + chunk);
+  KahanAcc<T> acc[G];
 #pragma unroll
-      for (int off = 16; off > 0; off >>= 1) tot += __shfl_down_sync(0xffffffffu, tot, off);
-      if (lane == 0) red[ii][warp] = tot;
-    }
-    __syncthreads();
-    if (threadIdx.x < cnt) {
-      double t = 0.0;
-      for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += red[threadIdx.x][wi];
-      scratch[(long long)blockIdx.x * nv + i0 + threadIdx.x] = t;
-    }
-    __syncthreads();
+  for (int g = 0; g < G; ++g) acc[g].zero();
+  const VT *wv = reinterpret_cast<const VT *>(w);
+  for (long long e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    VT x = wv[e];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (g < cnt) acc[g].add(X::dot(reinterpret_cast<const VT *>(V + (long long)(i0 + g) * ldv)[e], x));
+  }
+  if (blockIdx.x == gridDim.x - 1)
+    for (long long e = nvec * W + threadIdx.x; e < n; e += blockDim.x)
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (g < cnt) acc[g].add(V[(long long)(i0 + g) * ldv + e] * w[e]);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    if (g >= cnt) break;
+    double t = acc[g].value();
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    if (lane == 0) red[g][warp] = t;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < cnt) {
+    double t = 0.0;
+    for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += red[threadIdx.x][wi];
+    partial[(long long)(i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
   }
 }
 
-__global__ void reduce_blocks_kernel(double *__restrict__ out, const double *__restrict__ scratch, int nblocks,
+__global__ void reduce_blocks_kernel(double *__restrict__ out, const double *__restrict__ partial, int nblocks,
                                      int nv) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nv) return;
   double t = 0.0;
-  for (int b = 0; b < nblocks; ++b) t += scratch[(long long)b * nv + i];
+  const double *p = partial + (long long)i * nblocks;
+  for (int b = 0; b < nblocks; ++b) t += p[b];
   out[i] = t;
 }
 
-// w -= sum_i h_i V_i (classical Gram-Schmidt update).
+// w <- (w - sum_{i<nv} h_i V_i) * s, with s = 1 or, when nrm is given,
+// s = 1 / sqrt(nrm[0] - sum h_i^2): the norm of the updated vector by
+// Pythagoras from <w, w> and the projection coefficients (classical
+// Gram-Schmidt update fused with the normalization).  16-byte aligned rows.
 template <typename T>
-__global__ void multi_axpy_kernel(T *__restrict__ w, const T *__restrict__ V, long long ldv, int nv,
-                                  const double *__restrict__ h, long long n) {
+__global__ void __launch_bounds__(256) maxpy_kernel(T *__restrict__ w, const T *__restrict__ V, long long ldv,
+                                                    int nv, const double *__restrict__ h, long long n,
+                                                    const double *__restrict__ nrm) {
+  typedef V16<T> X;
+  typedef typename X::type VT;
+  constexpr int W = X::W;
   __shared__ T hs[512];
+  __shared__ double sc;
   for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = (T)h[i];
-  __syncthreads();
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x) {
-    T s = T(0);
-    for (int i = 0; i < nv; ++i) s += hs[i] * V[(long long)i * ldv + e];
-    w[e] -= s;
+  if (threadIdx.x == 0) {
+    double s = 1.0;
+    if (nrm) {
+      double q = nrm[0];
+      for (int i = 0; i < nv; ++i) q -= h[i] * h[i];
+      q = q > 0.0 ? sqrt(q) : 0.0;
+      s = q > 0.0 ? 1.0 / q : 0.0;
+    }
+    sc = s;
   }
+  __syncthreads();
+  const T s = (T)sc;
+  const long long nvec = n / W;
+  VT *wv = reinterpret_cast<VT *>(w);
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nvec;
+       e += (long long)gridDim.x * blockDim.x) {
+    VT a = X::zero();
+#pragma unroll 8
+    for (int i = 0; i < nv; ++i) a = X::fma(hs[i], reinterpret_cast<const VT *>(V + (long long)i * ldv)[e], a);
+    wv[e] = X::upd(wv[e], a, s);
+  }
+  if (blockIdx.x == 0)
+    for (long long e = nvec * W + threadIdx.x; e < n; e += blockDim.x) {
+      T a = T(0);
+      for (int i = 0; i < nv; ++i) a += hs[i] * V[(long long)i * ldv + e];
+      w[e] = (w[e] - a) * s;
+    }
 }
 
 template <typename T>
@@ -383,7 +551,7 @@ __global__ void to_f32_kernel(float *__restrict__ y, const double *__restrict__ 
     y[e] = (float)x[e];
 }
 
-constexpr int kDotBlocks = 304;
+constexpr int kDotBlocks = 608;
 
 }  // namespace
 
@@ -399,22 +567,47 @@ void launch_band_pass(cudaStream_t s, T *out, int nterms, const T *const *bands,
     bt.coef[t] = t < nterms ? (T)coefs[t] : T(0);
   }
   long long total = outer * n * inner;
-  st_count_launch(); band_pass_kernel<T><<<grid_for(total), kThreads, 0, s>>>(out, bt, n, inner, outer, p, accumulate ? 1 : 0);
+  int acc = accumulate ? 1 : 0;
+  Split3 sp(inner, n);
+  int g = grid_for(total);
+  st_count_launch();
+  switch (p) {
+    case 1: band_pass_kernel<T, 1><<<g, kThreads, 0, s>>>(out, bt, n, inner, outer, acc, sp); break;
+    case 2: band_pass_kernel<T, 2><<<g, kThreads, 0, s>>>(out, bt, n, inner, outer, acc, sp); break;
+    case 3: band_pass_kernel<T, 3><<<g, kThreads, 0, s>>>(out, bt, n, inner, outer, acc, sp); break;
+    default: band_pass_kernel<T, 4><<<g, kThreads, 0, s>>>(out, bt, n, inner, outer, acc, sp); break;
+  }
 }
 
 template <typename T>
 void launch_interp_fwd(cudaStream_t s, T *out, const T *in, const T *tab, int nel, int p, int nq,
                        long long inner, long long outer) {
   long long total = outer * (long long)nel * nq * inner;
-  st_count_launch(); interp_fwd_kernel<T><<<grid_for(total), kThreads, 0, s>>>(out, in, tab, nel, p, nq, inner, outer);
+  Split3 sp(inner, (long long)nel * nq);
+  int g = grid_for(total);
+  st_count_launch();
+  switch (p) {
+    case 1: interp_fwd_kernel<T, 1><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, sp); break;
+    case 2: interp_fwd_kernel<T, 2><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, sp); break;
+    case 3: interp_fwd_kernel<T, 3><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, sp); break;
+    default: interp_fwd_kernel<T, 4><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, sp); break;
+  }
 }
 
 template <typename T>
 void launch_interp_bwd(cudaStream_t s, T *out, const T *in, const T *tab, int nel, int p, int nq,
                        long long inner, long long outer, bool accumulate) {
   long long total = outer * (long long)(nel + p) * inner;
-  st_count_launch(); interp_bwd_kernel<T><<<grid_for(total), kThreads, 0, s>>>(out, in, tab, nel, p, nq, inner, outer,
-                                                            accumulate ? 1 : 0);
+  Split3 sp(inner, nel + p);
+  int acc = accumulate ? 1 : 0;
+  int g = grid_for(total);
+  st_count_launch();
+  switch (p) {
+    case 1: interp_bwd_kernel<T, 1><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, acc, sp); break;
+    case 2: interp_bwd_kernel<T, 2><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, acc, sp); break;
+    case 3: interp_bwd_kernel<T, 3><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, acc, sp); break;
+    default: interp_bwd_kernel<T, 4><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, acc, sp); break;
+  }
 }
 
 template <typename T>
@@ -475,14 +668,18 @@ void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt
 template <typename T>
 void launch_multi_dot(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *w, long long n,
                       double *scratch) {
-  int blocks = (int)std::min<long long>(kDotBlocks, std::max<long long>(1, (n + 1023) / 1024));
-  st_count_launch(); multi_dot_kernel<T><<<blocks, 256, 0, s>>>(scratch, V, ldv, nv, w, n);
-  st_count_launch(); reduce_blocks_kernel<<<(nv + 127) / 128, 128, 0, s>>>(out, scratch, blocks, nv);
+  constexpr int G = 8;
+  int bx = (int)std::min<long long>(kDotBlocks, std::max<long long>(1, (n + 2047) / 2048));
+  dim3 grid(bx, (nv + G - 1) / G);
+  st_count_launch(); mdot_kernel<T, G><<<grid, 256, 0, s>>>(scratch, V, ldv, nv, w, n);
+  st_count_launch(); reduce_blocks_kernel<<<(nv + 127) / 128, 128, 0, s>>>(out, scratch, bx, nv);
 }
 
 template <typename T>
-void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, const double *h, long long n) {
-  st_count_launch(); multi_axpy_kernel<T><<<grid_for(n), kThreads, 0, s>>>(w, V, ldv, nv, h, n);
+void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, const double *h, long long n,
+                       const double *nrm) {
+  long long nvec = n / V16<T>::W;
+  st_count_launch(); maxpy_kernel<T><<<grid_for(std::max<long long>(nvec, 1)), kThreads, 0, s>>>(w, V, ldv, nv, h, n, nrm);
 }
 
 template <typename T>
@@ -536,7 +733,7 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
   template void launch_multi_dot<T>(cudaStream_t, double *, const T *, long long, int, const T *,      \
                                     long long, double *);                                             \
   template void launch_multi_axpy<T>(cudaStream_t, T *, const T *, long long, int, const double *,     \
-                                     long long);                                                      \
+                                     long long, const double *);                                      \
   template void launch_scale_copy<T>(cudaStream_t, T *, const T *, double, long long);
 INST(float)
 INST(double)

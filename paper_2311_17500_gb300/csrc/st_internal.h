@@ -104,6 +104,7 @@ struct st_handle {
   double *red_host = nullptr;  // pinned host mirror
   // Krylov
   int m = 0;
+  long long ldv = 0;          // Krylov basis leading dimension (16-byte aligned rows)
   double *V64 = nullptr; float *V32 = nullptr;
   double *r64 = nullptr, *x64 = nullptr, *t64a = nullptr, *t64b = nullptr;
   double *z64 = nullptr, *b64 = nullptr;   // GMRES preconditioner output, Newton right-hand side
@@ -175,7 +176,7 @@ void launch_multi_dot(cudaStream_t s, double *out, const T *V, long long ldv, in
                       long long n, double *scratch);
 template <typename T>
 void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, const double *h,
-                       long long n);
+                       long long n, const double *nrm = nullptr);
 template <typename T>
 void launch_scale_copy(cudaStream_t s, T *y, const T *x, double alpha, long long n);
 void launch_axpby64(cudaStream_t s, double *y, const double *x, double a, double b, long long n);
