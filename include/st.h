@@ -71,8 +71,8 @@ typedef struct {
 typedef struct {
   int d;                 /* spatial dimension, 1..3 */
   int p;                 /* spline degree in space and time, 1..4 (p_s = p_t, Sec. 4) */
-  int n_el[3];           /* elements per spatial direction (unit interval, uniform) */
-  int n_el_t;            /* time elements on [0, T] (uniform) */
+  int n_el[3];           /* elements per spatial direction (unit interval, uniform), 1..1024 */
+  int n_el_t;            /* time elements on [0, T] (uniform), 1..60000 */
   double T, C_m, D[3];   /* final time, membrane capacitance, diagonal conductivity */
   double a, b, c1, c2, d_e;   /* Rogers-McCulloch constants */
   int source_kind;       /* ST_SRC_* */

@@ -9,7 +9,7 @@
 
 void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, int M, int N, int K,
                    long long sam, long long sak, long long sbk, long long sbc, long long scm, long long scc,
-                   double alpha, double beta);
+                   double alpha, double beta, double *work = nullptr, long long work_elems = 0);
 
 namespace {
 
@@ -26,8 +26,8 @@ st_status validate(const st_problem_desc *d) {
   if (!d) return ST_ERR_ARG;
   if (d->d < 1 || d->d > 3 || d->p < 1 || d->p > ST_MAXP) return ST_ERR_ARG;
   for (int l = 0; l < d->d; ++l)
-    if (d->n_el[l] < 1 || d->n_el[l] > (1 << 16) || !(d->D[l] > 0)) return ST_ERR_ARG;
-  if (d->n_el_t < 1 || d->n_el_t > (1 << 16)) return ST_ERR_ARG;
+    if (d->n_el[l] < 1 || d->n_el[l] > 1024 || !(d->D[l] > 0)) return ST_ERR_ARG;
+  if (d->n_el_t < 1 || d->n_el_t > 60000) return ST_ERR_ARG;
   if (!(d->T > 0) || !(d->C_m > 0)) return ST_ERR_ARG;
   if (d->source_kind < ST_SRC_ZERO || d->source_kind > ST_SRC_E1_MMS) return ST_ERR_ARG;
   if (d->source_kind == ST_SRC_E1_MMS && d->d != 1) return ST_ERR_ARG;
@@ -531,6 +531,20 @@ static st_status setup_impl(st_handle *h) {
   ST_TRY(upload<float>(h, &h->Mtb32, hs.Mt));
   ST_TRY(upload<float>(h, &h->Wtb32, hs.Wt));
   ST_TRY(upload<double>(h, &h->bt, hs.tdir.tab));
+  {
+    // products w_t b_i b_{i+k} at the time Gauss points for the reaction bands
+    const Dir1D &td = hs.tdir;
+    int np = (h->p + 1) * (h->p + 2) / 2;
+    std::vector<double> bp((size_t)td.n_el * td.nq * np);
+    for (int e = 0; e < td.n_el; ++e)
+      for (int q = 0; q < td.nq; ++q) {
+        int pr = 0;
+        for (int i = 0; i <= h->p; ++i)
+          for (int k = 0; k <= h->p - i; ++k)
+            bp[((size_t)e * td.nq + q) * np + pr++] = td.wq[e * td.nq + q] * td.at(0, e, q, i) * td.at(0, e, q, i + k);
+      }
+    ST_TRY(upload<double>(h, &h->bprod, bp));
+  }
   ST_TRY(upload<double>(h, &h->wt, hs.tdir.wq));
   ST_TRY(upload<double>(h, &h->xt, hs.tdir.xq));
   ST_TRY(upload<double>(h, &h->tauq, hs.tau_q));

@@ -23,7 +23,7 @@ namespace cg = cooperative_groups;
 
 void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, int M, int N, int K,
                    long long sam, long long sak, long long sbk, long long sbc, long long scm, long long scc,
-                   double alpha, double beta);
+                   double alpha, double beta, double *work = nullptr, long long work_elems = 0);
 
 namespace {
 

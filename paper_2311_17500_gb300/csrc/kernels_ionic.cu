@@ -6,7 +6,7 @@
 
 void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, int M, int N, int K,
                    long long sam, long long sak, long long sbk, long long sbc, long long scm, long long scc,
-                   double alpha, double beta);
+                   double alpha, double beta, double *work = nullptr, long long work_elems = 0);
 
 namespace {
 
@@ -89,32 +89,50 @@ struct IonicArgs {
   st_problem_desc D;
   GeomArgs g;
   const double *U0, *L0, *W0;   // [Nt][Qs]: u, sum D_l d_ll u, w at spatial Gauss points
-  const double *bt, *wt, *xt;   // time tables
+  const double *bt, *xt;        // time tables: values/derivatives, points
+  const double *bprod;          // [e][qt][pair]: w_t b_i b_{i+k} for the band pairs (i, k), k <= P - i
   int Nt, nel_t;
   long long Qs, Nel_s;
   int kind;                     // ST_PICARD: C_r, ST_NEWTON: C_J
   int want_stats;
   double *band;                 // [k][it][q]
   unsigned long long *emax;     // [et][es]
-  unsigned long long *stats;    // max|u|, max|d_t u|, max|R|
+  unsigned long long *stats;    // max|u|, max|d_t u|, max|R| (bit patterns)
 };
+
+// |v| as the bit pattern of a non-negative double: the unsigned order of these
+// patterns is the order of the values (NaN above +inf), so maxima are
+// integer operations.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
 
 // One thread per spatial Gauss point sweeps the time elements: evaluates u,
 // d_t u, the Laplacian and w at the time Gauss points from the time
-// coefficients, forms the residual R (Eq. theta_ce_u numerator) and the
-// reaction coefficient, keeps max |R| per space-time element, and assembles
-// the time band sum_qt w C b_i b_j of the reaction mass term at this spatial
-// point (multiplied by its spatial weight).  Rows are written once complete.
+// coefficients, forms the residual R = C_m d_t u - lap + C_r u - f (Eq.
+// theta_ce_u numerator, with the ionic current written as C_r u) and the
+// linearization coefficient (C_r of Eq. reaction, or its u-derivative for
+// Newton), keeps max |R| per space-time element, and assembles the time band
+// sum_qt w_t C b_i b_j of the reaction mass term at this spatial point
+// (times its spatial weight).  Rows are written once complete.
 template <int P>
-__global__ void ionic_tline_kernel(IonicArgs a) {
+__global__ void __launch_bounds__(128) ionic_tline_kernel(IonicArgs a) {
+  constexpr int nq = P + 1, NPAIR = (P + 1) * (P + 2) / 2;
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  __shared__ double red[3][32];
-  double mu = 0.0, mut = 0.0, mr = 0.0;
+  __shared__ unsigned long long red[3][4];
+  unsigned long long mu = 0, mut = 0, mr = 0;
   if (q < a.Qs) {
-    const int nq = P + 1;
-    const double *D1 = a.D.D;
-    (void)D1;
     SpatialPoint sp = spatial_point(a.g, q);
+    // stimulus boxes containing this point (the spatial factor of f)
+    unsigned inbox = 0;
+    const bool stim = a.D.source_kind == ST_SRC_STIM;
+    if (stim)
+      for (int b = 0; b < a.D.n_stim; ++b) {
+        bool in = true;
+        for (int l = 0; l < a.D.d; ++l) in = in && (sp.x[l] >= a.D.stim[b].lo[l]) && (sp.x[l] <= a.D.stim[b].hi[l]);
+        if (in) inbox |= 1u << b;
+      }
+    const double c1 = a.D.c1, c2 = a.D.c2, aa = a.D.a, Cm = a.D.C_m, apl = 1.0 + aa;
     const long long plane = (long long)a.Nt * a.Qs;
     double acc[P + 1][P + 1];
 #pragma unroll
@@ -132,38 +150,48 @@ __global__ void ionic_tline_kernel(IonicArgs a) {
         cl[j] = ok ? a.L0[off] : 0.0;
         cw[j] = ok ? a.W0[off] : 0.0;
       }
-      double rloc = 0.0;
+      unsigned long long rloc = 0;
+#pragma unroll
       for (int qt = 0; qt < nq; ++qt) {
         const double *b0 = a.bt + ((size_t)(0 * a.nel_t + e) * nq + qt) * (P + 1);
         const double *b1 = a.bt + ((size_t)(1 * a.nel_t + e) * nq + qt) * (P + 1);
         double u = 0.0, ut = 0.0, lap = 0.0, w = 0.0;
 #pragma unroll
         for (int j = 0; j <= P; ++j) {
-          u += b0[j] * cu[j];
-          ut += b1[j] * cu[j];
-          lap += b0[j] * cl[j];
-          w += b0[j] * cw[j];
+          double v0 = __ldg(b0 + j);
+          u = fma(v0, cu[j], u);
+          ut = fma(__ldg(b1 + j), cu[j], ut);
+          lap = fma(v0, cl[j], lap);
+          w = fma(v0, cw[j], w);
         }
         double t = a.xt[e * nq + qt];
-        double f = source_at(a.D, sp.x, t);
-        double R = a.D.C_m * ut - lap + a.D.c1 * u * (u - a.D.a) * (u - 1.0) + a.D.c2 * u * w - f;
-        double C;
-        if (a.kind == ST_NEWTON)
-          C = a.D.c1 * (3.0 * u * u - 2.0 * (1.0 + a.D.a) * u + a.D.a) + a.D.c2 * w;
-        else
-          C = a.D.c1 * (u - a.D.a) * (u - 1.0) + a.D.c2 * w;
-        double aR = fabs(R);
-        rloc = fmax(rloc, aR != aR ? INFINITY : aR);
-        mu = fmax(mu, fabs(u));
-        mut = fmax(mut, fabs(ut));
-        double wc = a.wt[e * nq + qt] * sp.ws * C;
+        double f = 0.0;
+        if (stim) {
+          for (int b = 0; b < a.D.n_stim; ++b)
+            if (((inbox >> b) & 1u) && t >= a.D.stim[b].t0 && t < a.D.stim[b].t1) f += a.D.stim[b].amp;
+        } else if (a.D.source_kind != ST_SRC_ZERO) {
+          f = source_at(a.D, sp.x, t);
+        }
+        // C_r = c1 (u - a)(u - 1) + c2 w = c1 ((u - (1 + a)) u + a) + c2 w
+        double Cr = fma(c1, fma(u - apl, u, aa), c2 * w);
+        double R = fma(Cr, u, fma(Cm, ut, -lap) - f);
+        double C = Cr;
+        if (a.kind == ST_NEWTON) C = fma(c1, fma(fma(3.0, u, -2.0 * apl), u, aa), c2 * w);
+        unsigned long long rb = abs_bits(R);
+        rloc = rloc > rb ? rloc : rb;
+        unsigned long long ub = abs_bits(u), utb = abs_bits(ut);
+        mu = mu > ub ? mu : ub;
+        mut = mut > utb ? mut : utb;
+        double wc = sp.ws * C;
+        const double *bp = a.bprod + ((size_t)e * nq + qt) * NPAIR;
+        int pr = 0;
 #pragma unroll
         for (int i = 0; i <= P; ++i)
 #pragma unroll
-          for (int k = 0; k <= P - i; ++k) acc[i][k] += wc * b0[i] * b0[i + k];
+          for (int k = 0; k <= P - i; ++k) { acc[i][k] = fma(wc, __ldg(bp + pr), acc[i][k]); ++pr; }
       }
-      mr = fmax(mr, rloc);
-      if (a.want_stats) atomic_max_pos(&a.emax[(long long)e * a.Nel_s + sp.es], rloc);
+      mr = mr > rloc ? mr : rloc;
+      if (a.want_stats) atomicMax(&a.emax[(long long)e * a.Nel_s + sp.es], rloc);
       // row e-1 is complete
       int row = e - 1;
       if (row >= 0)
@@ -186,20 +214,25 @@ __global__ void ionic_tline_kernel(IonicArgs a) {
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      mu = fmax(mu, __shfl_down_sync(0xffffffffu, mu, off));
-      mut = fmax(mut, __shfl_down_sync(0xffffffffu, mut, off));
-      mr = fmax(mr, __shfl_down_sync(0xffffffffu, mr, off));
+      unsigned long long o0 = __shfl_down_sync(0xffffffffu, mu, off);
+      unsigned long long o1 = __shfl_down_sync(0xffffffffu, mut, off);
+      unsigned long long o2 = __shfl_down_sync(0xffffffffu, mr, off);
+      mu = mu > o0 ? mu : o0;
+      mut = mut > o1 ? mut : o1;
+      mr = mr > o2 ? mr : o2;
     }
     if (lane == 0) { red[0][warp] = mu; red[1][warp] = mut; red[2][warp] = mr; }
     __syncthreads();
     if (threadIdx.x == 0) {
-      double m0 = 0, m1 = 0, m2 = 0;
+      unsigned long long m0 = 0, m1 = 0, m2 = 0;
       for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-        m0 = fmax(m0, red[0][i]); m1 = fmax(m1, red[1][i]); m2 = fmax(m2, red[2][i]);
+        m0 = m0 > red[0][i] ? m0 : red[0][i];
+        m1 = m1 > red[1][i] ? m1 : red[1][i];
+        m2 = m2 > red[2][i] ? m2 : red[2][i];
       }
-      atomic_max_pos(&a.stats[0], m0);
-      atomic_max_pos(&a.stats[1], m1);
-      atomic_max_pos(&a.stats[2], m2);
+      atomicMax(&a.stats[0], m0);
+      atomicMax(&a.stats[1], m1);
+      atomicMax(&a.stats[2], m2);
     }
   }
 }
@@ -500,7 +533,7 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   a.D = h->desc;
   a.g = geom(h);
   a.U0 = h->U0; a.L0 = h->L0; a.W0 = h->Wq0;
-  a.bt = h->bt; a.wt = h->wt; a.xt = h->xt;
+  a.bt = h->bt; a.xt = h->xt; a.bprod = h->bprod;
   a.Nt = h->Nt; a.nel_t = h->nel_t;
   a.Qs = h->Qs; a.Nel_s = h->Nel_s;
   a.kind = kind;
@@ -561,7 +594,8 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
   st_count_launch(); theta_kernel<<<grid_for(NtNs), 256, 0, s>>>(h->theta, cur, den, NtNs);
   // Gram matrix G = Theta Theta^T (N_t x N_t, FP64)
   int Nt = h->Nt;
-  launch_gemm64(s, h->gram, h->theta, h->theta, Nt, Nt, (int)h->Ns, h->Ns, 1, 1, h->Ns, Nt, 1, 1.0, 0.0);
+  launch_gemm64(s, h->gram, h->theta, h->theta, Nt, Nt, (int)h->Ns, h->Ns, 1, 1, h->Ns, Nt, 1, 1.0, 0.0,
+                h->W64[0], h->NtQs);
   std::vector<double> G((size_t)Nt * Nt);
   // trace = ||Theta||_F^2
   ST_CUDA(cudaMemcpyAsync(G.data(), h->gram, G.size() * sizeof(double), cudaMemcpyDeviceToHost, s));

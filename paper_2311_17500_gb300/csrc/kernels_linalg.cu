@@ -149,6 +149,568 @@ __global__ void interp_bwd_kernel(T *__restrict__ out, const T *__restrict__ in,
   }
 }
 
+// Division-free variants of the three axis passes.  "rows" kernels serve the
+// fastest axis (inner == 1): a thread per position along the axis, blockIdx.y
+// over the outer index.  "cols" kernels serve the other axes: a thread per
+// inner index c, blockIdx.y over the axis position, blockIdx.z over the outer
+// index.  Outer indices beyond the grid limit are covered by a stride loop.
+template <typename T, int P>
+__global__ void band_rows_kernel(T *__restrict__ out, BandTerms<T> bt, int n, long long outer, int accumulate) {
+  constexpr int B = 2 * P + 1;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int k0 = max(0, P - i), k1 = min(B - 1, n - 1 - i + P);
+  for (long long o = blockIdx.y; o < outer; o += gridDim.y) {
+    long long idx = o * n + i;
+    T acc = accumulate ? out[idx] : T(0);
+    for (int t = 0; t < bt.nterms; ++t) {
+      const T *bd = bt.band[t] + (size_t)i * B;
+      const T *src = bt.in[t] + o * n + (i - P);
+      T s = T(0);
+      for (int k = k0; k <= k1; ++k) s += __ldg(bd + k) * src[k];
+      acc += bt.coef[t] * s;
+    }
+    out[idx] = acc;
+  }
+}
+
+template <typename T, int P>
+__global__ void band_cols_kernel(T *__restrict__ out, BandTerms<T> bt, int n, long long inner, long long outer,
+                                 int accumulate) {
+  constexpr int B = 2 * P + 1;
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= inner) return;
+  const int i = blockIdx.y;
+  const int k0 = max(0, P - i), k1 = min(B - 1, n - 1 - i + P);
+  for (long long o = blockIdx.z; o < outer; o += gridDim.z) {
+    long long idx = (o * n + i) * inner + c;
+    T acc = accumulate ? out[idx] : T(0);
+    for (int t = 0; t < bt.nterms; ++t) {
+      const T *bd = bt.band[t] + (size_t)i * B;
+      const T *src = bt.in[t] + (o * n + (i - P)) * inner + c;
+      T s = T(0);
+      if (k0 == 0 && k1 == B - 1) {
+#pragma unroll
+        for (int k = 0; k < B; ++k) s += __ldg(bd + k) * src[(long long)k * inner];
+      } else {
+        for (int k = k0; k <= k1; ++k) s += __ldg(bd + k) * src[(long long)k * inner];
+      }
+      acc += bt.coef[t] * s;
+    }
+    out[idx] = acc;
+  }
+}
+
+template <typename T, int P>
+__global__ void ifwd_rows_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab, int nel,
+                                 long long outer) {
+  constexpr int nq = P + 1;
+  const int nout = nel * nq, nin = nel + P;
+  int eq = blockIdx.x * blockDim.x + threadIdx.x;
+  if (eq >= nout) return;
+  const int e = eq / nq;
+  T tb[P + 1];
+#pragma unroll
+  for (int a = 0; a <= P; ++a) tb[a] = __ldg(tab + (size_t)eq * (P + 1) + a);
+  for (long long o = blockIdx.y; o < outer; o += gridDim.y) {
+    const T *src = in + o * nin + e;
+    T s = T(0);
+#pragma unroll
+    for (int a = 0; a <= P; ++a) s += tb[a] * src[a];
+    out[o * nout + eq] = s;
+  }
+}
+
+template <typename T, int P>
+__global__ void ifwd_cols_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab, int nel,
+                                 long long inner, long long outer) {
+  constexpr int nq = P + 1;
+  const int nout = nel * nq, nin = nel + P;
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= inner) return;
+  const int eq = blockIdx.y, e = eq / nq;
+  T tb[P + 1];
+#pragma unroll
+  for (int a = 0; a <= P; ++a) tb[a] = __ldg(tab + (size_t)eq * (P + 1) + a);
+  for (long long o = blockIdx.z; o < outer; o += gridDim.z) {
+    const T *src = in + (o * nin + e) * inner + c;
+    T s = T(0);
+#pragma unroll
+    for (int a = 0; a <= P; ++a) s += tb[a] * src[(long long)a * inner];
+    out[(o * nout + eq) * inner + c] = s;
+  }
+}
+
+template <typename T, int P>
+__global__ void ibwd_rows_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab, int nel,
+                                 long long outer, int accumulate) {
+  constexpr int nq = P + 1;
+  const int nin = nel * nq, nout = nel + P;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nout) return;
+  for (long long o = blockIdx.y; o < outer; o += gridDim.y) {
+    T s = T(0);
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      int e = i - a;
+      if (e < 0 || e >= nel) continue;
+      const T *src = in + o * nin + (long long)e * nq;
+      const T *tb = tab + (size_t)e * nq * (P + 1) + a;
+#pragma unroll
+      for (int q = 0; q < nq; ++q) s += __ldg(tb + q * (P + 1)) * src[q];
+    }
+    long long idx = o * nout + i;
+    out[idx] = accumulate ? out[idx] + s : s;
+  }
+}
+
+template <typename T, int P>
+__global__ void ibwd_cols_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab, int nel,
+                                 long long inner, long long outer, int accumulate) {
+  constexpr int nq = P + 1;
+  const int nin = nel * nq, nout = nel + P;
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= inner) return;
+  const int i = blockIdx.y;
+  T tb[P + 1][P + 1];
+#pragma unroll
+  for (int a = 0; a <= P; ++a)
+#pragma unroll
+    for (int q = 0; q < nq; ++q) {
+      int e = i - a;
+      tb[a][q] = (e >= 0 && e < nel) ? __ldg(tab + ((size_t)e * nq + q) * (P + 1) + a) : T(0);
+    }
+  for (long long o = blockIdx.z; o < outer; o += gridDim.z) {
+    T s = T(0);
+#pragma unroll
+    for (int a = 0; a <= P; ++a) {
+      int e = i - a;
+      if (e < 0 || e >= nel) continue;
+      const T *src = in + (o * nin + (long long)e * nq) * inner + c;
+#pragma unroll
+      for (int q = 0; q < nq; ++q) s += tb[a][q] * src[(long long)q * inner];
+    }
+    long long idx = (o * nout + i) * inner + c;
+    out[idx] = accumulate ? out[idx] + s : s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory tiled axis passes.  All three one-axis operations have the
+// form out[o][i][c] = sum_{j in window(i)} W(i, j) in[o][j][c] with a
+// contiguous window: OP_BAND (banded 1D matrix, j in [i-P, i+P]), OP_FWD
+// (coefficients -> Gauss points, i = e*nq+q, j in [e, e+P]) and OP_BWD (Gauss
+// points -> coefficients, j over the Gauss points of spans i-P..i).  A block
+// stages the input rows of its output tile in shared memory once (coalesced
+// along c, or along the axis for the fastest axis), then every output reads
+// its window from shared memory.
+enum { OP_BAND = 0, OP_FWD = 1, OP_BWD = 2 };
+
+template <int P, int OP>
+struct AxisWin {
+  static constexpr int nq = P + 1;
+  // first input row needed by output row i (clamped later), and window length bound
+  __device__ __forceinline__ static int lo(int i) {
+    return OP == OP_BAND ? i - P : OP == OP_FWD ? i / nq : (i - P) * nq;
+  }
+  __device__ __forceinline__ static int hi(int i) {
+    return OP == OP_BAND ? i + P : OP == OP_FWD ? i / nq + P : i * nq + nq - 1;
+  }
+  // weight of input row j for output row i (j inside the window)
+  template <typename T>
+  __device__ __forceinline__ static T w(const T *tab, int i, int j) {
+    if (OP == OP_BAND) return __ldg(tab + (size_t)i * (2 * P + 1) + (j - i + P));
+    if (OP == OP_FWD) return __ldg(tab + (size_t)i * (P + 1) + (j - i / nq));
+    const int e = j / nq, q = j - e * nq;
+    return __ldg(tab + ((size_t)e * nq + q) * (P + 1) + (i - e));
+  }
+};
+
+template <typename T>
+struct TiledTerms {
+  const T *in[3];
+  const T *tab[3];
+  T coef[3];
+  int nterms;
+};
+
+constexpr int kTileC = 32, kTileI = 32;
+
+template <typename T, int P, int OP>
+__global__ void __launch_bounds__(256) tiled_cols_kernel(T *__restrict__ out, TiledTerms<T> tt, int nin, int nout,
+                                                         long long inner, long long outer, int accumulate) {
+  extern __shared__ unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  typedef AxisWin<P, OP> Win;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+  const long long c = (long long)blockIdx.x * kTileC + tx;
+  const int i0 = blockIdx.y * kTileI;
+  const int i1 = min(nout, i0 + kTileI);
+  const int jlo = max(0, Win::lo(i0)), jhi = min(nin - 1, Win::hi(i1 - 1));
+  const int rows = jhi - jlo + 1;
+  for (long long o = blockIdx.z; o < outer; o += gridDim.z) {
+    for (int t = 0; t < tt.nterms; ++t) {
+      const T *src = tt.in[t] + (o * nin + jlo) * inner;
+      T *dst = tile + (size_t)t * rows * kTileC;
+      for (int r = ty; r < rows; r += 8) dst[r * kTileC + tx] = (c < inner) ? src[(long long)r * inner + c] : T(0);
+    }
+    __syncthreads();
+    for (int i = i0 + ty; i < i1; i += 8) {
+      const int a = max(jlo, Win::lo(i)), b = min(jhi, Win::hi(i));
+      T acc = T(0);
+      for (int t = 0; t < tt.nterms; ++t) {
+        const T *tl = tile + (size_t)t * rows * kTileC;
+        T s = T(0);
+        for (int j = a; j <= b; ++j) s += Win::w(tt.tab[t], i, j) * tl[(j - jlo) * kTileC + tx];
+        acc += tt.coef[t] * s;
+      }
+      if (c < inner) {
+        long long idx = (o * nout + i) * inner + c;
+        out[idx] = accumulate ? out[idx] + acc : acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int P, int OP>
+__global__ void __launch_bounds__(256) tiled_rows_kernel(T *__restrict__ out, TiledTerms<T> tt, int nin, int nout,
+                                                         long long outer, int rb, int accumulate) {
+  extern __shared__ unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);   // [term][rb][nin]
+  typedef AxisWin<P, OP> Win;
+  for (long long o0 = (long long)blockIdx.x * rb; o0 < outer; o0 += (long long)gridDim.x * rb) {
+    const int nr = (int)min((long long)rb, outer - o0);
+    for (int t = 0; t < tt.nterms; ++t) {
+      const T *src = tt.in[t] + o0 * nin;
+      T *dst = tile + (size_t)t * rb * nin;
+      for (int k = threadIdx.x; k < nr * nin; k += blockDim.x) dst[k] = src[k];
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < nr * nout; k += blockDim.x) {
+      const int r = k / nout, i = k - r * nout;
+      const int a = max(0, Win::lo(i)), b = min(nin - 1, Win::hi(i));
+      T acc = T(0);
+      for (int t = 0; t < tt.nterms; ++t) {
+        const T *tl = tile + ((size_t)t * rb + r) * nin;
+        T s = T(0);
+        for (int j = a; j <= b; ++j) s += Win::w(tt.tab[t], i, j) * tl[j];
+        acc += tt.coef[t] * s;
+      }
+      long long idx = (o0 + r) * nout + i;
+      out[idx] = accumulate ? out[idx] + acc : acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Streaming variants for the non-fastest axes (inner > 1): a thread owns one
+// inner index c, one outer index o and a run of output rows along the axis,
+// and slides a register window over the input rows it needs, so every input
+// row of the run is loaded once (coalesced across c) and no barrier is used.
+constexpr int kRun = 32;
+
+template <typename T, int P>
+__global__ void band_stream_kernel(T *__restrict__ out, TiledTerms<T> tt, int n, long long inner, long long outer,
+                                   int nruns, int accumulate) {
+  constexpr int B = 2 * P + 1, U = 8;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= inner) return;
+  for (long long yr = blockIdx.y; yr < outer * nruns; yr += gridDim.y) {
+    const long long o = yr / nruns;
+    const int i0 = (int)(yr - o * nruns) * kRun, i1 = min(n, i0 + kRun);
+    T w[3][B];
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      if (t >= tt.nterms) break;
+      const T *src = tt.in[t] + o * n * inner + c;
+#pragma unroll
+      for (int k = 0; k < B - 1; ++k) {
+        int j = i0 - P + k;   // w[k+1] holds row i0-P+k before the first shift
+        w[t][k + 1] = (j >= 0 && j < n) ? src[(long long)j * inner] : T(0);
+      }
+    }
+    for (int ib = i0; ib < i1; ib += U) {
+      // request the U next rows of every term before using them
+      T nx[3][U];
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        if (t >= tt.nterms) break;
+        const T *src = tt.in[t] + o * n * inner + c;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          int j = ib + u + P;
+          nx[t][u] = (ib + u < i1 && j < n) ? src[(long long)j * inner] : T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = ib + u;
+        if (i >= i1) break;
+        T acc = accumulate ? out[(o * n + i) * inner + c] : T(0);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          if (t >= tt.nterms) break;
+#pragma unroll
+          for (int k = 0; k < B - 1; ++k) w[t][k] = w[t][k + 1];
+          w[t][B - 1] = nx[t][u];
+          const T *bd = tt.tab[t] + (size_t)i * B;
+          T sacc = T(0);
+#pragma unroll
+          for (int k = 0; k < B; ++k) sacc += __ldg(bd + k) * w[t][k];
+          acc += tt.coef[t] * sacc;
+        }
+        out[(o * n + i) * inner + c] = acc;
+      }
+    }
+  }
+}
+
+template <typename T, int P>
+__global__ void ifwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab, int nel,
+                                   long long inner, long long outer, int nruns) {
+  constexpr int nq = P + 1, U = 8;
+  const int nin = nel + P, nout = nel * nq;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= inner) return;
+  for (long long yr = blockIdx.y; yr < outer * nruns; yr += gridDim.y) {
+    const long long o = yr / nruns;
+    const int e0 = (int)(yr - o * nruns) * kRun, e1 = min(nel, e0 + kRun);
+    const T *src = in + o * nin * inner + c;
+    T *dst = out + o * nout * inner + c;
+    T w[P + 1];
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[a + 1] = src[(long long)(e0 + a) * inner];
+    for (int eb = e0; eb < e1; eb += U) {
+      T nx[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) nx[u] = (eb + u < e1) ? src[(long long)(eb + u + P) * inner] : T(0);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = eb + u;
+        if (e >= e1) break;
+#pragma unroll
+        for (int a = 0; a < P; ++a) w[a] = w[a + 1];
+        w[P] = nx[u];
+#pragma unroll
+        for (int q = 0; q < nq; ++q) {
+          const T *tb = tab + ((size_t)e * nq + q) * (P + 1);
+          T sacc = T(0);
+#pragma unroll
+          for (int a = 0; a <= P; ++a) sacc += __ldg(tb + a) * w[a];
+          dst[((long long)e * nq + q) * inner] = sacc;
+        }
+      }
+    }
+  }
+}
+
+template <typename T, int P>
+__global__ void ibwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab, int nel,
+                                   long long inner, long long outer, int nruns, int accumulate) {
+  constexpr int nq = P + 1;
+  const int nin = nel * nq, nout = nel + P;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= inner) return;
+  for (long long yr = blockIdx.y; yr < outer * nruns; yr += gridDim.y) {
+    const long long o = yr / nruns;
+    const int i0 = (int)(yr - o * nruns) * kRun, i1 = min(nout, i0 + kRun);
+    const T *src = in + o * nin * inner + c;
+    T *dst = out + o * nout * inner + c;
+    T acc[P + 1];   // acc[a]: coefficient e + a while element e is processed
+#pragma unroll
+    for (int a = 0; a <= P; ++a) acc[a] = T(0);
+    const int ea = max(0, i0 - P), eb = min(nel - 1, i1 - 1);
+    T zn[nq];
+#pragma unroll
+    for (int q = 0; q < nq; ++q) zn[q] = src[((long long)ea * nq + q) * inner];
+    for (int e = ea; e <= eb; ++e) {
+      T z[nq];
+#pragma unroll
+      for (int q = 0; q < nq; ++q) z[q] = zn[q];
+      if (e + 1 <= eb) {
+#pragma unroll
+        for (int q = 0; q < nq; ++q) zn[q] = src[((long long)(e + 1) * nq + q) * inner];
+      }
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < nq; ++q) s += __ldg(tab + ((size_t)e * nq + q) * (P + 1) + a) * z[q];
+        acc[a] += s;
+      }
+      // coefficient e receives nothing from later elements
+      if (e >= i0) {
+        long long idx = (long long)e * inner;
+        dst[idx] = accumulate ? dst[idx] + acc[0] : acc[0];
+      }
+#pragma unroll
+      for (int a = 0; a < P; ++a) acc[a] = acc[a + 1];
+      acc[P] = T(0);
+    }
+    // coefficients eb+1 .. i1-1 (only past the last element); acc[0] is eb+1
+    for (int i = eb + 1; i < i1; ++i) {
+      if (i >= i0) {
+        long long idx = (long long)i * inner;
+        T v = acc[0];
+        dst[idx] = accumulate ? dst[idx] + v : v;
+      }
+#pragma unroll
+      for (int a = 0; a < P; ++a) acc[a] = acc[a + 1];
+      acc[P] = T(0);
+    }
+  }
+}
+
+// Fastest-axis passes: a block stages rb whole rows in shared memory
+// (coalesced), and each thread keeps the weights of its output positions in
+// registers across the rows of the block.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) band_rows2_kernel(T *__restrict__ out, const T *__restrict__ in,
+                                                         const T *__restrict__ band, T coef, int n, long long outer,
+                                                         int rb, int accumulate) {
+  extern __shared__ unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  constexpr int B = 2 * P + 1;
+  for (long long o0 = (long long)blockIdx.x * rb; o0 < outer; o0 += (long long)gridDim.x * rb) {
+    const int nr = (int)min((long long)rb, outer - o0);
+    for (int k = threadIdx.x; k < nr * n; k += blockDim.x) tile[k] = in[o0 * n + k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      T wv[B];
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        int j = i - P + k;
+        wv[k] = (j >= 0 && j < n) ? coef * __ldg(band + (size_t)i * B + k) : T(0);
+      }
+      for (int r = 0; r < nr; ++r) {
+        const T *tl = tile + r * n;
+        T sacc = T(0);
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+          int j = i - P + k;
+          if (j >= 0 && j < n) sacc += wv[k] * tl[j];
+        }
+        long long idx = (o0 + r) * n + i;
+        out[idx] = accumulate ? out[idx] + sacc : sacc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) ifwd_rows2_kernel(T *__restrict__ out, const T *__restrict__ in,
+                                                         const T *__restrict__ tab, int nel, long long outer, int rb) {
+  extern __shared__ unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  constexpr int nq = P + 1;
+  const int nin = nel + P, nout = nel * nq;
+  for (long long o0 = (long long)blockIdx.x * rb; o0 < outer; o0 += (long long)gridDim.x * rb) {
+    const int nr = (int)min((long long)rb, outer - o0);
+    for (int k = threadIdx.x; k < nr * nin; k += blockDim.x) tile[k] = in[o0 * nin + k];
+    __syncthreads();
+    for (int eq = threadIdx.x; eq < nout; eq += blockDim.x) {
+      const int e = eq / nq;
+      T wv[P + 1];
+#pragma unroll
+      for (int a = 0; a <= P; ++a) wv[a] = __ldg(tab + (size_t)eq * (P + 1) + a);
+      for (int r = 0; r < nr; ++r) {
+        const T *tl = tile + r * nin + e;
+        T sacc = T(0);
+#pragma unroll
+        for (int a = 0; a <= P; ++a) sacc += wv[a] * tl[a];
+        out[(o0 + r) * nout + eq] = sacc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(256) ibwd_rows2_kernel(T *__restrict__ out, const T *__restrict__ in,
+                                                         const T *__restrict__ tab, int nel, long long outer, int rb,
+                                                         int accumulate) {
+  extern __shared__ unsigned char smem_raw[];
+  T *tile = reinterpret_cast<T *>(smem_raw);
+  constexpr int nq = P + 1;
+  const int nin = nel * nq, nout = nel + P;
+  for (long long o0 = (long long)blockIdx.x * rb; o0 < outer; o0 += (long long)gridDim.x * rb) {
+    const int nr = (int)min((long long)rb, outer - o0);
+    for (int k = threadIdx.x; k < nr * nin; k += blockDim.x) tile[k] = in[o0 * nin + k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < nout; i += blockDim.x) {
+      T wv[P + 1][nq];
+#pragma unroll
+      for (int a = 0; a <= P; ++a)
+#pragma unroll
+        for (int q = 0; q < nq; ++q) {
+          int e = i - a;
+          wv[a][q] = (e >= 0 && e < nel) ? __ldg(tab + ((size_t)e * nq + q) * (P + 1) + a) : T(0);
+        }
+      for (int r = 0; r < nr; ++r) {
+        const T *tl = tile + r * nin;
+        T sacc = T(0);
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+          int e = i - a;
+          if (e < 0 || e >= nel) continue;
+#pragma unroll
+          for (int q = 0; q < nq; ++q) sacc += wv[a][q] * tl[e * nq + q];
+        }
+        long long idx = (o0 + r) * nout + i;
+        out[idx] = accumulate ? out[idx] + sacc : sacc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T, int P, int OP>
+void launch_tiled(cudaStream_t s, T *out, const TiledTerms<T> &tt, int nin, int nout, long long inner,
+                  long long outer, bool accumulate) {
+  int acc = accumulate ? 1 : 0;
+  st_count_launch();
+  if (inner == 1) {
+    // whole rows in shared memory, at most 40 KB per block
+    int rb = (int)std::max<long long>(1, std::min<long long>(32, 40960 / ((long long)tt.nterms * sizeof(T) * std::max(nin, 1))));
+    size_t sh = (size_t)tt.nterms * rb * nin * sizeof(T);
+    long long blocks = std::min<long long>((outer + rb - 1) / rb, 152LL * 16);
+    if (tt.nterms == 1 && OP == OP_BAND) {
+      band_rows2_kernel<T, P><<<(unsigned)blocks, 256, sh, s>>>(out, tt.in[0], tt.tab[0], tt.coef[0], nin, outer, rb, acc);
+    } else if (OP == OP_FWD) {
+      ifwd_rows2_kernel<T, P><<<(unsigned)blocks, 256, sh, s>>>(out, tt.in[0], tt.tab[0], nin - P, outer, rb);
+    } else if (OP == OP_BWD) {
+      ibwd_rows2_kernel<T, P><<<(unsigned)blocks, 256, sh, s>>>(out, tt.in[0], tt.tab[0], nout - P, outer, rb, acc);
+    } else {
+      tiled_rows_kernel<T, P, OP><<<(unsigned)blocks, 256, sh, s>>>(out, tt, nin, nout, outer, rb, acc);
+    }
+  } else {
+    int bx = (int)std::min<long long>(256, (inner + 31) / 32 * 32);
+    long long gx = (inner + bx - 1) / bx;
+    int nruns = OP == OP_FWD ? (nin - P + kRun - 1) / kRun : (nout + kRun - 1) / kRun;
+    long long gy = std::min<long long>(outer * nruns, 65535);
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    if (OP == OP_BAND)
+      band_stream_kernel<T, P><<<grid, bx, 0, s>>>(out, tt, nout, inner, outer, nruns, acc);
+    else if (OP == OP_FWD)
+      ifwd_stream_kernel<T, P><<<grid, bx, 0, s>>>(out, tt.in[0], tt.tab[0], nin - P, inner, outer, nruns);
+    else
+      ibwd_stream_kernel<T, P><<<grid, bx, 0, s>>>(out, tt.in[0], tt.tab[0], nout - P, inner, outer, nruns, acc);
+  }
+}
+
+template <typename T, int OP>
+void launch_tiled_p(cudaStream_t s, int p, T *out, const TiledTerms<T> &tt, int nin, int nout, long long inner,
+                    long long outer, bool accumulate) {
+  switch (p) {
+    case 1: launch_tiled<T, 1, OP>(s, out, tt, nin, nout, inner, outer, accumulate); break;
+    case 2: launch_tiled<T, 2, OP>(s, out, tt, nin, nout, inner, outer, accumulate); break;
+    case 3: launch_tiled<T, 3, OP>(s, out, tt, nin, nout, inner, outer, accumulate); break;
+    default: launch_tiled<T, 4, OP>(s, out, tt, nin, nout, inner, outer, accumulate); break;
+  }
+}
+
 // Per spatial Gauss point q, the symmetric time band of the reaction and SU
 // terms: z[it][q] = sum_{k=-P..P} band(it, it+k; q) x[it+k][q], band stored as
 // the upper half [k][it][q] (entry (it, it+k)), k = 0..P.  One thread sweeps
@@ -197,6 +759,7 @@ __global__ void qband_kernel(T *__restrict__ z, const T *__restrict__ x, const T
 // of Theta-hat and the products of the eigen-refinement.
 struct GemmDesc {
   int M, N, K, batch;
+  int splits = 1;                // K partitions; partial results go to C + split * M * N (scm, scc layout)
   long long sam, sak;            // A(m,k) = A[m*sam + k*sak]
   long long sbb, sbk, sbc;       // X(b,k,c)
   long long scb, scm, scc;       // C(b,m,c)
@@ -208,7 +771,10 @@ __global__ void __launch_bounds__(256) gemm_kernel(T *__restrict__ C, const T *_
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ T As[BK][BM + 1];
   __shared__ T Xs[BK][BN + 1];
-  int b = blockIdx.z;
+  int b = blockIdx.z % g.batch;
+  int split = blockIdx.z / g.batch;
+  int kchunk = ((g.K + g.splits - 1) / g.splits + BK - 1) / BK * BK;
+  int kbeg = split * kchunk, kend = min(g.K, kbeg + kchunk);
   int m0 = blockIdx.y * BM, c0 = blockIdx.x * BN;
   int tid = threadIdx.x;
   int tx = tid % 16, ty = tid / 16;
@@ -220,18 +786,18 @@ __global__ void __launch_bounds__(256) gemm_kernel(T *__restrict__ C, const T *_
   const T *Xb = X + (long long)b * g.sbb;
   bool a_k_fast = (g.sak == 1);
   bool x_c_fast = (g.sbc == 1);
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
     for (int l = tid; l < BM * BK; l += 256) {
       int mm, kk;
       if (a_k_fast) { kk = l % BK; mm = l / BK; } else { mm = l % BM; kk = l / BM; }
       int m = m0 + mm, k = k0 + kk;
-      As[kk][mm] = (m < g.M && k < g.K) ? A[m * g.sam + k * g.sak] : T(0);
+      As[kk][mm] = (m < g.M && k < kend) ? A[m * g.sam + k * g.sak] : T(0);
     }
     for (int l = tid; l < BN * BK; l += 256) {
       int cc, kk;
       if (x_c_fast) { cc = l % BN; kk = l / BN; } else { kk = l % BK; cc = l / BK; }
       int c = c0 + cc, k = k0 + kk;
-      Xs[kk][cc] = (c < g.N && k < g.K) ? Xb[k * g.sbk + c * g.sbc] : T(0);
+      Xs[kk][cc] = (c < g.N && k < kend) ? Xb[k * g.sbk + c * g.sbc] : T(0);
     }
     __syncthreads();
 #pragma unroll
@@ -248,7 +814,7 @@ __global__ void __launch_bounds__(256) gemm_kernel(T *__restrict__ C, const T *_
     }
     __syncthreads();
   }
-  T *Cb = C + (long long)b * g.scb;
+  T *Cb = C + (long long)b * g.scb + (long long)split * g.M * g.N;
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -428,14 +994,19 @@ __global__ void __launch_bounds__(256) mdot_kernel(double *__restrict__ partial,
   }
 }
 
+// out[i] = sum_b partial[i][b]: one warp per i, lanes take blocks in a fixed
+// stride pattern and a fixed shuffle tree combines them (deterministic).
 __global__ void reduce_blocks_kernel(double *__restrict__ out, const double *__restrict__ partial, int nblocks,
                                      int nv) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int lane = threadIdx.x & 31;
   if (i >= nv) return;
-  double t = 0.0;
   const double *p = partial + (long long)i * nblocks;
-  for (int b = 0; b < nblocks; ++b) t += p[b];
-  out[i] = t;
+  double t = 0.0;
+  for (int b = lane; b < nblocks; b += 32) t += p[b];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+  if (lane == 0) out[i] = t;
 }
 
 // w <- (w - sum_{i<nv} h_i V_i) * s, with s = 1 or, when nrm is given,
@@ -466,8 +1037,20 @@ __global__ void __launch_bounds__(256) maxpy_kernel(T *__restrict__ w, const T *
   const T s = (T)sc;
   const long long nvec = n / W;
   VT *wv = reinterpret_cast<VT *>(w);
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nvec;
-       e += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (; e + stride < nvec; e += 2 * stride) {
+    VT a = X::zero(), b = X::zero();
+#pragma unroll 8
+    for (int i = 0; i < nv; ++i) {
+      const VT *vi = reinterpret_cast<const VT *>(V + (long long)i * ldv);
+      a = X::fma(hs[i], vi[e], a);
+      b = X::fma(hs[i], vi[e + stride], b);
+    }
+    wv[e] = X::upd(wv[e], a, s);
+    wv[e + stride] = X::upd(wv[e + stride], b, s);
+  }
+  for (; e < nvec; e += stride) {
     VT a = X::zero();
 #pragma unroll 8
     for (int i = 0; i < nv; ++i) a = X::fma(hs[i], reinterpret_cast<const VT *>(V + (long long)i * ldv)[e], a);
@@ -553,61 +1136,50 @@ __global__ void to_f32_kernel(float *__restrict__ y, const double *__restrict__ 
 
 constexpr int kDotBlocks = 608;
 
+// Blocks along the outer index so that the whole grid is about 16 blocks per
+// SM (each thread then loops over several outer indices).
+unsigned outer_blocks(long long outer, long long other_blocks) {
+  long long target = 152LL * 16;
+  long long g = std::max<long long>(1, target / std::max<long long>(1, other_blocks));
+  return (unsigned)std::min<long long>(std::min<long long>(outer, g), 65535);
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- launchers
 template <typename T>
 void launch_band_pass(cudaStream_t s, T *out, int nterms, const T *const *bands, const T *const *ins,
                       const double *coefs, int n, long long inner, long long outer, int p, bool accumulate) {
-  BandTerms<T> bt;
-  bt.nterms = nterms;
+  TiledTerms<T> tt;
+  tt.nterms = nterms;
   for (int t = 0; t < 3; ++t) {
-    bt.band[t] = t < nterms ? bands[t] : nullptr;
-    bt.in[t] = t < nterms ? ins[t] : nullptr;
-    bt.coef[t] = t < nterms ? (T)coefs[t] : T(0);
+    tt.in[t] = t < nterms ? ins[t] : nullptr;
+    tt.tab[t] = t < nterms ? bands[t] : nullptr;
+    tt.coef[t] = t < nterms ? (T)coefs[t] : T(0);
   }
-  long long total = outer * n * inner;
-  int acc = accumulate ? 1 : 0;
-  Split3 sp(inner, n);
-  int g = grid_for(total);
-  st_count_launch();
-  switch (p) {
-    case 1: band_pass_kernel<T, 1><<<g, kThreads, 0, s>>>(out, bt, n, inner, outer, acc, sp); break;
-    case 2: band_pass_kernel<T, 2><<<g, kThreads, 0, s>>>(out, bt, n, inner, outer, acc, sp); break;
-    case 3: band_pass_kernel<T, 3><<<g, kThreads, 0, s>>>(out, bt, n, inner, outer, acc, sp); break;
-    default: band_pass_kernel<T, 4><<<g, kThreads, 0, s>>>(out, bt, n, inner, outer, acc, sp); break;
-  }
+  launch_tiled_p<T, OP_BAND>(s, p, out, tt, n, n, inner, outer, accumulate);
 }
 
 template <typename T>
 void launch_interp_fwd(cudaStream_t s, T *out, const T *in, const T *tab, int nel, int p, int nq,
                        long long inner, long long outer) {
-  long long total = outer * (long long)nel * nq * inner;
-  Split3 sp(inner, (long long)nel * nq);
-  int g = grid_for(total);
-  st_count_launch();
-  switch (p) {
-    case 1: interp_fwd_kernel<T, 1><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, sp); break;
-    case 2: interp_fwd_kernel<T, 2><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, sp); break;
-    case 3: interp_fwd_kernel<T, 3><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, sp); break;
-    default: interp_fwd_kernel<T, 4><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, sp); break;
-  }
+  (void)nq;
+  TiledTerms<T> tt;
+  tt.nterms = 1;
+  tt.in[0] = in; tt.tab[0] = tab; tt.coef[0] = T(1);
+  for (int t = 1; t < 3; ++t) { tt.in[t] = nullptr; tt.tab[t] = nullptr; tt.coef[t] = T(0); }
+  launch_tiled_p<T, OP_FWD>(s, p, out, tt, nel + p, nel * (p + 1), inner, outer, false);
 }
 
 template <typename T>
 void launch_interp_bwd(cudaStream_t s, T *out, const T *in, const T *tab, int nel, int p, int nq,
                        long long inner, long long outer, bool accumulate) {
-  long long total = outer * (long long)(nel + p) * inner;
-  Split3 sp(inner, nel + p);
-  int acc = accumulate ? 1 : 0;
-  int g = grid_for(total);
-  st_count_launch();
-  switch (p) {
-    case 1: interp_bwd_kernel<T, 1><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, acc, sp); break;
-    case 2: interp_bwd_kernel<T, 2><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, acc, sp); break;
-    case 3: interp_bwd_kernel<T, 3><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, acc, sp); break;
-    default: interp_bwd_kernel<T, 4><<<g, kThreads, 0, s>>>(out, in, tab, nel, inner, outer, acc, sp); break;
-  }
+  (void)nq;
+  TiledTerms<T> tt;
+  tt.nterms = 1;
+  tt.in[0] = in; tt.tab[0] = tab; tt.coef[0] = T(1);
+  for (int t = 1; t < 3; ++t) { tt.in[t] = nullptr; tt.tab[t] = nullptr; tt.coef[t] = T(0); }
+  launch_tiled_p<T, OP_BWD>(s, p, out, tt, nel * (p + 1), nel + p, inner, outer, accumulate);
 }
 
 template <typename T>
@@ -669,17 +1241,21 @@ template <typename T>
 void launch_multi_dot(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *w, long long n,
                       double *scratch) {
   constexpr int G = 8;
-  int bx = (int)std::min<long long>(kDotBlocks, std::max<long long>(1, (n + 2047) / 2048));
-  dim3 grid(bx, (nv + G - 1) / G);
+  int groups = (nv + G - 1) / G;
+  // enough blocks for about four waves in total, at least 8 vector steps per thread
+  long long want = std::max<long long>(38, 4 * 304 / groups);
+  long long cap = std::max<long long>(1, n / (V16<T>::W * 256 * 8));
+  int bx = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(want, cap), kDotBlocks));
+  dim3 grid(bx, groups);
   st_count_launch(); mdot_kernel<T, G><<<grid, 256, 0, s>>>(scratch, V, ldv, nv, w, n);
-  st_count_launch(); reduce_blocks_kernel<<<(nv + 127) / 128, 128, 0, s>>>(out, scratch, bx, nv);
+  st_count_launch(); reduce_blocks_kernel<<<(nv + 3) / 4, 128, 0, s>>>(out, scratch, bx, nv);
 }
 
 template <typename T>
 void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, const double *h, long long n,
                        const double *nrm) {
   long long nvec = n / V16<T>::W;
-  st_count_launch(); maxpy_kernel<T><<<grid_for(std::max<long long>(nvec, 1)), kThreads, 0, s>>>(w, V, ldv, nv, h, n, nrm);
+  st_count_launch(); maxpy_kernel<T><<<grid_for(std::max<long long>(nvec / 2, 1)), kThreads, 0, s>>>(w, V, ldv, nv, h, n, nrm);
 }
 
 template <typename T>
@@ -711,13 +1287,45 @@ void launch_band_to_f32(cudaStream_t s, float *out, const double *in, long long 
   st_count_launch(); to_f32_kernel<<<grid_for(n), kThreads, 0, s>>>(out, in, n);
 }
 
+// C(m, c) = alpha sum_s P[s][m][c] + beta C(m, c): the fixed-order sum of split-K partials.
+__global__ void splitk_reduce_kernel(double *C, const double *P, int M, int N, int S, long long scm, long long scc,
+                                     double alpha, double beta) {
+  long long total = (long long)M * N;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    int m = (int)(e / N), c = (int)(e % N);
+    double t = 0.0;
+    for (int k = 0; k < S; ++k) t += P[(long long)k * total + e];
+    double *dst = C + m * scm + c * scc;
+    *dst = beta == 0.0 ? alpha * t : alpha * t + beta * *dst;
+  }
+}
+
+// FP64 GEMM; with a workspace of at least `work_elems` doubles, small
+// output grids with long K are split along K over more blocks (partials
+// reduced in a fixed order, so results do not depend on the split).
 void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, int M, int N, int K,
                    long long sam, long long sak, long long sbk, long long sbc, long long scm, long long scc,
-                   double alpha, double beta) {
+                   double alpha, double beta, double *work, long long work_elems) {
   GemmDesc g;
   g.M = M; g.N = N; g.K = K; g.batch = 1;
   g.sam = sam; g.sak = sak; g.sbb = 0; g.sbk = sbk; g.sbc = sbc; g.scb = 0; g.scm = scm; g.scc = scc;
-  launch_gemm<double>(s, C, A, X, g, alpha, beta);
+  long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
+  int S = 1;
+  if (work && tiles < 2 * 152 && K >= 512) {
+    S = (int)std::min<long long>(std::max<long long>(1, 4 * 152 / tiles), K / 256);
+    while (S > 1 && (long long)S * M * N > work_elems) --S;
+  }
+  if (S <= 1) {
+    launch_gemm<double>(s, C, A, X, g, alpha, beta);
+    return;
+  }
+  GemmDesc gp = g;
+  gp.splits = S;
+  gp.scm = N; gp.scc = 1;          // partials are dense row-major M x N
+  dim3 grid((N + 63) / 64, (M + 63) / 64, S);
+  st_count_launch(); gemm_kernel<double><<<grid, 256, 0, s>>>(work, A, X, gp, 1.0, 0.0);
+  st_count_launch(); splitk_reduce_kernel<<<grid_for((long long)M * N), kThreads, 0, s>>>(C, work, M, N, S, scm, scc, alpha, beta);
 }
 
 #define INST(T)                                                                                        \

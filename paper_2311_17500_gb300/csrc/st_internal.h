@@ -61,6 +61,7 @@ struct st_handle {
   double *xt = nullptr;       // time points [e*nq+q]
   double *xs[3] = {};         // spatial points per direction [e*nq+q]
   double *tauq = nullptr;     // [l-1][e][q]
+  double *bprod = nullptr;    // [e][q][pair] w_t b_i b_{i+k}, pairs (i, k) with k <= p - i
   double *wlu = nullptr;      // LU of W_t + b d_e M_t
   // hat-function data of the Greville interpolation, per 1D Gauss point
   int *hat_i_t = nullptr, *hat_i_s[3] = {};
