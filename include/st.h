@@ -224,6 +224,11 @@ enum {
   ST_STAGE_COUNT = 9
 };
 st_status st_profile(st_handle *h, int enable);
+/* Self-test of the tensor-core (tcgen05, TF32) spatial transforms of the
+ * preconditioner against the CUDA-core transform, run once per process on a
+ * ragged problem; *usable = 1 when the FP32 preconditioner uses them, and
+ * *max_rel_err is the largest difference relative to the largest value. */
+st_status st_tc_selftest(int *usable, double *max_rel_err);
 /* Number of kernel launches this library has issued in the process so far. */
 long long st_launch_count(void);
 st_status st_profile_read(st_handle *h, int stage, double *ms, double *bytes, double *flops, long long *launches);

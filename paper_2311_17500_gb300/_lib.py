@@ -24,7 +24,8 @@ GET = dict(theta_hat=0, lowrank_s=1, lowrank_u=2, lowrank_v=3, tau_q=4, fd_eig=5
 
 EXPORTS = ["st_footprint", "st_setup", "st_destroy", "st_error_string", "st_get_dims", "st_ionic",
            "st_linearize", "st_apply", "st_precond", "st_linsolve", "st_wupdate", "st_rhs", "st_solve",
-           "st_get", "st_profile", "st_profile_read", "st_launch_count"]
+           "st_get", "st_profile", "st_profile_read", "st_launch_count",
+           "st_tc_selftest"]
 STAGES = ["kron", "interp", "qband", "fd_gemm", "fd_lu", "arnoldi", "ionic", "lowrank"]
 
 
@@ -100,6 +101,7 @@ def load(path=None):
     lib.st_profile.argtypes = [vp, i]
     d = ctypes.c_double
     lib.st_profile_read.argtypes = [vp, i, P(d), P(d), P(d), P(ctypes.c_longlong)]
+    lib.st_tc_selftest.argtypes = [P(i), P(ctypes.c_double)]
     lib.st_launch_count.argtypes = []
     lib.st_launch_count.restype = ctypes.c_longlong
     for name in EXPORTS:
@@ -149,6 +151,14 @@ def _check(code, what):
     if code != ST_OK:
         msg = load().st_error_string(code).decode()
         raise StError(code, f"{what} failed ({msg})")
+
+
+def tc_selftest():
+    """(usable, max_rel_err) of the tensor-core transform self-test."""
+    lib = load()
+    u, e = ctypes.c_int(0), ctypes.c_double(0.0)
+    _check(lib.st_tc_selftest(ctypes.byref(u), ctypes.byref(e)), "st_tc_selftest")
+    return bool(u.value), e.value
 
 
 def footprint(desc):

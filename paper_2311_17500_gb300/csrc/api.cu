@@ -76,8 +76,8 @@ Sizes plan(const st_problem_desc &D) {
   b += (size_t)z.NtQs * d8 * 5;                                    // two work buffers + ionic fields
   b += (size_t)z.NtQs * f4 * 2;
   b += (size_t)z.Ndof * (d8 + f4) * 7;                             // Kronecker temporaries
-  if (D.precision == ST_FP64) b += (size_t)(z.m + 1) * z.Ndof * d8;
-  else b += (size_t)(z.m + 1) * z.Ndof * f4;
+  if (D.precision == ST_FP64) b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * d8;
+  else b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * f4;
   b += (size_t)(608 * (z.m + 48) + 4096) * d8;
   z.bytes = b;
   return z;
@@ -147,20 +147,24 @@ double absmax_diff(st_handle *h, const double *x, const double *y) {
 template <typename T> T *basis(st_handle *h);
 template <> double *basis<double>(st_handle *h) { return h->V64; }
 template <> float *basis<float>(st_handle *h) { return h->V32; }
-template <typename T> T *ztmp(st_handle *h);
-template <> double *ztmp<double>(st_handle *h) { return h->z64; }
-template <> float *ztmp<float>(st_handle *h) { return h->t32a; }
 
-// Right-preconditioned GMRES(m) on A_T d = b from d = 0, one cycle of at most
-// `maxit` (<= m) iterations; stops when the Arnoldi residual estimate drops to
-// tol * ||b||.  Gram-Schmidt: classical with one reorthogonalization, inner
-// products accumulated in FP64 in a fixed order.  Hessenberg and Givens in FP64.
+// Flexible right-preconditioned GMRES(m) on A_T d = b from d = 0, one cycle of
+// at most `maxit` (<= m) iterations; stops when the Arnoldi residual estimate
+// drops to tol * ||b||.  The preconditioned vectors z_j = M^{-1} v_j are kept
+// (Z basis) and d = Z y, so the update matches the Arnoldi relation even when
+// the preconditioner is applied with rounded (TF32) transform inputs.
+// Gram-Schmidt: classical with one reorthogonalization, inner products
+// accumulated in FP64 in a fixed order; Hessenberg and Givens in FP64.
+template <typename T> T *zbasis(st_handle *h);
+template <> double *zbasis<double>(st_handle *h) { return h->Z64; }
+template <> float *zbasis<float>(st_handle *h) { return h->Z32; }
+
 template <typename T>
 st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int *its, double *est) {
   cudaStream_t s = h->stream;
   long long N = h->Ndof, ld = h->ldv;
   T *V = basis<T>(h);
-  T *z = ztmp<T>(h);
+  T *Z = zbasis<T>(h);
   int m = std::min(maxit, h->m);
   double *hd = h->hcol;           // device: h1 [0..m+1], h2 [m+2 .. 2m+3]
   double *scratch = h->red + 4096;
@@ -174,14 +178,14 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
   }
   launch_scale_copy<T>(s, V, b, 1.0 / beta, N);
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
-  std::vector<double> hh(2 * (m + 2));
+  std::vector<double> hh(2 * (m + 2) + 2);
   g[0] = beta;
   int j = 0;
   double res = beta;
   for (; j < m; ++j) {
-    T *vj = V + (long long)j * ld, *w = V + (long long)(j + 1) * ld;
-    ST_TRY(precond_T<T>(h, vj, z));
-    ST_TRY(apply_T<T>(h, z, w));
+    T *vj = V + (long long)j * ld, *w = V + (long long)(j + 1) * ld, *zj = Z + (long long)j * ld;
+    ST_TRY(precond_T<T>(h, vj, zj));
+    ST_TRY(apply_T<T>(h, zj, w));
     double *h1 = hd, *h2 = hd + (m + 2);
     {
       // CGS2: <V_i, w> for i <= j+1 (the last one is |w|^2), update, again,
@@ -193,8 +197,12 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
       launch_multi_dot<T>(s, h2, V, ld, j + 2, w, N, scratch);
       launch_multi_axpy<T>(s, w, V, ld, j + 1, h2, N, h2 + (j + 1));
     }
+    // Hessenberg column and the device error flag of the tensor-core transforms
     ST_CUDA(cudaMemcpyAsync(hh.data(), hd, 2 * (m + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    int tc_flag = 0;
+    if (h->use_tc && sizeof(T) == 4) ST_CUDA(cudaMemcpyAsync(&tc_flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ST_CUDA(cudaStreamSynchronize(s));
+    if (tc_flag) return ST_ERR_TIMEOUT;
     double q = hh[(m + 2) + (j + 1)];
     for (int i = 0; i <= j; ++i) q -= hh[(m + 2) + i] * hh[(m + 2) + i];
     double hnorm = q > 0.0 ? std::sqrt(q) : 0.0;
@@ -227,12 +235,11 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
     double piv = H[(size_t)i * m + i];
     y[i] = piv != 0.0 ? t / piv : 0.0;
   }
-  // d = M^{-1} (V y): accumulate V y into z with the multi-axpy (z -= sum (-y_i) V_i)
+  // d = Z y, accumulated with the multi-axpy (d -= sum (-y_i) Z_i)
   for (int i = 0; i < k; ++i) y[i] = -y[i];
   ST_CUDA(cudaMemcpyAsync(hd, y.data(), std::max(k, 1) * sizeof(double), cudaMemcpyHostToDevice, s));
-  ST_CUDA(cudaMemsetAsync(z, 0, N * sizeof(T), s));
-  if (k > 0) launch_multi_axpy<T>(s, z, V, ld, k, hd, N);
-  ST_TRY(precond_T<T>(h, z, d));
+  ST_CUDA(cudaMemsetAsync(d, 0, N * sizeof(T), s));
+  if (k > 0) launch_multi_axpy<T>(s, d, Z, ld, k, hd, N);
   *its = k;
   *est = res / beta;
   ST_CUDA(cudaStreamSynchronize(s));
@@ -407,24 +414,40 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   return ST_OK;
 }
 
-// z = A-hat^{-1} r by fast diagonalization (Eq. factorized): transforms with
-// U_l^T along each spatial axis, one banded LU solve along time per spatial
-// eigen-index, transforms with U_l.
+// z = A-hat^{-1} r by fast diagonalization (Eq. factorized).  Each spatial
+// transform contracts the contiguous axis and writes the result rotated
+// ([T][a][b] -> [T][j][a]), so after the d forward transforms (with U_l^T)
+// the eigen-indices are back in the natural order for the banded LU solves
+// along time, and the d backward transforms (with U_l) restore [T][z][y][x].
+// FP32 transforms run on the tensor cores (TF32) when the self-test passed.
+template <typename T>
+static void rot_step(st_handle *h, T *out, const T *in, int l, bool fwd);
+template <>
+void rot_step<double>(st_handle *h, double *out, const double *in, int l, bool fwd) {
+  launch_rot_gemm<double>(h->stream, out, in, fwd ? h->UT64[l] : h->U64[l], h->n[l], h->n[l], h->Ns / h->n[l], h->Nt);
+}
+template <>
+void rot_step<float>(st_handle *h, float *out, const float *in, int l, bool fwd) {
+  long long Aa = h->Ns / h->n[l];
+  if (h->use_tc) {
+    launch_tc_rot_gemm(h->stream, out, in, fwd ? h->UTp[l] : h->Up[l], (long long)h->Nt * Aa, h->n[l], h->n[l],
+                       h->Npad[l], h->Kpad[l], Aa, h->tc_err);
+  } else {
+    launch_rot_gemm<float>(h->stream, out, in, fwd ? h->UT32[l] : h->U32[l], h->n[l], h->n[l], Aa, h->Nt);
+  }
+}
+
 template <typename T>
 st_status precond_T(st_handle *h, const T *r, T *z) {
   typedef Prec<T> P;
   cudaStream_t s = h->stream;
-  long long nd[3] = {h->n[0], h->n[1], h->n[2]};
   const T *cur = r;
   T *bufs[2] = {P::K(h, 0), P::K(h, 1)};
   int ping = 0;
   const double vec = (double)h->Ndof * sizeof(T);
   for (int l = 0; l < h->d; ++l) {
-    long long inner = 1, outer = h->Nt;
-    for (int k = 0; k < l; ++k) inner *= nd[k];
-    for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
     ProfScope ps(h, PROF_FD_GEMM, 2 * vec, 2.0 * h->n[l] * (double)h->Ndof);
-    launch_mode_gemm<T>(s, bufs[ping], cur, P::UT(h, l), h->n[l], inner, outer);
+    rot_step<T>(h, bufs[ping], cur, l, true);
     cur = bufs[ping];
     ping ^= 1;
   }
@@ -435,12 +458,9 @@ st_status precond_T(st_handle *h, const T *r, T *z) {
   cur = bufs[ping];
   ping ^= 1;
   for (int l = 0; l < h->d; ++l) {
-    long long inner = 1, outer = h->Nt;
-    for (int k = 0; k < l; ++k) inner *= nd[k];
-    for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
     T *out = (l == h->d - 1) ? z : bufs[ping];
     ProfScope ps(h, PROF_FD_GEMM, 2 * vec, 2.0 * h->n[l] * (double)h->Ndof);
-    launch_mode_gemm<T>(s, out, cur, P::U(h, l), h->n[l], inner, outer);
+    rot_step<T>(h, out, cur, l, false);
     cur = out;
     ping ^= 1;
   }
@@ -602,8 +622,13 @@ static st_status setup_impl(st_handle *h) {
   h->L0 = dalloc<double>(h, h->NtQs, &e);
   h->Wq0 = dalloc<double>(h, h->NtQs, &e);
   h->red = dalloc<double>(h, 4096 + 608 * (size_t)(h->m + 48), &e);
-  if (D.precision == ST_FP64) h->V64 = dalloc<double>(h, (size_t)(h->m + 1) * h->ldv, &e);
-  else h->V32 = dalloc<float>(h, (size_t)(h->m + 1) * h->ldv, &e);
+  if (D.precision == ST_FP64) {
+    h->V64 = dalloc<double>(h, (size_t)(h->m + 1) * h->ldv, &e);
+    h->Z64 = dalloc<double>(h, (size_t)h->m * h->ldv, &e);
+  } else {
+    h->V32 = dalloc<float>(h, (size_t)(h->m + 1) * h->ldv, &e);
+    h->Z32 = dalloc<float>(h, (size_t)h->m * h->ldv, &e);
+  }
   h->r64 = dalloc<double>(h, h->Ndof, &e);
   h->x64 = dalloc<double>(h, h->Ndof, &e);
   h->t64a = dalloc<double>(h, h->Ndof, &e);
@@ -616,8 +641,35 @@ static st_status setup_impl(st_handle *h) {
   h->d32 = dalloc<float>(h, h->Ndof, &e);
   h->hcol = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
   if (e != ST_OK) return e;
+  h->tc_err = dalloc<int>(h, 4, &e);
+  if (e != ST_OK) return e;
+  ST_CUDA(cudaMemsetAsync(h->tc_err, 0, 4 * sizeof(int), h->stream));
   // ---- device set-up: fast diagonalization, right-hand side
   ST_TRY(fd_setup(h));
+  {
+    // zero-padded FP32 copies of U_l^T and U_l for the tensor-core transforms
+    bool fits = true;
+    for (int l = 0; l < h->d; ++l) fits = fits && h->n[l] <= 256;
+    if (fits && tc_state(h->stream, nullptr) == 1) {
+      for (int l = 0; l < h->d; ++l) {
+        int n = h->n[l];
+        h->Npad[l] = (n + 15) / 16 * 16;
+        h->Kpad[l] = (n + 31) / 32 * 32;
+        std::vector<double> U((size_t)n * n);
+        ST_CUDA(cudaMemcpyAsync(U.data(), h->U64[l], U.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        ST_CUDA(cudaStreamSynchronize(h->stream));
+        std::vector<double> ut((size_t)h->Npad[l] * h->Kpad[l], 0.0), uu((size_t)h->Npad[l] * h->Kpad[l], 0.0);
+        for (int j = 0; j < n; ++j)
+          for (int k = 0; k < n; ++k) {
+            ut[(size_t)j * h->Kpad[l] + k] = U[(size_t)k * n + j];   // (U^T)[j][k]
+            uu[(size_t)j * h->Kpad[l] + k] = U[(size_t)j * n + k];   // U[j][k]
+          }
+        ST_TRY(upload<float>(h, &h->UTp[l], ut));
+        ST_TRY(upload<float>(h, &h->Up[l], uu));
+      }
+      h->use_tc = true;
+    }
+  }
   ST_TRY(source_assemble(h));
   ST_CUDA(cudaStreamSynchronize(h->stream));
   ST_CUDA(cudaGetLastError());
@@ -814,6 +866,15 @@ st_status st_solve(st_handle *h, double *u, double *w, st_stats *stats) {
 }
 
 long long st_launch_count(void) { return g_launches.load(); }
+
+st_status st_tc_selftest(int *usable, double *max_rel_err) {
+  if (!usable || !max_rel_err) return ST_ERR_ARG;
+  double err = 0.0;
+  int st = tc_state(nullptr, &err);
+  *usable = st == 1 ? 1 : 0;
+  *max_rel_err = err;
+  return ST_OK;
+}
 
 st_status st_profile(st_handle *h, int enable) {
   if (!h) return ST_ERR_ARG;

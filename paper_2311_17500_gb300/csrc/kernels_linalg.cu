@@ -1225,6 +1225,23 @@ void launch_mode_gemm(cudaStream_t s, T *out, const T *in, const T *A, int n, lo
   }
 }
 
+// Rotating transform out[(t nj + j) A + a] = sum_k M[j][k] in[(t A + a) nb + k]
+// as a batched strided GEMM (batch t, rows j, columns a).
+template <typename T>
+void launch_rot_gemm(cudaStream_t s, T *out, const T *in, const T *M, int nb, int nj, long long Aa, long long Nt) {
+  GemmDesc g;
+  g.M = nj; g.N = (int)Aa; g.K = nb; g.batch = 1;
+  g.sam = nb; g.sak = 1;
+  g.sbb = Aa * nb; g.sbk = 1; g.sbc = nb;
+  g.scb = (long long)nj * Aa; g.scm = Aa; g.scc = 1;
+  const long long maxb = 65535;
+  for (long long b0 = 0; b0 < Nt; b0 += maxb) {
+    GemmDesc gb = g;
+    gb.batch = (int)std::min<long long>(maxb, Nt - b0);
+    launch_gemm<T>(s, out + b0 * g.scb, M, in + b0 * g.sbb, gb, 1.0, 0.0);
+  }
+}
+
 template <typename T>
 void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p) {
   int threads = 128;
@@ -1338,6 +1355,7 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
   template void launch_qband_apply<T>(cudaStream_t, T *, const T *, const T *, int, long long, int);   \
   template void launch_mode_gemm<T>(cudaStream_t, T *, const T *, const T *, int, long long, long long); \
   template void launch_tline_lu_solve<T>(cudaStream_t, T *, const T *, const T *, int, long long, int); \
+  template void launch_rot_gemm<T>(cudaStream_t, T *, const T *, const T *, int, int, long long, long long); \
   template void launch_multi_dot<T>(cudaStream_t, double *, const T *, long long, int, const T *,      \
                                     long long, double *);                                             \
   template void launch_multi_axpy<T>(cudaStream_t, T *, const T *, long long, int, const double *,     \

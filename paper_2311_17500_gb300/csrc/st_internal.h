@@ -71,6 +71,10 @@ struct st_handle {
   double *U64[3] = {}, *UT64[3] = {}, *lam[3] = {};
   float *U32[3] = {}, *UT32[3] = {};
   double *mu = nullptr;       // spatial eigenvalues mu_j, j over N_s
+  float *UTp[3] = {}, *Up[3] = {};   // TF32 operands: U_l^T, U_l zero-padded to [Npad][Kpad]
+  int Npad[3] = {}, Kpad[3] = {};
+  bool use_tc = false;
+  int *tc_err = nullptr;
   double *lu64 = nullptr;     // [it][k][j], k = 0..2p
   float *lu32 = nullptr;
 
@@ -107,6 +111,7 @@ struct st_handle {
   int m = 0;
   long long ldv = 0;          // Krylov basis leading dimension (16-byte aligned rows)
   double *V64 = nullptr; float *V32 = nullptr;
+  double *Z64 = nullptr; float *Z32 = nullptr;   // preconditioned Krylov vectors (flexible GMRES)
   double *r64 = nullptr, *x64 = nullptr, *t64a = nullptr, *t64b = nullptr;
   double *z64 = nullptr, *b64 = nullptr;   // GMRES preconditioner output, Newton right-hand side
   float *r32 = nullptr, *t32a = nullptr, *t32b = nullptr, *d32 = nullptr;
@@ -172,6 +177,12 @@ template <typename T>
 void launch_mode_gemm(cudaStream_t s, T *out, const T *in, const T *A, int n, long long inner, long long outer);
 template <typename T>
 void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p);
+template <typename T>
+void launch_rot_gemm(cudaStream_t s, T *out, const T *in, const T *M, int nb, int nj, long long Aa, long long Nt);
+st_status launch_tc_rot_gemm(cudaStream_t s, float *out, const float *X, const float *Mpad, long long R, int nb,
+                             int nj, int Npad, int Kpad, long long Aa, int *err);
+// tensor-core transforms: process-wide self-test state (0 untested, 1 usable, -1 not usable)
+int tc_state(cudaStream_t s, double *err_out);
 template <typename T>
 void launch_multi_dot(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *w,
                       long long n, double *scratch);

@@ -148,7 +148,9 @@ def test_precond(P, c):
     assert rel(host(dz), ref) < 1e-10
     dr32, dz32 = dev(r, np.float32), empty(o.st.N_dof, "float32")
     s.precond(ptr(dr32), ptr(dz32), P.ST_MIXED)
-    assert rel(host(dz32), ref) < 1e-3
+    # FP32 path: transforms with TF32 inputs on the tensor cores (unit roundoff
+    # 2^-11 per rounded input, four transforms) and FP32 time solves
+    assert rel(host(dz32), ref) < 1e-2
     s.close()
 
 
