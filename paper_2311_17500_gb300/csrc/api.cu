@@ -76,6 +76,7 @@ Sizes plan(const st_problem_desc &D) {
   b += (size_t)z.NtQs * d8 * 5;                                    // two work buffers + ionic fields
   b += (size_t)z.NtQs * f4 * 2;
   b += (size_t)z.Ndof * (d8 + f4) * 7;                             // Kronecker temporaries
+  b += (size_t)z.Ndof * f4 * 4;                                    // padded transform buffers
   if (D.precision == ST_FP64) b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * d8;
   else b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * f4;
   b += (size_t)(608 * (z.m + 48) + 4096) * d8;
@@ -420,49 +421,118 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
 // the eigen-indices are back in the natural order for the banded LU solves
 // along time, and the d backward transforms (with U_l) restore [T][z][y][x].
 // FP32 transforms run on the tensor cores (TF32) when the self-test passed.
-template <typename T>
-static void rot_step(st_handle *h, T *out, const T *in, int l, bool fwd);
-template <>
-void rot_step<double>(st_handle *h, double *out, const double *in, int l, bool fwd) {
-  launch_rot_gemm<double>(h->stream, out, in, fwd ? h->UT64[l] : h->U64[l], h->n[l], h->n[l], h->Ns / h->n[l], h->Nt);
-}
-template <>
-void rot_step<float>(st_handle *h, float *out, const float *in, int l, bool fwd) {
-  long long Aa = h->Ns / h->n[l];
-  if (h->use_tc) {
-    launch_tc_rot_gemm(h->stream, out, in, fwd ? h->UTp[l] : h->Up[l], (long long)h->Nt * Aa, h->n[l], h->n[l],
-                       h->Npad[l], h->Kpad[l], Aa, h->tc_err);
-  } else {
-    launch_rot_gemm<float>(h->stream, out, in, fwd ? h->UT32[l] : h->U32[l], h->n[l], h->n[l], Aa, h->Nt);
+// One transform of the sequence: contract the innermost axis (length n_l,
+// row stride in_stride) and write [T][j][remaining axes], the new innermost
+// axis of length A_inner stored with row stride A_stride.
+struct RotStep {
+  int l;
+  long long Aa, A_inner, A_stride;
+};
+
+// Steps of the forward (and, identically, the backward) sequence: axis order
+// outer -> inner starts as (z, y, x); each step contracts the innermost axis
+// and moves the new index to the front.
+static void rot_plan(const st_handle *h, RotStep *steps, bool pad_last) {
+  int order[3], no = 0;
+  for (int l = h->d - 1; l >= 0; --l) order[no++] = l;   // outer .. inner
+  for (int s = 0; s < h->d; ++s) {
+    int c = order[no - 1];
+    long long Aa = 1;
+    for (int i = 0; i < no - 1; ++i) Aa *= h->n[order[i]];
+    long long A_inner = no >= 2 ? h->n[order[no - 2]] : 1;
+    bool last = (s == h->d - 1);
+    long long A_stride = (!last || pad_last) ? (A_inner + 3) / 4 * 4 : A_inner;
+    if (no == 1) A_stride = 1;
+    steps[s] = RotStep{c, Aa, A_inner, A_stride};
+    // new order: [j_c, order[0 .. no-2]]
+    for (int i = no - 1; i > 0; --i) order[i] = order[i - 1];
+    order[0] = c;
   }
 }
 
 template <typename T>
+static void rot_simt(st_handle *h, T *out, const T *in, int l, bool fwd);
+template <>
+void rot_simt<double>(st_handle *h, double *out, const double *in, int l, bool fwd) {
+  launch_rot_gemm<double>(h->stream, out, in, fwd ? h->UT64[l] : h->U64[l], h->n[l], h->n[l], h->Ns / h->n[l], h->Nt);
+}
+template <>
+void rot_simt<float>(st_handle *h, float *out, const float *in, int l, bool fwd) {
+  launch_rot_gemm<float>(h->stream, out, in, fwd ? h->UT32[l] : h->U32[l], h->n[l], h->n[l], h->Ns / h->n[l], h->Nt);
+}
+
+// Tensor-core sequence of d transforms (FP32): a first input with rows not
+// 16-byte aligned is copied into a padded buffer, intermediate results use
+// padded rows, the last result is written unpadded.
+static st_status tc_sequence(st_handle *h, const float *in, float *out, bool fwd) {
+  cudaStream_t s = h->stream;
+  RotStep st[3];
+  rot_plan(h, st, false);
+  const float *cur = in;
+  long long cur_stride = h->n[st[0].l];
+  float *P[2] = {h->P32[0], h->P32[1]};
+  int ping = 0;
+  if (cur_stride % 4 != 0) {
+    long long rows = h->Ndof / cur_stride;
+    long long sp = (cur_stride + 3) / 4 * 4;
+    launch_pad_rows(s, P[ping], cur, rows, cur_stride, sp);
+    cur = P[ping];
+    cur_stride = sp;
+    ping ^= 1;
+  }
+  for (int k = 0; k < h->d; ++k) {
+    const RotStep &r = st[k];
+    int l = r.l;
+    float *dst = (k == h->d - 1) ? out : P[ping];
+    ProfScope ps(h, PROF_FD_GEMM, 2.0 * h->Ndof * sizeof(float), 2.0 * h->n[l] * (double)h->Ndof);
+    ST_TRY(launch_tc_xform(s, dst, cur, (long long)h->Nt * r.Aa, h->n[l], cur_stride, fwd ? h->UTp[l] : h->Up[l],
+                           h->n[l], h->Npad[l], h->Kpad[l], r.Aa, r.A_inner, r.A_stride, h->tc_err));
+    cur = dst;
+    cur_stride = r.A_stride;
+    ping ^= 1;
+  }
+  return ST_OK;
+}
+
+// z = A-hat^{-1} r by fast diagonalization (Eq. factorized).  Each spatial
+// transform contracts the contiguous axis and writes the result rotated
+// ([T][a][b] -> [T][j][a]), so after the d forward transforms (with U_l^T)
+// the eigen-indices are back in the natural order for the banded LU solves
+// along time, and the d backward transforms (with U_l) restore [T][z][y][x].
+// FP32 transforms run on the tensor cores (TF32) when the self-test passed.
+template <typename T>
 st_status precond_T(st_handle *h, const T *r, T *z) {
   typedef Prec<T> P;
   cudaStream_t s = h->stream;
-  const T *cur = r;
   T *bufs[2] = {P::K(h, 0), P::K(h, 1)};
-  int ping = 0;
   const double vec = (double)h->Ndof * sizeof(T);
-  for (int l = 0; l < h->d; ++l) {
-    ProfScope ps(h, PROF_FD_GEMM, 2 * vec, 2.0 * h->n[l] * (double)h->Ndof);
-    rot_step<T>(h, bufs[ping], cur, l, true);
-    cur = bufs[ping];
-    ping ^= 1;
+  const bool tc = (sizeof(T) == 4) && h->use_tc;
+  if (tc) {
+    ST_TRY(tc_sequence(h, (const float *)r, (float *)bufs[0], true));
+  } else {
+    // r -> ... -> bufs[0], alternating so that no step writes its input
+    const T *cur = r;
+    for (int l = 0; l < h->d; ++l) {
+      T *dst = bufs[(h->d - 1 - l) % 2];
+      ProfScope ps(h, PROF_FD_GEMM, 2 * vec, 2.0 * h->n[l] * (double)h->Ndof);
+      rot_simt<T>(h, dst, cur, l, true);
+      cur = dst;
+    }
   }
   {
     ProfScope ps(h, PROF_FD_LU, vec * (2 + h->B));
-    launch_tline_lu_solve<T>(s, bufs[ping], cur, P::lu(h), h->Nt, h->Ns, h->p);
+    launch_tline_lu_solve<T>(s, bufs[1], bufs[0], P::lu(h), h->Nt, h->Ns, h->p);
   }
-  cur = bufs[ping];
-  ping ^= 1;
-  for (int l = 0; l < h->d; ++l) {
-    T *out = (l == h->d - 1) ? z : bufs[ping];
-    ProfScope ps(h, PROF_FD_GEMM, 2 * vec, 2.0 * h->n[l] * (double)h->Ndof);
-    rot_step<T>(h, out, cur, l, false);
-    cur = out;
-    ping ^= 1;
+  if (tc) {
+    ST_TRY(tc_sequence(h, (const float *)bufs[1], (float *)z, false));
+  } else {
+    const T *cur = bufs[1];
+    for (int l = 0; l < h->d; ++l) {
+      T *dst = (l == h->d - 1) ? z : bufs[l % 2];
+      ProfScope ps(h, PROF_FD_GEMM, 2 * vec, 2.0 * h->n[l] * (double)h->Ndof);
+      rot_simt<T>(h, dst, cur, l, false);
+      cur = dst;
+    }
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;
@@ -641,6 +711,8 @@ static st_status setup_impl(st_handle *h) {
   h->d32 = dalloc<float>(h, h->Ndof, &e);
   h->hcol = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
   if (e != ST_OK) return e;
+  h->P32[0] = dalloc<float>(h, 2 * h->Ndof + 64, &e);
+  h->P32[1] = dalloc<float>(h, 2 * h->Ndof + 64, &e);
   h->tc_err = dalloc<int>(h, 4, &e);
   if (e != ST_OK) return e;
   ST_CUDA(cudaMemsetAsync(h->tc_err, 0, 4 * sizeof(int), h->stream));

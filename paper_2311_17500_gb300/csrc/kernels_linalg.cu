@@ -1280,6 +1280,21 @@ void launch_scale_copy(cudaStream_t s, T *y, const T *x, double alpha, long long
   st_count_launch(); scale_copy_kernel<T><<<grid_for(n), kThreads, 0, s>>>(y, x, alpha, n);
 }
 
+// out[r * stride + k] = in[r * n + k] (rows copied into 16-byte aligned rows)
+__global__ void pad_rows_kernel(float *__restrict__ out, const float *__restrict__ in, long long rows, long long n,
+                                long long stride) {
+  long long total = rows * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e / n, k = e - r * n;
+    out[r * stride + k] = in[e];
+  }
+}
+
+void launch_pad_rows(cudaStream_t s, float *out, const float *in, long long rows, long long n, long long stride) {
+  st_count_launch(); pad_rows_kernel<<<grid_for(rows * n), kThreads, 0, s>>>(out, in, rows, n, stride);
+}
+
 void launch_axpby64(cudaStream_t s, double *y, const double *x, double a, double b, long long n) {
   st_count_launch(); axpby64_kernel<<<grid_for(n), kThreads, 0, s>>>(y, x, a, b, n);
 }

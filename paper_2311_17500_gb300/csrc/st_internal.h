@@ -74,6 +74,7 @@ struct st_handle {
   float *UTp[3] = {}, *Up[3] = {};   // TF32 operands: U_l^T, U_l zero-padded to [Npad][Kpad]
   int Npad[3] = {}, Kpad[3] = {};
   bool use_tc = false;
+  float *P32[2] = {};          // padded-row buffers of the tensor-core transforms
   int *tc_err = nullptr;
   double *lu64 = nullptr;     // [it][k][j], k = 0..2p
   float *lu32 = nullptr;
@@ -179,8 +180,10 @@ template <typename T>
 void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p);
 template <typename T>
 void launch_rot_gemm(cudaStream_t s, T *out, const T *in, const T *M, int nb, int nj, long long Aa, long long Nt);
-st_status launch_tc_rot_gemm(cudaStream_t s, float *out, const float *X, const float *Mpad, long long R, int nb,
-                             int nj, int Npad, int Kpad, long long Aa, int *err);
+st_status launch_tc_xform(cudaStream_t s, float *out, const float *X, long long R, int nb, long long in_stride,
+                          const float *Mpad, int nj, int Npad, int Kpad, long long Aa, long long A_inner,
+                          long long A_in_stride, int *err);
+void launch_pad_rows(cudaStream_t s, float *out, const float *in, long long rows, long long n, long long stride);
 // tensor-core transforms: process-wide self-test state (0 untested, 1 usable, -1 not usable)
 int tc_state(cudaStream_t s, double *err_out);
 template <typename T>
