@@ -41,7 +41,8 @@ typedef enum {
   ST_ERR_BREAKDOWN = 5,      /* zero pivot in a factorization */
   ST_ERR_NAN = 6,            /* NaN or Inf detected in a result */
   ST_ERR_TIMEOUT = 7,        /* a bounded device wait gave up */
-  ST_ERR_STATE = 8           /* call order violated (e.g. st_apply before st_ionic) */
+  ST_ERR_STATE = 8,          /* call order violated (e.g. st_apply before st_ionic) */
+  ST_ERR_CAPACITY = 9        /* problem too large for the fixed scratch of st_wupdate_static */
 } st_status;
 
 /* source kinds: f in eq. 3.1 */
@@ -182,6 +183,38 @@ st_status st_linsolve(st_handle *h, const double *b_dev, double *x_dev, st_stats
 /* w_dev = L^{-1} g(u) (Eq. lin_sys_L): by the exact elimination of Sec. 3.2,
  * w = b (W_t + b d_e M_t)^{-1} M_t applied along time at every spatial index. */
 st_status st_wupdate(st_handle *h, const double *u_dev, double *w_dev);
+
+/* Allocation-free w-update.  The paper has no counterpart: this is the
+ * operation of st_wupdate (Sec. 3.2, w = b (W_t + b d_e M_t)^{-1} M_t applied
+ * along time at every spatial index) without a handle, for callers that
+ * cannot allocate device memory -- e.g. a serving process whose device memory
+ * is committed to admitted requests (admission by st_footprint) or owned by
+ * another allocator, where cudaMalloc may fail and cudaFree would synchronize
+ * the whole device and stall the other requests' streams.
+ *
+ * desc: the problem (only d, p, n_el, n_el_t, T, b, d_e are used; the whole
+ * description must pass the checks of st_setup).  u_dev, w_dev: device
+ * vectors of N_dof FP64 values in the layout above, u_dev != w_dev; w_dev is
+ * overwritten.  cuda_stream: the stream the work is enqueued on (asynchronous;
+ * 0 = legacy default stream).  Result: the same values as st_wupdate on a
+ * handle set up from the same description.
+ *
+ * Memory: no device memory is allocated (no cudaMalloc, cudaFree or
+ * allocating library call).  The two time bands M_t and LU(W_t + b d_e M_t),
+ * 2 N_t (2p+1) FP64 values, are built on the host (ordinary heap vectors)
+ * and copied into one file-scope __device__ array of ST_WUPDATE_STATIC_CAPACITY
+ * doubles (576 KiB; N_t <= 4096 at p = 4) per device.  Larger problems return
+ * ST_ERR_CAPACITY before any work.  Nothing in that array has to start at
+ * zero: each call writes both bands in full before its kernel reads them.
+ * The first call on each device (that device current) looks up the array's
+ * device address with cudaGetSymbolAddress and caches it; make that first
+ * call before any stream capture.
+ *
+ * Concurrency: the array is shared by every call on a device, so calls that
+ * overlap in time (other streams or host threads) race on it; serialize them
+ * on one stream. */
+#define ST_WUPDATE_STATIC_CAPACITY 73728
+st_status st_wupdate_static(const st_problem_desc *desc, const double *u_dev, double *w_dev, void *cuda_stream);
 
 /* Copy the assembled right-hand side f of Eq. (rhsfun) to f_dev (FP64). */
 st_status st_rhs(st_handle *h, double *f_dev);

@@ -6,5 +6,6 @@ a C ABI.  This package holds the in-tree build script and a thin ctypes
 binding; it has no CPU fallback.
 """
 
-from ._lib import (Solver, footprint, load, make_desc, StError,  # noqa: F401
-                   ST_FP64, ST_MIXED, ST_PICARD, ST_NEWTON, EXPORTS)
+from ._lib import (Solver, footprint, load, make_desc, StError, wupdate_static,  # noqa: F401
+                   ST_FP64, ST_MIXED, ST_PICARD, ST_NEWTON, EXPORTS,
+                   ST_ERR_CAPACITY, ST_WUPDATE_STATIC_CAPACITY)

@@ -13,7 +13,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libst.so")
 
 ST_OK, ST_ERR_ARG, ST_ERR_OOM, ST_ERR_CUDA, ST_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
-ST_ERR_BREAKDOWN, ST_ERR_NAN, ST_ERR_TIMEOUT, ST_ERR_STATE = 5, 6, 7, 8
+ST_ERR_BREAKDOWN, ST_ERR_NAN, ST_ERR_TIMEOUT, ST_ERR_STATE, ST_ERR_CAPACITY = 5, 6, 7, 8, 9
+ST_WUPDATE_STATIC_CAPACITY = 73728
 ST_SRC = {"zero": 0, "stim": 1, "heat_mms": 2, "e1_mms": 3}
 ST_GALERKIN, ST_SU = 0, 1
 ST_PICARD, ST_NEWTON = 0, 1
@@ -25,7 +26,7 @@ GET = dict(theta_hat=0, lowrank_s=1, lowrank_u=2, lowrank_v=3, tau_q=4, fd_eig=5
 EXPORTS = ["st_footprint", "st_setup", "st_destroy", "st_error_string", "st_get_dims", "st_ionic",
            "st_linearize", "st_apply", "st_precond", "st_linsolve", "st_wupdate", "st_rhs", "st_solve",
            "st_get", "st_profile", "st_profile_read", "st_launch_count",
-           "st_tc_selftest"]
+           "st_tc_selftest", "st_wupdate_static"]
 STAGES = ["kron", "interp", "qband", "fd_gemm", "fd_lu", "arnoldi", "ionic", "lowrank"]
 
 
@@ -95,6 +96,7 @@ def load(path=None):
     lib.st_precond.argtypes = [vp, i, vp, vp]
     lib.st_linsolve.argtypes = [vp, vp, vp, P(StStats)]
     lib.st_wupdate.argtypes = [vp, vp, vp]
+    lib.st_wupdate_static.argtypes = [P(StProblemDesc), vp, vp, vp]
     lib.st_rhs.argtypes = [vp, vp]
     lib.st_solve.argtypes = [vp, vp, vp, P(StStats)]
     lib.st_get.argtypes = [vp, i, vp, sz]
@@ -159,6 +161,16 @@ def tc_selftest():
     u, e = ctypes.c_int(0), ctypes.c_double(0.0)
     _check(lib.st_tc_selftest(ctypes.byref(u), ctypes.byref(e)), "st_tc_selftest")
     return bool(u.value), e.value
+
+
+def wupdate_static(desc, u_ptr, w_ptr, stream=0):
+    """Handle-free w-update into the library's fixed device scratch
+    (st_wupdate_static); raises StError(ST_ERR_CAPACITY) when
+    2 N_t (2p+1) exceeds ST_WUPDATE_STATIC_CAPACITY doubles."""
+    lib = load()
+    c = make_desc(desc)
+    _check(lib.st_wupdate_static(ctypes.byref(c), ctypes.c_void_p(u_ptr), ctypes.c_void_p(w_ptr),
+                                 ctypes.c_void_p(stream)), "st_wupdate_static")
 
 
 def footprint(desc):

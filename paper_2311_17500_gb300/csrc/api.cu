@@ -557,6 +557,7 @@ const char *st_error_string(st_status s) {
     case ST_ERR_NAN: return "NaN or Inf detected";
     case ST_ERR_TIMEOUT: return "device wait timed out";
     case ST_ERR_STATE: return "invalid call order";
+    case ST_ERR_CAPACITY: return "problem exceeds the fixed scratch of st_wupdate_static (2 N_t (2p+1) > ST_WUPDATE_STATIC_CAPACITY doubles)";
   }
   return "unknown status";
 }
@@ -831,6 +832,18 @@ st_status st_rhs(st_handle *h, double *f) {
 st_status st_wupdate(st_handle *h, const double *u, double *w) {
   if (!h || !u || !w || u == w) return ST_ERR_ARG;
   return wupdate_run(h, u, w);
+}
+
+// Handle-free w-update for callers that cannot allocate device memory: the
+// time bands are built on the host and staged in a fixed device array.
+st_status st_wupdate_static(const st_problem_desc *desc, const double *u, double *w, void *stream) {
+  ST_TRY(validate(desc));
+  if (!u || !w || u == w) return ST_ERR_ARG;
+  const Sizes z = plan(*desc);
+  if (2 * (long long)z.Nt * z.B > ST_WUPDATE_STATIC_CAPACITY) return ST_ERR_CAPACITY;
+  std::vector<double> Mt, lu;
+  ST_TRY(host_time_bands(*desc, Mt, lu));
+  return wupdate_static_run((cudaStream_t)stream, u, w, Mt.data(), lu.data(), desc->b, (int)z.Nt, z.Ns, desc->p);
 }
 
 st_status st_linsolve(st_handle *h, const double *b, double *x, st_stats *stats) {

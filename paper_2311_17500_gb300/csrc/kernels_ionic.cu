@@ -1,6 +1,7 @@
 // Ionic quadrature, Theta-hat, the low-rank theta, the SU and reaction time
 // bands, the right-hand side and the w-update (Sec. 3 and Sec. 3.1).
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include "st_internal.h"
 
@@ -696,6 +697,57 @@ st_status source_assemble(st_handle *h) {
     launch_interp_bwd<double>(s, out, cur, h->Bq[l], h->nel[l], h->p, h->nq, inner, outer, false);
     cur = out;
     ping ^= 1;
+  }
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+// Fixed scratch of the handle-free w-update: M_t at [0, Nt B) and the LU of
+// W_t + b d_e M_t at [Nt B, 2 Nt B), B = 2p+1.  It lives in the module's
+// static device storage, so that call allocates no device memory; every call
+// on a device shares it, and each call rewrites both bands before reading.
+static __device__ __align__(256) double g_wupdate_scratch[ST_WUPDATE_STATIC_CAPACITY];
+
+namespace {
+constexpr int kScratchDevices = 64;
+std::atomic<double *> g_wupdate_scratch_addr[kScratchDevices];
+
+// Device address of the scratch on the current device.  The first call on a
+// device asks the runtime (cudaGetSymbolAddress) and caches the answer.
+st_status wupdate_scratch_addr(double **out) {
+  int dev = 0;
+  ST_CUDA(cudaGetDevice(&dev));
+  if (dev >= 0 && dev < kScratchDevices) {
+    double *p = g_wupdate_scratch_addr[dev].load(std::memory_order_acquire);
+    if (p) { *out = p; return ST_OK; }
+  }
+  void *p = nullptr;
+  ST_CUDA(cudaGetSymbolAddress(&p, g_wupdate_scratch));
+  if (!p) return ST_ERR_CUDA;
+  if (dev >= 0 && dev < kScratchDevices) g_wupdate_scratch_addr[dev].store((double *)p, std::memory_order_release);
+  *out = (double *)p;
+  return ST_OK;
+}
+}  // namespace
+
+st_status wupdate_static_run(cudaStream_t s, const double *u, double *w, const double *Mt_host,
+                             const double *lu_host, double bcoef, int Nt, long long Ns, int p) {
+  const long long band = (long long)Nt * (2 * p + 1);
+  if (Nt < 1 || p < 1 || p > 4 || Ns < 1) return ST_ERR_ARG;
+  if (2 * band > ST_WUPDATE_STATIC_CAPACITY) return ST_ERR_CAPACITY;
+  double *scratch = nullptr;
+  ST_TRY(wupdate_scratch_addr(&scratch));
+  double *Mt = scratch, *lu = scratch + band;
+  // Pageable-host sources: each copy returns once its source has been staged,
+  // and stays ordered on s before the kernel that reads it.
+  ST_CUDA(cudaMemcpyAsync(Mt, Mt_host, band * sizeof(double), cudaMemcpyHostToDevice, s));
+  ST_CUDA(cudaMemcpyAsync(lu, lu_host, band * sizeof(double), cudaMemcpyHostToDevice, s));
+  unsigned blocks = (unsigned)((Ns + 127) / 128);
+  switch (p) {
+    case 1: st_count_launch(); wupdate_kernel<1><<<blocks, 128, 0, s>>>(w, u, Mt, lu, bcoef, Nt, Ns); break;
+    case 2: st_count_launch(); wupdate_kernel<2><<<blocks, 128, 0, s>>>(w, u, Mt, lu, bcoef, Nt, Ns); break;
+    case 3: st_count_launch(); wupdate_kernel<3><<<blocks, 128, 0, s>>>(w, u, Mt, lu, bcoef, Nt, Ns); break;
+    default: st_count_launch(); wupdate_kernel<4><<<blocks, 128, 0, s>>>(w, u, Mt, lu, bcoef, Nt, Ns); break;
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;

@@ -329,3 +329,19 @@ st_status host_setup(const st_problem_desc &d, HostSetup &hs) {
   if (band_lu_inplace(hs.wlu.data(), Nt, p) != 0) return ST_ERR_BREAKDOWN;
   return ST_OK;
 }
+
+// Time bands only (M_t and the banded LU of W_t + b d_e M_t), with the same
+// arithmetic as host_setup; used by the handle-free w-update.
+st_status host_time_bands(const st_problem_desc &d, std::vector<double> &Mt, std::vector<double> &wlu) {
+  int p = d.p;
+  Dir1D td;
+  build_dir(td, d.n_el_t, p, d.T, p);
+  Mt = band_matrix(td, 0, 0, 1);
+  std::vector<double> Wt = band_matrix(td, 0, 1, 1);
+  int Nt = td.n - 1;
+  int B = 2 * p + 1;
+  wlu.assign((size_t)Nt * B, 0.0);
+  for (size_t i = 0; i < wlu.size(); ++i) wlu[i] = Wt[i] + d.b * d.d_e * Mt[i];
+  if (band_lu_inplace(wlu.data(), Nt, p) != 0) return ST_ERR_BREAKDOWN;
+  return ST_OK;
+}

@@ -37,6 +37,8 @@ struct HostSetup {
 };
 
 st_status host_setup(const st_problem_desc &d, HostSetup &hs);
+// M_t and LU(W_t + b d_e M_t) alone, both N_t x (2p+1) banded.
+st_status host_time_bands(const st_problem_desc &d, std::vector<double> &Mt, std::vector<double> &wlu);
 // Banded LU without pivoting in place (n x (2p+1)); stores 1/u_ii on the diagonal.
 int band_lu_inplace(double *a, int n, int p);
 
@@ -208,6 +210,10 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info);
 st_status su_band_add(st_handle *h);
 st_status source_assemble(st_handle *h);
 st_status wupdate_run(st_handle *h, const double *u, double *w);
+// w-update with the time bands taken from host arrays and staged in the
+// file-scope device scratch (no device allocation); Nt (2p+1) values each.
+st_status wupdate_static_run(cudaStream_t s, const double *u, double *w, const double *Mt_host,
+                             const double *lu_host, double bcoef, int Nt, long long Ns, int p);
 
 // eigen / FD
 st_status fd_setup(st_handle *h);
