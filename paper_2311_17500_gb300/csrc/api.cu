@@ -79,7 +79,7 @@ Sizes plan(const st_problem_desc &D) {
   b += (size_t)z.Ndof * f4 * 4;                                    // padded transform buffers
   if (D.precision == ST_FP64) b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * d8;
   else b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * f4;
-  b += (size_t)(608 * (z.m + 48) + 4096) * d8;
+  b += (size_t)(608 * (2 * z.m + 56) + 4096) * d8;
   z.bytes = b;
   return z;
 }
@@ -167,7 +167,8 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
   T *V = basis<T>(h);
   T *Z = zbasis<T>(h);
   int m = std::min(maxit, h->m);
-  double *hd = h->hcol;           // device: h1 [0..m+1], h2 [m+2 .. 2m+3]
+  double *hd = h->hcol;           // device: dots D[0 .. 2(m+2)), then (nu, gam, sw)
+  double *sc = hd + 2 * (m + 2);
   double *scratch = h->red + 4096;
   launch_multi_dot<T>(s, hd, b, N, 1, b, N, scratch);
   double beta = std::sqrt(host_scalar(h, hd));
@@ -177,57 +178,86 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
     *est = std::isfinite(beta) ? 0.0 : INFINITY;
     return std::isfinite(beta) ? ST_OK : ST_ERR_NAN;
   }
-  launch_scale_copy<T>(s, V, b, 1.0 / beta, N);
+  launch_scale_copy<T>(s, V, b, 1.0 / beta, N);   // u_0
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m, 0.0), sn(m, 0.0), g(m + 1, 0.0);
-  std::vector<double> hh(2 * (m + 2) + 2);
-  g[0] = beta;
-  int j = 0;
+  std::vector<double> hh(2 * (m + 2) + 3);
+  // first-projection coefficients of the previous column: <V_i, w> (i < j-1),
+  // <v_{j-1}, w> and the scale of the vector it left behind
+  std::vector<double> bprev(m + 1, 0.0);
+  double gprev = 0.0, sprev = 1.0;
   double res = beta;
-  for (; j < m; ++j) {
-    T *vj = V + (long long)j * ld, *w = V + (long long)(j + 1) * ld, *zj = Z + (long long)j * ld;
-    ST_TRY(precond_T<T>(h, vj, zj));
-    ST_TRY(apply_T<T>(h, zj, w));
-    double *h1 = hd, *h2 = hd + (m + 2);
-    {
-      // CGS2: <V_i, w> for i <= j+1 (the last one is |w|^2), update, again,
-      // then the second update fused with the normalization by Pythagoras
-      double vb = (double)N * sizeof(T);
-      ProfScope ps(h, PROF_ARNOLDI, vb * (4.0 * (j + 1) + 6.0), 8.0 * (j + 1) * (double)N);
-      launch_multi_dot<T>(s, h1, V, ld, j + 2, w, N, scratch);
-      launch_multi_axpy<T>(s, w, V, ld, j + 1, h1, N);
-      launch_multi_dot<T>(s, h2, V, ld, j + 2, w, N, scratch);
-      launch_multi_axpy<T>(s, w, V, ld, j + 1, h2, N, h2 + (j + 1));
+  int k = 0;
+  bool done = false;
+  // Givens rotations of the finished column c, residual estimate |g[c+1]|
+  auto close_column = [&](int c) {
+    for (int i = 0; i < c; ++i) {
+      double a = H[(size_t)i * m + c], e = H[(size_t)(i + 1) * m + c];
+      H[(size_t)i * m + c] = cs[i] * a + sn[i] * e;
+      H[(size_t)(i + 1) * m + c] = -sn[i] * a + cs[i] * e;
     }
-    // Hessenberg column and the device error flag of the tensor-core transforms
-    ST_CUDA(cudaMemcpyAsync(hh.data(), hd, 2 * (m + 2) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    double a = H[(size_t)c * m + c], e = H[(size_t)(c + 1) * m + c];
+    double r = std::hypot(a, e);
+    cs[c] = r > 0 ? a / r : 1.0;
+    sn[c] = r > 0 ? e / r : 0.0;
+    H[(size_t)c * m + c] = r;
+    H[(size_t)(c + 1) * m + c] = 0.0;
+    g[c + 1] = -sn[c] * g[c];
+    g[c] = cs[c] * g[c];
+    res = std::fabs(g[c + 1]);
+  };
+  // column c = j-1 from its first projection and the reorthogonalization of
+  // u_j (a_i = <V_i, u_j>, nu = |u_j - V a|):  A z_c = V (b + a/s) + (nu/s) v_j
+  auto finish_column = [&](int j, const double *a, double nu) {
+    const int c = j - 1;
+    for (int i = 0; i < c; ++i) H[(size_t)i * m + c] = bprev[i] + a[i] / sprev;
+    H[(size_t)c * m + c] = gprev + a[c] / sprev;
+    H[(size_t)j * m + c] = nu / sprev;
+    close_column(c);
+  };
+  std::vector<double> acol(m + 1);
+  int j = 0;
+  for (; j < m; ++j) {
+    T *uj = V + (long long)j * ld, *w = V + (long long)(j + 1) * ld, *zj = Z + (long long)j * ld;
+    ST_TRY(precond_T<T>(h, uj, zj));
+    ST_TRY(apply_T<T>(h, zj, w));
+    {
+      // delayed CGS2: one dot pass of [V_0..V_{j-1}, u_j, w] against (u_j, w),
+      // one update pass writing v_j and u_{j+1}
+      double vb = (double)N * sizeof(T);
+      ProfScope ps(h, PROF_ARNOLDI, vb * (2.0 * (j + 2) + 2.0), 8.0 * (j + 2) * (double)N);
+      launch_multi_dot2<T>(s, hd, V, ld, j + 2, uj, w, N, scratch);
+      launch_dcgs2_update<T>(s, V, ld, j, hd, N, sc);
+    }
+    ST_CUDA(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     int tc_flag = 0;
     if (h->use_tc && sizeof(T) == 4) ST_CUDA(cudaMemcpyAsync(&tc_flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ST_CUDA(cudaStreamSynchronize(s));
     if (tc_flag) return ST_ERR_TIMEOUT;
-    double q = hh[(m + 2) + (j + 1)];
-    for (int i = 0; i <= j; ++i) q -= hh[(m + 2) + i] * hh[(m + 2) + i];
-    double hnorm = q > 0.0 ? std::sqrt(q) : 0.0;
-    if (!std::isfinite(hnorm) || !std::isfinite(hh[j + 1])) return ST_ERR_NAN;
-    for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[(m + 2) + i];
-    H[(size_t)(j + 1) * m + j] = hnorm;
-    // apply the previous Givens rotations to the new column, then a new one
-    for (int i = 0; i < j; ++i) {
-      double a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
-      H[(size_t)i * m + j] = cs[i] * a + sn[i] * c;
-      H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+    const double nu = hh[2 * (m + 2)], gam = hh[2 * (m + 2) + 1], sw = hh[2 * (m + 2) + 2];
+    if (!std::isfinite(nu) || !std::isfinite(gam) || !std::isfinite(sw)) return ST_ERR_NAN;
+    if (j == 0) {
+      g[0] = beta * nu;   // b = beta u_0 = beta nu v_0
+    } else {
+      for (int i = 0; i < j; ++i) acol[i] = hh[2 * i];
+      finish_column(j, acol.data(), nu);
+      if (res <= tol * beta || nu == 0.0) { k = j; done = true; break; }
     }
-    double a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
-    double r = std::hypot(a, c);
-    cs[j] = r > 0 ? a / r : 1.0;
-    sn[j] = r > 0 ? c / r : 0.0;
-    H[(size_t)j * m + j] = r;
-    H[(size_t)(j + 1) * m + j] = 0.0;
-    g[j + 1] = -sn[j] * g[j];
-    g[j] = cs[j] * g[j];
-    res = std::fabs(g[j + 1]);
-    if (res <= tol * beta || hnorm == 0.0) { ++j; break; }
+    for (int i = 0; i < j; ++i) bprev[i] = hh[2 * i + 1];
+    gprev = gam;
+    sprev = sw;
   }
-  int k = j;   // columns used
+  if (!done) {
+    // the last column: reorthogonalization dots of u_m alone
+    launch_multi_dot<T>(s, hd, V, ld, m + 1, V + (long long)m * ld, N, scratch);
+    ST_CUDA(cudaMemcpyAsync(hh.data(), hd, (m + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaStreamSynchronize(s));
+    double q = hh[m];
+    for (int i = 0; i < m; ++i) q -= hh[i] * hh[i];
+    const double nu = q > 0.0 ? std::sqrt(q) : 0.0;
+    if (!std::isfinite(nu)) return ST_ERR_NAN;
+    finish_column(m, hh.data(), nu);
+    k = m;
+  }
   // back substitution H(0:k,0:k) y = g(0:k)
   std::vector<double> y(k, 0.0);
   for (int i = k - 1; i >= 0; --i) {
@@ -241,7 +271,7 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
   ST_CUDA(cudaMemcpyAsync(hd, y.data(), std::max(k, 1) * sizeof(double), cudaMemcpyHostToDevice, s));
   ST_CUDA(cudaMemsetAsync(d, 0, N * sizeof(T), s));
   if (k > 0) launch_multi_axpy<T>(s, d, Z, ld, k, hd, N);
-  *its = k;
+  *its = done ? k + 1 : k;   // operator applications (a converged cycle has one past its last column)
   *est = res / beta;
   ST_CUDA(cudaStreamSynchronize(s));
   return ST_OK;
@@ -384,6 +414,43 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   long long nd[3] = {h->n[0], h->n[1], h->n[2]};
   const T *cur = x;
   int ping = 0;
+  if (h->d >= 2 && (h->nel[0] + p + 31) / 32 * 32 <= xband_fused_limit(sizeof(T), p)) {
+    // the other axes to their Gauss points (last axis first), x kept in
+    // coefficients; then the fused x pass; then the other axes back, the
+    // last one accumulated onto the Kronecker part
+    for (int l = h->d - 1; l >= 1; --l) {
+      long long inner = 1, outer = Nt;
+      for (int k = 0; k < l; ++k) inner *= nd[k];
+      for (int k = l + 1; k < h->d; ++k) outer *= qd[k];
+      T *out = P::W(h, ping);
+      ProfScope ps(h, PROF_INTERP, sz * (double)outer * inner * (h->n[l] + (double)h->Q[l]));
+      launch_interp_fwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer);
+      cur = out;
+      ping ^= 1;
+    }
+    long long rows = 1;
+    for (int k = 1; k < h->d; ++k) rows *= qd[k];
+    T *Y1 = P::W(h, ping);
+    {
+      ProfScope ps(h, PROF_QBAND, sz * ((double)(p + 1) * h->NtQs + 2.0 * (double)Nt * rows * nx));
+      launch_xband_fused<T>(s, Y1, cur, P::band(h), P::Bq(h, 0), h->nel[0], (int)Nt, rows, p);
+    }
+    cur = Y1;
+    ping ^= 1;
+    for (int l = 1; l < h->d; ++l) {
+      long long inner = 1, outer = Nt;
+      for (int k = 0; k < l; ++k) inner *= nd[k];
+      for (int k = l + 1; k < h->d; ++k) outer *= qd[k];
+      const bool last = l == h->d - 1;
+      T *out = last ? y : P::W(h, ping);
+      ProfScope ps(h, PROF_INTERP, sz * (double)outer * inner * (h->n[l] * (last ? 2.0 : 1.0) + (double)h->Q[l]));
+      launch_interp_bwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer, last);
+      cur = out;
+      ping ^= 1;
+    }
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+  }
   for (int l = 0; l < h->d; ++l) {
     long long inner = 1, outer = Nt;
     for (int k = 0; k < l; ++k) inner *= qd[k];
@@ -692,7 +759,7 @@ static st_status setup_impl(st_handle *h) {
   h->U0 = dalloc<double>(h, h->NtQs, &e);
   h->L0 = dalloc<double>(h, h->NtQs, &e);
   h->Wq0 = dalloc<double>(h, h->NtQs, &e);
-  h->red = dalloc<double>(h, 4096 + 608 * (size_t)(h->m + 48), &e);
+  h->red = dalloc<double>(h, 4096 + 608 * (size_t)(2 * h->m + 56), &e);
   if (D.precision == ST_FP64) {
     h->V64 = dalloc<double>(h, (size_t)(h->m + 1) * h->ldv, &e);
     h->Z64 = dalloc<double>(h, (size_t)h->m * h->ldv, &e);

@@ -482,6 +482,177 @@ st_status jacobi32(st_handle *h, const double *A64, int n, double *X64) {
 }
 
 
+
+// ---------------------------------------------------------------------------
+// Lanczos with full reorthogonalization for the leading eigenpairs of the
+// Gram matrix (symmetric positive semidefinite, FP64, one thread block, the
+// matrix read from L2).  Steps j = j0 .. j1-1 extend the orthonormal basis
+// Q (rows q_0 .. q_j1) and the tridiagonal T (alpha_j on the diagonal, beta_j
+// coupling j and j+1); the new vector is orthogonalized against all earlier
+// ones by classical Gram-Schmidt applied twice.  A step whose beta does not
+// exceed `tiny` has found an invariant subspace: the run stops there and
+// *kdone = j+1 (else j1).  All reductions are in a fixed order.
+constexpr int kLzThreads = 1024;
+
+__device__ __forceinline__ double lz_warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; every thread receives the same value.
+__device__ double lz_block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = lz_warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  return lz_warp_sum(lane < nw ? red[lane] : 0.0);
+}
+
+__global__ void __launch_bounds__(kLzThreads) lanczos_kernel(const double *__restrict__ G, int n, double *Q,
+                                                             double *alpha, double *beta, int j0, int j1,
+                                                             double tiny, int *kdone) {
+  extern __shared__ double lz_sh[];
+  double *w = lz_sh;        // [n]
+  double *hc = lz_sh + n;   // [j1 + 1] Gram-Schmidt coefficients
+  __shared__ double red[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int j = j0; j < j1; ++j) {
+    const double *qj = Q + (size_t)j * n;
+    for (int i = warp; i < n; i += nw) {
+      const double *gr = G + (size_t)i * n;
+      double v = 0.0;
+      for (int c = lane; c < n; c += 32) v += gr[c] * qj[c];
+      v = lz_warp_sum(v);
+      if (lane == 0) w[i] = v;
+    }
+    __syncthreads();
+    if (j > 0) {
+      const double *qp = Q + (size_t)(j - 1) * n;
+      const double b = beta[j - 1];
+      for (int i = tid; i < n; i += blockDim.x) w[i] -= b * qp[i];
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int i = tid; i < n; i += blockDim.x) part += qj[i] * w[i];
+    const double a = lz_block_sum(part, red);
+    for (int i = tid; i < n; i += blockDim.x) w[i] -= a * qj[i];
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int m = warp; m <= j; m += nw) {
+        const double *qm = Q + (size_t)m * n;
+        double v = 0.0;
+        for (int i = lane; i < n; i += 32) v += qm[i] * w[i];
+        v = lz_warp_sum(v);
+        if (lane == 0) hc[m] = v;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += blockDim.x) {
+        double v = w[i];
+        for (int m = 0; m <= j; ++m) v -= hc[m] * Q[(size_t)m * n + i];
+        w[i] = v;
+      }
+      __syncthreads();
+    }
+    part = 0.0;
+    for (int i = tid; i < n; i += blockDim.x) part += w[i] * w[i];
+    const double b = sqrt(lz_block_sum(part, red));
+    if (tid == 0) { alpha[j] = a; beta[j] = b; }
+    if (!(b > tiny)) {
+      if (tid == 0) *kdone = j + 1;
+      return;
+    }
+    double *qn = Q + (size_t)(j + 1) * n;
+    const double inv = 1.0 / b;
+    for (int i = tid; i < n; i += blockDim.x) qn[i] = w[i] * inv;
+    __syncthreads();
+  }
+  if (tid == 0) *kdone = j1;
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below x (Sturm
+// sequence of the LDL^T pivots of T - x I).
+int sturm_below(int k, const double *d, const double *e, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (int i = 0; i < k; ++i) {
+    q = (d[i] - x) - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// r-th largest eigenvalue (r = 1..k) of the tridiagonal by bisection on the
+// Sturm count, to full double precision.
+double tridiag_eig_bisect(int k, const double *d, const double *e, int r, double lo, double hi) {
+  for (int it = 0; it < 400 && hi - lo > 4e-16 * std::max(std::fabs(lo), std::fabs(hi)); ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_below(k, d, e, mid) >= k - r + 1) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Eigenvector of the tridiagonal for the eigenvalue th by inverse iteration:
+// three solves with T - th I, each followed by orthogonalization against
+// `prev` (vectors of nearby eigenvalues) and normalization.  The solve is
+// Gaussian elimination with partial pivoting, carried as one running row:
+// row i of U has entries at columns i, i+1 and (after a row swap) i+2; a zero
+// pivot is replaced by a tiny multiple of ||T||.
+void tridiag_eigvec(int k, const double *d, const double *e, double th, double tnorm,
+                    const std::vector<const double *> &prev, double *y) {
+  std::vector<double> U0(k), U1(k), U2(k), z(k);
+  const double small = 1e-300 + 1e-15 * tnorm;
+  double nrm = 0.0;
+  for (int i = 0; i < k; ++i) {
+    y[i] = 1.0 + 0.1 * ((i * 7919) % 13);
+    nrm += y[i] * y[i];
+  }
+  for (int i = 0; i < k; ++i) y[i] /= std::sqrt(nrm);
+  for (int iter = 0; iter < 3; ++iter) {
+    // running row: entries at columns i, i+1 (column i+2 is zero), rhs
+    double c0 = d[0] - th, c1 = k > 1 ? e[0] : 0.0, cr = y[0];
+    for (int i = 0; i + 1 < k; ++i) {
+      const double n0 = e[i], n1 = d[i + 1] - th, n2 = i + 2 < k ? e[i + 1] : 0.0, nr = y[i + 1];
+      double p0, p1, p2, pr, o0, o1, o2, orr;
+      if (std::fabs(n0) > std::fabs(c0)) {
+        p0 = n0; p1 = n1; p2 = n2; pr = nr;
+        o0 = c0; o1 = c1; o2 = 0.0; orr = cr;
+      } else {
+        p0 = c0; p1 = c1; p2 = 0.0; pr = cr;
+        o0 = n0; o1 = n1; o2 = n2; orr = nr;
+      }
+      if (p0 == 0.0) p0 = small;
+      U0[i] = p0; U1[i] = p1; U2[i] = p2; z[i] = pr;
+      const double m = o0 / p0;
+      c0 = o1 - m * p1;
+      c1 = o2 - m * p2;
+      cr = orr - m * pr;
+    }
+    U0[k - 1] = c0 == 0.0 ? small : c0;
+    U1[k - 1] = 0.0; U2[k - 1] = 0.0; z[k - 1] = cr;
+    for (int i = k - 1; i >= 0; --i) {
+      double v = z[i];
+      if (i + 1 < k) v -= U1[i] * y[i + 1];
+      if (i + 2 < k) v -= U2[i] * y[i + 2];
+      y[i] = v / U0[i];
+    }
+    for (const double *pv : prev) {
+      double dot = 0.0;
+      for (int i = 0; i < k; ++i) dot += pv[i] * y[i];
+      for (int i = 0; i < k; ++i) y[i] -= dot * pv[i];
+    }
+    nrm = 0.0;
+    for (int i = 0; i < k; ++i) nrm += y[i] * y[i];
+    nrm = std::sqrt(nrm);
+    if (!(nrm > 0.0) || !std::isfinite(nrm)) return;
+    for (int i = 0; i < k; ++i) y[i] /= nrm;
+  }
+}
+
 }  // namespace
 
 // Eigenpairs of the dense symmetric n x n matrix A (device), eigenvalues
@@ -503,6 +674,116 @@ st_status sym_eig_desc(st_handle *h, const double *A, int n, double *evec, doubl
 // Fast-diagonalization set-up (Sec. 3.2): for every spatial direction the
 // generalized eigendecomposition of (D_ll K_l, M_l) with M_l-orthonormal
 // eigenvectors, then one banded LU per spatial eigenvalue.
+// Leading eigenpairs of the Gram matrix G (n x n, device) for the low-rank
+// step (Eq. tol): Lanczos on the device, Rayleigh-Ritz on the tridiagonal on
+// the host.  R is the smallest r with tr - sum_{i<=r} theta_i <= eps^2 tr over
+// the Ritz values theta (which never exceed the eigenvalues they approach);
+// the run extends the basis in batches until the Ritz pairs 1..R have
+// residual estimates beta_k |s_{k,i}| <= 1e-14 theta_1, or the basis spans an
+// invariant subspace.  On success Ur (n x R, row-major) holds the Ritz
+// vectors and lam the Ritz values; ST_ERR_NOT_CONVERGED when kmax basis
+// vectors did not suffice (the caller then takes the full decomposition).
+st_status gram_top_eigs(st_handle *h, const double *G, int n, double tr, double eps, int cap, double *Ur, int *R_out,
+                        std::vector<double> &lam) {
+  cudaStream_t s = h->stream;
+  const int kmax = std::min(n, 192);
+  size_t shb = (size_t)(n + kmax + 2) * sizeof(double);
+  if (shb > 200 * 1024) return ST_ERR_NOT_CONVERGED;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(lanczos_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
+  double *Q = h->eig_work;                       // (kmax + 1) x n
+  double *ab = Q + (size_t)(kmax + 1) * n;       // alpha[kmax], beta[kmax]
+  double *Sd = ab + 2 * kmax;                    // k x R coefficients of the Ritz vectors
+  int *kd = (int *)(Sd + (size_t)kmax * kmax);
+  // deterministic pseudo-random start vector (splitmix64), normalized
+  std::vector<double> q0(n);
+  unsigned long long st = 0x9e3779b97f4a7c15ull;
+  double nrm = 0.0;
+  for (int i = 0; i < n; ++i) {
+    st += 0x9e3779b97f4a7c15ull;
+    unsigned long long z = st;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    z ^= z >> 31;
+    q0[i] = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    nrm += q0[i] * q0[i];
+  }
+  nrm = std::sqrt(nrm);
+  for (double &v : q0) v /= nrm;
+  ST_CUDA(cudaMemcpyAsync(Q, q0.data(), n * sizeof(double), cudaMemcpyHostToDevice, s));
+  const double tiny = 1e-15 * tr;
+  std::vector<double> al(kmax), be(kmax);
+  int k = 0;
+  while (k < kmax) {
+    const int k1 = std::min(kmax, k + (k == 0 ? 24 : 16));
+    size_t sh = (size_t)(n + k1 + 1) * sizeof(double);
+    st_count_launch();
+    lanczos_kernel<<<1, kLzThreads, sh, s>>>(G, n, Q, ab, ab + kmax, k, k1, tiny, kd);
+    ST_CUDA(cudaGetLastError());
+    int kdone = 0;
+    ST_CUDA(cudaMemcpyAsync(&kdone, kd, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaMemcpyAsync(al.data(), ab, k1 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaMemcpyAsync(be.data(), ab + kmax, k1 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaStreamSynchronize(s));
+    if (kdone < 1 || kdone > k1) return ST_ERR_CUDA;
+    for (int i = 0; i < kdone; ++i)
+      if (!std::isfinite(al[i]) || !std::isfinite(be[i])) return ST_ERR_NAN;
+    k = kdone;
+    const bool exact = kdone < k1 || k == n;   // invariant subspace, or the whole space
+    // Ritz values, descending, until the kept energy reaches (1 - eps^2) tr
+    double lo = al[0], hi = al[0], tnorm = 0.0;
+    for (int i = 0; i < k; ++i) {
+      double rad = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(be[i]) : 0.0);
+      lo = std::min(lo, al[i] - rad);
+      hi = std::max(hi, al[i] + rad);
+      tnorm = std::max(tnorm, std::fabs(al[i]) + rad);
+    }
+    std::vector<double> theta;
+    double kept = 0.0;
+    int R = -1;
+    double upper = hi;
+    for (int r = 1; r <= k; ++r) {
+      double th = tridiag_eig_bisect(k, al.data(), be.data(), r, lo, upper);
+      theta.push_back(th);
+      upper = th + 4e-16 * std::fabs(th) + 1e-300;
+      kept += std::max(th, 0.0);
+      if (tr - kept <= eps * eps * tr) { R = r; break; }
+    }
+    if (R < 0) {
+      if (exact) R = k;
+      else continue;
+    }
+    // Ritz vectors of T for the pairs 1..R and their residual estimates
+    std::vector<double> Y((size_t)R * k);
+    std::vector<const double *> prev;
+    bool converged = true;
+    for (int r = 0; r < R; ++r) {
+      prev.clear();
+      for (int q = 0; q < r; ++q)
+        if (std::fabs(theta[q] - theta[r]) <= 1e-8 * tnorm) prev.push_back(&Y[(size_t)q * k]);
+      tridiag_eigvec(k, al.data(), be.data(), theta[r], tnorm, prev, &Y[(size_t)r * k]);
+      double res = std::fabs(be[k - 1] * Y[(size_t)r * k + k - 1]);
+      if (!(res <= 1e-14 * theta[0])) converged = false;
+    }
+    if (!converged && !exact) continue;
+    if (R > cap) R = cap;
+    // Ur = Q^T S with S[m][r] = Y[r][m]  (n x R)
+    std::vector<double> S((size_t)k * R);
+    for (int m = 0; m < k; ++m)
+      for (int r = 0; r < R; ++r) S[(size_t)m * R + r] = Y[(size_t)r * k + m];
+    ST_CUDA(cudaMemcpyAsync(Sd, S.data(), S.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    launch_gemm64(s, Ur, Q, Sd, n, R, k, 1, n, R, 1, R, 1, 1.0, 0.0);
+    ST_CUDA(cudaStreamSynchronize(s));   // S lives on the host stack of this call
+    lam.assign(theta.begin(), theta.begin() + R);
+    *R_out = R;
+    return ST_OK;
+  }
+  return ST_ERR_NOT_CONVERGED;
+}
+
 st_status fd_setup(st_handle *h) {
   cudaStream_t s = h->stream;
   const st_problem_desc &D = h->desc;

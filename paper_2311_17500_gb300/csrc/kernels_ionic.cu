@@ -610,28 +610,35 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
     if (info) info->rank = 0;
     return ST_OK;
   }
-  // eigen-decomposition of G on the device (eigenvalues descending)
-  ST_TRY(sym_eig_desc(h, h->gram, Nt, h->evec, h->eval));
-  std::vector<double> lam(Nt);
-  ST_CUDA(cudaMemcpyAsync(lam.data(), h->eval, Nt * sizeof(double), cudaMemcpyDeviceToHost, s));
-  ST_CUDA(cudaStreamSynchronize(s));
-  // smallest R with ||Theta - U S V^T||_F^2 = tr - sum_{i<R} lam_i <= eps^2 tr (Eq. tol)
+  // leading eigenpairs of G and the rank R: smallest R with
+  // ||Theta - U S V^T||_F^2 = tr - sum_{i<=R} lam_i <= eps^2 tr (Eq. tol)
   double eps = D.eps_theta;
-  double kept = 0.0;
-  int R = Nt;
-  for (int r = 1; r <= Nt; ++r) {
-    kept += std::max(lam[r - 1], 0.0);
-    if (tr - kept <= eps * eps * tr) { R = r; break; }
+  std::vector<double> lam;
+  int R = 0;
+  st_status lz = gram_top_eigs(h, h->gram, Nt, tr, eps, h->rank_cap, h->Ur, &R, lam);
+  if (lz == ST_ERR_NAN) return lz;
+  if (lz != ST_OK) {
+    // full decomposition (eigenvalues descending) when Lanczos did not settle
+    ST_TRY(sym_eig_desc(h, h->gram, Nt, h->evec, h->eval));
+    lam.assign(Nt, 0.0);
+    ST_CUDA(cudaMemcpyAsync(lam.data(), h->eval, Nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaStreamSynchronize(s));
+    double kept = 0.0;
+    R = Nt;
+    for (int r = 1; r <= Nt; ++r) {
+      kept += std::max(lam[r - 1], 0.0);
+      if (tr - kept <= eps * eps * tr) { R = r; break; }
+    }
+    if (R > h->rank_cap) R = h->rank_cap;
+    // U_R (N_t x R) = first R columns of evec (evec[i][c], c sorted descending)
+    ST_CUDA(cudaMemcpy2DAsync(h->Ur, R * sizeof(double), h->evec, Nt * sizeof(double), R * sizeof(double), Nt,
+                              cudaMemcpyDeviceToDevice, s));
   }
-  if (R > h->rank_cap) R = h->rank_cap;
   h->rank = R;
   if (info) info->rank = R;
-  // U_R (N_t x R) = first R columns of evec (evec[i][c], c sorted descending)
   std::vector<double> sig(R);
   for (int r = 0; r < R; ++r) sig[r] = std::sqrt(std::max(lam[r], 0.0));
   ST_CUDA(cudaMemcpyAsync(h->sr, sig.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
-  ST_CUDA(cudaMemcpy2DAsync(h->Ur, R * sizeof(double), h->evec, Nt * sizeof(double), R * sizeof(double), Nt,
-                            cudaMemcpyDeviceToDevice, s));
   // V = Theta^T U_R diag(1/sigma): (N_s x R)
   launch_gemm64(s, h->Vr, h->theta, h->Ur, (int)h->Ns, R, Nt, 1, h->Ns, R, 1, R, 1, 1.0, 0.0);
   st_count_launch(); scale_cols_kernel<<<grid_for(h->Ns * R), 256, 0, s>>>(h->Vr, h->sr, R, h->Ns);

@@ -753,6 +753,262 @@ __global__ void qband_kernel(T *__restrict__ z, const T *__restrict__ x, const T
   }
 }
 
+// Per-thread asynchronous copies (cp.async, 4 or 8 bytes) into shared memory.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T *smem, const T *gmem) {
+  unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// nq consecutive values into shared memory with 16-byte copies where the
+// size allows (addresses aligned as for load_nq), else element by element.
+template <typename T, int NQ>
+__device__ __forceinline__ void cp_async_nq(T *smem, const T *gmem) {
+  constexpr int bytes = NQ * (int)sizeof(T);
+  if constexpr (bytes % 16 == 0) {
+#pragma unroll
+    for (int c = 0; c < bytes / 16; ++c) {
+      unsigned sa = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char *>(smem) + 16 * c);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(reinterpret_cast<const char *>(gmem) + 16 * c)
+                   : "memory");
+    }
+  } else if constexpr (bytes == 8) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+  } else {
+#pragma unroll
+    for (int g = 0; g < NQ; ++g) cp_async_elem(smem + g, gmem + g);
+  }
+}
+
+// nq consecutive band values of one element (vector loads where aligned:
+// nq = 4 floats or doubles start on a 16-byte boundary, nq = 2 on 8 bytes).
+template <typename T, int NQ>
+__device__ __forceinline__ void load_nq(T (&v)[NQ], const T *p) {
+  if constexpr (NQ == 4 && sizeof(T) == 4) {
+    float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else if constexpr (NQ == 4 && sizeof(T) == 8) {
+    double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    double2 b = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+  } else if constexpr (NQ == 2 && sizeof(T) == 4) {
+    float2 a = __ldg(reinterpret_cast<const float2 *>(p));
+    v[0] = a.x; v[1] = a.y;
+  } else {
+#pragma unroll
+    for (int g = 0; g < NQ; ++g) v[g] = __ldg(p + g);
+  }
+}
+
+// nq consecutive values from shared memory (16-byte aligned slots).
+template <typename T, int NQ>
+__device__ __forceinline__ void load_nq_shared(T (&v)[NQ], const T *p) {
+  if constexpr (NQ == 4 && sizeof(T) == 4) {
+    float4 a = *reinterpret_cast<const float4 *>(p);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+  } else {
+#pragma unroll
+    for (int g = 0; g < NQ; ++g) v[g] = p[g];
+  }
+}
+
+// Reaction + SU part of the operator (the M_R and S-tilde terms of Sec. 3.1.1,
+// both folded into one symmetric time band per spatial Gauss point), fused
+// along the fastest spatial axis:  Y1 = Bx^T (band) Bx X1  for every row o of
+// the other axes (already at their Gauss points) and every time step.
+//   X1, Y1 : [Nt][rows][nx]        x-coefficients of each Gauss row
+//   band   : [k][Nt][rows][Qx]     band[k][it] = T(it, it+k), k = 0..P
+//   tab    : [ex][g][a]            local basis a at Gauss point g of element ex
+// One block per (row, time segment), one thread per x element (its nq Gauss
+// points) plus P threads for the trailing coefficients (at most 512 threads,
+// 256 for FP64 or p = 4 so that the window stays in registers).  The block
+// sweeps its segment with a register window x(it..it+P) per Gauss point and
+// scatters the lower-triangle terms band[k][it] x(it) into accumulators of
+// the steps it+k; a segment first replays the P steps before it (band and x,
+// no output) to rebuild those accumulators, so every output is complete and
+// each band entry is read once plus a halo of P(P+1)/2 rows per segment.
+// Operands stream through an S-step ring in shared memory filled by cp.async
+// S-1 steps ahead: each thread copies its element's band values and its own
+// x coefficient of row it+P.  One barrier per step publishes the coefficient
+// row and the cross-warp partial sums of the previous step: the projection
+// onto coefficient ex+a collects the contributions of elements ex-a..ex by
+// warp shuffles, and across warps through shared memory, in a fixed order.
+template <typename T, int P>
+constexpr int xband_max_threads() { return (sizeof(T) == 8 || P >= 4) ? 256 : 512; }
+
+template <typename T, int P, int S>
+__global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(T *__restrict__ Y1, const T *__restrict__ X1,
+                                                           const T *__restrict__ band, const T *__restrict__ tab,
+                                                           int nel, int Nt, long long rows, int seglen) {
+  constexpr int nq = P + 1;
+  static_assert(S >= 2, "ring depth");
+  __shared__ T xch[2][16][P][P];   // [step parity][warp][a-1][lane-(32-P)]
+  extern __shared__ __align__(16) unsigned char xb_raw[];
+  const int nth = blockDim.x;
+  T *bring = reinterpret_cast<T *>(xb_raw);              // [S][P+1][thread][nq]
+  T *xring = bring + (size_t)S * (P + 1) * nth * nq;     // [S][thread]
+  const int nx = nel + P, Qx = nel * nq;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const bool owns = t < nel;
+  T wv[nq][P + 1];
+#pragma unroll
+  for (int g = 0; g < nq; ++g)
+#pragma unroll
+    for (int a = 0; a <= P; ++a) wv[g][a] = owns ? __ldg(tab + ((size_t)t * nq + g) * (P + 1) + a) : T(0);
+  const long long planeX = rows * nx, planeQ = rows * Qx, bandK = (long long)Nt * planeQ;
+  const int nseg = (Nt + seglen - 1) / seglen;
+  for (long long blk = blockIdx.x; blk < rows * nseg; blk += gridDim.x) {
+    const long long o = blk % rows;
+    const int t0 = (int)(blk / rows) * seglen, t1 = min(Nt, t0 + seglen);
+    const T *xrow = X1 + o * nx + t;
+    const T *brow = band + o * Qx + (long long)t * nq;
+    T *yrow = Y1 + o * nx;
+    auto gauss = [&](const T (&c)[P + 1], T (&xq)[nq]) {
+#pragma unroll
+      for (int g = 0; g < nq; ++g) {
+        T v = T(0);
+#pragma unroll
+        for (int a = 0; a <= P; ++a) v += wv[g][a] * c[a];
+        xq[g] = v;
+      }
+    };
+    auto interp_global = [&](int it, T (&xq)[nq]) {
+      T c[P + 1];
+#pragma unroll
+      for (int a = 0; a <= P; ++a) c[a] = (owns && it >= 0 && it < Nt) ? xrow[(long long)it * planeX + a] : T(0);
+      gauss(c, xq);
+    };
+    T acc[P][nq];      // lower-triangle terms owed to steps it .. it+P-1
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+#pragma unroll
+      for (int g = 0; g < nq; ++g) acc[k][g] = T(0);
+    // replay steps t0-P .. t0-1: band[k][it'] x(it') owed to t0 + m, m = it'+k-t0
+#pragma unroll
+    for (int r = P; r >= 1; --r) {
+      const int itp = t0 - r;
+      if (itp < 0 || !owns) continue;
+      T xp[nq];
+      interp_global(itp, xp);
+#pragma unroll
+      for (int k = 1; k <= P; ++k) {
+        const int m = k - r;
+        if (m < 0) continue;
+        T bv[nq];
+        load_nq<T, nq>(bv, brow + k * bandK + (long long)itp * planeQ);
+#pragma unroll
+        for (int g = 0; g < nq; ++g) acc[m][g] += bv[g] * xp[g];
+      }
+    }
+    T xw[P + 1][nq];   // x(it + k) at the element's Gauss points
+#pragma unroll
+    for (int k = 0; k < P; ++k) interp_global(t0 + k, xw[k + 1]);
+    // step u needs band row u and coefficient row u + P
+    auto bslot = [&](int u, int k) -> T * { return bring + ((size_t)((u % S) * (P + 1) + k) * nth + t) * nq; };
+    auto xslot = [&](int u) -> T * { return xring + (size_t)(u % S) * nth; };
+    auto issue = [&](int u) {
+      if (u < t1) {
+        if (owns) {
+#pragma unroll
+          for (int k = 0; k <= P; ++k) cp_async_nq<T, nq>(bslot(u, k), brow + k * bandK + (long long)u * planeQ);
+        }
+        if (t < nx && u + P < Nt) cp_async_elem(xslot(u) + t, X1 + (long long)(u + P) * planeX + o * nx + t);
+      }
+      cp_async_commit();
+    };
+#pragma unroll
+    for (int u = 0; u < S - 1; ++u) issue(t0 + u);
+    T pend = T(0);   // this thread's output of the previous step, before its cross-warp part
+    for (int it = t0; it < t1; ++it) {
+      cp_async_wait<S - 2>();
+      __syncthreads();
+      if (it > t0) {
+        const int pp = (it - 1) & 1;
+        if (lane < P && warp > 0) {
+#pragma unroll
+          for (int a = 1; a <= P; ++a)
+            if (a > lane) pend += xch[pp][warp - 1][a - 1][lane + P - a];
+        }
+        if (t < nx) yrow[(long long)(it - 1) * planeX + t] = pend;
+      }
+      issue(it + S - 1);
+      T b[P + 1][nq];
+#pragma unroll
+      for (int k = 0; k <= P; ++k) {
+        if (owns) load_nq_shared<T, nq>(b[k], bslot(it, k));
+        else {
+#pragma unroll
+          for (int g = 0; g < nq; ++g) b[k][g] = T(0);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k)
+#pragma unroll
+        for (int g = 0; g < nq; ++g) xw[k][g] = xw[k + 1][g];
+      {
+        T c[P + 1];
+        const T *xs = xslot(it);
+#pragma unroll
+        for (int a = 0; a <= P; ++a) c[a] = (owns && it + P < Nt) ? xs[t + a] : T(0);
+        gauss(c, xw[P]);
+      }
+      T yq[nq];
+#pragma unroll
+      for (int g = 0; g < nq; ++g) {
+        T v = acc[0][g] + b[0][g] * xw[0][g];
+#pragma unroll
+        for (int k = 1; k <= P; ++k) v += b[k][g] * xw[k][g];
+        yq[g] = v;
+      }
+#pragma unroll
+      for (int k = 0; k < P - 1; ++k)
+#pragma unroll
+        for (int g = 0; g < nq; ++g) acc[k][g] = acc[k + 1][g] + b[k + 1][g] * xw[0][g];
+#pragma unroll
+      for (int g = 0; g < nq; ++g) acc[P - 1][g] = b[P][g] * xw[0][g];
+      // contributions c[a] of this element to coefficient t + a
+      T c[P + 1];
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        T v = T(0);
+#pragma unroll
+        for (int g = 0; g < nq; ++g) v += wv[g][a] * yq[g];
+        c[a] = v;
+      }
+      T out = c[0];
+#pragma unroll
+      for (int a = 1; a <= P; ++a) {
+        T v = __shfl_up_sync(0xffffffffu, c[a], a);
+        if (lane >= a) out += v;
+      }
+      if (lane >= 32 - P) {
+#pragma unroll
+        for (int a = 1; a <= P; ++a) xch[it & 1][warp][a - 1][lane - (32 - P)] = c[a];
+      }
+      pend = out;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    if (t1 > t0) {
+      const int pp = (t1 - 1) & 1;
+      if (lane < P && warp > 0) {
+#pragma unroll
+        for (int a = 1; a <= P; ++a)
+          if (a > lane) pend += xch[pp][warp - 1][a - 1][lane + P - a];
+      }
+      if (t < nx) yrow[(long long)(t1 - 1) * planeX + t] = pend;
+    }
+    __syncthreads();   // the next segment reuses the rings and xch
+  }
+}
+
 // Dense strided GEMM C[b](m, c) = sum_k A(m, k) X[b](k, c) with 64x64 tiles,
 // 256 threads, 4x4 outputs per thread: the spatial transforms U_l, U_l^T of
 // the fast-diagonalization preconditioner (Eq. factorized), the Gram matrix
@@ -830,68 +1086,113 @@ __global__ void __launch_bounds__(256) gemm_kernel(T *__restrict__ C, const T *_
 // One banded LU solve along time per spatial eigen-index j (the block-diagonal
 // middle factor of the fast-diagonalization preconditioner): lu[it][k][j] holds
 // L below the diagonal (unit diagonal), 1/u_ii on it and U above.
-template <typename T, int P>
+// Banded forward/back substitution along time for every spatial eigen-index j
+// (one thread per j; LU stored [it][k][j], 1/u_ii on the diagonal).  Only
+// N_s threads exist, so the recurrence is latency-bound unless many time
+// steps of operands are in flight: each thread streams its own operands
+// through an S-stage ring of C-step chunks in shared memory with cp.async
+// (no registers held by outstanding loads, no barriers: a thread reads only
+// the slots it filled itself).  Ring slot layout [stage][step][P+1][thread].
+template <typename T, int P, int C, int S>
 __global__ void tline_lu_kernel(T *__restrict__ z, const T *__restrict__ r, const T *__restrict__ lu, int Nt,
                                 long long Ns) {
-  long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (j >= Ns) return;
-  constexpr int B = 2 * P + 1;
-  constexpr int U = 8;     // time steps whose operands are loaded ahead of the recurrence
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *ring = reinterpret_cast<T *>(smem_raw);
+  constexpr int B = 2 * P + 1, R = P + 1;
+  const int nth = blockDim.x, tid = threadIdx.x;
+  const long long j = blockIdx.x * (long long)nth + tid;
+  const bool active = j < Ns;
+  const int nch = (Nt + C - 1) / C;
+  auto slot = [&](int ch, int c, int k) -> T * { return ring + (((ch % S) * C + c) * R + k) * nth + tid; };
+  // forward: step it needs r[it] (slot 0) and l_{it,it-k} (slot k), k = 1..P
+  auto issue_fwd = [&](int ch) {
+    if (active && ch < nch) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int it = ch * C + c;
+        if (it < Nt) {
+          cp_async_elem(slot(ch, c, 0), r + (long long)it * Ns + j);
+#pragma unroll
+          for (int k = 1; k <= P; ++k)
+            if (it - k >= 0) cp_async_elem(slot(ch, c, k), lu + ((long long)it * B + (P - k)) * Ns + j);
+        }
+      }
+    }
+    cp_async_commit();
+  };
   T yw[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) yw[k] = T(0);
-  // forward substitution with the unit lower factor
-  for (int it0 = 0; it0 < Nt; it0 += U) {
-    T rv[U], lv[U][P];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int it = it0 + u;
-      bool ok = it < Nt;
-      rv[u] = ok ? r[(long long)it * Ns + j] : T(0);
+  for (int ch = 0; ch < S - 1; ++ch) issue_fwd(ch);
+  for (int ch = 0; ch < nch; ++ch) {
+    issue_fwd(ch + S - 1);
+    cp_async_wait<S - 1>();
+    if (active) {
 #pragma unroll
-      for (int k = 1; k <= P; ++k) lv[u][k - 1] = (ok && it - k >= 0) ? lu[((long long)it * B + (P - k)) * Ns + j] : T(0);
-    }
+      for (int c = 0; c < C; ++c) {
+        const int it = ch * C + c;
+        if (it >= Nt) break;
+        T v = *slot(ch, c, 0);
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int it = it0 + u;
-      if (it >= Nt) break;
-      T s = rv[u];
+        for (int k = 1; k <= P; ++k)
+          if (it - k >= 0) v -= *slot(ch, c, k) * yw[P - k];
 #pragma unroll
-      for (int k = 1; k <= P; ++k) s -= lv[u][k - 1] * yw[P - k];
-#pragma unroll
-      for (int k = 0; k < P - 1; ++k) yw[k] = yw[k + 1];
-      yw[P - 1] = s;
-      z[(long long)it * Ns + j] = s;
+        for (int k = 0; k < P - 1; ++k) yw[k] = yw[k + 1];
+        yw[P - 1] = v;
+        z[(long long)it * Ns + j] = v;
+      }
     }
   }
-  // backward substitution with the upper factor (1/u_ii stored on the diagonal)
+  cp_async_wait<0>();
+  // backward: step it = Nt-1-(ch*C+c) needs u_{it,it+k} (slot k), k = 0..P;
+  // y[it] comes back from z with plain loads (this thread wrote it above)
+  auto issue_bwd = [&](int ch) {
+    if (active && ch < nch) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int it = Nt - 1 - (ch * C + c);
+        if (it >= 0) {
+#pragma unroll
+          for (int k = 0; k <= P; ++k)
+            if (it + k < Nt) cp_async_elem(slot(ch, c, k), lu + ((long long)it * B + (P + k)) * Ns + j);
+        }
+      }
+    }
+    cp_async_commit();
+  };
   T zw[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) zw[k] = T(0);
-  for (int it0 = Nt - 1; it0 >= 0; it0 -= U) {
-    T yv[U], uv[U][P + 1];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int it = it0 - u;
-      bool ok = it >= 0;
-      yv[u] = ok ? z[(long long)it * Ns + j] : T(0);
+  for (int ch = 0; ch < S - 1; ++ch) issue_bwd(ch);
+  for (int ch = 0; ch < nch; ++ch) {
+    issue_bwd(ch + S - 1);
+    T yv[C];
 #pragma unroll
-      for (int k = 0; k <= P; ++k) uv[u][k] = (ok && it + k < Nt) ? lu[((long long)it * B + (P + k)) * Ns + j] : T(0);
+    for (int c = 0; c < C; ++c) {
+      const int it = Nt - 1 - (ch * C + c);
+      yv[c] = (active && it >= 0) ? z[(long long)it * Ns + j] : T(0);
     }
+    cp_async_wait<S - 1>();
+    if (active) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      int it = it0 - u;
-      if (it < 0) break;
-      T s = yv[u];
+      for (int c = 0; c < C; ++c) {
+        const int it = Nt - 1 - (ch * C + c);
+        if (it < 0) break;
+        T v = yv[c];
 #pragma unroll
-      for (int k = 1; k <= P; ++k) s -= uv[u][k] * zw[k - 1];
-      s *= uv[u][0];
+        for (int k = 1; k <= P; ++k)
+          if (it + k < Nt) v -= *slot(ch, c, k) * zw[k - 1];
+        v *= *slot(ch, c, 0);
 #pragma unroll
-      for (int k = P - 1; k > 0; --k) zw[k] = zw[k - 1];
-      zw[0] = s;
-      z[(long long)it * Ns + j] = s;
+        for (int k = P - 1; k > 0; --k) zw[k] = zw[k - 1];
+        zw[0] = v;
+        z[(long long)it * Ns + j] = v;
+      }
     }
   }
+  cp_async_wait<0>();
 }
 
 template <typename T> struct Acc;
@@ -1064,6 +1365,148 @@ __global__ void __launch_bounds__(256) maxpy_kernel(T *__restrict__ w, const T *
     }
 }
 
+// Partial inner products of rows V_i (i < nv) with two vectors x1, x2 in one
+// pass over the rows: partial[(2 i + c) * gridDim.x + b] = <V_i, x_c> over
+// block b's chunk (Kahan FP32 / plain FP64 per thread, FP64 across threads in
+// a fixed order), the dot pass of the delayed Gram-Schmidt below.
+template <typename T, int G>
+__global__ void __launch_bounds__(256) mdot2_kernel(double *__restrict__ partial, const T *__restrict__ V,
+                                                    long long ldv, int nv, const T *__restrict__ x1,
+                                                    const T *__restrict__ x2, long long n) {
+  typedef V16<T> X;
+  typedef typename X::type VT;
+  constexpr int W = X::W;
+  __shared__ double red[2 * G][8];
+  const int i0 = blockIdx.y * G;
+  const int cnt = min(G, nv - i0);
+  const long long nvec = n / W;
+  const long long chunk = (nvec + gridDim.x - 1) / gridDim.x;
+  const long long beg = (long long)blockIdx.x * chunk, end = min(nvec, beg + chunk);
+  KahanAcc<T> acc[G][2];
+#pragma unroll
+  for (int g = 0; g < G; ++g) { acc[g][0].zero(); acc[g][1].zero(); }
+  const VT *y1 = reinterpret_cast<const VT *>(x1), *y2 = reinterpret_cast<const VT *>(x2);
+  for (long long e = beg + threadIdx.x; e < end; e += blockDim.x) {
+    VT a = y1[e], b = y2[e];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (g < cnt) {
+        VT v = reinterpret_cast<const VT *>(V + (long long)(i0 + g) * ldv)[e];
+        acc[g][0].add(X::dot(v, a));
+        acc[g][1].add(X::dot(v, b));
+      }
+  }
+  if (blockIdx.x == gridDim.x - 1)
+    for (long long e = nvec * W + threadIdx.x; e < n; e += blockDim.x)
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (g < cnt) {
+          T v = V[(long long)(i0 + g) * ldv + e];
+          acc[g][0].add(v * x1[e]);
+          acc[g][1].add(v * x2[e]);
+        }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < G; ++g) {
+    if (g >= cnt) break;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      double t = acc[g][c].value();
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+      if (lane == 0) red[2 * g + c][warp] = t;
+    }
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < 2 * cnt) {
+    double t = 0.0;
+    for (int wi = 0; wi < (int)(blockDim.x >> 5); ++wi) t += red[threadIdx.x][wi];
+    partial[(long long)(2 * i0 + threadIdx.x) * gridDim.x + blockIdx.x] = t;
+  }
+}
+
+// Update pass of the delayed classical Gram-Schmidt (two passes over the
+// basis per Arnoldi step instead of four).  Rows 0..j-1 of V are final; row
+// j holds u_j (projected once), row j+1 holds w = A z_j.  From the dots
+// D[2i+c] = <V_i, (u_j, w)_c> (i <= j+1) of the dot pass:
+//   nu = sqrt(<u,u> - |a|^2), a_i = <V_i,u>   (Pythagoras: u is nearly orthogonal)
+//   v_j = (u - sum a_i V_i) / nu              (reorthogonalized, normalized)
+//   gam = <v_j, w> = (<u,w> - a.b) / nu,      b_i = <V_i, w>
+//   u_{j+1} = sw (w - sum b_i V_i - gam v_j)  (projected once; sw scales it to
+//             about unit norm, sw = 1/sqrt(<w,w> - |b|^2 - gam^2))
+// written in place over rows j and j+1 in one pass; block 0 stores (nu, gam,
+// sw) in sc for the Hessenberg bookkeeping.  16-byte aligned rows.
+template <typename T>
+__global__ void __launch_bounds__(256) dcgs2_update_kernel(T *__restrict__ V, long long ldv, int j,
+                                                           const double *__restrict__ D, long long n,
+                                                           double *__restrict__ sc) {
+  typedef V16<T> X;
+  typedef typename X::type VT;
+  constexpr int W = X::W;
+  __shared__ T ca[512], cb[512];
+  __shared__ double scal[4];
+  if (threadIdx.x == 0) {
+    double sa2 = 0.0, sab = 0.0, sb2 = 0.0;
+    for (int i = 0; i < j; ++i) {
+      const double a = D[2 * i], b = D[2 * i + 1];
+      sa2 += a * a; sab += a * b; sb2 += b * b;
+    }
+    const double uu = D[2 * j], uw = D[2 * j + 1], ww = D[2 * (j + 1) + 1];
+    const double nu2 = uu - sa2;
+    const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
+    const double inu = nu > 0.0 ? 1.0 / nu : 0.0;
+    const double gam = (uw - sab) * inu;
+    const double q = ww - sb2 - gam * gam;
+    const double sw = (q > 0.0 && q > 1e-30 * ww) ? 1.0 / sqrt(q) : (ww > 0.0 ? 1.0 / sqrt(ww) : 1.0);
+    scal[0] = inu; scal[1] = gam * inu; scal[2] = sw; scal[3] = gam;
+    if (blockIdx.x == 0) { sc[0] = nu; sc[1] = gam; sc[2] = sw; }
+  }
+  __syncthreads();
+  const double inu = scal[0], gin = scal[1];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    ca[i] = (T)(D[2 * i] * inu);
+    cb[i] = (T)(D[2 * i + 1] - D[2 * i] * gin);
+  }
+  __syncthreads();
+  const T tinu = (T)inu, tg = (T)gin, tsw = (T)scal[2];
+  T *U = V + (long long)j * ldv, *Wr = V + (long long)(j + 1) * ldv;
+  const long long nvec = n / W;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nvec; e += stride) {
+    VT aa = X::zero(), bb = X::zero();
+#pragma unroll 8
+    for (int i = 0; i < j; ++i) {
+      const VT vi = reinterpret_cast<const VT *>(V + (long long)i * ldv)[e];
+      aa = X::fma(ca[i], vi, aa);
+      bb = X::fma(cb[i], vi, bb);
+    }
+    VT u = reinterpret_cast<VT *>(U)[e], w = reinterpret_cast<VT *>(Wr)[e];
+    const T *ua = reinterpret_cast<const T *>(&u), *wa = reinterpret_cast<const T *>(&w);
+    const T *aA = reinterpret_cast<const T *>(&aa), *bA = reinterpret_cast<const T *>(&bb);
+    VT vo, wo;
+    T *vA = reinterpret_cast<T *>(&vo), *woA = reinterpret_cast<T *>(&wo);
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      vA[c] = ua[c] * tinu - aA[c];
+      woA[c] = tsw * (wa[c] - bA[c] - tg * ua[c]);
+    }
+    reinterpret_cast<VT *>(U)[e] = vo;
+    reinterpret_cast<VT *>(Wr)[e] = wo;
+  }
+  if (blockIdx.x == 0)
+    for (long long e = nvec * W + threadIdx.x; e < n; e += blockDim.x) {
+      T a = T(0), b = T(0);
+      for (int i = 0; i < j; ++i) {
+        const T vi = V[(long long)i * ldv + e];
+        a += ca[i] * vi;
+        b += cb[i] * vi;
+      }
+      const T u = U[e], w = Wr[e];
+      U[e] = u * tinu - a;
+      Wr[e] = tsw * (w - b - tg * u);
+    }
+}
+
 template <typename T>
 __global__ void scale_copy_kernel(T *__restrict__ y, const T *__restrict__ x, double alpha, long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -1194,6 +1637,40 @@ void launch_qband_apply(cudaStream_t s, T *z, const T *x, const T *band, int Nt,
   }
 }
 
+int xband_fused_limit(size_t elem, int p) { return (elem == 8 || p >= 4) ? 256 : 512; }
+
+template <typename T>
+bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const T *band, const T *tab, int nel, int Nt,
+                        long long rows, int p) {
+  const int threads = (nel + p + 31) / 32 * 32;
+  if (threads > xband_fused_limit(sizeof(T), p) || rows < 1) return false;
+  // time segments so that the grid holds about 16 blocks per SM, each
+  // segment at least 16 P steps long (its replay halo is P steps)
+  long long want = (152LL * 16 + rows - 1) / rows;
+  int nseg = (int)std::max<long long>(1, std::min<long long>(want, Nt / (16 * p)));
+  int seglen = (Nt + nseg - 1) / nseg;
+  nseg = (Nt + seglen - 1) / seglen;
+  unsigned blocks = (unsigned)std::min<long long>(rows * nseg, 1LL << 30);
+  constexpr int S = sizeof(T) == 4 ? 4 : 3;
+  auto go = [&](auto kern, int P) {
+    size_t sh = ((size_t)S * (P + 1) * threads * (P + 1) + (size_t)S * threads) * sizeof(T);
+    static bool attr[5] = {false, false, false, false, false};
+    if (!attr[P]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr[P] = true;
+    }
+    st_count_launch();
+    kern<<<blocks, threads, sh, s>>>(Y1, X1, band, tab, nel, Nt, rows, seglen);
+  };
+  switch (p) {
+    case 1: go(xband_fused_kernel<T, 1, S>, 1); break;
+    case 2: go(xband_fused_kernel<T, 2, S>, 2); break;
+    case 3: go(xband_fused_kernel<T, 3, S>, 3); break;
+    default: go(xband_fused_kernel<T, 4, S>, 4); break;
+  }
+  return true;
+}
+
 template <typename T>
 void launch_gemm(cudaStream_t s, T *C, const T *A, const T *X, const GemmDesc &g, double alpha, double beta) {
   dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.batch);
@@ -1244,13 +1721,23 @@ void launch_rot_gemm(cudaStream_t s, T *out, const T *in, const T *M, int nb, in
 
 template <typename T>
 void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p) {
-  int threads = 128;
+  constexpr int threads = 64, C = 4, S = sizeof(T) == 4 ? 10 : 6;
   unsigned blocks = (unsigned)((Ns + threads - 1) / threads);
+  auto go = [&](auto kern, int P) {
+    size_t sh = (size_t)S * C * (P + 1) * threads * sizeof(T);
+    static bool attr[5] = {false, false, false, false, false};
+    if (!attr[P]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
+      attr[P] = true;
+    }
+    st_count_launch();
+    kern<<<blocks, threads, sh, s>>>(z, r, lu, Nt, Ns);
+  };
   switch (p) {
-    case 1: st_count_launch(); tline_lu_kernel<T, 1><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
-    case 2: st_count_launch(); tline_lu_kernel<T, 2><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
-    case 3: st_count_launch(); tline_lu_kernel<T, 3><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
-    default: st_count_launch(); tline_lu_kernel<T, 4><<<blocks, threads, 0, s>>>(z, r, lu, Nt, Ns); break;
+    case 1: go(tline_lu_kernel<T, 1, C, S>, 1); break;
+    case 2: go(tline_lu_kernel<T, 2, C, S>, 2); break;
+    case 3: go(tline_lu_kernel<T, 3, C, S>, 3); break;
+    default: go(tline_lu_kernel<T, 4, C, S>, 4); break;
   }
 }
 
@@ -1273,6 +1760,25 @@ void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, 
                        const double *nrm) {
   long long nvec = n / V16<T>::W;
   st_count_launch(); maxpy_kernel<T><<<grid_for(std::max<long long>(nvec / 2, 1)), kThreads, 0, s>>>(w, V, ldv, nv, h, n, nrm);
+}
+
+template <typename T>
+void launch_multi_dot2(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *x1, const T *x2,
+                       long long n, double *scratch) {
+  constexpr int G = 8;
+  int groups = (nv + G - 1) / G;
+  long long want = std::max<long long>(38, 4 * 304 / groups);
+  long long cap = std::max<long long>(1, n / (V16<T>::W * 256 * 8));
+  int bx = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(want, cap), kDotBlocks));
+  dim3 grid(bx, groups);
+  st_count_launch(); mdot2_kernel<T, G><<<grid, 256, 0, s>>>(scratch, V, ldv, nv, x1, x2, n);
+  st_count_launch(); reduce_blocks_kernel<<<(2 * nv + 3) / 4, 128, 0, s>>>(out, scratch, bx, 2 * nv);
+}
+
+template <typename T>
+void launch_dcgs2_update(cudaStream_t s, T *V, long long ldv, int j, const double *D, long long n, double *sc) {
+  long long nvec = n / V16<T>::W;
+  st_count_launch(); dcgs2_update_kernel<T><<<grid_for(std::max<long long>(nvec, 1)), kThreads, 0, s>>>(V, ldv, j, D, n, sc);
 }
 
 template <typename T>
@@ -1368,6 +1874,8 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
   template void launch_interp_bwd<T>(cudaStream_t, T *, const T *, const T *, int, int, int, long long, \
                                      long long, bool);                                                \
   template void launch_qband_apply<T>(cudaStream_t, T *, const T *, const T *, int, long long, int);   \
+  template bool launch_xband_fused<T>(cudaStream_t, T *, const T *, const T *, const T *, int, int,    \
+                                      long long, int);                                                 \
   template void launch_mode_gemm<T>(cudaStream_t, T *, const T *, const T *, int, long long, long long); \
   template void launch_tline_lu_solve<T>(cudaStream_t, T *, const T *, const T *, int, long long, int); \
   template void launch_rot_gemm<T>(cudaStream_t, T *, const T *, const T *, int, int, long long, long long); \
@@ -1375,7 +1883,11 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
                                     long long, double *);                                             \
   template void launch_multi_axpy<T>(cudaStream_t, T *, const T *, long long, int, const double *,     \
                                      long long, const double *);                                      \
-  template void launch_scale_copy<T>(cudaStream_t, T *, const T *, double, long long);
+  template void launch_scale_copy<T>(cudaStream_t, T *, const T *, double, long long);              \
+  template void launch_multi_dot2<T>(cudaStream_t, double *, const T *, long long, int, const T *,     \
+                                     const T *, long long, double *);                                  \
+  template void launch_dcgs2_update<T>(cudaStream_t, T *, long long, int, const double *, long long,   \
+                                       double *);
 INST(float)
 INST(double)
 #undef INST

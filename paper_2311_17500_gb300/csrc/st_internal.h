@@ -176,6 +176,14 @@ void launch_interp_bwd(cudaStream_t s, T *out, const T *in, const T *tab, int ne
                        long long inner, long long outer, bool accumulate);
 template <typename T>
 void launch_qband_apply(cudaStream_t s, T *z, const T *x, const T *band, int Nt, long long Qs, int p);
+// Fused x-axis reaction/SU pass Y1 = Bx^T band Bx X1 ([Nt][rows][nx] rows of
+// x-coefficients at Gauss rows of the other axes); false when the x axis has
+// too many elements for one block (then the caller takes the unfused path).
+// Largest block (threads) of the fused x pass for this element size and degree.
+int xband_fused_limit(size_t elem, int p);
+template <typename T>
+bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const T *band, const T *tab, int nel, int Nt,
+                        long long rows, int p);
 template <typename T>
 void launch_mode_gemm(cudaStream_t s, T *out, const T *in, const T *A, int n, long long inner, long long outer);
 template <typename T>
@@ -191,6 +199,14 @@ int tc_state(cudaStream_t s, double *err_out);
 template <typename T>
 void launch_multi_dot(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *w,
                       long long n, double *scratch);
+// <V_i, x1>, <V_i, x2> for i < nv in one pass: out[2 i + c] (FP64).
+template <typename T>
+void launch_multi_dot2(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *x1, const T *x2,
+                       long long n, double *scratch);
+// Update pass of the delayed classical Gram-Schmidt step j (rows j, j+1 of V
+// rewritten in place from the dots D of launch_multi_dot2; (nu, gam, sw) -> sc).
+template <typename T>
+void launch_dcgs2_update(cudaStream_t s, T *V, long long ldv, int j, const double *D, long long n, double *sc);
 template <typename T>
 void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, const double *h,
                        long long n, const double *nrm = nullptr);
@@ -218,6 +234,10 @@ st_status wupdate_static_run(cudaStream_t s, const double *u, double *w, const d
 // eigen / FD
 st_status fd_setup(st_handle *h);
 st_status sym_eig_desc(st_handle *h, const double *A, int n, double *evec, double *eval);
+// Leading Ritz pairs of the Gram matrix by Lanczos (rank R of Eq. tol chosen
+// from them); ST_ERR_NOT_CONVERGED when the full decomposition is needed.
+st_status gram_top_eigs(st_handle *h, const double *G, int n, double tr, double eps, int cap, double *Ur, int *R_out,
+                        std::vector<double> &lam);
 
 // apply / precond
 template <typename T>

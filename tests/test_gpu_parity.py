@@ -135,6 +135,26 @@ def test_linearization_and_apply(P, c, kind):
     s.close()
 
 
+def test_lowrank_long_time(P):
+    """A Gram matrix larger than one batch of Lanczos steps (N_t = 61 against
+    24), so the leading Ritz pairs must pass the residual test before the rank
+    is taken: rank, Theta-hat and the FP64 operator as in the cases above."""
+    c = dict(d=2, p=2, n_el=[8, 8], n_el_t=60)
+    desc = problem(c)
+    o = Oracle(desc)
+    u, w = iterate(o, 2)
+    A, info = o.linearization(u, w, "picard")
+    s = solver(P, desc)
+    du, dw = dev(u), dev(w)
+    ginfo = s.ionic(ptr(du), ptr(dw))
+    assert ginfo["rank"] == len(info["s"]) and ginfo["rank"] >= 1
+    x = W.random_vector(o.st.N_dof, seed=5)
+    dx, dy = dev(x), empty(o.st.N_dof)
+    s.apply(ptr(dx), ptr(dy), P.ST_FP64)
+    assert rel(host(dy), A @ x) < 1e-12
+    s.close()
+
+
 @pytest.mark.parametrize("c", CASES, ids=IDS)
 def test_precond(P, c):
     desc = problem(c)
