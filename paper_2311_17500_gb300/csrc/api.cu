@@ -361,54 +361,62 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   const double sz = sizeof(T);
   const double vec = (double)h->Ndof * sz;
   // --- Kronecker part
-  ProfScope *pk = new ProfScope(h, PROF_KRON, vec * (h->d == 1 ? 7 : h->d == 2 ? 12 : 19));
+  const bool plane2 = h->d == 2;
+  ProfScope *pk = new ProfScope(h, PROF_KRON, vec * (h->d == 1 ? 7 : plane2 ? 6 : 19));
+  if (plane2 && launch_kron2d<T>(s, y, P::K(h, 0), P::K(h, 1), x, P::Wt(h), P::Mt(h), P::Mb(h, 0), P::Kb(h, 0),
+                                 P::Mb(h, 1), P::Kb(h, 1), (int)nx, (int)ny, (int)Nt, p, D.C_m, D.D[0], D.D[1])) {
+    delete pk;
+    pk = nullptr;
+  }
   const T *bands[3];
   const T *ins[3];
   double cf[3];
-  T *m = nullptr, *sK = nullptr;
-  if (h->d == 1) {
-    m = P::K(h, 0); sK = P::K(h, 1);
-    bands[0] = P::Mb(h, 0); ins[0] = x; cf[0] = 1.0;
-    launch_band_pass<T>(s, m, 1, bands, ins, cf, (int)nx, 1, Nt, p, false);
-    bands[0] = P::Kb(h, 0); cf[0] = D.D[0];
-    launch_band_pass<T>(s, sK, 1, bands, ins, cf, (int)nx, 1, Nt, p, false);
-  } else if (h->d == 2) {
-    T *a = P::K(h, 0), *b = P::K(h, 1);
-    m = P::K(h, 2); sK = P::K(h, 3);
-    bands[0] = P::Mb(h, 0); ins[0] = x; cf[0] = 1.0;
-    launch_band_pass<T>(s, a, 1, bands, ins, cf, (int)nx, 1, Nt * ny, p, false);
-    bands[0] = P::Kb(h, 0);
-    launch_band_pass<T>(s, b, 1, bands, ins, cf, (int)nx, 1, Nt * ny, p, false);
-    bands[0] = P::Mb(h, 1); ins[0] = a;
-    launch_band_pass<T>(s, m, 1, bands, ins, cf, (int)ny, nx, Nt, p, false);
-    bands[0] = P::Mb(h, 1); ins[0] = b; cf[0] = D.D[0];
-    bands[1] = P::Kb(h, 1); ins[1] = a; cf[1] = D.D[1];
-    launch_band_pass<T>(s, sK, 2, bands, ins, cf, (int)ny, nx, Nt, p, false);
-  } else {
-    T *a = P::K(h, 0), *b = P::K(h, 1), *c = P::K(h, 2), *e = P::K(h, 3), *g = P::K(h, 4);
-    m = P::K(h, 5); sK = P::K(h, 6);
-    cf[0] = 1.0;
-    bands[0] = P::Mb(h, 0); ins[0] = x;
-    launch_band_pass<T>(s, a, 1, bands, ins, cf, (int)nx, 1, Nt * ny * nz, p, false);
-    bands[0] = P::Kb(h, 0);
-    launch_band_pass<T>(s, b, 1, bands, ins, cf, (int)nx, 1, Nt * ny * nz, p, false);
-    bands[0] = P::Mb(h, 1); ins[0] = a;
-    launch_band_pass<T>(s, c, 1, bands, ins, cf, (int)ny, nx, Nt * nz, p, false);
-    ins[0] = b;
-    launch_band_pass<T>(s, e, 1, bands, ins, cf, (int)ny, nx, Nt * nz, p, false);
-    bands[0] = P::Kb(h, 1); ins[0] = a;
-    launch_band_pass<T>(s, g, 1, bands, ins, cf, (int)ny, nx, Nt * nz, p, false);
-    bands[0] = P::Mb(h, 2); ins[0] = c;
-    launch_band_pass<T>(s, m, 1, bands, ins, cf, (int)nz, nx * ny, Nt, p, false);
-    bands[0] = P::Mb(h, 2); ins[0] = e; cf[0] = D.D[0];
-    bands[1] = P::Mb(h, 2); ins[1] = g; cf[1] = D.D[1];
-    bands[2] = P::Kb(h, 2); ins[2] = c; cf[2] = D.D[2];
-    launch_band_pass<T>(s, sK, 3, bands, ins, cf, (int)nz, nx * ny, Nt, p, false);
+  if (pk) {
+    T *m = nullptr, *sK = nullptr;
+    if (h->d == 1) {
+      m = P::K(h, 0); sK = P::K(h, 1);
+      bands[0] = P::Mb(h, 0); ins[0] = x; cf[0] = 1.0;
+      launch_band_pass<T>(s, m, 1, bands, ins, cf, (int)nx, 1, Nt, p, false);
+      bands[0] = P::Kb(h, 0); cf[0] = D.D[0];
+      launch_band_pass<T>(s, sK, 1, bands, ins, cf, (int)nx, 1, Nt, p, false);
+    } else if (h->d == 2) {
+      T *a = P::K(h, 0), *b = P::K(h, 1);
+      m = P::K(h, 2); sK = P::K(h, 3);
+      bands[0] = P::Mb(h, 0); ins[0] = x; cf[0] = 1.0;
+      launch_band_pass<T>(s, a, 1, bands, ins, cf, (int)nx, 1, Nt * ny, p, false);
+      bands[0] = P::Kb(h, 0);
+      launch_band_pass<T>(s, b, 1, bands, ins, cf, (int)nx, 1, Nt * ny, p, false);
+      bands[0] = P::Mb(h, 1); ins[0] = a;
+      launch_band_pass<T>(s, m, 1, bands, ins, cf, (int)ny, nx, Nt, p, false);
+      bands[0] = P::Mb(h, 1); ins[0] = b; cf[0] = D.D[0];
+      bands[1] = P::Kb(h, 1); ins[1] = a; cf[1] = D.D[1];
+      launch_band_pass<T>(s, sK, 2, bands, ins, cf, (int)ny, nx, Nt, p, false);
+    } else {
+      T *a = P::K(h, 0), *b = P::K(h, 1), *c = P::K(h, 2), *e = P::K(h, 3), *g = P::K(h, 4);
+      m = P::K(h, 5); sK = P::K(h, 6);
+      cf[0] = 1.0;
+      bands[0] = P::Mb(h, 0); ins[0] = x;
+      launch_band_pass<T>(s, a, 1, bands, ins, cf, (int)nx, 1, Nt * ny * nz, p, false);
+      bands[0] = P::Kb(h, 0);
+      launch_band_pass<T>(s, b, 1, bands, ins, cf, (int)nx, 1, Nt * ny * nz, p, false);
+      bands[0] = P::Mb(h, 1); ins[0] = a;
+      launch_band_pass<T>(s, c, 1, bands, ins, cf, (int)ny, nx, Nt * nz, p, false);
+      ins[0] = b;
+      launch_band_pass<T>(s, e, 1, bands, ins, cf, (int)ny, nx, Nt * nz, p, false);
+      bands[0] = P::Kb(h, 1); ins[0] = a;
+      launch_band_pass<T>(s, g, 1, bands, ins, cf, (int)ny, nx, Nt * nz, p, false);
+      bands[0] = P::Mb(h, 2); ins[0] = c;
+      launch_band_pass<T>(s, m, 1, bands, ins, cf, (int)nz, nx * ny, Nt, p, false);
+      bands[0] = P::Mb(h, 2); ins[0] = e; cf[0] = D.D[0];
+      bands[1] = P::Mb(h, 2); ins[1] = g; cf[1] = D.D[1];
+      bands[2] = P::Kb(h, 2); ins[2] = c; cf[2] = D.D[2];
+      launch_band_pass<T>(s, sK, 3, bands, ins, cf, (int)nz, nx * ny, Nt, p, false);
+    }
+    bands[0] = P::Wt(h); ins[0] = m; cf[0] = D.C_m;
+    bands[1] = P::Mt(h); ins[1] = sK; cf[1] = 1.0;
+    launch_band_pass<T>(s, y, 2, bands, ins, cf, (int)Nt, Ns, 1, p, false);
+    delete pk;
   }
-  bands[0] = P::Wt(h); ins[0] = m; cf[0] = D.C_m;
-  bands[1] = P::Mt(h); ins[1] = sK; cf[1] = 1.0;
-  launch_band_pass<T>(s, y, 2, bands, ins, cf, (int)Nt, Ns, 1, p, false);
-  delete pk;
   // --- reaction + SU part
   long long qd[3] = {h->Q[0], h->Q[1], h->Q[2]};
   long long nd[3] = {h->n[0], h->n[1], h->n[2]};

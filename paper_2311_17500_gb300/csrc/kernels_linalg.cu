@@ -1009,6 +1009,129 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
   }
 }
 
+// Kronecker part of the operator for d = 2 (Sec. 3.1.1),
+//   y = C_m (W_t (x) M_y (x) M_x) x + (M_t (x) (D_x M_y (x) K_x + D_y K_y (x) M_x)) x,
+// in two passes: the time bands first (xW = W_t x, xM = M_t x, one read of x),
+// then every time slice in the plane.
+// Time pass: one thread per (spatial index j, run of time steps), a register
+// window of x along time; the two band rows of each step come from shared
+// memory (broadcast reads).  Bands [i][k] = A(i, i-P+k).
+template <typename T, int P>
+__global__ void __launch_bounds__(256) time_band2_kernel(T *__restrict__ xW, T *__restrict__ xM, const T *__restrict__ x,
+                                                         const T *__restrict__ Wt, const T *__restrict__ Mt, int Nt,
+                                                         long long Ns, int run) {
+  constexpr int B = 2 * P + 1, U = 8;
+  __shared__ __align__(16) T rows[64][16];   // [step in run][W_t row (8) | M_t row (8)]
+  const int it0 = blockIdx.y * run, it1 = min(Nt, it0 + run);
+  for (int e = threadIdx.x; e < (it1 - it0) * 16; e += blockDim.x) {
+    const int r = e >> 4, c = e & 15, i = it0 + r;
+    const int k = c & 7;
+    T v = T(0);
+    if (k < B) {
+      const int jc = i - P + k;
+      if (jc >= 0 && jc < Nt) v = (c < 8 ? Wt : Mt)[(size_t)i * B + k];
+    }
+    rows[r][c] = v;
+  }
+  __syncthreads();
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= Ns) return;
+  T w[B];
+#pragma unroll
+  for (int k = 0; k < B - 1; ++k) {
+    const int it = it0 - P + k;
+    w[k + 1] = (it >= 0 && it < Nt) ? x[(long long)it * Ns + j] : T(0);
+  }
+  for (int ib = it0; ib < it1; ib += U) {
+    T nx[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int it = ib + u + P;
+      nx[u] = (ib + u < it1 && it < Nt) ? x[(long long)it * Ns + j] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = ib + u;
+      if (i >= it1) break;
+#pragma unroll
+      for (int k = 0; k < B - 1; ++k) w[k] = w[k + 1];
+      w[B - 1] = nx[u];
+      const T *rw = rows[i - it0];
+      T sw = T(0), sm = T(0);
+#pragma unroll
+      for (int k = 0; k < B; ++k) {
+        sw += rw[k] * w[k];
+        sm += rw[8 + k] * w[k];
+      }
+      xW[(long long)i * Ns + j] = sw;
+      xM[(long long)i * Ns + j] = sm;
+    }
+  }
+}
+
+// Plane pass: block = (32-column strip, time slice).  Stages xW, xM of the
+// strip with a P-column halo, applies the x bands (r1 = C_m M_x xW + D_x K_x xM,
+// r2 = M_x xM) into shared memory, then the y bands:
+//   y = M_y r1 + D_y K_y r2   (written, or added to y).
+// Shared memory: ny * (2 (32 + 2P) + 2 * 32) values.
+template <typename T, int P>
+__global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, const T *__restrict__ xW,
+                                                         const T *__restrict__ xM, const T *__restrict__ Mx,
+                                                         const T *__restrict__ Kx, const T *__restrict__ My,
+                                                         const T *__restrict__ Ky, int nx, int ny, T Cm, T Dx, T Dy,
+                                                         int accumulate) {
+  constexpr int B = 2 * P + 1, SW = 32, HW = SW + 2 * P;
+  extern __shared__ __align__(16) unsigned char pk_raw[];
+  T *iW = reinterpret_cast<T *>(pk_raw);   // [ny][HW]
+  T *iM = iW + (size_t)ny * HW;            // [ny][HW]
+  T *r1 = iM + (size_t)ny * HW;            // [ny][SW]
+  T *r2 = r1 + (size_t)ny * SW;            // [ny][SW]
+  const int cx0 = blockIdx.x * SW;
+  const long long plane = (long long)nx * ny;
+  const long long base = (long long)blockIdx.y * plane;
+  for (int e = threadIdx.x; e < ny * HW; e += blockDim.x) {
+    const int r = e / HW, c = e - r * HW, cx = cx0 - P + c;
+    const bool in = cx >= 0 && cx < nx;
+    iW[e] = in ? xW[base + (long long)r * nx + cx] : T(0);
+    iM[e] = in ? xM[base + (long long)r * nx + cx] : T(0);
+  }
+  __syncthreads();
+  const int c = threadIdx.x & 31, rg = threadIdx.x >> 5, nrg = blockDim.x >> 5;
+  const int cx = cx0 + c;
+  T mx[B], kx[B];
+#pragma unroll
+  for (int k = 0; k < B; ++k) {
+    const bool ok = cx < nx && cx - P + k >= 0 && cx - P + k < nx;
+    mx[k] = ok ? Mx[(size_t)cx * B + k] : T(0);
+    kx[k] = ok ? Kx[(size_t)cx * B + k] : T(0);
+  }
+  for (int r = rg; r < ny; r += nrg) {
+    const T *pw = iW + (size_t)r * HW + c, *pm = iM + (size_t)r * HW + c;
+    T a = T(0), b = T(0), m2 = T(0);
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      a += mx[k] * pw[k];
+      b += kx[k] * pm[k];
+      m2 += mx[k] * pm[k];
+    }
+    r1[(size_t)r * SW + c] = Cm * a + Dx * b;
+    r2[(size_t)r * SW + c] = m2;
+  }
+  __syncthreads();
+  if (cx >= nx) return;
+  for (int r = rg; r < ny; r += nrg) {
+    T v = T(0);
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+      const int rr = r - P + k;
+      if (rr < 0 || rr >= ny) continue;
+      v += My[(size_t)r * B + k] * r1[(size_t)rr * SW + c] + Dy * Ky[(size_t)r * B + k] * r2[(size_t)rr * SW + c];
+    }
+    const long long idx = base + (long long)r * nx + cx;
+    y[idx] = accumulate ? y[idx] + v : v;
+  }
+}
+
 // Dense strided GEMM C[b](m, c) = sum_k A(m, k) X[b](k, c) with 64x64 tiles,
 // 256 threads, 4x4 outputs per thread: the spatial transforms U_l, U_l^T of
 // the fast-diagonalization preconditioner (Eq. factorized), the Gram matrix
@@ -1672,6 +1795,34 @@ bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const T *band, const
 }
 
 template <typename T>
+bool launch_kron2d(cudaStream_t s, T *y, T *xW, T *xM, const T *x, const T *Wt, const T *Mt, const T *Mx,
+                   const T *Kx, const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx,
+                   double Dy) {
+  const size_t sh = (size_t)ny * (2 * (32 + 2 * p) + 2 * 32) * sizeof(T);
+  if (sh > 200 * 1024 || p > 4) return false;
+  const long long Ns = (long long)nx * ny;
+  const int run = 32;
+  dim3 g1((unsigned)((Ns + 255) / 256), (unsigned)((Nt + run - 1) / run));
+  dim3 g2((unsigned)((nx + 31) / 32), (unsigned)Nt);
+  auto go = [&](auto k1, auto k2, int P) {
+    static bool attr[5] = {false, false, false, false, false};
+    if (!attr[P]) {
+      cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr[P] = true;
+    }
+    st_count_launch(); k1<<<g1, 256, 0, s>>>(xW, xM, x, Wt, Mt, Nt, Ns, run);
+    st_count_launch(); k2<<<g2, 256, sh, s>>>(y, xW, xM, Mx, Kx, My, Ky, nx, ny, (T)Cm, (T)Dx, (T)Dy, 0);
+  };
+  switch (p) {
+    case 1: go(time_band2_kernel<T, 1>, plane_kron_kernel<T, 1>, 1); break;
+    case 2: go(time_band2_kernel<T, 2>, plane_kron_kernel<T, 2>, 2); break;
+    case 3: go(time_band2_kernel<T, 3>, plane_kron_kernel<T, 3>, 3); break;
+    default: go(time_band2_kernel<T, 4>, plane_kron_kernel<T, 4>, 4); break;
+  }
+  return true;
+}
+
+template <typename T>
 void launch_gemm(cudaStream_t s, T *C, const T *A, const T *X, const GemmDesc &g, double alpha, double beta) {
   dim3 grid((g.N + 63) / 64, (g.M + 63) / 64, g.batch);
   st_count_launch(); gemm_kernel<T><<<grid, 256, 0, s>>>(C, A, X, g, (T)alpha, (T)beta);
@@ -1874,6 +2025,9 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
   template void launch_interp_bwd<T>(cudaStream_t, T *, const T *, const T *, int, int, int, long long, \
                                      long long, bool);                                                \
   template void launch_qband_apply<T>(cudaStream_t, T *, const T *, const T *, int, long long, int);   \
+  template bool launch_kron2d<T>(cudaStream_t, T *, T *, T *, const T *, const T *, const T *, const T *, \
+                                 const T *, const T *, const T *, int, int, int, int, double, double,   \
+                                 double);                                                              \
   template bool launch_xband_fused<T>(cudaStream_t, T *, const T *, const T *, const T *, int, int,    \
                                       long long, int);                                                 \
   template void launch_mode_gemm<T>(cudaStream_t, T *, const T *, const T *, int, long long, long long); \

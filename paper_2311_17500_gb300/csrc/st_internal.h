@@ -179,6 +179,12 @@ void launch_qband_apply(cudaStream_t s, T *z, const T *x, const T *band, int Nt,
 // Fused x-axis reaction/SU pass Y1 = Bx^T band Bx X1 ([Nt][rows][nx] rows of
 // x-coefficients at Gauss rows of the other axes); false when the x axis has
 // too many elements for one block (then the caller takes the unfused path).
+// Kronecker part of the operator for d = 2 (time pass into xW, xM, then the
+// plane pass into y); false when a plane column does not fit shared memory.
+template <typename T>
+bool launch_kron2d(cudaStream_t s, T *y, T *xW, T *xM, const T *x, const T *Wt, const T *Mt, const T *Mx,
+                   const T *Kx, const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx,
+                   double Dy);
 // Largest block (threads) of the fused x pass for this element size and degree.
 int xband_fused_limit(size_t elem, int p);
 template <typename T>
