@@ -508,7 +508,7 @@ __global__ void ifwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in
 template <typename T, int P>
 __global__ void ibwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab, int nel,
                                    long long inner, long long outer, int nruns, int accumulate) {
-  constexpr int nq = P + 1;
+  constexpr int nq = P + 1, UE = 4;   // elements whose Gauss values are loaded together
   const int nin = nel * nq, nout = nel + P;
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= inner) return;
@@ -521,32 +521,32 @@ __global__ void ibwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in
 #pragma unroll
     for (int a = 0; a <= P; ++a) acc[a] = T(0);
     const int ea = max(0, i0 - P), eb = min(nel - 1, i1 - 1);
-    T zn[nq];
+    for (int e0 = ea; e0 <= eb; e0 += UE) {
+      T z[UE][nq];
 #pragma unroll
-    for (int q = 0; q < nq; ++q) zn[q] = src[((long long)ea * nq + q) * inner];
-    for (int e = ea; e <= eb; ++e) {
-      T z[nq];
+      for (int u = 0; u < UE; ++u)
 #pragma unroll
-      for (int q = 0; q < nq; ++q) z[q] = zn[q];
-      if (e + 1 <= eb) {
+        for (int q = 0; q < nq; ++q) z[u][q] = (e0 + u <= eb) ? src[((long long)(e0 + u) * nq + q) * inner] : T(0);
 #pragma unroll
-        for (int q = 0; q < nq; ++q) zn[q] = src[((long long)(e + 1) * nq + q) * inner];
+      for (int u = 0; u < UE; ++u) {
+        const int e = e0 + u;
+        if (e > eb) break;
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+          T sacc = T(0);
+#pragma unroll
+          for (int q = 0; q < nq; ++q) sacc += __ldg(tab + ((size_t)e * nq + q) * (P + 1) + a) * z[u][q];
+          acc[a] += sacc;
+        }
+        // coefficient e receives nothing from later elements
+        if (e >= i0) {
+          long long idx = (long long)e * inner;
+          dst[idx] = accumulate ? dst[idx] + acc[0] : acc[0];
+        }
+#pragma unroll
+        for (int a = 0; a < P; ++a) acc[a] = acc[a + 1];
+        acc[P] = T(0);
       }
-#pragma unroll
-      for (int a = 0; a <= P; ++a) {
-        T s = T(0);
-#pragma unroll
-        for (int q = 0; q < nq; ++q) s += __ldg(tab + ((size_t)e * nq + q) * (P + 1) + a) * z[q];
-        acc[a] += s;
-      }
-      // coefficient e receives nothing from later elements
-      if (e >= i0) {
-        long long idx = (long long)e * inner;
-        dst[idx] = accumulate ? dst[idx] + acc[0] : acc[0];
-      }
-#pragma unroll
-      for (int a = 0; a < P; ++a) acc[a] = acc[a + 1];
-      acc[P] = T(0);
     }
     // coefficients eb+1 .. i1-1 (only past the last element); acc[0] is eb+1
     for (int i = eb + 1; i < i1; ++i) {
@@ -1073,7 +1073,7 @@ __global__ void __launch_bounds__(256) time_band2_kernel(T *__restrict__ xW, T *
 // strip with a P-column halo, applies the x bands (r1 = C_m M_x xW + D_x K_x xM,
 // r2 = M_x xM) into shared memory, then the y bands:
 //   y = M_y r1 + D_y K_y r2   (written, or added to y).
-// Shared memory: ny * (2 (32 + 2P) + 2 * 32) values.
+// Shared memory: ny * (2 (32 + 2P) + 2 * 32 + 2 (2P+1)) values.
 template <typename T, int P>
 __global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, const T *__restrict__ xW,
                                                          const T *__restrict__ xM, const T *__restrict__ Mx,
@@ -1086,17 +1086,36 @@ __global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, cons
   T *iM = iW + (size_t)ny * HW;            // [ny][HW]
   T *r1 = iM + (size_t)ny * HW;            // [ny][SW]
   T *r2 = r1 + (size_t)ny * SW;            // [ny][SW]
+  T *by = r2 + (size_t)ny * SW;            // [ny][2B]: M_y row, D_y K_y row
   const int cx0 = blockIdx.x * SW;
   const long long plane = (long long)nx * ny;
   const long long base = (long long)blockIdx.y * plane;
-  for (int e = threadIdx.x; e < ny * HW; e += blockDim.x) {
-    const int r = e / HW, c = e - r * HW, cx = cx0 - P + c;
-    const bool in = cx >= 0 && cx < nx;
-    iW[e] = in ? xW[base + (long long)r * nx + cx] : T(0);
-    iM[e] = in ? xM[base + (long long)r * nx + cx] : T(0);
+  const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5, nrg = blockDim.x >> 5;
+  // stage the strip with asynchronous copies (all in flight at once); halo
+  // columns outside the plane are zero
+  for (int r = rg; r < ny; r += nrg) {
+    const T *rw = xW + base + (long long)r * nx, *rm = xM + base + (long long)r * nx;
+    for (int c = lane; c < HW; c += 32) {
+      const int cx = cx0 - P + c;
+      if (cx >= 0 && cx < nx) {
+        cp_async_elem(iW + (size_t)r * HW + c, rw + cx);
+        cp_async_elem(iM + (size_t)r * HW + c, rm + cx);
+      } else {
+        iW[(size_t)r * HW + c] = T(0);
+        iM[(size_t)r * HW + c] = T(0);
+      }
+    }
   }
+  cp_async_commit();
+  for (int e = threadIdx.x; e < ny * B; e += blockDim.x) {
+    const int r = e / B, k = e - r * B, rr = r - P + k;
+    const bool ok = rr >= 0 && rr < ny;
+    by[(size_t)r * 2 * B + k] = ok ? My[e] : T(0);
+    by[(size_t)r * 2 * B + B + k] = ok ? Dy * Ky[e] : T(0);
+  }
+  cp_async_wait<0>();
   __syncthreads();
-  const int c = threadIdx.x & 31, rg = threadIdx.x >> 5, nrg = blockDim.x >> 5;
+  const int c = lane;
   const int cx = cx0 + c;
   T mx[B], kx[B];
 #pragma unroll
@@ -1120,12 +1139,12 @@ __global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, cons
   __syncthreads();
   if (cx >= nx) return;
   for (int r = rg; r < ny; r += nrg) {
+    const T *br = by + (size_t)r * 2 * B;
     T v = T(0);
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      const int rr = r - P + k;
-      if (rr < 0 || rr >= ny) continue;
-      v += My[(size_t)r * B + k] * r1[(size_t)rr * SW + c] + Dy * Ky[(size_t)r * B + k] * r2[(size_t)rr * SW + c];
+      const int rr = min(max(r - P + k, 0), ny - 1);   // out-of-range rows carry zero weights
+      v += br[k] * r1[(size_t)rr * SW + c] + br[B + k] * r2[(size_t)rr * SW + c];
     }
     const long long idx = base + (long long)r * nx + cx;
     y[idx] = accumulate ? y[idx] + v : v;
@@ -1390,11 +1409,16 @@ __global__ void __launch_bounds__(256) mdot_kernel(double *__restrict__ partial,
 #pragma unroll
   for (int g = 0; g < G; ++g) acc[g].zero();
   const VT *wv = reinterpret_cast<const VT *>(w);
+  const VT *rowp[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) rowp[g] = reinterpret_cast<const VT *>(V + (long long)(i0 + min(g, cnt - 1)) * ldv);
   for (long long e = beg + threadIdx.x; e < end; e += blockDim.x) {
     VT x = wv[e];
+    VT v[G];
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < cnt) acc[g].add(X::dot(reinterpret_cast<const VT *>(V + (long long)(i0 + g) * ldv)[e], x));
+    for (int g = 0; g < G; ++g) v[g] = rowp[g][e];
+#pragma unroll
+    for (int g = 0; g < G; ++g) acc[g].add(X::dot(v[g], x));
   }
   if (blockIdx.x == gridDim.x - 1)
     for (long long e = nvec * W + threadIdx.x; e < n; e += blockDim.x)
@@ -1509,15 +1533,35 @@ __global__ void __launch_bounds__(256) mdot2_kernel(double *__restrict__ partial
 #pragma unroll
   for (int g = 0; g < G; ++g) { acc[g][0].zero(); acc[g][1].zero(); }
   const VT *y1 = reinterpret_cast<const VT *>(x1), *y2 = reinterpret_cast<const VT *>(x2);
-  for (long long e = beg + threadIdx.x; e < end; e += blockDim.x) {
-    VT a = y1[e], b = y2[e];
+  // rows past the group end repeat the last row (loads stay unconditional so
+  // they are all in flight together); their sums are never written.  The
+  // operands of the next element are loaded before the current one is used.
+  const VT *rowp[G];
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < cnt) {
-        VT v = reinterpret_cast<const VT *>(V + (long long)(i0 + g) * ldv)[e];
-        acc[g][0].add(X::dot(v, a));
-        acc[g][1].add(X::dot(v, b));
-      }
+  for (int g = 0; g < G; ++g) rowp[g] = reinterpret_cast<const VT *>(V + (long long)(i0 + min(g, cnt - 1)) * ldv);
+  long long e = beg + threadIdx.x;
+  VT a, b, v[G];
+  if (e < end) {
+    a = y1[e]; b = y2[e];
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = rowp[g][e];
+  }
+  for (; e < end; e += blockDim.x) {
+    const long long en = e + blockDim.x;
+    VT an, bn, vn[G];
+    if (en < end) {
+      an = y1[en]; bn = y2[en];
+#pragma unroll
+      for (int g = 0; g < G; ++g) vn[g] = rowp[g][en];
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      acc[g][0].add(X::dot(v[g], a));
+      acc[g][1].add(X::dot(v[g], b));
+    }
+    a = an; b = bn;
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = vn[g];
   }
   if (blockIdx.x == gridDim.x - 1)
     for (long long e = nvec * W + threadIdx.x; e < n; e += blockDim.x)
@@ -1568,21 +1612,36 @@ __global__ void __launch_bounds__(256) dcgs2_update_kernel(T *__restrict__ V, lo
   constexpr int W = X::W;
   __shared__ T ca[512], cb[512];
   __shared__ double scal[4];
-  if (threadIdx.x == 0) {
+  __shared__ double part[3][8];
+  {
+    // |a|^2, a.b, |b|^2 over i < j: strided per thread, then a fixed tree
     double sa2 = 0.0, sab = 0.0, sb2 = 0.0;
-    for (int i = 0; i < j; ++i) {
+    for (int i = threadIdx.x; i < j; i += blockDim.x) {
       const double a = D[2 * i], b = D[2 * i + 1];
       sa2 += a * a; sab += a * b; sb2 += b * b;
     }
-    const double uu = D[2 * j], uw = D[2 * j + 1], ww = D[2 * (j + 1) + 1];
-    const double nu2 = uu - sa2;
-    const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
-    const double inu = nu > 0.0 ? 1.0 / nu : 0.0;
-    const double gam = (uw - sab) * inu;
-    const double q = ww - sb2 - gam * gam;
-    const double sw = (q > 0.0 && q > 1e-30 * ww) ? 1.0 / sqrt(q) : (ww > 0.0 ? 1.0 / sqrt(ww) : 1.0);
-    scal[0] = inu; scal[1] = gam * inu; scal[2] = sw; scal[3] = gam;
-    if (blockIdx.x == 0) { sc[0] = nu; sc[1] = gam; sc[2] = sw; }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      sa2 += __shfl_down_sync(0xffffffffu, sa2, off);
+      sab += __shfl_down_sync(0xffffffffu, sab, off);
+      sb2 += __shfl_down_sync(0xffffffffu, sb2, off);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { part[0][warp] = sa2; part[1][warp] = sab; part[2][warp] = sb2; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sa2 = sab = sb2 = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sa2 += part[0][w]; sab += part[1][w]; sb2 += part[2][w]; }
+      const double uu = D[2 * j], uw = D[2 * j + 1], ww = D[2 * (j + 1) + 1];
+      const double nu2 = uu - sa2;
+      const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
+      const double inu = nu > 0.0 ? 1.0 / nu : 0.0;
+      const double gam = (uw - sab) * inu;
+      const double q = ww - sb2 - gam * gam;
+      const double sw = (q > 0.0 && q > 1e-30 * ww) ? 1.0 / sqrt(q) : (ww > 0.0 ? 1.0 / sqrt(ww) : 1.0);
+      scal[0] = inu; scal[1] = gam * inu; scal[2] = sw; scal[3] = gam;
+      if (blockIdx.x == 0) { sc[0] = nu; sc[1] = gam; sc[2] = sw; }
+    }
   }
   __syncthreads();
   const double inu = scal[0], gin = scal[1];
@@ -1798,7 +1857,7 @@ template <typename T>
 bool launch_kron2d(cudaStream_t s, T *y, T *xW, T *xM, const T *x, const T *Wt, const T *Mt, const T *Mx,
                    const T *Kx, const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx,
                    double Dy) {
-  const size_t sh = (size_t)ny * (2 * (32 + 2 * p) + 2 * 32) * sizeof(T);
+  const size_t sh = (size_t)ny * (2 * (32 + 2 * p) + 2 * 32 + 2 * (2 * p + 1)) * sizeof(T);
   if (sh > 200 * 1024 || p > 4) return false;
   const long long Ns = (long long)nx * ny;
   const int run = 32;
@@ -1916,10 +1975,10 @@ void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, 
 template <typename T>
 void launch_multi_dot2(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *x1, const T *x2,
                        long long n, double *scratch) {
-  constexpr int G = 8;
+  constexpr int G = 4;
   int groups = (nv + G - 1) / G;
   long long want = std::max<long long>(38, 4 * 304 / groups);
-  long long cap = std::max<long long>(1, n / (V16<T>::W * 256 * 8));
+  long long cap = std::max<long long>(1, n / (V16<T>::W * 256 * 2));
   int bx = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(want, cap), kDotBlocks));
   dim3 grid(bx, groups);
   st_count_launch(); mdot2_kernel<T, G><<<grid, 256, 0, s>>>(scratch, V, ldv, nv, x1, x2, n);
