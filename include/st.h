@@ -172,10 +172,12 @@ st_status st_apply(st_handle *h, int prec, const void *x_dev, void *y_dev);
 st_status st_precond(st_handle *h, int prec, const void *r_dev, void *z_dev);
 
 /* Solve A x = b_dev to ||b - A x||_2 / ||b||_2 <= desc.rtol (true residual in
- * FP64), starting from the x_dev passed in.  FP64 mode: right-preconditioned
- * restarted GMRES in FP64.  Mixed mode: FP64 iterative refinement around
- * FP32 right-preconditioned GMRES.  Arnoldi uses classical Gram-Schmidt with
- * one reorthogonalization and FP64-accumulated inner products.
+ * FP64), starting from the x_dev passed in.  FP64 mode: flexible
+ * right-preconditioned restarted GMRES in FP64.  Mixed mode: FP64 iterative
+ * refinement around FP32 flexible GMRES (the FP32 preconditioner uses TF32
+ * tensor cores, so it is kept as Z = M^{-1} V).  Arnoldi uses classical
+ * Gram-Schmidt with one delayed reorthogonalization (two passes over the
+ * basis per step) and FP64-accumulated inner products.
  * ST_ERR_NOT_CONVERGED after desc.max_it inner iterations (x holds the best
  * iterate). */
 st_status st_linsolve(st_handle *h, const double *b_dev, double *x_dev, st_stats *stats);
@@ -254,7 +256,8 @@ enum {
   ST_STAGE_ARNOLDI = 5,  /* Gram-Schmidt inner products, updates and norms */
   ST_STAGE_IONIC = 6,    /* ionic quadrature and reaction band assembly */
   ST_STAGE_LOWRANK = 7,  /* Theta-hat, Gram matrix, eigen-decomposition, SU bands */
-  ST_STAGE_COUNT = 9
+  ST_STAGE_APPLY64 = 8,  /* the operator in FP64 (outer residuals; stages 0-2 then hold FP32 work only) */
+  ST_STAGE_COUNT = 10
 };
 st_status st_profile(st_handle *h, int enable);
 /* Self-test of the tensor-core (tcgen05, TF32) spatial transforms of the

@@ -27,7 +27,7 @@ EXPORTS = ["st_footprint", "st_setup", "st_destroy", "st_error_string", "st_get_
            "st_linearize", "st_apply", "st_precond", "st_linsolve", "st_wupdate", "st_rhs", "st_solve",
            "st_get", "st_profile", "st_profile_read", "st_launch_count",
            "st_tc_selftest", "st_wupdate_static"]
-STAGES = ["kron", "interp", "qband", "fd_gemm", "fd_lu", "arnoldi", "ionic", "lowrank"]
+STAGES = ["kron", "interp", "qband", "fd_gemm", "fd_lu", "arnoldi", "ionic", "lowrank", "apply64"]
 
 
 class StStim(ctypes.Structure):

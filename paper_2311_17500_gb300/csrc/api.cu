@@ -362,7 +362,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   const double vec = (double)h->Ndof * sz;
   // --- Kronecker part
   const bool plane2 = h->d == 2;
-  ProfScope *pk = new ProfScope(h, PROF_KRON, vec * (h->d == 1 ? 7 : plane2 ? 6 : 19));
+  ProfScope *pk = new ProfScope(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_KRON, vec * (h->d == 1 ? 7 : plane2 ? 6 : 19));
   if (plane2 && launch_kron2d<T>(s, y, P::K(h, 0), P::K(h, 1), x, P::Wt(h), P::Mt(h), P::Mb(h, 0), P::Kb(h, 0),
                                  P::Mb(h, 1), P::Kb(h, 1), (int)nx, (int)ny, (int)Nt, p, D.C_m, D.D[0], D.D[1])) {
     delete pk;
@@ -431,7 +431,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
       for (int k = 0; k < l; ++k) inner *= nd[k];
       for (int k = l + 1; k < h->d; ++k) outer *= qd[k];
       T *out = P::W(h, ping);
-      ProfScope ps(h, PROF_INTERP, sz * (double)outer * inner * (h->n[l] + (double)h->Q[l]));
+      ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_INTERP, sz * (double)outer * inner * (h->n[l] + (double)h->Q[l]));
       launch_interp_fwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer);
       cur = out;
       ping ^= 1;
@@ -440,7 +440,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
     for (int k = 1; k < h->d; ++k) rows *= qd[k];
     T *Y1 = P::W(h, ping);
     {
-      ProfScope ps(h, PROF_QBAND, sz * ((double)(p + 1) * h->NtQs + 2.0 * (double)Nt * rows * nx));
+      ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_QBAND, sz * ((double)(p + 1) * h->NtQs + 2.0 * (double)Nt * rows * nx));
       launch_xband_fused<T>(s, Y1, cur, P::band(h), P::Bq(h, 0), h->nel[0], (int)Nt, rows, p);
     }
     cur = Y1;
@@ -451,7 +451,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
       for (int k = l + 1; k < h->d; ++k) outer *= qd[k];
       const bool last = l == h->d - 1;
       T *out = last ? y : P::W(h, ping);
-      ProfScope ps(h, PROF_INTERP, sz * (double)outer * inner * (h->n[l] * (last ? 2.0 : 1.0) + (double)h->Q[l]));
+      ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_INTERP, sz * (double)outer * inner * (h->n[l] * (last ? 2.0 : 1.0) + (double)h->Q[l]));
       launch_interp_bwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer, last);
       cur = out;
       ping ^= 1;
@@ -464,14 +464,14 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
     for (int k = 0; k < l; ++k) inner *= qd[k];
     for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
     T *out = P::W(h, ping);
-    ProfScope ps(h, PROF_INTERP, sz * (double)outer * inner * (h->n[l] + (double)h->Q[l]));
+    ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_INTERP, sz * (double)outer * inner * (h->n[l] + (double)h->Q[l]));
     launch_interp_fwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer);
     cur = out;
     ping ^= 1;
   }
   T *zq = P::W(h, ping);
   {
-    ProfScope ps(h, PROF_QBAND, sz * (double)h->NtQs * (p + 3));
+    ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_QBAND, sz * (double)h->NtQs * (p + 3));
     launch_qband_apply<T>(s, zq, cur, P::band(h), h->Nt, h->Qs, p);
   }
   cur = zq;
@@ -481,7 +481,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
     for (int k = 0; k < l; ++k) inner *= qd[k];
     for (int k = l + 1; k < h->d; ++k) outer *= nd[k];
     T *out = (l == 0) ? y : P::W(h, ping);
-    ProfScope ps(h, PROF_INTERP, sz * (double)outer * inner * (h->n[l] * (l == 0 ? 2.0 : 1.0) + (double)h->Q[l]));
+    ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_INTERP, sz * (double)outer * inner * (h->n[l] * (l == 0 ? 2.0 : 1.0) + (double)h->Q[l]));
     launch_interp_bwd<T>(s, out, cur, P::Bq(h, l), h->nel[l], p, h->nq, inner, outer, l == 0);
     cur = out;
     ping ^= 1;

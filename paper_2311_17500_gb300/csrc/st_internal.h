@@ -138,8 +138,9 @@ enum {
   PROF_ARNOLDI = 5,   // Gram-Schmidt inner products and updates, norms
   PROF_IONIC = 6,     // ionic quadrature and band assembly
   PROF_LOWRANK = 7,   // Theta-hat, Gram matrix, eigen-decomposition, SU band update
-  PROF_OTHER = 8,
-  PROF_NCAT = 9
+  PROF_APPLY64 = 8,   // the operator applied in FP64 (all of its passes)
+  PROF_OTHER = 9,
+  PROF_NCAT = 10
 };
 
 // Records events around the enclosed launches when profiling is on.
