@@ -42,7 +42,8 @@ def _compile(src):
 def build(force=False, verbose=False):
     """Compile (if sources are newer than the library) and return the .so path."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "st_internal.h"), os.path.join(INCLUDE, "st.h")]
+    deps = srcs + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    deps.append(os.path.join(INCLUDE, "st.h"))
     if not force and os.path.exists(LIB):
         lib_t = os.path.getmtime(LIB)
         if all(os.path.getmtime(d) <= lib_t for d in deps):

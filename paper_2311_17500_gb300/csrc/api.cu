@@ -230,7 +230,7 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
     }
     ST_CUDA(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     int tc_flag = 0;
-    if (h->use_tc && sizeof(T) == 4) ST_CUDA(cudaMemcpyAsync(&tc_flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaMemcpyAsync(&tc_flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     ST_CUDA(cudaStreamSynchronize(s));
     if (tc_flag) return ST_ERR_TIMEOUT;
     const double nu = hh[2 * (m + 2)], gam = hh[2 * (m + 2) + 1], sw = hh[2 * (m + 2) + 2];
@@ -596,7 +596,7 @@ st_status precond_T(st_handle *h, const T *r, T *z) {
   }
   {
     ProfScope ps(h, PROF_FD_LU, vec * (2 + h->B));
-    launch_tline_lu_solve<T>(s, bufs[1], bufs[0], P::lu(h), h->Nt, h->Ns, h->p);
+    launch_tline_lu_solve<T>(s, bufs[1], bufs[0], P::lu(h), h->Nt, h->Ns, h->p, h->tc_err);
   }
   if (tc) {
     ST_TRY(tc_sequence(h, (const float *)bufs[1], (float *)z, false));

@@ -5,6 +5,7 @@
 // along the axis, `inner` contiguous entries after it, `outer` blocks before.
 #include <algorithm>
 #include "st_internal.h"
+#include "dev_sync.cuh"
 
 namespace {
 
@@ -1229,112 +1230,132 @@ __global__ void __launch_bounds__(256) gemm_kernel(T *__restrict__ C, const T *_
 // middle factor of the fast-diagonalization preconditioner): lu[it][k][j] holds
 // L below the diagonal (unit diagonal), 1/u_ii on it and U above.
 // Banded forward/back substitution along time for every spatial eigen-index j
-// (one thread per j; LU stored [it][k][j], 1/u_ii on the diagonal).  Only
-// N_s threads exist, so the recurrence is latency-bound unless many time
-// steps of operands are in flight: each thread streams its own operands
-// through an S-stage ring of C-step chunks in shared memory with cp.async
-// (no registers held by outstanding loads, no barriers: a thread reads only
-// the slots it filled itself).  Ring slot layout [stage][step][P+1][thread].
-template <typename T, int P, int C, int S>
-__global__ void tline_lu_kernel(T *__restrict__ z, const T *__restrict__ r, const T *__restrict__ lu, int Nt,
-                                long long Ns) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *ring = reinterpret_cast<T *>(smem_raw);
-  constexpr int B = 2 * P + 1, R = P + 1;
-  const int nth = blockDim.x, tid = threadIdx.x;
-  const long long j = blockIdx.x * (long long)nth + tid;
+// (LU stored [it][k][j], 1/u_ii on the diagonal).  There are only N_s time
+// lines, each a serial recurrence, so the kernel is warp-specialized: per
+// block, warp 0 runs the recurrences of 32 consecutive j (one lane each) and
+// warps 1..3 keep an S-stage ring of C-step chunks filled with the operands
+// ((P+1) rows of 32 values per step) by per-lane cp.async copies, whose
+// completion arrives on the stage's "full" barrier; the consumer frees a stage
+// through its "empty" barrier.  Forward chunks come first (r and the P
+// multipliers of each step), then backward chunks (the P+1 entries of U);
+// the backward right-hand side y is read back by the consumer lane that wrote
+// it, from shared memory when the whole time line fits (else from z).  Every wait is bounded: a wait that gives up sets *err and the warp
+// stops (the output is then invalid and the caller reports ST_ERR_TIMEOUT).
+constexpr int kLuC = 8, kLuS = 6;
+constexpr long long kLuWaitLimit = 1ll << 22;
+
+template <typename T, int P, bool YS>
+__global__ void __launch_bounds__(128) tline_lu_kernel(T *__restrict__ z, const T *__restrict__ r,
+                                                       const T *__restrict__ lu, int Nt, long long Ns, int *err) {
+  constexpr int B = 2 * P + 1, R = P + 1, C = kLuC, S = kLuS;
+  extern __shared__ __align__(16) unsigned char lu_raw[];
+  T *ring = reinterpret_cast<T *>(lu_raw);   // [S][C][R][32]
+  T *ybuf = ring + (size_t)S * C * R * 32;   // [Nt][32] forward results (YS)
+  __shared__ __align__(8) uint64_t full[S], empty[S];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long j = (long long)blockIdx.x * 32 + lane;
   const bool active = j < Ns;
-  const int nch = (Nt + C - 1) / C;
-  auto slot = [&](int ch, int c, int k) -> T * { return ring + (((ch % S) * C + c) * R + k) * nth + tid; };
-  // forward: step it needs r[it] (slot 0) and l_{it,it-k} (slot k), k = 1..P
-  auto issue_fwd = [&](int ch) {
-    if (active && ch < nch) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int it = ch * C + c;
-        if (it < Nt) {
-          cp_async_elem(slot(ch, c, 0), r + (long long)it * Ns + j);
-#pragma unroll
-          for (int k = 1; k <= P; ++k)
-            if (it - k >= 0) cp_async_elem(slot(ch, c, k), lu + ((long long)it * B + (P - k)) * Ns + j);
+  const int nch = (Nt + C - 1) / C, njobs = 2 * nch;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 96);    // one arrival per producer thread
+      mbar_init(&empty[i], 1);    // the consumer's elected lane
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto cell = [&](int u, int c, int k) -> T * { return ring + (((size_t)(u % S) * C + c) * R + k) * 32 + lane; };
+  if (warp > 0) {
+    // producers: slice (c, k) of chunk u is copied by warp 1 + (c*R + k) % 3
+    const int pw = warp - 1;
+    for (int u = 0; u < njobs; ++u) {
+      if (u >= S && !mbar_wait(smem_u32(&empty[u % S]), (uint32_t)(((u / S) - 1) & 1), kLuWaitLimit)) {
+        atomicExch(err, 1);
+        break;
+      }
+      const bool fwd = u < nch;
+      const int cb = fwd ? u : u - nch;
+      for (int sl = pw; sl < C * R; sl += 3) {
+        const int c = sl / R, k = sl - c * R;
+        if (!active) continue;
+        if (fwd) {
+          const int it = cb * C + c;
+          if (it >= Nt) continue;
+          if (k == 0) cp_async_elem(cell(u, c, 0), r + (long long)it * Ns + j);
+          else if (it - k >= 0) cp_async_elem(cell(u, c, k), lu + ((long long)it * B + (P - k)) * Ns + j);
+        } else {
+          const int it = Nt - 1 - (cb * C + c);
+          if (it < 0 || it + k >= Nt) continue;
+          cp_async_elem(cell(u, c, k), lu + ((long long)it * B + (P + k)) * Ns + j);
         }
       }
+      mbar_arrive_cp_async(&full[u % S]);
     }
-    cp_async_commit();
-  };
+    cp_async_wait<0>();
+    return;
+  }
+  // consumer
   T yw[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) yw[k] = T(0);
-#pragma unroll
-  for (int ch = 0; ch < S - 1; ++ch) issue_fwd(ch);
-  for (int ch = 0; ch < nch; ++ch) {
-    issue_fwd(ch + S - 1);
-    cp_async_wait<S - 1>();
+  for (int u = 0; u < nch; ++u) {
+    if (!mbar_wait(smem_u32(&full[u % S]), (uint32_t)((u / S) & 1), kLuWaitLimit)) {
+      atomicExch(err, 1);
+      return;
+    }
     if (active) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const int it = ch * C + c;
+        const int it = u * C + c;
         if (it >= Nt) break;
-        T v = *slot(ch, c, 0);
+        T v = *cell(u, c, 0);
 #pragma unroll
         for (int k = 1; k <= P; ++k)
-          if (it - k >= 0) v -= *slot(ch, c, k) * yw[P - k];
+          if (it - k >= 0) v -= *cell(u, c, k) * yw[P - k];
 #pragma unroll
         for (int k = 0; k < P - 1; ++k) yw[k] = yw[k + 1];
         yw[P - 1] = v;
-        z[(long long)it * Ns + j] = v;
+        if (YS) ybuf[(size_t)it * 32 + lane] = v;
+        else z[(long long)it * Ns + j] = v;
       }
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[u % S]);
   }
-  cp_async_wait<0>();
-  // backward: step it = Nt-1-(ch*C+c) needs u_{it,it+k} (slot k), k = 0..P;
-  // y[it] comes back from z with plain loads (this thread wrote it above)
-  auto issue_bwd = [&](int ch) {
-    if (active && ch < nch) {
-#pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int it = Nt - 1 - (ch * C + c);
-        if (it >= 0) {
-#pragma unroll
-          for (int k = 0; k <= P; ++k)
-            if (it + k < Nt) cp_async_elem(slot(ch, c, k), lu + ((long long)it * B + (P + k)) * Ns + j);
-        }
-      }
-    }
-    cp_async_commit();
-  };
   T zw[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) zw[k] = T(0);
-#pragma unroll
-  for (int ch = 0; ch < S - 1; ++ch) issue_bwd(ch);
-  for (int ch = 0; ch < nch; ++ch) {
-    issue_bwd(ch + S - 1);
+  for (int cb = 0; cb < nch; ++cb) {
+    const int u = nch + cb;
     T yv[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const int it = Nt - 1 - (ch * C + c);
-      yv[c] = (active && it >= 0) ? z[(long long)it * Ns + j] : T(0);
+      const int it = Nt - 1 - (cb * C + c);
+      yv[c] = (active && it >= 0) ? (YS ? ybuf[(size_t)it * 32 + lane] : z[(long long)it * Ns + j]) : T(0);
     }
-    cp_async_wait<S - 1>();
+    if (!mbar_wait(smem_u32(&full[u % S]), (uint32_t)((u / S) & 1), kLuWaitLimit)) {
+      atomicExch(err, 1);
+      return;
+    }
     if (active) {
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const int it = Nt - 1 - (ch * C + c);
+        const int it = Nt - 1 - (cb * C + c);
         if (it < 0) break;
         T v = yv[c];
 #pragma unroll
         for (int k = 1; k <= P; ++k)
-          if (it + k < Nt) v -= *slot(ch, c, k) * zw[k - 1];
-        v *= *slot(ch, c, 0);
+          if (it + k < Nt) v -= *cell(u, c, k) * zw[k - 1];
+        v *= *cell(u, c, 0);
 #pragma unroll
         for (int k = P - 1; k > 0; --k) zw[k] = zw[k - 1];
         zw[0] = v;
         z[(long long)it * Ns + j] = v;
       }
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[u % S]);
   }
-  cp_async_wait<0>();
 }
 
 template <typename T> struct Acc;
@@ -1930,24 +1951,32 @@ void launch_rot_gemm(cudaStream_t s, T *out, const T *in, const T *M, int nb, in
 }
 
 template <typename T>
-void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p) {
-  constexpr int threads = 64, C = 4, S = sizeof(T) == 4 ? 10 : 6;
-  unsigned blocks = (unsigned)((Ns + threads - 1) / threads);
-  auto go = [&](auto kern, int P) {
-    size_t sh = (size_t)S * C * (P + 1) * threads * sizeof(T);
-    static bool attr[5] = {false, false, false, false, false};
-    if (!attr[P]) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh);
-      attr[P] = true;
+void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p, int *err) {
+  const unsigned blocks = (unsigned)((Ns + 31) / 32);
+  // forward results kept in shared memory when a block's time lines fit
+  // (keeping them in shared memory caps residency at 3 blocks per SM and costs
+  // a second wave on the 2D workload, so y goes through z)
+  const bool ys = false;
+  auto go = [&](auto kern, int P, int slot) {
+    size_t sh = (size_t)kLuS * kLuC * (P + 1) * 32 * sizeof(T);
+    if (ys) sh += (size_t)Nt * 32 * sizeof(T);
+    static bool attr[10] = {false};
+    if (!attr[slot]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+      attr[slot] = true;
     }
     st_count_launch();
-    kern<<<blocks, threads, sh, s>>>(z, r, lu, Nt, Ns);
+    kern<<<blocks, 128, sh, s>>>(z, r, lu, Nt, Ns, err);
   };
-  switch (p) {
-    case 1: go(tline_lu_kernel<T, 1, C, S>, 1); break;
-    case 2: go(tline_lu_kernel<T, 2, C, S>, 2); break;
-    case 3: go(tline_lu_kernel<T, 3, C, S>, 3); break;
-    default: go(tline_lu_kernel<T, 4, C, S>, 4); break;
+  switch (p * 2 + (ys ? 1 : 0)) {
+    case 2: go(tline_lu_kernel<T, 1, false>, 1, 0); break;
+    case 3: go(tline_lu_kernel<T, 1, true>, 1, 1); break;
+    case 4: go(tline_lu_kernel<T, 2, false>, 2, 2); break;
+    case 5: go(tline_lu_kernel<T, 2, true>, 2, 3); break;
+    case 6: go(tline_lu_kernel<T, 3, false>, 3, 4); break;
+    case 7: go(tline_lu_kernel<T, 3, true>, 3, 5); break;
+    case 8: go(tline_lu_kernel<T, 4, false>, 4, 6); break;
+    default: go(tline_lu_kernel<T, 4, true>, 4, 7); break;
   }
 }
 
@@ -2090,7 +2119,8 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
   template bool launch_xband_fused<T>(cudaStream_t, T *, const T *, const T *, const T *, int, int,    \
                                       long long, int);                                                 \
   template void launch_mode_gemm<T>(cudaStream_t, T *, const T *, const T *, int, long long, long long); \
-  template void launch_tline_lu_solve<T>(cudaStream_t, T *, const T *, const T *, int, long long, int); \
+  template void launch_tline_lu_solve<T>(cudaStream_t, T *, const T *, const T *, int, long long, int,  \
+                                          int *);                                                          \
   template void launch_rot_gemm<T>(cudaStream_t, T *, const T *, const T *, int, int, long long, long long); \
   template void launch_multi_dot<T>(cudaStream_t, double *, const T *, long long, int, const T *,      \
                                     long long, double *);                                             \

@@ -194,7 +194,7 @@ bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const T *band, const
 template <typename T>
 void launch_mode_gemm(cudaStream_t s, T *out, const T *in, const T *A, int n, long long inner, long long outer);
 template <typename T>
-void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p);
+void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p, int *err);
 template <typename T>
 void launch_rot_gemm(cudaStream_t s, T *out, const T *in, const T *M, int nb, int nj, long long Aa, long long Nt);
 st_status launch_tc_xform(cudaStream_t s, float *out, const float *X, long long R, int nb, long long in_stride,

@@ -31,6 +31,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include "st_internal.h"
+#include "dev_sync.cuh"
 
 namespace {
 
@@ -38,9 +39,6 @@ constexpr int kTcKC = 32;          // K columns per chunk (128 bytes of TF32 = o
 constexpr int kTcRows = 128;       // MMA M (rows of X per tile)
 constexpr long long kWaitLimit = 1ll << 22;
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
 
 // Shared-memory matrix descriptor (tcgen05): start address, leading-dimension
 // byte offset (K direction, no-swizzle K-major only), stride-dimension byte
@@ -62,20 +60,6 @@ __host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t phase, long long limit) {
-  for (long long it = 0; it < limit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(addr), "r"(phase)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
 
 __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
