@@ -101,6 +101,15 @@ st_status upload(st_handle *h, T **dst, const std::vector<double> &src) {
 }
 
 template <typename T>
+st_status upload_vec(st_handle *h, T **dst, const std::vector<T> &src) {
+  st_status e = ST_OK;
+  *dst = dalloc<T>(h, std::max<size_t>(src.size(), 1), &e);
+  if (e != ST_OK) return e;
+  if (!src.empty()) ST_CUDA(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  ST_CUDA(cudaStreamSynchronize(h->stream));
+  return ST_OK;
+}
+
 st_status upload_i(st_handle *h, int **dst, const std::vector<int> &src) {
   st_status e = ST_OK;
   *dst = dalloc<int>(h, std::max<size_t>(src.size(), 1), &e);
@@ -710,6 +719,18 @@ static st_status setup_impl(st_handle *h) {
             bp[((size_t)e * td.nq + q) * np + pr++] = td.wq[e * td.nq + q] * td.at(0, e, q, i) * td.at(0, e, q, i + k);
       }
     ST_TRY(upload<double>(h, &h->bprod, bp));
+    // the same tables split into double-float pairs for the ionic kernel
+    auto split = [](const double *v, size_t n) {
+      std::vector<float2> out(n);
+      for (size_t i = 0; i < n; ++i) {
+        float hi = (float)v[i];
+        out[i] = make_float2(hi, (float)(v[i] - (double)hi));
+      }
+      return out;
+    };
+    const size_t nbt = (size_t)2 * td.n_el * td.nq * (h->p + 1);   // k = 0, 1 of [k][e][q][a]
+    ST_TRY(upload_vec<float2>(h, &h->bt2, split(hs.tdir.tab.data(), nbt)));
+    ST_TRY(upload_vec<float2>(h, &h->bprod2, split(bp.data(), bp.size())));
   }
   ST_TRY(upload<double>(h, &h->wt, hs.tdir.wq));
   ST_TRY(upload<double>(h, &h->xt, hs.tdir.xq));
@@ -720,11 +741,11 @@ static st_status setup_impl(st_handle *h) {
     std::vector<int> ii;
     std::vector<double> ll;
     hat_data(gt, hs.tdir.xq, ii, ll);
-    ST_TRY(upload_i<int>(h, &h->hat_i_t, ii));
+    ST_TRY(upload_i(h, &h->hat_i_t, ii));
     ST_TRY(upload<double>(h, &h->hat_l_t, ll));
     for (int l = 0; l < h->d; ++l) {
       hat_data(hs.sdir[l].greville, hs.sdir[l].xq, ii, ll);
-      ST_TRY(upload_i<int>(h, &h->hat_i_s[l], ii));
+      ST_TRY(upload_i(h, &h->hat_i_s[l], ii));
       ST_TRY(upload<double>(h, &h->hat_l_s[l], ll));
     }
   }

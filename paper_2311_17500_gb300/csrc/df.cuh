@@ -1,0 +1,70 @@
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi)/2, about 48 significant bits.  Built from the
+// error-free transformations of Dekker (Numer. Math. 18, 1971) and Knuth
+// (TAOCP vol. 2): the exact sum of two floats (two_sum, fast_two_sum when
+// |a| >= |b|) and the exact product through a fused multiply-add.  Used where
+// FP64 accuracy is needed but FP64 throughput (1/64 of the FP32 rate on
+// GB300) would bound the kernel.  Requires IEEE float semantics (no fast-math
+// reassociation), which the build keeps.
+#pragma once
+
+struct df {
+  float hi, lo;
+};
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+
+__device__ __forceinline__ df df_from(double d) {
+  const float h = __double2float_rn(d);
+  return {h, __double2float_rn(d - (double)h)};
+}
+
+__device__ __forceinline__ df df_from2(float2 v) { return {v.x, v.y}; }
+
+__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ df df_add(df a, df b) {
+  df s = df_two_sum(a.hi, b.hi);
+  return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p, e);
+}
+
+// a * b + c
+__device__ __forceinline__ df df_fma(df a, df b, df c) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  df s = df_two_sum(p, c.hi);
+  return df_fast_two_sum(s.hi, s.lo + (e + c.lo));
+}
+
+__device__ __forceinline__ df df_abs(df a) { return a.hi < 0.f ? df_neg(a) : a; }
+
+// larger of two non-negative values (ordered by hi, then lo); a NaN wins, so
+// that it reaches the statistics built from these maxima
+__device__ __forceinline__ df df_max_nonneg(df a, df b) {
+  if (!(a.hi == a.hi)) return a;
+  if (!(b.hi == b.hi)) return b;
+  return (a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo)) ? a : b;
+}

@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include "st_internal.h"
+#include "df.cuh"
 
 void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, int M, int N, int K,
                    long long sam, long long sak, long long sbk, long long sbc, long long scm, long long scc,
@@ -92,6 +93,7 @@ struct IonicArgs {
   const double *U0, *L0, *W0;   // [Nt][Qs]: u, sum D_l d_ll u, w at spatial Gauss points
   const double *bt, *xt;        // time tables: values/derivatives, points
   const double *bprod;          // [e][qt][pair]: w_t b_i b_{i+k} for the band pairs (i, k), k <= P - i
+  const float2 *bt2, *bprod2;   // the same tables as double-float pairs (bt for k = 0, 1)
   int Nt, nel_t;
   long long Qs, Nel_s;
   int kind;                     // ST_PICARD: C_r, ST_NEWTON: C_J
@@ -116,6 +118,8 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 // Newton), keeps max |R| per space-time element, and assembles the time band
 // sum_qt w_t C b_i b_j of the reaction mass term at this spatial point
 // (times its spatial weight).  Rows are written once complete.
+// The arithmetic is double-float (about 48 bits): FP64 is used only to
+// convert each input row once, the element maxima and the band rows.
 template <int P>
 __global__ void __launch_bounds__(128) ionic_tline_kernel(IonicArgs a) {
   constexpr int nq = P + 1, NPAIR = (P + 1) * (P + 2) / 2;
@@ -133,83 +137,100 @@ __global__ void __launch_bounds__(128) ionic_tline_kernel(IonicArgs a) {
         for (int l = 0; l < a.D.d; ++l) in = in && (sp.x[l] >= a.D.stim[b].lo[l]) && (sp.x[l] <= a.D.stim[b].hi[l]);
         if (in) inbox |= 1u << b;
       }
-    const double c1 = a.D.c1, c2 = a.D.c2, aa = a.D.a, Cm = a.D.C_m, apl = 1.0 + aa;
+    const df c1 = df_from(a.D.c1), c2 = df_from(a.D.c2), aa = df_from(a.D.a), Cm = df_from(a.D.C_m);
+    const df apl = df_from(1.0 + a.D.a), apl2 = df_from(2.0 * (1.0 + a.D.a)), three = {3.f, 0.f};
+    const df ws = df_from(sp.ws);
+    const df zero = {0.f, 0.f};
+    const bool newton = a.kind == ST_NEWTON;
     const long long plane = (long long)a.Nt * a.Qs;
-    double acc[P + 1][P + 1];
+    df acc[P + 1][P + 1];
 #pragma unroll
     for (int r = 0; r <= P; ++r)
 #pragma unroll
-      for (int k = 0; k <= P; ++k) acc[r][k] = 0.0;
-    for (int e = 0; e < a.nel_t; ++e) {
-      double cu[P + 1], cl[P + 1], cw[P + 1];
+      for (int k = 0; k <= P; ++k) acc[r][k] = zero;
+    // window of coefficient rows e-1 .. e+P-1 (row -1 is zero)
+    df cu[P + 1], cl[P + 1], cw[P + 1];
+    cu[0] = cl[0] = cw[0] = zero;
 #pragma unroll
-      for (int j = 0; j <= P; ++j) {
-        int it = e + j - 1;
-        bool ok = it >= 0;
-        long long off = (long long)it * a.Qs + q;
-        cu[j] = ok ? a.U0[off] : 0.0;
-        cl[j] = ok ? a.L0[off] : 0.0;
-        cw[j] = ok ? a.W0[off] : 0.0;
+    for (int j = 1; j <= P; ++j) {
+      const long long off = (long long)(j - 1) * a.Qs + q;
+      cu[j] = df_from(a.U0[off]);
+      cl[j] = df_from(a.L0[off]);
+      cw[j] = df_from(a.W0[off]);
+    }
+    df mu_d = zero, mut_d = zero;
+    for (int e = 0; e < a.nel_t; ++e) {
+      // next row (e + P), requested before this element's work
+      double nu = 0.0, nl = 0.0, nw = 0.0;
+      if (e + 1 < a.nel_t) {
+        const long long off = (long long)(e + P) * a.Qs + q;
+        nu = a.U0[off]; nl = a.L0[off]; nw = a.W0[off];
       }
-      unsigned long long rloc = 0;
+      df rloc = zero;
 #pragma unroll
       for (int qt = 0; qt < nq; ++qt) {
-        const double *b0 = a.bt + ((size_t)(0 * a.nel_t + e) * nq + qt) * (P + 1);
-        const double *b1 = a.bt + ((size_t)(1 * a.nel_t + e) * nq + qt) * (P + 1);
-        double u = 0.0, ut = 0.0, lap = 0.0, w = 0.0;
+        const float2 *b0 = a.bt2 + ((size_t)(0 * a.nel_t + e) * nq + qt) * (P + 1);
+        const float2 *b1 = a.bt2 + ((size_t)(1 * a.nel_t + e) * nq + qt) * (P + 1);
+        df u = zero, ut = zero, lap = zero, w = zero;
 #pragma unroll
         for (int j = 0; j <= P; ++j) {
-          double v0 = __ldg(b0 + j);
-          u = fma(v0, cu[j], u);
-          ut = fma(__ldg(b1 + j), cu[j], ut);
-          lap = fma(v0, cl[j], lap);
-          w = fma(v0, cw[j], w);
+          const df v0 = df_from2(__ldg(b0 + j)), v1 = df_from2(__ldg(b1 + j));
+          u = df_fma(v0, cu[j], u);
+          ut = df_fma(v1, cu[j], ut);
+          lap = df_fma(v0, cl[j], lap);
+          w = df_fma(v0, cw[j], w);
         }
-        double t = a.xt[e * nq + qt];
         double f = 0.0;
+        const double t = a.xt[e * nq + qt];
         if (stim) {
           for (int b = 0; b < a.D.n_stim; ++b)
             if (((inbox >> b) & 1u) && t >= a.D.stim[b].t0 && t < a.D.stim[b].t1) f += a.D.stim[b].amp;
         } else if (a.D.source_kind != ST_SRC_ZERO) {
           f = source_at(a.D, sp.x, t);
         }
+        const df fd = f == 0.0 ? zero : df_from(f);
         // C_r = c1 (u - a)(u - 1) + c2 w = c1 ((u - (1 + a)) u + a) + c2 w
-        double Cr = fma(c1, fma(u - apl, u, aa), c2 * w);
-        double R = fma(Cr, u, fma(Cm, ut, -lap) - f);
-        double C = Cr;
-        if (a.kind == ST_NEWTON) C = fma(c1, fma(fma(3.0, u, -2.0 * apl), u, aa), c2 * w);
-        unsigned long long rb = abs_bits(R);
-        rloc = rloc > rb ? rloc : rb;
-        unsigned long long ub = abs_bits(u), utb = abs_bits(ut);
-        mu = mu > ub ? mu : ub;
-        mut = mut > utb ? mut : utb;
-        double wc = sp.ws * C;
-        const double *bp = a.bprod + ((size_t)e * nq + qt) * NPAIR;
+        const df c2w = df_mul(c2, w);
+        const df Cr = df_fma(c1, df_fma(df_sub(u, apl), u, aa), c2w);
+        const df R = df_fma(Cr, u, df_sub(df_sub(df_mul(Cm, ut), lap), fd));
+        df C = Cr;
+        if (newton) C = df_fma(c1, df_fma(df_sub(df_mul(three, u), apl2), u, aa), c2w);
+        rloc = df_max_nonneg(rloc, df_abs(R));
+        mu_d = df_max_nonneg(mu_d, df_abs(u));
+        mut_d = df_max_nonneg(mut_d, df_abs(ut));
+        const df wc = df_mul(ws, C);
+        const float2 *bp = a.bprod2 + ((size_t)e * nq + qt) * NPAIR;
         int pr = 0;
 #pragma unroll
         for (int i = 0; i <= P; ++i)
 #pragma unroll
-          for (int k = 0; k <= P - i; ++k) { acc[i][k] = fma(wc, __ldg(bp + pr), acc[i][k]); ++pr; }
+          for (int k = 0; k <= P - i; ++k) { acc[i][k] = df_fma(wc, df_from2(__ldg(bp + pr)), acc[i][k]); ++pr; }
       }
-      mr = mr > rloc ? mr : rloc;
-      if (a.want_stats) atomicMax(&a.emax[(long long)e * a.Nel_s + sp.es], rloc);
+      const unsigned long long rb = abs_bits(df_to(rloc));
+      mr = mr > rb ? mr : rb;
+      if (a.want_stats) atomicMax(&a.emax[(long long)e * a.Nel_s + sp.es], rb);
       // row e-1 is complete
       int row = e - 1;
       if (row >= 0)
 #pragma unroll
-        for (int k = 0; k <= P; ++k) a.band[k * plane + (long long)row * a.Qs + q] = acc[0][k];
+        for (int k = 0; k <= P; ++k) a.band[k * plane + (long long)row * a.Qs + q] = df_to(acc[0][k]);
 #pragma unroll
       for (int r = 0; r < P; ++r)
 #pragma unroll
         for (int k = 0; k <= P; ++k) acc[r][k] = acc[r + 1][k];
 #pragma unroll
-      for (int k = 0; k <= P; ++k) acc[P][k] = 0.0;
+      for (int k = 0; k <= P; ++k) acc[P][k] = zero;
+#pragma unroll
+      for (int j = 0; j < P; ++j) { cu[j] = cu[j + 1]; cl[j] = cl[j + 1]; cw[j] = cw[j + 1]; }
+      cu[P] = df_from(nu); cl[P] = df_from(nl); cw[P] = df_from(nw);
     }
     for (int r = 0; r < P; ++r) {
       int row = a.nel_t - 1 + r;
       if (row < a.Nt)
-        for (int k = 0; k <= P; ++k) a.band[k * plane + (long long)row * a.Qs + q] = acc[r][k];
+        for (int k = 0; k <= P; ++k) a.band[k * plane + (long long)row * a.Qs + q] = df_to(acc[r][k]);
     }
+    mu = abs_bits(df_to(mu_d));
+    mut = abs_bits(df_to(mut_d));
   }
   if (a.want_stats) {
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -535,6 +556,7 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   a.g = geom(h);
   a.U0 = h->U0; a.L0 = h->L0; a.W0 = h->Wq0;
   a.bt = h->bt; a.xt = h->xt; a.bprod = h->bprod;
+  a.bt2 = h->bt2; a.bprod2 = h->bprod2;
   a.Nt = h->Nt; a.nel_t = h->nel_t;
   a.Qs = h->Qs; a.Nel_s = h->Nel_s;
   a.kind = kind;

@@ -64,6 +64,8 @@ struct st_handle {
   double *xs[3] = {};         // spatial points per direction [e*nq+q]
   double *tauq = nullptr;     // [l-1][e][q]
   double *bprod = nullptr;    // [e][q][pair] w_t b_i b_{i+k}, pairs (i, k) with k <= p - i
+  float2 *bt2 = nullptr;      // bt for k = 0, 1 as double-float pairs (hi, lo)
+  float2 *bprod2 = nullptr;   // bprod as double-float pairs
   double *wlu = nullptr;      // LU of W_t + b d_e M_t
   // hat-function data of the Greville interpolation, per 1D Gauss point
   int *hat_i_t = nullptr, *hat_i_s[3] = {};
