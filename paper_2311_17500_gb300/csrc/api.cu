@@ -67,12 +67,12 @@ Sizes plan(const st_problem_desc &D) {
   b += (size_t)(3 * z.nmax * z.nq * z.nq * 4) * d8;
   b += (size_t)z.Ns * d8;                                          // mu
   b += (size_t)z.Nt * z.B * z.Ns * (d8 + f4);                      // LU per eigen-index
-  b += (size_t)(z.p + 1) * z.NtQs * (d8 + f4);                     // bands
+  b += (size_t)(z.p + 1) * z.NtQs * (f4 + f4);                     // bands (high + low parts)
   b += (size_t)z.Ndof * d8 * 9;                                    // f, theta, FP64 vectors
   b += (size_t)z.Ndof * f4 * 4;                                    // FP32 vectors
   b += (size_t)z.nel_t * z.Nel_s * 8;                              // element maxima
   b += (size_t)z.Nt * z.Nt * d8 * 2 + (size_t)z.nmax * z.nmax * (12 * d8 + 2 * f4);
-  b += (size_t)z.cap * (z.Nt + z.Ns + 1 + z.Qt + (z.p + 1) * z.Nt) * d8;
+  b += (size_t)z.cap * (z.Nt + z.Ns + 1 + z.Qt + 2 * (z.p + 1) * z.Nt) * d8;
   b += (size_t)z.NtQs * d8 * 5;                                    // two work buffers + ionic fields
   b += (size_t)z.NtQs * f4 * 2;
   b += (size_t)z.Ndof * (d8 + f4) * 7;                             // Kronecker temporaries
@@ -337,7 +337,7 @@ template <> struct Prec<double> {
   static const double *Bq(st_handle *h, int l) { return h->Bq[l]; }
   static double *W(st_handle *h, int i) { return h->W64[i]; }
   static double *K(st_handle *h, int i) { return h->K64[i]; }
-  static const double *band(st_handle *h) { return h->band64; }
+  static const float *band_lo(st_handle *h) { return h->band_lo; }
   static const double *UT(st_handle *h, int l) { return h->UT64[l]; }
   static const double *U(st_handle *h, int l) { return h->U64[l]; }
   static const double *lu(st_handle *h) { return h->lu64; }
@@ -350,7 +350,7 @@ template <> struct Prec<float> {
   static const float *Bq(st_handle *h, int l) { return h->Bq32[l]; }
   static float *W(st_handle *h, int i) { return h->W32[i]; }
   static float *K(st_handle *h, int i) { return h->K32[i]; }
-  static const float *band(st_handle *h) { return h->band32; }
+  static const float *band_lo(st_handle *) { return nullptr; }
   static const float *UT(st_handle *h, int l) { return h->UT32[l]; }
   static const float *U(st_handle *h, int l) { return h->U32[l]; }
   static const float *lu(st_handle *h) { return h->lu32; }
@@ -450,7 +450,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
     T *Y1 = P::W(h, ping);
     {
       ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_QBAND, sz * ((double)(p + 1) * h->NtQs + 2.0 * (double)Nt * rows * nx));
-      launch_xband_fused<T>(s, Y1, cur, P::band(h), P::Bq(h, 0), h->nel[0], (int)Nt, rows, p);
+      launch_xband_fused<T>(s, Y1, cur, h->band32, P::band_lo(h), P::Bq(h, 0), h->nel[0], (int)Nt, rows, p);
     }
     cur = Y1;
     ping ^= 1;
@@ -481,7 +481,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   T *zq = P::W(h, ping);
   {
     ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_QBAND, sz * (double)h->NtQs * (p + 3));
-    launch_qband_apply<T>(s, zq, cur, P::band(h), h->Nt, h->Qs, p);
+    launch_qband_apply<T>(s, zq, cur, h->band32, P::band_lo(h), h->Nt, h->Qs, p);
   }
   cur = zq;
   ping ^= 1;
@@ -760,8 +760,8 @@ static st_status setup_impl(st_handle *h) {
   h->mu = dalloc<double>(h, h->Ns, &e);
   h->lu64 = dalloc<double>(h, (size_t)h->Nt * h->B * h->Ns, &e);
   h->lu32 = dalloc<float>(h, (size_t)h->Nt * h->B * h->Ns, &e);
-  h->band64 = dalloc<double>(h, (size_t)(h->p + 1) * h->NtQs, &e);
   h->band32 = dalloc<float>(h, (size_t)(h->p + 1) * h->NtQs, &e);
+  h->band_lo = dalloc<float>(h, (size_t)(h->p + 1) * h->NtQs, &e);
   h->f64 = dalloc<double>(h, h->Ndof, &e);
   h->emax = dalloc<unsigned long long>(h, (size_t)h->nel_t * h->Nel_s, &e);
   h->stats = dalloc<double>(h, 8, &e);
@@ -777,6 +777,7 @@ static st_status setup_impl(st_handle *h) {
   h->Vr = dalloc<double>(h, (size_t)h->Ns * cap, &e);
   h->th_t = dalloc<double>(h, (size_t)cap * h->Qt, &e);
   h->Tr = dalloc<double>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
+  h->Tr2 = dalloc<float2>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
   for (int i = 0; i < 2; ++i) {
     h->W64[i] = dalloc<double>(h, h->NtQs, &e);
     h->W32[i] = dalloc<float>(h, h->NtQs, &e);

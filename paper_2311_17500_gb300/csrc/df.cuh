@@ -68,3 +68,29 @@ __device__ __forceinline__ df df_max_nonneg(df a, df b) {
   if (!(b.hi == b.hi)) return b;
   return (a.hi > b.hi || (a.hi == b.hi && a.lo >= b.lo)) ? a : b;
 }
+
+// Arithmetic shared by float and double-float code paths (the compute type
+// of a kernel instantiated for FP32 or for FP64 accuracy).
+__device__ __forceinline__ float ct_fma(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ df ct_fma(df a, df b, df c) { return df_fma(a, b, c); }
+__device__ __forceinline__ float ct_add(float a, float b) { return a + b; }
+__device__ __forceinline__ df ct_add(df a, df b) { return df_add(a, b); }
+__device__ __forceinline__ float ct_shfl_up(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ df ct_shfl_up(df v, int d) {
+  return {__shfl_up_sync(0xffffffffu, v.hi, d), __shfl_up_sync(0xffffffffu, v.lo, d)};
+}
+__device__ __forceinline__ float ct_shfl_down(float v, int d) { return __shfl_down_sync(0xffffffffu, v, d); }
+__device__ __forceinline__ df ct_shfl_down(df v, int d) {
+  return {__shfl_down_sync(0xffffffffu, v.hi, d), __shfl_down_sync(0xffffffffu, v.lo, d)};
+}
+template <typename CT> __device__ __forceinline__ CT ct_zero();
+template <> __device__ __forceinline__ float ct_zero<float>() { return 0.f; }
+template <> __device__ __forceinline__ df ct_zero<df>() { return {0.f, 0.f}; }
+template <typename CT> __device__ __forceinline__ CT ct_from(float v);
+template <> __device__ __forceinline__ float ct_from<float>(float v) { return v; }
+template <> __device__ __forceinline__ df ct_from<df>(float v) { return {v, 0.f}; }
+template <typename CT> __device__ __forceinline__ CT ct_from(double v);
+template <> __device__ __forceinline__ float ct_from<float>(double v) { return (float)v; }
+template <> __device__ __forceinline__ df ct_from<df>(double v) { return df_from(v); }
+__device__ __forceinline__ void ct_store(float *p, float v) { *p = v; }
+__device__ __forceinline__ void ct_store(double *p, df v) { *p = df_to(v); }

@@ -98,7 +98,7 @@ struct IonicArgs {
   long long Qs, Nel_s;
   int kind;                     // ST_PICARD: C_r, ST_NEWTON: C_J
   int want_stats;
-  double *band;                 // [k][it][q]
+  float *band_hi, *band_lo;     // [k][it][q] as double-float pairs
   unsigned long long *emax;     // [et][es]
   unsigned long long *stats;    // max|u|, max|d_t u|, max|R| (bit patterns)
 };
@@ -118,8 +118,9 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 // Newton), keeps max |R| per space-time element, and assembles the time band
 // sum_qt w_t C b_i b_j of the reaction mass term at this spatial point
 // (times its spatial weight).  Rows are written once complete.
-// The arithmetic is double-float (about 48 bits): FP64 is used only to
-// convert each input row once, the element maxima and the band rows.
+// The arithmetic is double-float (about 48 bits) and the band rows are stored
+// as their (high, low) float parts; FP64 is used only to convert each input
+// row once and for the element maxima.
 template <int P>
 __global__ void __launch_bounds__(128) ionic_tline_kernel(IonicArgs a) {
   constexpr int nq = P + 1, NPAIR = (P + 1) * (P + 2) / 2;
@@ -213,7 +214,11 @@ __global__ void __launch_bounds__(128) ionic_tline_kernel(IonicArgs a) {
       int row = e - 1;
       if (row >= 0)
 #pragma unroll
-        for (int k = 0; k <= P; ++k) a.band[k * plane + (long long)row * a.Qs + q] = df_to(acc[0][k]);
+        for (int k = 0; k <= P; ++k) {
+          const long long bi = k * plane + (long long)row * a.Qs + q;
+          a.band_hi[bi] = acc[0][k].hi;
+          a.band_lo[bi] = acc[0][k].lo;
+        }
 #pragma unroll
       for (int r = 0; r < P; ++r)
 #pragma unroll
@@ -227,7 +232,11 @@ __global__ void __launch_bounds__(128) ionic_tline_kernel(IonicArgs a) {
     for (int r = 0; r < P; ++r) {
       int row = a.nel_t - 1 + r;
       if (row < a.Nt)
-        for (int k = 0; k <= P; ++k) a.band[k * plane + (long long)row * a.Qs + q] = df_to(acc[r][k]);
+        for (int k = 0; k <= P; ++k) {
+          const long long bi = k * plane + (long long)row * a.Qs + q;
+          a.band_hi[bi] = acc[r][k].hi;
+          a.band_lo[bi] = acc[r][k].lo;
+        }
     }
     mu = abs_bits(df_to(mu_d));
     mut = abs_bits(df_to(mut_d));
@@ -461,22 +470,33 @@ __global__ void wupdate_kernel(double *__restrict__ w, const double *__restrict_
   }
 }
 
-// band64[m][q] += sum_r Tr[r][m] Cq[r][q] (the SU ranks of Eq. tildeS added to
-// the reaction band), and the FP32 copy band32 = band64, in one pass.
+// FP64 values split into double-float pairs.
+__global__ void d2df_kernel(float2 *__restrict__ out, const double *__restrict__ in, long long n) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const df v = df_from(in[e]);
+    out[e] = make_float2(v.hi, v.lo);
+  }
+}
+
+// band[m][q] += sum_{r0 <= r < r0 + RMAX, r < R} Tr[r][m] Cq[r][q] (SU ranks of
+// Eq. tildeS added to the reaction band) in double-float arithmetic on the
+// (high, low) pairs; Tr and Cq come split into pairs.
 template <int RMAX>
-__global__ void su_band_update_kernel(double *__restrict__ band64, float *__restrict__ band32,
-                                      const double *__restrict__ Tr, const double *__restrict__ Cq, int R,
+__global__ void su_band_update_kernel(float *__restrict__ bhi, float *__restrict__ blo,
+                                      const float2 *__restrict__ Tr, const float2 *__restrict__ Cq, int r0, int R,
                                       long long Mrows, long long Qs) {
   long long total = Mrows * Qs;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
     long long m = idx / Qs, q = idx - m * Qs;
-    double v = band64[idx];
+    df v = {bhi[idx], blo[idx]};
 #pragma unroll
-    for (int r = 0; r < RMAX; ++r)
-      if (r < R) v += Tr[(long long)r * Mrows + m] * Cq[(long long)r * Qs + q];
-    band64[idx] = v;
-    band32[idx] = (float)v;
+    for (int rr = 0; rr < RMAX; ++rr) {
+      const int r = r0 + rr;
+      if (r < R) v = df_fma(df_from2(__ldg(Tr + (long long)r * Mrows + m)), df_from2(__ldg(Cq + (long long)r * Qs + q)), v);
+    }
+    bhi[idx] = v.hi;
+    blo[idx] = v.lo;
   }
 }
 
@@ -561,7 +581,8 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   a.Qs = h->Qs; a.Nel_s = h->Nel_s;
   a.kind = kind;
   a.want_stats = want_stats ? 1 : 0;
-  a.band = h->band64;
+  a.band_hi = h->band32;
+  a.band_lo = h->band_lo;
   a.emax = h->emax;
   a.stats = (unsigned long long *)h->stats;
   unsigned blocks = (unsigned)((h->Qs + 127) / 128);
@@ -669,10 +690,7 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
 }
 
 st_status su_band_add(st_handle *h) {
-  if (h->desc.stabilization != ST_SU || h->rank == 0) {
-    launch_band_to_f32(h->stream, h->band32, h->band64, (long long)(h->p + 1) * h->NtQs);
-    return ST_OK;
-  }
+  if (h->desc.stabilization != ST_SU || h->rank == 0) return ST_OK;   // the reaction band alone
   cudaStream_t s = h->stream;
   int R = h->rank, p = h->p;
   st_count_launch(); theta_t_kernel<<<grid_for((long long)h->Qt * R), 256, 0, s>>>(h->th_t, h->Ur, R, h->Qt, h->hat_i_t, h->hat_l_t);
@@ -687,16 +705,21 @@ st_status su_band_add(st_handle *h) {
     hat.n[l] = h->n[l];
   }
   st_count_launch(); su_space_coef_kernel<<<grid_for(h->Qs * R), 256, 0, s>>>(Cq, h->Vr, h->sr, geom(h), hat, h->desc.C_m, R, h->Qs);
-  // band[(k,it)][q] += sum_r Tr[r][(k,it)] Cq[r][q], and the FP32 copy
+  // band[(k,it)][q] += sum_r Tr[r][(k,it)] Cq[r][q], 16 ranks per pass, with
+  // both factors split into double-float pairs first (Cq into the second work
+  // buffer: R Q_s <= N_t Q_s pairs)
   int Mrows = (p + 1) * h->Nt;
   long long total = (long long)Mrows * h->Qs;
-  if (R <= 8) {
-    st_count_launch(); su_band_update_kernel<8><<<grid_for(total), 256, 0, s>>>(h->band64, h->band32, h->Tr, Cq, R, Mrows, h->Qs);
-  } else if (R <= 16) {
-    st_count_launch(); su_band_update_kernel<16><<<grid_for(total), 256, 0, s>>>(h->band64, h->band32, h->Tr, Cq, R, Mrows, h->Qs);
-  } else {
-    launch_gemm64(s, h->band64, h->Tr, Cq, Mrows, (int)h->Qs, R, 1, Mrows, h->Qs, 1, h->Qs, 1, 1.0, 1.0);
-    launch_band_to_f32(s, h->band32, h->band64, total);
+  float2 *Cq2 = reinterpret_cast<float2 *>(h->W64[1]);
+  float2 *Tr2 = h->Tr2;
+  st_count_launch(); d2df_kernel<<<grid_for((long long)R * h->Qs), 256, 0, s>>>(Cq2, Cq, (long long)R * h->Qs);
+  st_count_launch(); d2df_kernel<<<grid_for((long long)R * Mrows), 256, 0, s>>>(Tr2, h->Tr, (long long)R * Mrows);
+  for (int r0 = 0; r0 < R; r0 += 16) {
+    if (R - r0 <= 8) {
+      st_count_launch(); su_band_update_kernel<8><<<grid_for(total), 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+    } else {
+      st_count_launch(); su_band_update_kernel<16><<<grid_for(total), 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+    }
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;

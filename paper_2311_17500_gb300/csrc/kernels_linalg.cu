@@ -6,6 +6,7 @@
 #include <algorithm>
 #include "st_internal.h"
 #include "dev_sync.cuh"
+#include "df.cuh"
 
 namespace {
 
@@ -718,8 +719,8 @@ void launch_tiled_p(cudaStream_t s, int p, T *out, const TiledTerms<T> &tt, int 
 // the whole time line of a column; the window of x and band rows lives in
 // registers, so every band entry and x value is read once.
 template <typename T, int P>
-__global__ void qband_kernel(T *__restrict__ z, const T *__restrict__ x, const T *__restrict__ band,
-                             int Nt, long long Qs) {
+__global__ void qband_kernel(T *__restrict__ z, const T *__restrict__ x, const float *__restrict__ bhi,
+                             const float *__restrict__ blo, int Nt, long long Qs) {
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= Qs) return;
   const long long plane = (long long)Nt * Qs;
@@ -740,7 +741,10 @@ __global__ void qband_kernel(T *__restrict__ z, const T *__restrict__ x, const T
     xw[2 * P] = (it + P < Nt) ? x[(long long)(it + P) * Qs + q] : T(0);
     T b[P + 1];
 #pragma unroll
-    for (int k = 0; k <= P; ++k) b[k] = band[k * plane + (long long)it * Qs + q];
+    for (int k = 0; k <= P; ++k) {
+      const long long bi = k * plane + (long long)it * Qs + q;
+      b[k] = sizeof(T) == 8 ? (T)((double)bhi[bi] + (double)blo[bi]) : (T)bhi[bi];
+    }
     T s = b[0] * xw[P];
 #pragma unroll
     for (int k = 1; k <= P; ++k) s += b[k] * xw[P + k] + bl[P - k][k] * xw[P - k];
@@ -825,8 +829,11 @@ __device__ __forceinline__ void load_nq_shared(T (&v)[NQ], const T *p) {
 // along the fastest spatial axis:  Y1 = Bx^T (band) Bx X1  for every row o of
 // the other axes (already at their Gauss points) and every time step.
 //   X1, Y1 : [Nt][rows][nx]        x-coefficients of each Gauss row
-//   band   : [k][Nt][rows][Qx]     band[k][it] = T(it, it+k), k = 0..P
+//   band   : [k][Nt][rows][Qx]     band[k][it] = T(it, it+k), k = 0..P, as
+//                                   double-float pairs (bhi, blo)
 //   tab    : [ex][g][a]            local basis a at Gauss point g of element ex
+// The FP32 instance reads bhi and computes in float; the FP64 instance reads
+// both parts and computes in double-float (FP64 accuracy on the FP32 pipe).
 // One block per (row, time segment), one thread per x element (its nq Gauss
 // points) plus P threads for the trailing coefficients (at most 512 threads,
 // 256 for FP64 or p = 4 so that the window stays in registers).  The block
@@ -844,81 +851,107 @@ __device__ __forceinline__ void load_nq_shared(T (&v)[NQ], const T *p) {
 template <typename T, int P>
 constexpr int xband_max_threads() { return (sizeof(T) == 8 || P >= 4) ? 256 : 512; }
 
+template <typename T> struct XbandCT { typedef float type; };
+template <> struct XbandCT<double> { typedef df type; };
+
 template <typename T, int P, int S>
-__global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(T *__restrict__ Y1, const T *__restrict__ X1,
-                                                           const T *__restrict__ band, const T *__restrict__ tab,
-                                                           int nel, int Nt, long long rows, int seglen) {
-  constexpr int nq = P + 1;
+__global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
+    T *__restrict__ Y1, const T *__restrict__ X1, const float *__restrict__ bhi, const float *__restrict__ blo,
+    const T *__restrict__ tab, int nel, int Nt, long long rows, int seglen) {
+  typedef typename XbandCT<T>::type CT;
+  constexpr bool DF = sizeof(T) == 8;
+  constexpr int nq = P + 1, NB = DF ? 2 : 1;   // band parts per value
   static_assert(S >= 2, "ring depth");
-  __shared__ T xch[2][16][P][P];   // [step parity][warp][a-1][lane-(32-P)]
+  __shared__ CT xch[2][16][P][P];   // [step parity][warp][a-1][lane-(32-P)]
   extern __shared__ __align__(16) unsigned char xb_raw[];
   const int nth = blockDim.x;
-  T *bring = reinterpret_cast<T *>(xb_raw);              // [S][P+1][thread][nq]
-  T *xring = bring + (size_t)S * (P + 1) * nth * nq;     // [S][thread]
+  float *bring = reinterpret_cast<float *>(xb_raw);                  // [S][NB][P+1][thread][nq]
+  T *xring = reinterpret_cast<T *>(bring + (size_t)S * NB * (P + 1) * nth * nq);   // [S][thread]
   const int nx = nel + P, Qx = nel * nq;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const bool owns = t < nel;
-  T wv[nq][P + 1];
+  const CT zero = ct_zero<CT>();
+  CT wv[nq][P + 1];
 #pragma unroll
   for (int g = 0; g < nq; ++g)
 #pragma unroll
-    for (int a = 0; a <= P; ++a) wv[g][a] = owns ? __ldg(tab + ((size_t)t * nq + g) * (P + 1) + a) : T(0);
+    for (int a = 0; a <= P; ++a) wv[g][a] = owns ? ct_from<CT>(__ldg(tab + ((size_t)t * nq + g) * (P + 1) + a)) : zero;
   const long long planeX = rows * nx, planeQ = rows * Qx, bandK = (long long)Nt * planeQ;
   const int nseg = (Nt + seglen - 1) / seglen;
   for (long long blk = blockIdx.x; blk < rows * nseg; blk += gridDim.x) {
     const long long o = blk % rows;
     const int t0 = (int)(blk / rows) * seglen, t1 = min(Nt, t0 + seglen);
     const T *xrow = X1 + o * nx + t;
-    const T *brow = band + o * Qx + (long long)t * nq;
+    const long long boff = o * Qx + (long long)t * nq;
     T *yrow = Y1 + o * nx;
-    auto gauss = [&](const T (&c)[P + 1], T (&xq)[nq]) {
+    auto gauss = [&](const CT (&c)[P + 1], CT (&xq)[nq]) {
 #pragma unroll
       for (int g = 0; g < nq; ++g) {
-        T v = T(0);
+        CT v = zero;
 #pragma unroll
-        for (int a = 0; a <= P; ++a) v += wv[g][a] * c[a];
+        for (int a = 0; a <= P; ++a) v = ct_fma(wv[g][a], c[a], v);
         xq[g] = v;
       }
     };
-    auto interp_global = [&](int it, T (&xq)[nq]) {
-      T c[P + 1];
+    auto interp_global = [&](int it, CT (&xq)[nq]) {
+      CT c[P + 1];
 #pragma unroll
-      for (int a = 0; a <= P; ++a) c[a] = (owns && it >= 0 && it < Nt) ? xrow[(long long)it * planeX + a] : T(0);
+      for (int a = 0; a <= P; ++a)
+        c[a] = (owns && it >= 0 && it < Nt) ? ct_from<CT>(xrow[(long long)it * planeX + a]) : zero;
       gauss(c, xq);
     };
-    T acc[P][nq];      // lower-triangle terms owed to steps it .. it+P-1
+    auto band_global = [&](long long idx, CT (&v)[nq]) {
+      float h[nq];
+      load_nq<float, nq>(h, bhi + idx);
+      if constexpr (DF) {
+        float l[nq];
+        load_nq<float, nq>(l, blo + idx);
+#pragma unroll
+        for (int g = 0; g < nq; ++g) v[g] = CT{h[g], l[g]};
+      } else {
+#pragma unroll
+        for (int g = 0; g < nq; ++g) v[g] = ct_from<CT>(h[g]);
+      }
+    };
+    CT acc[P][nq];      // lower-triangle terms owed to steps it .. it+P-1
 #pragma unroll
     for (int k = 0; k < P; ++k)
 #pragma unroll
-      for (int g = 0; g < nq; ++g) acc[k][g] = T(0);
+      for (int g = 0; g < nq; ++g) acc[k][g] = zero;
     // replay steps t0-P .. t0-1: band[k][it'] x(it') owed to t0 + m, m = it'+k-t0
 #pragma unroll
     for (int r = P; r >= 1; --r) {
       const int itp = t0 - r;
       if (itp < 0 || !owns) continue;
-      T xp[nq];
+      CT xp[nq];
       interp_global(itp, xp);
 #pragma unroll
       for (int k = 1; k <= P; ++k) {
         const int m = k - r;
         if (m < 0) continue;
-        T bv[nq];
-        load_nq<T, nq>(bv, brow + k * bandK + (long long)itp * planeQ);
+        CT bv[nq];
+        band_global(boff + k * bandK + (long long)itp * planeQ, bv);
 #pragma unroll
-        for (int g = 0; g < nq; ++g) acc[m][g] += bv[g] * xp[g];
+        for (int g = 0; g < nq; ++g) acc[m][g] = ct_fma(bv[g], xp[g], acc[m][g]);
       }
     }
-    T xw[P + 1][nq];   // x(it + k) at the element's Gauss points
+    CT xw[P + 1][nq];   // x(it + k) at the element's Gauss points
 #pragma unroll
     for (int k = 0; k < P; ++k) interp_global(t0 + k, xw[k + 1]);
     // step u needs band row u and coefficient row u + P
-    auto bslot = [&](int u, int k) -> T * { return bring + ((size_t)((u % S) * (P + 1) + k) * nth + t) * nq; };
+    auto bslot = [&](int u, int part, int k) -> float * {
+      return bring + ((size_t)(((u % S) * NB + part) * (P + 1) + k) * nth + t) * nq;
+    };
     auto xslot = [&](int u) -> T * { return xring + (size_t)(u % S) * nth; };
     auto issue = [&](int u) {
       if (u < t1) {
         if (owns) {
 #pragma unroll
-          for (int k = 0; k <= P; ++k) cp_async_nq<T, nq>(bslot(u, k), brow + k * bandK + (long long)u * planeQ);
+          for (int k = 0; k <= P; ++k) {
+            const long long idx = boff + k * bandK + (long long)u * planeQ;
+            cp_async_nq<float, nq>(bslot(u, 0, k), bhi + idx);
+            if constexpr (DF) cp_async_nq<float, nq>(bslot(u, 1, k), blo + idx);
+          }
         }
         if (t < nx && u + P < Nt) cp_async_elem(xslot(u) + t, X1 + (long long)(u + P) * planeX + o * nx + t);
       }
@@ -926,7 +959,7 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
     };
 #pragma unroll
     for (int u = 0; u < S - 1; ++u) issue(t0 + u);
-    T pend = T(0);   // this thread's output of the previous step, before its cross-warp part
+    CT pend = zero;   // this thread's output of the previous step, before its cross-warp part
     for (int it = t0; it < t1; ++it) {
       cp_async_wait<S - 2>();
       __syncthreads();
@@ -935,18 +968,29 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
         if (lane < P && warp > 0) {
 #pragma unroll
           for (int a = 1; a <= P; ++a)
-            if (a > lane) pend += xch[pp][warp - 1][a - 1][lane + P - a];
+            if (a > lane) pend = ct_add(pend, xch[pp][warp - 1][a - 1][lane + P - a]);
         }
-        if (t < nx) yrow[(long long)(it - 1) * planeX + t] = pend;
+        if (t < nx) ct_store(yrow + (long long)(it - 1) * planeX + t, pend);
       }
       issue(it + S - 1);
-      T b[P + 1][nq];
+      CT b[P + 1][nq];
 #pragma unroll
       for (int k = 0; k <= P; ++k) {
-        if (owns) load_nq_shared<T, nq>(b[k], bslot(it, k));
-        else {
+        if (owns) {
+          float h[nq];
+          load_nq_shared<float, nq>(h, bslot(it, 0, k));
+          if constexpr (DF) {
+            float l[nq];
+            load_nq_shared<float, nq>(l, bslot(it, 1, k));
 #pragma unroll
-          for (int g = 0; g < nq; ++g) b[k][g] = T(0);
+            for (int g = 0; g < nq; ++g) b[k][g] = CT{h[g], l[g]};
+          } else {
+#pragma unroll
+            for (int g = 0; g < nq; ++g) b[k][g] = ct_from<CT>(h[g]);
+          }
+        } else {
+#pragma unroll
+          for (int g = 0; g < nq; ++g) b[k][g] = zero;
         }
       }
 #pragma unroll
@@ -954,40 +998,54 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
 #pragma unroll
         for (int g = 0; g < nq; ++g) xw[k][g] = xw[k + 1][g];
       {
-        T c[P + 1];
+        CT c[P + 1];
         const T *xs = xslot(it);
+        const bool ok = it + P < Nt;
+        if constexpr (DF) {
+          // each coefficient converted once: by its own thread, then shuffled
+          // down to the elements that use it (across the warp edge, read again)
+          const CT mine = (ok && t < nx) ? ct_from<CT>(xs[t]) : zero;
+          c[0] = owns ? mine : zero;
 #pragma unroll
-        for (int a = 0; a <= P; ++a) c[a] = (owns && it + P < Nt) ? xs[t + a] : T(0);
+          for (int a = 1; a <= P; ++a) {
+            CT v = ct_shfl_down(mine, a);
+            if (lane + a >= 32) v = (ok && t + a < nx) ? ct_from<CT>(xs[t + a]) : zero;
+            c[a] = owns ? v : zero;
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a <= P; ++a) c[a] = (owns && ok) ? ct_from<CT>(xs[t + a]) : zero;
+        }
         gauss(c, xw[P]);
       }
-      T yq[nq];
+      CT yq[nq];
 #pragma unroll
       for (int g = 0; g < nq; ++g) {
-        T v = acc[0][g] + b[0][g] * xw[0][g];
+        CT v = ct_fma(b[0][g], xw[0][g], acc[0][g]);
 #pragma unroll
-        for (int k = 1; k <= P; ++k) v += b[k][g] * xw[k][g];
+        for (int k = 1; k <= P; ++k) v = ct_fma(b[k][g], xw[k][g], v);
         yq[g] = v;
       }
 #pragma unroll
       for (int k = 0; k < P - 1; ++k)
 #pragma unroll
-        for (int g = 0; g < nq; ++g) acc[k][g] = acc[k + 1][g] + b[k + 1][g] * xw[0][g];
+        for (int g = 0; g < nq; ++g) acc[k][g] = ct_fma(b[k + 1][g], xw[0][g], acc[k + 1][g]);
 #pragma unroll
-      for (int g = 0; g < nq; ++g) acc[P - 1][g] = b[P][g] * xw[0][g];
+      for (int g = 0; g < nq; ++g) acc[P - 1][g] = ct_fma(b[P][g], xw[0][g], zero);
       // contributions c[a] of this element to coefficient t + a
-      T c[P + 1];
+      CT c[P + 1];
 #pragma unroll
       for (int a = 0; a <= P; ++a) {
-        T v = T(0);
+        CT v = zero;
 #pragma unroll
-        for (int g = 0; g < nq; ++g) v += wv[g][a] * yq[g];
+        for (int g = 0; g < nq; ++g) v = ct_fma(wv[g][a], yq[g], v);
         c[a] = v;
       }
-      T out = c[0];
+      CT out = c[0];
 #pragma unroll
       for (int a = 1; a <= P; ++a) {
-        T v = __shfl_up_sync(0xffffffffu, c[a], a);
-        if (lane >= a) out += v;
+        CT v = ct_shfl_up(c[a], a);
+        if (lane >= a) out = ct_add(out, v);
       }
       if (lane >= 32 - P) {
 #pragma unroll
@@ -1002,9 +1060,9 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
       if (lane < P && warp > 0) {
 #pragma unroll
         for (int a = 1; a <= P; ++a)
-          if (a > lane) pend += xch[pp][warp - 1][a - 1][lane + P - a];
+          if (a > lane) pend = ct_add(pend, xch[pp][warp - 1][a - 1][lane + P - a]);
       }
-      if (t < nx) yrow[(long long)(t1 - 1) * planeX + t] = pend;
+      if (t < nx) ct_store(yrow + (long long)(t1 - 1) * planeX + t, pend);
     }
     __syncthreads();   // the next segment reuses the rings and xch
   }
@@ -1829,22 +1887,23 @@ void launch_interp_bwd(cudaStream_t s, T *out, const T *in, const T *tab, int ne
 }
 
 template <typename T>
-void launch_qband_apply(cudaStream_t s, T *z, const T *x, const T *band, int Nt, long long Qs, int p) {
+void launch_qband_apply(cudaStream_t s, T *z, const T *x, const float *bhi, const float *blo, int Nt, long long Qs,
+                        int p) {
   int threads = 128;
   long long blocks = (Qs + threads - 1) / threads;
   switch (p) {
-    case 1: st_count_launch(); qband_kernel<T, 1><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
-    case 2: st_count_launch(); qband_kernel<T, 2><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
-    case 3: st_count_launch(); qband_kernel<T, 3><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
-    default: st_count_launch(); qband_kernel<T, 4><<<(unsigned)blocks, threads, 0, s>>>(z, x, band, Nt, Qs); break;
+    case 1: st_count_launch(); qband_kernel<T, 1><<<(unsigned)blocks, threads, 0, s>>>(z, x, bhi, blo, Nt, Qs); break;
+    case 2: st_count_launch(); qband_kernel<T, 2><<<(unsigned)blocks, threads, 0, s>>>(z, x, bhi, blo, Nt, Qs); break;
+    case 3: st_count_launch(); qband_kernel<T, 3><<<(unsigned)blocks, threads, 0, s>>>(z, x, bhi, blo, Nt, Qs); break;
+    default: st_count_launch(); qband_kernel<T, 4><<<(unsigned)blocks, threads, 0, s>>>(z, x, bhi, blo, Nt, Qs); break;
   }
 }
 
 int xband_fused_limit(size_t elem, int p) { return (elem == 8 || p >= 4) ? 256 : 512; }
 
 template <typename T>
-bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const T *band, const T *tab, int nel, int Nt,
-                        long long rows, int p) {
+bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, const float *blo, const T *tab, int nel,
+                        int Nt, long long rows, int p) {
   const int threads = (nel + p + 31) / 32 * 32;
   if (threads > xband_fused_limit(sizeof(T), p) || rows < 1) return false;
   // time segments so that the grid holds about 16 blocks per SM, each
@@ -1856,14 +1915,15 @@ bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const T *band, const
   unsigned blocks = (unsigned)std::min<long long>(rows * nseg, 1LL << 30);
   constexpr int S = sizeof(T) == 4 ? 4 : 3;
   auto go = [&](auto kern, int P) {
-    size_t sh = ((size_t)S * (P + 1) * threads * (P + 1) + (size_t)S * threads) * sizeof(T);
+    const int NB = sizeof(T) == 8 ? 2 : 1;
+    size_t sh = (size_t)S * NB * (P + 1) * threads * (P + 1) * sizeof(float) + (size_t)S * threads * sizeof(T);
     static bool attr[5] = {false, false, false, false, false};
     if (!attr[P]) {
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr[P] = true;
     }
     st_count_launch();
-    kern<<<blocks, threads, sh, s>>>(Y1, X1, band, tab, nel, Nt, rows, seglen);
+    kern<<<blocks, threads, sh, s>>>(Y1, X1, bhi, blo, tab, nel, Nt, rows, seglen);
   };
   switch (p) {
     case 1: go(xband_fused_kernel<T, 1, S>, 1); break;
@@ -2112,12 +2172,13 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
                                      long long);                                                      \
   template void launch_interp_bwd<T>(cudaStream_t, T *, const T *, const T *, int, int, int, long long, \
                                      long long, bool);                                                \
-  template void launch_qband_apply<T>(cudaStream_t, T *, const T *, const T *, int, long long, int);   \
+  template void launch_qband_apply<T>(cudaStream_t, T *, const T *, const float *, const float *, int, \
+                                      long long, int);                                                  \
   template bool launch_kron2d<T>(cudaStream_t, T *, T *, T *, const T *, const T *, const T *, const T *, \
                                  const T *, const T *, const T *, int, int, int, int, double, double,   \
                                  double);                                                              \
-  template bool launch_xband_fused<T>(cudaStream_t, T *, const T *, const T *, const T *, int, int,    \
-                                      long long, int);                                                 \
+  template bool launch_xband_fused<T>(cudaStream_t, T *, const T *, const float *, const float *,       \
+                                      const T *, int, int, long long, int);                             \
   template void launch_mode_gemm<T>(cudaStream_t, T *, const T *, const T *, int, long long, long long); \
   template void launch_tline_lu_solve<T>(cudaStream_t, T *, const T *, const T *, int, long long, int,  \
                                           int *);                                                          \

@@ -66,6 +66,7 @@ struct st_handle {
   double *bprod = nullptr;    // [e][q][pair] w_t b_i b_{i+k}, pairs (i, k) with k <= p - i
   float2 *bt2 = nullptr;      // bt for k = 0, 1 as double-float pairs (hi, lo)
   float2 *bprod2 = nullptr;   // bprod as double-float pairs
+  float2 *Tr2 = nullptr;      // SU time bands (rank_cap x (p+1) N_t) as double-float pairs
   double *wlu = nullptr;      // LU of W_t + b d_e M_t
   // hat-function data of the Greville interpolation, per 1D Gauss point
   int *hat_i_t = nullptr, *hat_i_s[3] = {};
@@ -84,8 +85,10 @@ struct st_handle {
   float *lu32 = nullptr;
 
   // linearization: symmetric time band per spatial Gauss point, [k][it][q], k = 0..p
-  double *band64 = nullptr;
+  // time bands per spatial Gauss point [k][it][q] as double-float pairs:
+  // band32 = high parts (the FP32 operator), band_lo = low parts
   float *band32 = nullptr;
+  float *band_lo = nullptr;
   bool have_lin = false;
   double *f64 = nullptr;
 
@@ -178,7 +181,8 @@ template <typename T>
 void launch_interp_bwd(cudaStream_t s, T *out, const T *in, const T *tab, int nel, int p, int nq,
                        long long inner, long long outer, bool accumulate);
 template <typename T>
-void launch_qband_apply(cudaStream_t s, T *z, const T *x, const T *band, int Nt, long long Qs, int p);
+void launch_qband_apply(cudaStream_t s, T *z, const T *x, const float *bhi, const float *blo, int Nt, long long Qs,
+                        int p);
 // Fused x-axis reaction/SU pass Y1 = Bx^T band Bx X1 ([Nt][rows][nx] rows of
 // x-coefficients at Gauss rows of the other axes); false when the x axis has
 // too many elements for one block (then the caller takes the unfused path).
@@ -191,8 +195,8 @@ bool launch_kron2d(cudaStream_t s, T *y, T *xW, T *xM, const T *x, const T *Wt, 
 // Largest block (threads) of the fused x pass for this element size and degree.
 int xband_fused_limit(size_t elem, int p);
 template <typename T>
-bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const T *band, const T *tab, int nel, int Nt,
-                        long long rows, int p);
+bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, const float *blo, const T *tab, int nel,
+                        int Nt, long long rows, int p);
 template <typename T>
 void launch_mode_gemm(cudaStream_t s, T *out, const T *in, const T *A, int n, long long inner, long long outer);
 template <typename T>
