@@ -235,7 +235,7 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
       double vb = (double)N * sizeof(T);
       ProfScope ps(h, PROF_ARNOLDI, vb * (2.0 * (j + 2) + 2.0), 8.0 * (j + 2) * (double)N);
       launch_multi_dot2<T>(s, hd, V, ld, j + 2, uj, w, N, scratch);
-      launch_dcgs2_update<T>(s, V, ld, j, hd, N, sc);
+      launch_dcgs2_update<T>(s, V, ld, j, hd, N, sc, reinterpret_cast<T *>(h->gs_coef));
     }
     ST_CUDA(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
     int tc_flag = 0;
@@ -808,6 +808,7 @@ static st_status setup_impl(st_handle *h) {
   h->t32b = dalloc<float>(h, h->Ndof, &e);
   h->d32 = dalloc<float>(h, h->Ndof, &e);
   h->hcol = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
+  h->gs_coef = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
   if (e != ST_OK) return e;
   h->P32[0] = dalloc<float>(h, 2 * h->Ndof + 64, &e);
   h->P32[1] = dalloc<float>(h, 2 * h->Ndof + 64, &e);

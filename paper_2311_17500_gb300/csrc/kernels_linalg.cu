@@ -1608,9 +1608,9 @@ __global__ void __launch_bounds__(256) mdot2_kernel(double *__restrict__ partial
   const long long nvec = n / W;
   const long long chunk = (nvec + gridDim.x - 1) / gridDim.x;
   const long long beg = (long long)blockIdx.x * chunk, end = min(nvec, beg + chunk);
-  KahanAcc<T> acc[G][2];
+  T acc[G][2];
 #pragma unroll
-  for (int g = 0; g < G; ++g) { acc[g][0].zero(); acc[g][1].zero(); }
+  for (int g = 0; g < G; ++g) { acc[g][0] = T(0); acc[g][1] = T(0); }
   const VT *y1 = reinterpret_cast<const VT *>(x1), *y2 = reinterpret_cast<const VT *>(x2);
   // rows past the group end repeat the last row (loads stay unconditional so
   // they are all in flight together); their sums are never written.  The
@@ -1635,8 +1635,8 @@ __global__ void __launch_bounds__(256) mdot2_kernel(double *__restrict__ partial
     }
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-      acc[g][0].add(X::dot(v[g], a));
-      acc[g][1].add(X::dot(v[g], b));
+      acc[g][0] += X::dot(v[g], a);
+      acc[g][1] += X::dot(v[g], b);
     }
     a = an; b = bn;
 #pragma unroll
@@ -1648,8 +1648,8 @@ __global__ void __launch_bounds__(256) mdot2_kernel(double *__restrict__ partial
       for (int g = 0; g < G; ++g)
         if (g < cnt) {
           T v = V[(long long)(i0 + g) * ldv + e];
-          acc[g][0].add(v * x1[e]);
-          acc[g][1].add(v * x2[e]);
+          acc[g][0] += v * x1[e];
+          acc[g][1] += v * x2[e];
         }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -1657,7 +1657,7 @@ __global__ void __launch_bounds__(256) mdot2_kernel(double *__restrict__ partial
     if (g >= cnt) break;
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      double t = acc[g][c].value();
+      double t = (double)acc[g][c];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
       if (lane == 0) red[2 * g + c][warp] = t;
@@ -1671,65 +1671,73 @@ __global__ void __launch_bounds__(256) mdot2_kernel(double *__restrict__ partial
   }
 }
 
-// Update pass of the delayed classical Gram-Schmidt (two passes over the
-// basis per Arnoldi step instead of four).  Rows 0..j-1 of V are final; row
-// j holds u_j (projected once), row j+1 holds w = A z_j.  From the dots
-// D[2i+c] = <V_i, (u_j, w)_c> (i <= j+1) of the dot pass:
+// Coefficients of the update pass of the delayed classical Gram-Schmidt (two
+// passes over the basis per Arnoldi step instead of four).  Rows 0..j-1 of V
+// are final; row j holds u_j (projected once), row j+1 holds w = A z_j.  From
+// the dots D[2i+c] = <V_i, (u_j, w)_c> (i <= j+1) of the dot pass:
 //   nu = sqrt(<u,u> - |a|^2), a_i = <V_i,u>   (Pythagoras: u is nearly orthogonal)
 //   v_j = (u - sum a_i V_i) / nu              (reorthogonalized, normalized)
 //   gam = <v_j, w> = (<u,w> - a.b) / nu,      b_i = <V_i, w>
 //   u_{j+1} = sw (w - sum b_i V_i - gam v_j)  (projected once; sw scales it to
 //             about unit norm, sw = 1/sqrt(<w,w> - |b|^2 - gam^2))
-// written in place over rows j and j+1 in one pass; block 0 stores (nu, gam,
-// sw) in sc for the Hessenberg bookkeeping.  16-byte aligned rows.
+// One block: the sums over i in a fixed tree, then coef = [a_i / nu (j),
+// b_i - a_i gam / nu (j), 1/nu, gam/nu, sw] in T and sc = (nu, gam, sw).
 template <typename T>
-__global__ void __launch_bounds__(256) dcgs2_update_kernel(T *__restrict__ V, long long ldv, int j,
-                                                           const double *__restrict__ D, long long n,
-                                                           double *__restrict__ sc) {
-  typedef V16<T> X;
-  typedef typename X::type VT;
-  constexpr int W = X::W;
-  __shared__ T ca[512], cb[512];
-  __shared__ double scal[4];
+__global__ void __launch_bounds__(256) dcgs2_coef_kernel(T *__restrict__ coef, double *__restrict__ sc,
+                                                         const double *__restrict__ D, int j) {
   __shared__ double part[3][8];
-  {
-    // |a|^2, a.b, |b|^2 over i < j: strided per thread, then a fixed tree
-    double sa2 = 0.0, sab = 0.0, sb2 = 0.0;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
-      const double a = D[2 * i], b = D[2 * i + 1];
-      sa2 += a * a; sab += a * b; sb2 += b * b;
-    }
+  __shared__ double scal[2];
+  double sa2 = 0.0, sab = 0.0, sb2 = 0.0;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    const double a = D[2 * i], b = D[2 * i + 1];
+    sa2 += a * a; sab += a * b; sb2 += b * b;
+  }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      sa2 += __shfl_down_sync(0xffffffffu, sa2, off);
-      sab += __shfl_down_sync(0xffffffffu, sab, off);
-      sb2 += __shfl_down_sync(0xffffffffu, sb2, off);
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { part[0][warp] = sa2; part[1][warp] = sab; part[2][warp] = sb2; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      sa2 = sab = sb2 = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sa2 += part[0][w]; sab += part[1][w]; sb2 += part[2][w]; }
-      const double uu = D[2 * j], uw = D[2 * j + 1], ww = D[2 * (j + 1) + 1];
-      const double nu2 = uu - sa2;
-      const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
-      const double inu = nu > 0.0 ? 1.0 / nu : 0.0;
-      const double gam = (uw - sab) * inu;
-      const double q = ww - sb2 - gam * gam;
-      const double sw = (q > 0.0 && q > 1e-30 * ww) ? 1.0 / sqrt(q) : (ww > 0.0 ? 1.0 / sqrt(ww) : 1.0);
-      scal[0] = inu; scal[1] = gam * inu; scal[2] = sw; scal[3] = gam;
-      if (blockIdx.x == 0) { sc[0] = nu; sc[1] = gam; sc[2] = sw; }
-    }
+  for (int off = 16; off > 0; off >>= 1) {
+    sa2 += __shfl_down_sync(0xffffffffu, sa2, off);
+    sab += __shfl_down_sync(0xffffffffu, sab, off);
+    sb2 += __shfl_down_sync(0xffffffffu, sb2, off);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) { part[0][warp] = sa2; part[1][warp] = sab; part[2][warp] = sb2; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    sa2 = sab = sb2 = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { sa2 += part[0][w]; sab += part[1][w]; sb2 += part[2][w]; }
+    const double uu = D[2 * j], uw = D[2 * j + 1], ww = D[2 * (j + 1) + 1];
+    const double nu2 = uu - sa2;
+    const double nu = nu2 > 0.0 ? sqrt(nu2) : 0.0;
+    const double inu = nu > 0.0 ? 1.0 / nu : 0.0;
+    const double gam = (uw - sab) * inu;
+    const double q = ww - sb2 - gam * gam;
+    const double sw = (q > 0.0 && q > 1e-30 * ww) ? 1.0 / sqrt(q) : (ww > 0.0 ? 1.0 / sqrt(ww) : 1.0);
+    scal[0] = inu; scal[1] = gam * inu;
+    coef[2 * j] = (T)inu; coef[2 * j + 1] = (T)(gam * inu); coef[2 * j + 2] = (T)sw;
+    sc[0] = nu; sc[1] = gam; sc[2] = sw;
   }
   __syncthreads();
   const double inu = scal[0], gin = scal[1];
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
-    ca[i] = (T)(D[2 * i] * inu);
-    cb[i] = (T)(D[2 * i + 1] - D[2 * i] * gin);
+    coef[i] = (T)(D[2 * i] * inu);
+    coef[j + i] = (T)(D[2 * i + 1] - D[2 * i] * gin);
   }
+}
+
+// The update pass itself, one read of rows 0..j+1, rows j and j+1 rewritten
+// in place (16-byte aligned rows).
+template <typename T>
+__global__ void __launch_bounds__(256) dcgs2_update_kernel(T *__restrict__ V, long long ldv, int j,
+                                                           const T *__restrict__ coef, long long n) {
+  typedef V16<T> X;
+  typedef typename X::type VT;
+  constexpr int W = X::W;
+  __shared__ T ca[512], cb[512];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    ca[i] = coef[i];
+    cb[i] = coef[j + i];
+  }
+  const T tinu = coef[2 * j], tg = coef[2 * j + 1], tsw = coef[2 * j + 2];
   __syncthreads();
-  const T tinu = (T)inu, tg = (T)gin, tsw = (T)scal[2];
   T *U = V + (long long)j * ldv, *Wr = V + (long long)(j + 1) * ldv;
   const long long nvec = n / W;
   const long long stride = (long long)gridDim.x * blockDim.x;
@@ -2075,9 +2083,11 @@ void launch_multi_dot2(cudaStream_t s, double *out, const T *V, long long ldv, i
 }
 
 template <typename T>
-void launch_dcgs2_update(cudaStream_t s, T *V, long long ldv, int j, const double *D, long long n, double *sc) {
+void launch_dcgs2_update(cudaStream_t s, T *V, long long ldv, int j, const double *D, long long n, double *sc,
+                         T *coef) {
   long long nvec = n / V16<T>::W;
-  st_count_launch(); dcgs2_update_kernel<T><<<grid_for(std::max<long long>(nvec, 1)), kThreads, 0, s>>>(V, ldv, j, D, n, sc);
+  st_count_launch(); dcgs2_coef_kernel<T><<<1, 256, 0, s>>>(coef, sc, D, j);
+  st_count_launch(); dcgs2_update_kernel<T><<<grid_for(std::max<long long>(nvec, 1)), kThreads, 0, s>>>(V, ldv, j, coef, n);
 }
 
 template <typename T>
@@ -2191,7 +2201,7 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
   template void launch_multi_dot2<T>(cudaStream_t, double *, const T *, long long, int, const T *,     \
                                      const T *, long long, double *);                                  \
   template void launch_dcgs2_update<T>(cudaStream_t, T *, long long, int, const double *, long long,   \
-                                       double *);
+                                       double *, T *);
 INST(float)
 INST(double)
 #undef INST

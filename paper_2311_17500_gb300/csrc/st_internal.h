@@ -124,6 +124,7 @@ struct st_handle {
   double *z64 = nullptr, *b64 = nullptr;   // GMRES preconditioner output, Newton right-hand side
   float *r32 = nullptr, *t32a = nullptr, *t32b = nullptr, *d32 = nullptr;
   double *hcol = nullptr;      // device [2*(m+2)] Arnoldi coefficients
+  double *gs_coef = nullptr;   // 2 (m + 2) values: Gram-Schmidt update coefficients (FP64 or FP32)
   std::vector<void *> allocs;
   // optional per-stage timing (CUDA events on the handle's stream)
   bool prof_on = false;
@@ -217,9 +218,11 @@ template <typename T>
 void launch_multi_dot2(cudaStream_t s, double *out, const T *V, long long ldv, int nv, const T *x1, const T *x2,
                        long long n, double *scratch);
 // Update pass of the delayed classical Gram-Schmidt step j (rows j, j+1 of V
-// rewritten in place from the dots D of launch_multi_dot2; (nu, gam, sw) -> sc).
+// rewritten in place from the dots D of launch_multi_dot2; (nu, gam, sw) -> sc;
+// coef: 2j + 3 values of work space).
 template <typename T>
-void launch_dcgs2_update(cudaStream_t s, T *V, long long ldv, int j, const double *D, long long n, double *sc);
+void launch_dcgs2_update(cudaStream_t s, T *V, long long ldv, int j, const double *D, long long n, double *sc,
+                         T *coef);
 template <typename T>
 void launch_multi_axpy(cudaStream_t s, T *w, const T *V, long long ldv, int nv, const double *h,
                        long long n, const double *nrm = nullptr);
