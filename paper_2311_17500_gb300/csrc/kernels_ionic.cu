@@ -485,10 +485,10 @@ template <int RMAX>
 __global__ void su_band_update_kernel(float *__restrict__ bhi, float *__restrict__ blo,
                                       const float2 *__restrict__ Tr, const float2 *__restrict__ Cq, int r0, int R,
                                       long long Mrows, long long Qs) {
-  long long total = Mrows * Qs;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    long long m = idx / Qs, q = idx - m * Qs;
+  // blockIdx.y strides over the band rows m, x over the spatial points q
+  for (long long m = blockIdx.y; m < Mrows; m += gridDim.y)
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Qs; q += (long long)gridDim.x * blockDim.x) {
+    const long long idx = m * Qs + q;
     df v = {bhi[idx], blo[idx]};
 #pragma unroll
     for (int rr = 0; rr < RMAX; ++rr) {
@@ -714,11 +714,13 @@ st_status su_band_add(st_handle *h) {
   float2 *Tr2 = h->Tr2;
   st_count_launch(); d2df_kernel<<<grid_for((long long)R * h->Qs), 256, 0, s>>>(Cq2, Cq, (long long)R * h->Qs);
   st_count_launch(); d2df_kernel<<<grid_for((long long)R * Mrows), 256, 0, s>>>(Tr2, h->Tr, (long long)R * Mrows);
+  const dim3 g2((unsigned)std::min<long long>((h->Qs + 255) / 256, 64), (unsigned)std::min<long long>(Mrows, 128));
+  (void)total;
   for (int r0 = 0; r0 < R; r0 += 16) {
     if (R - r0 <= 8) {
-      st_count_launch(); su_band_update_kernel<8><<<grid_for(total), 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+      st_count_launch(); su_band_update_kernel<8><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
     } else {
-      st_count_launch(); su_band_update_kernel<16><<<grid_for(total), 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+      st_count_launch(); su_band_update_kernel<16><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
     }
   }
   ST_CUDA(cudaGetLastError());

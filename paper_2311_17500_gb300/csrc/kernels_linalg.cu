@@ -2095,19 +2095,23 @@ void launch_scale_copy(cudaStream_t s, T *y, const T *x, double alpha, long long
   st_count_launch(); scale_copy_kernel<T><<<grid_for(n), kThreads, 0, s>>>(y, x, alpha, n);
 }
 
-// out[r * stride + k] = in[r * n + k] (rows copied into 16-byte aligned rows)
+// out[r * stride + k] = in[r * n + k] (rows copied into 16-byte aligned rows):
+// one warp per row, no index division.
 __global__ void pad_rows_kernel(float *__restrict__ out, const float *__restrict__ in, long long rows, long long n,
                                 long long stride) {
-  long long total = rows * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    long long r = e / n, k = e - r * n;
-    out[r * stride + k] = in[e];
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long r = w0; r < rows; r += nw) {
+    const float *src = in + r * n;
+    float *dst = out + r * stride;
+    for (long long k = lane; k < n; k += 32) dst[k] = src[k];
   }
 }
 
 void launch_pad_rows(cudaStream_t s, float *out, const float *in, long long rows, long long n, long long stride) {
-  st_count_launch(); pad_rows_kernel<<<grid_for(rows * n), kThreads, 0, s>>>(out, in, rows, n, stride);
+  long long blocks = std::min<long long>((rows + 7) / 8, 152LL * 32);
+  st_count_launch(); pad_rows_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(out, in, rows, n, stride);
 }
 
 void launch_axpby64(cudaStream_t s, double *y, const double *x, double a, double b, long long n) {

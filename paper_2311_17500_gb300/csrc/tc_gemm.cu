@@ -75,7 +75,9 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+// 16 consecutive TMEM columns of this thread's lane; the values are valid
+// only after tmem_ld_wait().
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t *v) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15}, [%16];"
@@ -83,7 +85,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  tmem_ld16_nowait(taddr, v);
+  tmem_ld_wait();
 }
 
 struct XformArgs {
@@ -228,10 +235,38 @@ __global__ void __launch_bounds__(256) tc_xform_tma_kernel(const __grid_constant
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const long long tile = blockIdx.x + i * gridDim.x;
       const long long row = tile * kTcRows + lw * 32 + lane;
-      for (int c0 = 0; c0 < x.Npad; c0 += 16) {
+      // output address of this row's j = 0 and the stride between j (once per tile)
+      const bool valid = row < x.R;
+      float *obase = x.out;
+      long long jstride = 0;
+      if (valid) {
+        const long long t = row / x.Aa, a = row - t * x.Aa;
+        const long long ao = a / x.A_inner, ai = a - ao * x.A_inner;
+        const long long A_outer = x.Aa / x.A_inner;
+        jstride = A_outer * x.A_in_stride;
+        obase = x.out + (t * x.nj * A_outer + ao) * x.A_in_stride + ai;
+      }
+      const uint32_t tl = tmem + ((uint32_t)(lw * 32) << 16) + (uint32_t)(acc * acc_cols);
+      int c0 = 0;
+      for (; c0 + 32 <= x.Npad; c0 += 32) {
+        uint32_t v[32];
+        tmem_ld16_nowait(tl + (uint32_t)c0, v);
+        tmem_ld16_nowait(tl + (uint32_t)(c0 + 16), v + 16);
+        tmem_ld_wait();
+        if (valid) {
+#pragma unroll
+          for (int u = 0; u < 32; ++u)
+            if (c0 + u < x.nj) obase[(long long)(c0 + u) * jstride] = __uint_as_float(v[u]);
+        }
+      }
+      if (c0 < x.Npad) {
         uint32_t v[16];
-        tmem_ld16(tmem + ((uint32_t)(lw * 32) << 16) + (uint32_t)(acc * acc_cols + c0), v);
-        store_row16(x, row, c0, v);
+        tmem_ld16(tl + (uint32_t)c0, v);
+        if (valid) {
+#pragma unroll
+          for (int u = 0; u < 16; ++u)
+            if (c0 + u < x.nj) obase[(long long)(c0 + u) * jstride] = __uint_as_float(v[u]);
+        }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
