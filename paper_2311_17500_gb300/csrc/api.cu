@@ -450,7 +450,7 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
     T *Y1 = P::W(h, ping);
     {
       ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_QBAND, sz * ((double)(p + 1) * h->NtQs + 2.0 * (double)Nt * rows * nx));
-      launch_xband_fused<T>(s, Y1, cur, h->band32, P::band_lo(h), P::Bq(h, 0), h->nel[0], (int)Nt, rows, p);
+      launch_xband_fused<T>(s, Y1, cur, h->band32, P::band_lo(h), P::Bq(h, 0), h->nel[0], (int)Nt, rows, p, h->tc_err);
     }
     cur = Y1;
     ping ^= 1;

@@ -851,18 +851,24 @@ __device__ __forceinline__ void load_nq_shared(T (&v)[NQ], const T *p) {
 template <typename T, int P>
 constexpr int xband_max_threads() { return (sizeof(T) == 8 || P >= 4) ? 256 : 512; }
 
+constexpr long long kXbWaitLimit = 1ll << 22;
+
 template <typename T> struct XbandCT { typedef float type; };
 template <> struct XbandCT<double> { typedef df type; };
 
-template <typename T, int P, int S>
+template <typename T, int P, int S, bool BULK>
 __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
     T *__restrict__ Y1, const T *__restrict__ X1, const float *__restrict__ bhi, const float *__restrict__ blo,
-    const T *__restrict__ tab, int nel, int Nt, long long rows, int seglen) {
+    const T *__restrict__ tab, int nel, int Nt, long long rows, int seglen, int *err) {
   typedef typename XbandCT<T>::type CT;
   constexpr bool DF = sizeof(T) == 8;
   constexpr int nq = P + 1, NB = DF ? 2 : 1;   // band parts per value
   static_assert(S >= 2, "ring depth");
   __shared__ CT xch[2][16][P][P];   // [step parity][warp][a-1][lane-(32-P)]
+  // BULK: the band slice of a step (Qx contiguous values per diagonal and
+  // part) arrives by bulk copies issued by thread 0 on bfull[slot]
+  __shared__ __align__(8) uint64_t bfull[S];
+  __shared__ int bfail;
   extern __shared__ __align__(16) unsigned char xb_raw[];
   const int nth = blockDim.x;
   float *bring = reinterpret_cast<float *>(xb_raw);                  // [S][NB][P+1][thread][nq]
@@ -878,6 +884,15 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
     for (int a = 0; a <= P; ++a) wv[g][a] = owns ? ct_from<CT>(__ldg(tab + ((size_t)t * nq + g) * (P + 1) + a)) : zero;
   const long long planeX = rows * nx, planeQ = rows * Qx, bandK = (long long)Nt * planeQ;
   const int nseg = (Nt + seglen - 1) / seglen;
+  if (BULK) {
+    if (t == 0) {
+      for (int i = 0; i < S; ++i) mbar_init(&bfull[i], 1);
+      mbar_fence_init();
+      bfail = 0;
+    }
+    __syncthreads();
+  }
+  long long gbase = 0;   // steps issued by this block before the current segment
   for (long long blk = blockIdx.x; blk < rows * nseg; blk += gridDim.x) {
     const long long o = blk % rows;
     const int t0 = (int)(blk / rows) * seglen, t1 = min(Nt, t0 + seglen);
@@ -945,7 +960,27 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
     auto xslot = [&](int u) -> T * { return xring + (size_t)(u % S) * nth; };
     auto issue = [&](int u) {
       if (u < t1) {
-        if (owns) {
+        if constexpr (BULK) {
+          if (t == 0) {
+            const long long g = gbase + (u - t0);
+            uint64_t *bar = &bfull[g % S];
+            const uint32_t bytes = (uint32_t)Qx * sizeof(float);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                         "r"(bytes * NB * (P + 1))
+                         : "memory");
+#pragma unroll
+            for (int part = 0; part < NB; ++part)
+#pragma unroll
+              for (int k = 0; k <= P; ++k) {
+                const float *src = (part ? blo : bhi) + o * Qx + k * bandK + (long long)u * planeQ;
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_u32(bring + (size_t)((((u % S) * NB + part) * (P + 1) + k) * nth) * nq)),
+                    "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                    : "memory");
+              }
+          }
+        } else if (owns) {
 #pragma unroll
           for (int k = 0; k <= P; ++k) {
             const long long idx = boff + k * bandK + (long long)u * planeQ;
@@ -962,7 +997,15 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
     CT pend = zero;   // this thread's output of the previous step, before its cross-warp part
     for (int it = t0; it < t1; ++it) {
       cp_async_wait<S - 2>();
+      if constexpr (BULK) {
+        const long long g = gbase + (it - t0);
+        if (!mbar_wait(smem_u32(&bfull[g % S]), (uint32_t)((g / S) & 1), kXbWaitLimit)) {
+          bfail = 1;
+          atomicExch(err, 1);
+        }
+      }
       __syncthreads();
+      if (BULK && bfail) break;
       if (it > t0) {
         const int pp = (it - 1) & 1;
         if (lane < P && warp > 0) {
@@ -1055,6 +1098,8 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
     }
     cp_async_wait<0>();
     __syncthreads();
+    if (BULK && bfail) break;
+    gbase += t1 - t0;
     if (t1 > t0) {
       const int pp = (t1 - 1) & 1;
       if (lane < P && warp > 0) {
@@ -1197,14 +1242,28 @@ __global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, cons
   }
   __syncthreads();
   if (cx >= nx) return;
-  for (int r = rg; r < ny; r += nrg) {
+  // column pass: each thread a contiguous run of rows, r1 and r2 in a sliding
+  // register window (every staged value read once)
+  const int per = (ny + nrg - 1) / nrg, ra = rg * per, rb = min(ny, ra + per);
+  if (ra >= rb) return;
+  T w1[B], w2[B];
+#pragma unroll
+  for (int k = 0; k < B - 1; ++k) {
+    const int rr = ra - P + k;
+    const bool ok = rr >= 0 && rr < ny;
+    w1[k + 1] = ok ? r1[(size_t)rr * SW + c] : T(0);
+    w2[k + 1] = ok ? r2[(size_t)rr * SW + c] : T(0);
+  }
+  for (int r = ra; r < rb; ++r) {
+#pragma unroll
+    for (int k = 0; k < B - 1; ++k) { w1[k] = w1[k + 1]; w2[k] = w2[k + 1]; }
+    const int rn = r + P;
+    w1[B - 1] = rn < ny ? r1[(size_t)rn * SW + c] : T(0);
+    w2[B - 1] = rn < ny ? r2[(size_t)rn * SW + c] : T(0);
     const T *br = by + (size_t)r * 2 * B;
     T v = T(0);
 #pragma unroll
-    for (int k = 0; k < B; ++k) {
-      const int rr = min(max(r - P + k, 0), ny - 1);   // out-of-range rows carry zero weights
-      v += br[k] * r1[(size_t)rr * SW + c] + br[B + k] * r2[(size_t)rr * SW + c];
-    }
+    for (int k = 0; k < B; ++k) v += br[k] * w1[k] + br[B + k] * w2[k];
     const long long idx = base + (long long)r * nx + cx;
     y[idx] = accumulate ? y[idx] + v : v;
   }
@@ -1911,7 +1970,7 @@ int xband_fused_limit(size_t elem, int p) { return (elem == 8 || p >= 4) ? 256 :
 
 template <typename T>
 bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, const float *blo, const T *tab, int nel,
-                        int Nt, long long rows, int p) {
+                        int Nt, long long rows, int p, int *err) {
   const int threads = (nel + p + 31) / 32 * 32;
   if (threads > xband_fused_limit(sizeof(T), p) || rows < 1) return false;
   // time segments so that the grid holds about 16 blocks per SM, each
@@ -1925,19 +1984,21 @@ bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, co
   auto go = [&](auto kern, int P) {
     const int NB = sizeof(T) == 8 ? 2 : 1;
     size_t sh = (size_t)S * NB * (P + 1) * threads * (P + 1) * sizeof(float) + (size_t)S * threads * sizeof(T);
-    static bool attr[5] = {false, false, false, false, false};
-    if (!attr[P]) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-      attr[P] = true;
-    }
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     st_count_launch();
-    kern<<<blocks, threads, sh, s>>>(Y1, X1, bhi, blo, tab, nel, Nt, rows, seglen);
+    kern<<<blocks, threads, sh, s>>>(Y1, X1, bhi, blo, tab, nel, Nt, rows, seglen, err);
   };
-  switch (p) {
-    case 1: go(xband_fused_kernel<T, 1, S>, 1); break;
-    case 2: go(xband_fused_kernel<T, 2, S>, 2); break;
-    case 3: go(xband_fused_kernel<T, 3, S>, 3); break;
-    default: go(xband_fused_kernel<T, 4, S>, 4); break;
+  // bulk band copies need 16-byte aligned slices: Q_x a multiple of 4 floats
+  const bool bulk = (nel * (p + 1)) % 4 == 0 && ((uintptr_t)bhi % 16) == 0 && (!blo || ((uintptr_t)blo % 16) == 0);
+  switch (p * 2 + (bulk ? 1 : 0)) {
+    case 2: go(xband_fused_kernel<T, 1, S, false>, 1); break;
+    case 3: go(xband_fused_kernel<T, 1, S, true>, 1); break;
+    case 4: go(xband_fused_kernel<T, 2, S, false>, 2); break;
+    case 5: go(xband_fused_kernel<T, 2, S, true>, 2); break;
+    case 6: go(xband_fused_kernel<T, 3, S, false>, 3); break;
+    case 7: go(xband_fused_kernel<T, 3, S, true>, 3); break;
+    case 8: go(xband_fused_kernel<T, 4, S, false>, 4); break;
+    default: go(xband_fused_kernel<T, 4, S, true>, 4); break;
   }
   return true;
 }
@@ -2192,7 +2253,7 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
                                  const T *, const T *, const T *, int, int, int, int, double, double,   \
                                  double);                                                              \
   template bool launch_xband_fused<T>(cudaStream_t, T *, const T *, const float *, const float *,       \
-                                      const T *, int, int, long long, int);                             \
+                                      const T *, int, int, long long, int, int *);                      \
   template void launch_mode_gemm<T>(cudaStream_t, T *, const T *, const T *, int, long long, long long); \
   template void launch_tline_lu_solve<T>(cudaStream_t, T *, const T *, const T *, int, long long, int,  \
                                           int *);                                                          \

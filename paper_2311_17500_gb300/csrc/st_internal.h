@@ -197,7 +197,7 @@ bool launch_kron2d(cudaStream_t s, T *y, T *xW, T *xM, const T *x, const T *Wt, 
 int xband_fused_limit(size_t elem, int p);
 template <typename T>
 bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, const float *blo, const T *tab, int nel,
-                        int Nt, long long rows, int p);
+                        int Nt, long long rows, int p, int *err);
 template <typename T>
 void launch_mode_gemm(cudaStream_t s, T *out, const T *in, const T *A, int n, long long inner, long long outer);
 template <typename T>
