@@ -545,20 +545,25 @@ void rot_simt<float>(st_handle *h, float *out, const float *in, int l, bool fwd)
   launch_rot_gemm<float>(h->stream, out, in, fwd ? h->UT32[l] : h->U32[l], h->n[l], h->n[l], h->Ns / h->n[l], h->Nt);
 }
 
-// Tensor-core sequence of d transforms (FP32): a first input with rows not
-// 16-byte aligned is copied into a padded buffer, intermediate results use
-// padded rows, the last result is written unpadded.
-static st_status tc_sequence(st_handle *h, const float *in, float *out, bool fwd) {
+// Tensor-core sequence of d transforms (FP32).  Intermediate results use
+// rows padded to a multiple of 4 floats (16-byte aligned for TMA).  The input
+// is either the natural layout (copied into a padded buffer first) or already
+// padded; the result is written to `out` in the natural layout, or, when out
+// is null, padded into one of the two ping-pong buffers, returned in *res.
+static st_status tc_sequence(st_handle *h, const float *in, bool in_padded, float *out, bool fwd, float **res) {
   cudaStream_t s = h->stream;
   RotStep st[3];
-  rot_plan(h, st, false);
+  rot_plan(h, st, out == nullptr);
   const float *cur = in;
   long long cur_stride = h->n[st[0].l];
   float *P[2] = {h->P32[0], h->P32[1]};
-  int ping = 0;
-  if (cur_stride % 4 != 0) {
+  int ping = (in == P[0]) ? 1 : 0;   // never write the buffer being read
+  if (in_padded) {
+    cur_stride = (cur_stride + 3) / 4 * 4;
+  } else if (cur_stride % 4 != 0) {
     long long rows = h->Ndof / cur_stride;
     long long sp = (cur_stride + 3) / 4 * 4;
+    ProfScope ps(h, PROF_FD_GEMM, 2.0 * h->Ndof * sizeof(float));
     launch_pad_rows(s, P[ping], cur, rows, cur_stride, sp);
     cur = P[ping];
     cur_stride = sp;
@@ -567,7 +572,7 @@ static st_status tc_sequence(st_handle *h, const float *in, float *out, bool fwd
   for (int k = 0; k < h->d; ++k) {
     const RotStep &r = st[k];
     int l = r.l;
-    float *dst = (k == h->d - 1) ? out : P[ping];
+    float *dst = (k == h->d - 1 && out) ? out : P[ping];
     ProfScope ps(h, PROF_FD_GEMM, 2.0 * h->Ndof * sizeof(float), 2.0 * h->n[l] * (double)h->Ndof);
     ST_TRY(launch_tc_xform(s, dst, cur, (long long)h->Nt * r.Aa, h->n[l], cur_stride, fwd ? h->UTp[l] : h->Up[l],
                            h->n[l], h->Npad[l], h->Kpad[l], r.Aa, r.A_inner, r.A_stride, h->tc_err));
@@ -575,6 +580,7 @@ static st_status tc_sequence(st_handle *h, const float *in, float *out, bool fwd
     cur_stride = r.A_stride;
     ping ^= 1;
   }
+  if (res) *res = const_cast<float *>(cur);
   return ST_OK;
 }
 
@@ -591,8 +597,29 @@ st_status precond_T(st_handle *h, const T *r, T *z) {
   T *bufs[2] = {P::K(h, 0), P::K(h, 1)};
   const double vec = (double)h->Ndof * sizeof(T);
   const bool tc = (sizeof(T) == 4) && h->use_tc;
+  if (tc && h->d == 1) {
+    ST_TRY(tc_sequence(h, (const float *)r, false, (float *)bufs[0], true, nullptr));
+    {
+      ProfScope ps(h, PROF_FD_LU, vec * (2 + h->B));
+      launch_tline_lu_solve<float>(s, (float *)bufs[1], (const float *)bufs[0], h->lu32, h->Nt, h->Ns, h->p, h->tc_err);
+    }
+    ST_TRY(tc_sequence(h, (const float *)bufs[1], false, (float *)z, false, nullptr));
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+  }
   if (tc) {
-    ST_TRY(tc_sequence(h, (const float *)r, (float *)bufs[0], true));
+    // padded layout from the forward transforms through the LU to the
+    // backward transforms
+    float *fw = nullptr;
+    ST_TRY(tc_sequence(h, (const float *)r, false, nullptr, true, &fw));
+    float *lu_out = (fw == h->P32[0]) ? h->P32[1] : h->P32[0];
+    {
+      ProfScope ps(h, PROF_FD_LU, vec * (2 + h->B));
+      launch_tline_lu_solve<float>(s, lu_out, fw, h->lu32, h->Nt, h->Ns_pad, h->p, h->tc_err);
+    }
+    ST_TRY(tc_sequence(h, lu_out, true, (float *)z, false, nullptr));
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
   } else {
     // r -> ... -> bufs[0], alternating so that no step writes its input
     const T *cur = r;
@@ -607,9 +634,7 @@ st_status precond_T(st_handle *h, const T *r, T *z) {
     ProfScope ps(h, PROF_FD_LU, vec * (2 + h->B));
     launch_tline_lu_solve<T>(s, bufs[1], bufs[0], P::lu(h), h->Nt, h->Ns, h->p, h->tc_err);
   }
-  if (tc) {
-    ST_TRY(tc_sequence(h, (const float *)bufs[1], (float *)z, false));
-  } else {
+  {
     const T *cur = bufs[1];
     for (int l = 0; l < h->d; ++l) {
       T *dst = (l == h->d - 1) ? z : bufs[l % 2];
@@ -759,7 +784,9 @@ static st_status setup_impl(st_handle *h) {
   }
   h->mu = dalloc<double>(h, h->Ns, &e);
   h->lu64 = dalloc<double>(h, (size_t)h->Nt * h->B * h->Ns, &e);
-  h->lu32 = dalloc<float>(h, (size_t)h->Nt * h->B * h->Ns, &e);
+  h->nxp = (h->n[0] + 3) / 4 * 4;
+  h->Ns_pad = h->Ns / h->n[0] * h->nxp;
+  h->lu32 = dalloc<float>(h, (size_t)h->Nt * h->B * h->Ns_pad, &e);
   h->band32 = dalloc<float>(h, (size_t)(h->p + 1) * h->NtQs, &e);
   h->band_lo = dalloc<float>(h, (size_t)(h->p + 1) * h->NtQs, &e);
   h->f64 = dalloc<double>(h, h->Ndof, &e);
@@ -810,8 +837,13 @@ static st_status setup_impl(st_handle *h) {
   h->hcol = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
   h->gs_coef = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
   if (e != ST_OK) return e;
-  h->P32[0] = dalloc<float>(h, 2 * h->Ndof + 64, &e);
-  h->P32[1] = dalloc<float>(h, 2 * h->Ndof + 64, &e);
+  {
+    // padded layouts of the tensor-core preconditioner: every axis rounded up to 4
+    size_t np = (size_t)h->Nt;
+    for (int l = 0; l < h->d; ++l) np *= (size_t)((h->n[l] + 3) / 4 * 4);
+    h->P32[0] = dalloc<float>(h, std::max<size_t>(np, 2 * h->Ndof) + 64, &e);
+    h->P32[1] = dalloc<float>(h, std::max<size_t>(np, 2 * h->Ndof) + 64, &e);
+  }
   h->tc_err = dalloc<int>(h, 4, &e);
   if (e != ST_OK) return e;
   ST_CUDA(cudaMemsetAsync(h->tc_err, 0, 4 * sizeof(int), h->stream));
@@ -839,6 +871,9 @@ static st_status setup_impl(st_handle *h) {
         ST_TRY(upload<float>(h, &h->Up[l], uu));
       }
       h->use_tc = true;
+      // FP32 LU factors in the padded layout of the tensor-core sequence (d >= 2)
+      if (h->d >= 2)
+        launch_pad_d2f(h->stream, h->lu32, h->lu64, (long long)h->Nt * h->B * (h->Ns / h->n[0]), h->n[0], h->nxp);
     }
   }
   ST_TRY(source_assemble(h));

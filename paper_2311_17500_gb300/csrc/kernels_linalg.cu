@@ -1475,6 +1475,16 @@ __global__ void __launch_bounds__(128) tline_lu_kernel(T *__restrict__ z, const 
   }
 }
 
+// FP64 rows (n values each) into FP32 rows of stride `stride`, the padding zero.
+__global__ void pad_d2f_kernel(float *__restrict__ out, const double *__restrict__ in, long long rows, long long n,
+                               long long stride) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long rr = w0; rr < rows; rr += nw)
+    for (long long k = lane; k < stride; k += 32) out[rr * stride + k] = k < n ? (float)in[rr * n + k] : 0.f;
+}
+
 template <typename T> struct Acc;
 template <> struct Acc<float> { typedef float type; };
 template <> struct Acc<double> { typedef double type; };
@@ -2107,6 +2117,11 @@ void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt
     case 8: go(tline_lu_kernel<T, 4, false>, 4, 6); break;
     default: go(tline_lu_kernel<T, 4, true>, 4, 7); break;
   }
+}
+
+void launch_pad_d2f(cudaStream_t s, float *out, const double *in, long long rows, long long n, long long stride) {
+  long long blocks = std::min<long long>((rows + 7) / 8, 152LL * 32);
+  st_count_launch(); pad_d2f_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(out, in, rows, n, stride);
 }
 
 template <typename T>

@@ -82,6 +82,8 @@ struct st_handle {
   float *P32[2] = {};          // padded-row buffers of the tensor-core transforms
   int *tc_err = nullptr;
   double *lu64 = nullptr;     // [it][k][j], k = 0..2p
+  long long Ns_pad = 0;       // spatial size with the innermost axis padded to a multiple of 4
+  int nxp = 0;                // padded innermost axis
   float *lu32 = nullptr;
 
   // linearization: symmetric time band per spatial Gauss point, [k][it][q], k = 0..p
@@ -207,6 +209,8 @@ void launch_rot_gemm(cudaStream_t s, T *out, const T *in, const T *M, int nb, in
 st_status launch_tc_xform(cudaStream_t s, float *out, const float *X, long long R, int nb, long long in_stride,
                           const float *Mpad, int nj, int Npad, int Kpad, long long Aa, long long A_inner,
                           long long A_in_stride, int *err);
+// FP64 rows of n values into zero-padded FP32 rows of `stride` values.
+void launch_pad_d2f(cudaStream_t s, float *out, const double *in, long long rows, long long n, long long stride);
 void launch_pad_rows(cudaStream_t s, float *out, const float *in, long long rows, long long n, long long stride);
 // tensor-core transforms: process-wide self-test state (0 untested, 1 usable, -1 not usable)
 int tc_state(cudaStream_t s, double *err_out);
