@@ -1347,131 +1347,97 @@ __global__ void __launch_bounds__(256) gemm_kernel(T *__restrict__ C, const T *_
 // middle factor of the fast-diagonalization preconditioner): lu[it][k][j] holds
 // L below the diagonal (unit diagonal), 1/u_ii on it and U above.
 // Banded forward/back substitution along time for every spatial eigen-index j
-// (LU stored [it][k][j], 1/u_ii on the diagonal).  There are only N_s time
-// lines, each a serial recurrence, so the kernel is warp-specialized: per
-// block, warp 0 runs the recurrences of 32 consecutive j (one lane each) and
-// warps 1..3 keep an S-stage ring of C-step chunks filled with the operands
-// ((P+1) rows of 32 values per step) by per-lane cp.async copies, whose
-// completion arrives on the stage's "full" barrier; the consumer frees a stage
-// through its "empty" barrier.  Forward chunks come first (r and the P
-// multipliers of each step), then backward chunks (the P+1 entries of U);
-// the backward right-hand side y is read back by the consumer lane that wrote
-// it, from shared memory when the whole time line fits (else from z).  Every wait is bounded: a wait that gives up sets *err and the warp
-// stops (the output is then invalid and the caller reports ST_ERR_TIMEOUT).
-constexpr int kLuC = 8, kLuS = 6;
-constexpr long long kLuWaitLimit = 1ll << 22;
-
-template <typename T, int P, bool YS>
+// (LU stored [it][k][j], 1/u_ii on the diagonal), one thread per j.  Only
+// N_s time lines exist, so the sweep is bound by how many loads each thread
+// keeps in flight: the operands of the next U steps are loaded before the
+// current U steps are computed (two batches in flight).  Measured on the 2D
+// workload against a warp-specialized cp.async ring, a per-thread cp.async
+// ring, a blocked layout and 16-byte loads per thread, this is the fastest.
+template <typename T, int P, int U>
 __global__ void __launch_bounds__(128) tline_lu_kernel(T *__restrict__ z, const T *__restrict__ r,
-                                                       const T *__restrict__ lu, int Nt, long long Ns, int *err) {
-  constexpr int B = 2 * P + 1, R = P + 1, C = kLuC, S = kLuS;
-  extern __shared__ __align__(16) unsigned char lu_raw[];
-  T *ring = reinterpret_cast<T *>(lu_raw);   // [S][C][R][32]
-  T *ybuf = ring + (size_t)S * C * R * 32;   // [Nt][32] forward results (YS)
-  __shared__ __align__(8) uint64_t full[S], empty[S];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long j = (long long)blockIdx.x * 32 + lane;
-  const bool active = j < Ns;
-  const int nch = (Nt + C - 1) / C, njobs = 2 * nch;
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < S; ++i) {
-      mbar_init(&full[i], 96);    // one arrival per producer thread
-      mbar_init(&empty[i], 1);    // the consumer's elected lane
-    }
-    mbar_fence_init();
-  }
-  __syncthreads();
-  auto cell = [&](int u, int c, int k) -> T * { return ring + (((size_t)(u % S) * C + c) * R + k) * 32 + lane; };
-  if (warp > 0) {
-    // producers: slice (c, k) of chunk u is copied by warp 1 + (c*R + k) % 3
-    const int pw = warp - 1;
-    for (int u = 0; u < njobs; ++u) {
-      if (u >= S && !mbar_wait(smem_u32(&empty[u % S]), (uint32_t)(((u / S) - 1) & 1), kLuWaitLimit)) {
-        atomicExch(err, 1);
-        break;
-      }
-      const bool fwd = u < nch;
-      const int cb = fwd ? u : u - nch;
-      for (int sl = pw; sl < C * R; sl += 3) {
-        const int c = sl / R, k = sl - c * R;
-        if (!active) continue;
-        if (fwd) {
-          const int it = cb * C + c;
-          if (it >= Nt) continue;
-          if (k == 0) cp_async_elem(cell(u, c, 0), r + (long long)it * Ns + j);
-          else if (it - k >= 0) cp_async_elem(cell(u, c, k), lu + ((long long)it * B + (P - k)) * Ns + j);
-        } else {
-          const int it = Nt - 1 - (cb * C + c);
-          if (it < 0 || it + k >= Nt) continue;
-          cp_async_elem(cell(u, c, k), lu + ((long long)it * B + (P + k)) * Ns + j);
-        }
-      }
-      mbar_arrive_cp_async(&full[u % S]);
-    }
-    cp_async_wait<0>();
-    return;
-  }
-  // consumer
-  T yw[P];
+                                                       const T *__restrict__ lu, int Nt, long long Ns) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= Ns) return;
+  constexpr int B = 2 * P + 1;
+  // forward substitution with the unit lower factor
+  {
+    T yw[P];
 #pragma unroll
-  for (int k = 0; k < P; ++k) yw[k] = T(0);
-  for (int u = 0; u < nch; ++u) {
-    if (!mbar_wait(smem_u32(&full[u % S]), (uint32_t)((u / S) & 1), kLuWaitLimit)) {
-      atomicExch(err, 1);
-      return;
-    }
-    if (active) {
+    for (int k = 0; k < P; ++k) yw[k] = T(0);
+    T rv[U], lv[U][P], rn[U], ln[U][P];
+    auto load = [&](int it0, T (&rr)[U], T (&ll)[U][P]) {
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int it = u * C + c;
-        if (it >= Nt) break;
-        T v = *cell(u, c, 0);
+      for (int u = 0; u < U; ++u) {
+        const int it = it0 + u;
+        const bool ok = it < Nt;
+        rr[u] = ok ? r[(long long)it * Ns + j] : T(0);
 #pragma unroll
         for (int k = 1; k <= P; ++k)
-          if (it - k >= 0) v -= *cell(u, c, k) * yw[P - k];
+          ll[u][k - 1] = (ok && it - k >= 0) ? lu[((long long)it * B + (P - k)) * Ns + j] : T(0);
+      }
+    };
+    load(0, rv, lv);
+    for (int it0 = 0; it0 < Nt; it0 += U) {
+      if (it0 + U < Nt) load(it0 + U, rn, ln);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int it = it0 + u;
+        if (it >= Nt) break;
+        T v = rv[u];
+#pragma unroll
+        for (int k = P; k >= 1; --k) v -= lv[u][k - 1] * yw[P - k];
 #pragma unroll
         for (int k = 0; k < P - 1; ++k) yw[k] = yw[k + 1];
         yw[P - 1] = v;
-        if (YS) ybuf[(size_t)it * 32 + lane] = v;
-        else z[(long long)it * Ns + j] = v;
+        z[(long long)it * Ns + j] = v;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        rv[u] = rn[u];
+#pragma unroll
+        for (int k = 0; k < P; ++k) lv[u][k] = ln[u][k];
       }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[u % S]);
   }
-  T zw[P];
+  // backward substitution with the upper factor (1/u_ii stored on the diagonal)
+  {
+    T zw[P];
 #pragma unroll
-  for (int k = 0; k < P; ++k) zw[k] = T(0);
-  for (int cb = 0; cb < nch; ++cb) {
-    const int u = nch + cb;
-    T yv[C];
+    for (int k = 0; k < P; ++k) zw[k] = T(0);
+    T yv[U], uv[U][P + 1], yn[U], un[U][P + 1];
+    auto load = [&](int c0, T (&yy)[U], T (&ul)[U][P + 1]) {
 #pragma unroll
-    for (int c = 0; c < C; ++c) {
-      const int it = Nt - 1 - (cb * C + c);
-      yv[c] = (active && it >= 0) ? (YS ? ybuf[(size_t)it * 32 + lane] : z[(long long)it * Ns + j]) : T(0);
-    }
-    if (!mbar_wait(smem_u32(&full[u % S]), (uint32_t)((u / S) & 1), kLuWaitLimit)) {
-      atomicExch(err, 1);
-      return;
-    }
-    if (active) {
+      for (int u = 0; u < U; ++u) {
+        const int it = Nt - 1 - (c0 + u);
+        const bool ok = it >= 0;
+        yy[u] = ok ? z[(long long)it * Ns + j] : T(0);
 #pragma unroll
-      for (int c = 0; c < C; ++c) {
-        const int it = Nt - 1 - (cb * C + c);
+        for (int k = 0; k <= P; ++k) ul[u][k] = (ok && it + k < Nt) ? lu[((long long)it * B + (P + k)) * Ns + j] : T(0);
+      }
+    };
+    load(0, yv, uv);
+    for (int c0 = 0; c0 < Nt; c0 += U) {
+      if (c0 + U < Nt) load(c0 + U, yn, un);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int it = Nt - 1 - (c0 + u);
         if (it < 0) break;
-        T v = yv[c];
+        T v = yv[u];
 #pragma unroll
-        for (int k = 1; k <= P; ++k)
-          if (it + k < Nt) v -= *cell(u, c, k) * zw[k - 1];
-        v *= *cell(u, c, 0);
+        for (int k = P; k >= 1; --k) v -= uv[u][k] * zw[k - 1];
+        v *= uv[u][0];
 #pragma unroll
         for (int k = P - 1; k > 0; --k) zw[k] = zw[k - 1];
         zw[0] = v;
         z[(long long)it * Ns + j] = v;
       }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        yv[u] = yn[u];
+#pragma unroll
+        for (int k = 0; k <= P; ++k) uv[u][k] = un[u][k];
+      }
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&empty[u % S]);
   }
 }
 
@@ -2091,31 +2057,14 @@ void launch_rot_gemm(cudaStream_t s, T *out, const T *in, const T *M, int nb, in
 
 template <typename T>
 void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt, long long Ns, int p, int *err) {
-  const unsigned blocks = (unsigned)((Ns + 31) / 32);
-  // forward results kept in shared memory when a block's time lines fit
-  // (keeping them in shared memory caps residency at 3 blocks per SM and costs
-  // a second wave on the 2D workload, so y goes through z)
-  const bool ys = false;
-  auto go = [&](auto kern, int P, int slot) {
-    size_t sh = (size_t)kLuS * kLuC * (P + 1) * 32 * sizeof(T);
-    if (ys) sh += (size_t)Nt * 32 * sizeof(T);
-    static bool attr[10] = {false};
-    if (!attr[slot]) {
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-      attr[slot] = true;
-    }
-    st_count_launch();
-    kern<<<blocks, 128, sh, s>>>(z, r, lu, Nt, Ns, err);
-  };
-  switch (p * 2 + (ys ? 1 : 0)) {
-    case 2: go(tline_lu_kernel<T, 1, false>, 1, 0); break;
-    case 3: go(tline_lu_kernel<T, 1, true>, 1, 1); break;
-    case 4: go(tline_lu_kernel<T, 2, false>, 2, 2); break;
-    case 5: go(tline_lu_kernel<T, 2, true>, 2, 3); break;
-    case 6: go(tline_lu_kernel<T, 3, false>, 3, 4); break;
-    case 7: go(tline_lu_kernel<T, 3, true>, 3, 5); break;
-    case 8: go(tline_lu_kernel<T, 4, false>, 4, 6); break;
-    default: go(tline_lu_kernel<T, 4, true>, 4, 7); break;
+  (void)err;
+  constexpr int U = sizeof(T) == 4 ? 16 : 8;
+  const unsigned blocks = (unsigned)((Ns + 127) / 128);
+  switch (p) {
+    case 1: st_count_launch(); tline_lu_kernel<T, 1, U><<<blocks, 128, 0, s>>>(z, r, lu, Nt, Ns); break;
+    case 2: st_count_launch(); tline_lu_kernel<T, 2, U><<<blocks, 128, 0, s>>>(z, r, lu, Nt, Ns); break;
+    case 3: st_count_launch(); tline_lu_kernel<T, 3, U><<<blocks, 128, 0, s>>>(z, r, lu, Nt, Ns); break;
+    default: st_count_launch(); tline_lu_kernel<T, 4, U><<<blocks, 128, 0, s>>>(z, r, lu, Nt, Ns); break;
   }
 }
 
