@@ -36,7 +36,7 @@ WORKLOAD = "c2_aniso_2d"
 # ncu capture of the same kernel build (a 96x96x192 case, scaled to the full
 # launch by its Gauss point-steps); cleared whenever that kernel changes,
 # until it is captured again.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {"c2_aniso_2d": 1.2371e9}
 CPU_SAMPLE = dict(n_el=[12, 12], n_el_t=24)
 
 
@@ -352,7 +352,7 @@ def run_ours(args):
                   "mixed vs FP64",
         "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
+        "dtype": "f32+df64+f64", "data": "synthetic",
         "config": {"workload": f"{WORKLOAD}: 2D unit square, p=3, {desc['n_el'][0]}x{desc['n_el'][1]} x "
                                f"{desc['n_el_t']} elements, D=diag(1e-3,2.5e-4), seeded corner stimulus, SU, "
                                f"Picard step from saved iterate k=2",
