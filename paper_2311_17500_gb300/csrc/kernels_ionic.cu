@@ -500,6 +500,77 @@ __global__ void su_band_update_kernel(float *__restrict__ bhi, float *__restrict
   }
 }
 
+// Gram matrix G = Theta Theta^T (n x n, Theta n x K row-major, FP64) in
+// double-float arithmetic: upper-triangle 64 x 64 tiles, K split into chunks;
+// each block stages 64 x 32 slices of the two row panels as double-float pairs
+// and accumulates 4 x 4 outputs per thread; part[split][tile][64][64] holds
+// the chunk sums as FP64.
+constexpr int kGT = 64, kGK = 32;
+
+__global__ void __launch_bounds__(256) gram_df_kernel(double *__restrict__ part, const double *__restrict__ Th, int n,
+                                                      long long K, int ntile, int kchunk) {
+  __shared__ float2 sa[kGK][kGT + 1], sb[kGK][kGT + 1];
+  // tile pair (ti <= tj) from the linear index
+  int tp = blockIdx.x, ti = 0;
+  while (tp >= ntile - ti) { tp -= ntile - ti; ++ti; }
+  const int tj = ti + tp;
+  const long long k0 = (long long)blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 outputs each
+  df acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = {0.f, 0.f};
+  for (long long kb = k0; kb < k1; kb += kGK) {
+    for (int e = threadIdx.x; e < kGK * kGT; e += blockDim.x) {
+      const int rr = e / kGK, kk = e - rr * kGK;
+      const long long kx = kb + kk;
+      const int ra = ti * kGT + rr, rb = tj * kGT + rr;
+      const df va = (ra < n && kx < k1) ? df_from(Th[(long long)ra * K + kx]) : df{0.f, 0.f};
+      const df vb = (rb < n && kx < k1) ? df_from(Th[(long long)rb * K + kx]) : df{0.f, 0.f};
+      sa[kk][rr] = make_float2(va.hi, va.lo);
+      sb[kk][rr] = make_float2(vb.hi, vb.lo);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < kGK; ++kk) {
+      df av[4], bv[4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a) av[a] = df_from2(sa[kk][ty * 4 + a]);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) bv[b] = df_from2(sb[kk][tx * 4 + b]);
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = df_fma(av[a], bv[b], acc[a][b]);
+    }
+    __syncthreads();
+  }
+  double *dst = part + ((long long)blockIdx.y * gridDim.x + blockIdx.x) * kGT * kGT;
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) dst[(ty * 4 + a) * kGT + tx * 4 + b] = df_to(acc[a][b]);
+}
+
+// G[i][j] = G[j][i] = sum over the K chunks (fixed order, FP64).
+__global__ void gram_reduce_kernel(double *__restrict__ G, const double *__restrict__ part, int n, int ntile,
+                                   int npair, int nsplit) {
+  const long long total = (long long)npair * kGT * kGT;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+    const int pr = (int)(e / (kGT * kGT)), w = (int)(e - (long long)pr * kGT * kGT);
+    int tp = pr, ti = 0;
+    while (tp >= ntile - ti) { tp -= ntile - ti; ++ti; }
+    const int tj = ti + tp;
+    const int i = ti * kGT + w / kGT, j = tj * kGT + w % kGT;
+    if (i >= n || j >= n || (ti == tj && j < i)) continue;
+    double v = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) v += part[((long long)sp * npair + pr) * kGT * kGT + w];
+    G[(long long)i * n + j] = v;
+    G[(long long)j * n + i] = v;
+  }
+}
+
 __global__ void zero_ull_kernel(unsigned long long *p, long long n) {
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
@@ -638,8 +709,16 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
   st_count_launch(); theta_kernel<<<grid_for(NtNs), 256, 0, s>>>(h->theta, cur, den, NtNs);
   // Gram matrix G = Theta Theta^T (N_t x N_t, FP64)
   int Nt = h->Nt;
-  launch_gemm64(s, h->gram, h->theta, h->theta, Nt, Nt, (int)h->Ns, h->Ns, 1, 1, h->Ns, Nt, 1, 1.0, 0.0,
-                h->W64[0], h->NtQs);
+  {
+    // G = Theta Theta^T in double-float, upper-triangle tiles, K split so that
+    // the grid holds several blocks per SM (partials in the first work buffer)
+    const int ntile = (Nt + kGT - 1) / kGT, npair = ntile * (ntile + 1) / 2;
+    int nsplit = (int)std::max<long long>(1, std::min<long long>((152LL * 6 + npair - 1) / npair, (h->Ns + 255) / 256));
+    while ((long long)nsplit * npair * kGT * kGT > h->NtQs && nsplit > 1) --nsplit;
+    const int kchunk = (int)((h->Ns + nsplit - 1) / nsplit);
+    st_count_launch(); gram_df_kernel<<<dim3(npair, nsplit), 256, 0, s>>>(h->W64[0], h->theta, Nt, h->Ns, ntile, kchunk);
+    st_count_launch(); gram_reduce_kernel<<<grid_for((long long)npair * kGT * kGT), 256, 0, s>>>(h->gram, h->W64[0], Nt, ntile, npair, nsplit);
+  }
   std::vector<double> G((size_t)Nt * Nt);
   // trace = ||Theta||_F^2
   ST_CUDA(cudaMemcpyAsync(G.data(), h->gram, G.size() * sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -1186,11 +1186,9 @@ __global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, cons
                                                          int accumulate) {
   constexpr int B = 2 * P + 1, SW = 32, HW = SW + 2 * P;
   extern __shared__ __align__(16) unsigned char pk_raw[];
-  T *iW = reinterpret_cast<T *>(pk_raw);   // [ny][HW]
-  T *iM = iW + (size_t)ny * HW;            // [ny][HW]
-  T *r1 = iM + (size_t)ny * HW;            // [ny][SW]
-  T *r2 = r1 + (size_t)ny * SW;            // [ny][SW]
-  T *by = r2 + (size_t)ny * SW;            // [ny][2B]: M_y row, D_y K_y row
+  T *iW = reinterpret_cast<T *>(pk_raw);   // [ny][HW]; after the row pass r1 in columns P..P+SW-1
+  T *iM = iW + (size_t)ny * HW;            // [ny][HW]; after the row pass r2 in columns P..P+SW-1
+  T *by = iM + (size_t)ny * HW;            // [ny][2B]: M_y row, D_y K_y row
   const int cx0 = blockIdx.x * SW;
   const long long plane = (long long)nx * ny;
   const long long base = (long long)blockIdx.y * plane;
@@ -1228,8 +1226,10 @@ __global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, cons
     mx[k] = ok ? Mx[(size_t)cx * B + k] : T(0);
     kx[k] = ok ? Kx[(size_t)cx * B + k] : T(0);
   }
+  // row pass in place: a warp owns whole rows; all its reads of a row precede
+  // the writes of the results into the row's centre columns
   for (int r = rg; r < ny; r += nrg) {
-    const T *pw = iW + (size_t)r * HW + c, *pm = iM + (size_t)r * HW + c;
+    T *pw = iW + (size_t)r * HW + c, *pm = iM + (size_t)r * HW + c;
     T a = T(0), b = T(0), m2 = T(0);
 #pragma unroll
     for (int k = 0; k < B; ++k) {
@@ -1237,9 +1237,12 @@ __global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, cons
       b += kx[k] * pm[k];
       m2 += mx[k] * pm[k];
     }
-    r1[(size_t)r * SW + c] = Cm * a + Dx * b;
-    r2[(size_t)r * SW + c] = m2;
+    __syncwarp();
+    pw[P] = Cm * a + Dx * b;
+    pm[P] = m2;
+    __syncwarp();
   }
+  const T *r1 = iW + P, *r2 = iM + P;   // row stride HW
   __syncthreads();
   if (cx >= nx) return;
   // column pass: each thread a contiguous run of rows, r1 and r2 in a sliding
@@ -1251,15 +1254,15 @@ __global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, cons
   for (int k = 0; k < B - 1; ++k) {
     const int rr = ra - P + k;
     const bool ok = rr >= 0 && rr < ny;
-    w1[k + 1] = ok ? r1[(size_t)rr * SW + c] : T(0);
-    w2[k + 1] = ok ? r2[(size_t)rr * SW + c] : T(0);
+    w1[k + 1] = ok ? r1[(size_t)rr * HW + c] : T(0);
+    w2[k + 1] = ok ? r2[(size_t)rr * HW + c] : T(0);
   }
   for (int r = ra; r < rb; ++r) {
 #pragma unroll
     for (int k = 0; k < B - 1; ++k) { w1[k] = w1[k + 1]; w2[k] = w2[k + 1]; }
     const int rn = r + P;
-    w1[B - 1] = rn < ny ? r1[(size_t)rn * SW + c] : T(0);
-    w2[B - 1] = rn < ny ? r2[(size_t)rn * SW + c] : T(0);
+    w1[B - 1] = rn < ny ? r1[(size_t)rn * HW + c] : T(0);
+    w2[B - 1] = rn < ny ? r2[(size_t)rn * HW + c] : T(0);
     const T *br = by + (size_t)r * 2 * B;
     T v = T(0);
 #pragma unroll
@@ -1983,7 +1986,7 @@ template <typename T>
 bool launch_kron2d(cudaStream_t s, T *y, T *xW, T *xM, const T *x, const T *Wt, const T *Mt, const T *Mx,
                    const T *Kx, const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx,
                    double Dy) {
-  const size_t sh = (size_t)ny * (2 * (32 + 2 * p) + 2 * 32 + 2 * (2 * p + 1)) * sizeof(T);
+  const size_t sh = (size_t)ny * (2 * (32 + 2 * p) + 2 * (2 * p + 1)) * sizeof(T);
   if (sh > 200 * 1024 || p > 4) return false;
   const long long Ns = (long long)nx * ny;
   const int run = 32;
