@@ -856,8 +856,11 @@ constexpr long long kXbWaitLimit = 1ll << 22;
 template <typename T> struct XbandCT { typedef float type; };
 template <> struct XbandCT<double> { typedef df type; };
 
+template <typename T, int P>
+constexpr int xband_min_blocks() { return (sizeof(T) == 8 && P <= 3) ? 2 : 1; }
+
 template <typename T, int P, int S, bool BULK>
-__global__ void __launch_bounds__(xband_max_threads<T, P>()) xband_fused_kernel(
+__global__ void __launch_bounds__(xband_max_threads<T, P>(), xband_min_blocks<T, P>()) xband_fused_kernel(
     T *__restrict__ Y1, const T *__restrict__ X1, const float *__restrict__ bhi, const float *__restrict__ blo,
     const T *__restrict__ tab, int nel, int Nt, long long rows, int seglen, int *err) {
   typedef typename XbandCT<T>::type CT;
