@@ -722,6 +722,18 @@ static st_status setup_impl(st_handle *h) {
     if (dr.kmax >= 2) b2.assign(dr.tab.begin() + 2 * per, dr.tab.begin() + 3 * per);
     ST_TRY(upload<double>(h, &h->Bq[l], b0));
     ST_TRY(upload<double>(h, &h->B2q[l], b2));
+    {
+      auto split = [](const std::vector<double> &v) {
+        std::vector<float2> out(v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+          float hi = (float)v[i];
+          out[i] = make_float2(hi, (float)(v[i] - (double)hi));
+        }
+        return out;
+      };
+      ST_TRY(upload_vec<float2>(h, &h->Bq2[l], split(b0)));
+      ST_TRY(upload_vec<float2>(h, &h->B2q2[l], split(b2)));
+    }
     ST_TRY(upload<float>(h, &h->Bq32[l], b0));
     ST_TRY(upload<double>(h, &h->wqs[l], dr.wq));
     ST_TRY(upload<double>(h, &h->xs[l], dr.xq));

@@ -90,7 +90,7 @@ __device__ __forceinline__ void atomic_max_pos(unsigned long long *addr, double 
 struct IonicArgs {
   st_problem_desc D;
   GeomArgs g;
-  const double *U0, *L0, *W0;   // [Nt][Qs]: u, sum D_l d_ll u, w at spatial Gauss points
+  const float2 *U0, *L0, *W0;   // [Nt][Qs]: u, sum D_l d_ll u, w at spatial Gauss points (double-float)
   const double *bt, *xt;        // time tables: values/derivatives, points
   const double *bprod;          // [e][qt][pair]: w_t b_i b_{i+k} for the band pairs (i, k), k <= P - i
   const float2 *bt2, *bprod2;   // the same tables as double-float pairs (bt for k = 0, 1)
@@ -118,11 +118,11 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 // Newton), keeps max |R| per space-time element, and assembles the time band
 // sum_qt w_t C b_i b_j of the reaction mass term at this spatial point
 // (times its spatial weight).  Rows are written once complete.
-// The arithmetic is double-float (about 48 bits) and the band rows are stored
-// as their (high, low) float parts; FP64 is used only to convert each input
-// row once and for the element maxima.
+// The arithmetic is double-float (about 48 bits): the fields arrive as
+// double-float pairs and the band rows are stored as their (high, low) float
+// parts; FP64 is used only for the element maxima.
 template <int P>
-__global__ void __launch_bounds__(128) ionic_tline_kernel(IonicArgs a) {
+__global__ void __launch_bounds__(128, P <= 3 ? 4 : 2) ionic_tline_kernel(IonicArgs a) {
   constexpr int nq = P + 1, NPAIR = (P + 1) * (P + 2) / 2;
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   __shared__ unsigned long long red[3][4];
@@ -155,14 +155,14 @@ __global__ void __launch_bounds__(128) ionic_tline_kernel(IonicArgs a) {
 #pragma unroll
     for (int j = 1; j <= P; ++j) {
       const long long off = (long long)(j - 1) * a.Qs + q;
-      cu[j] = df_from(a.U0[off]);
-      cl[j] = df_from(a.L0[off]);
-      cw[j] = df_from(a.W0[off]);
+      cu[j] = df_from2(a.U0[off]);
+      cl[j] = df_from2(a.L0[off]);
+      cw[j] = df_from2(a.W0[off]);
     }
     df mu_d = zero, mut_d = zero;
     for (int e = 0; e < a.nel_t; ++e) {
       // next row (e + P), requested before this element's work
-      double nu = 0.0, nl = 0.0, nw = 0.0;
+      float2 nu = make_float2(0.f, 0.f), nl = nu, nw = nu;
       if (e + 1 < a.nel_t) {
         const long long off = (long long)(e + P) * a.Qs + q;
         nu = a.U0[off]; nl = a.L0[off]; nw = a.W0[off];
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(128) ionic_tline_kernel(IonicArgs a) {
       for (int k = 0; k <= P; ++k) acc[P][k] = zero;
 #pragma unroll
       for (int j = 0; j < P; ++j) { cu[j] = cu[j + 1]; cl[j] = cl[j + 1]; cw[j] = cw[j + 1]; }
-      cu[P] = df_from(nu); cl[P] = df_from(nl); cw[P] = df_from(nw);
+      cu[P] = df_from2(nu); cl[P] = df_from2(nl); cw[P] = df_from2(nw);
     }
     for (int r = 0; r < P; ++r) {
       int row = a.nel_t - 1 + r;
@@ -609,35 +609,85 @@ GeomArgs geom(st_handle *h) {
 // coefficient tensor [N_t][n_z][n_y][n_x] -> values at spatial Gauss points
 // [N_t][Q_z][Q_y][Q_x]; `deriv_dir` selects the direction that uses the second
 // derivative table (-1: values only).  Uses both FP64 work buffers.
-double *spatial_to_qpts(st_handle *h, const double *x, int deriv_dir, double *dst) {
+// One spatial axis from coefficients to Gauss points in double-float:
+// out[o][e*nq+g][c] (= or += coef *) sum_a tab[e][g][a] in[o][e+a][c].
+// Grid y runs over o, grid x over the (e*nq+g, c) outputs of one o slice, so
+// consecutive threads write consecutive addresses whatever the inner extent.
+template <int P>
+__global__ void interp_df_kernel(float2 *__restrict__ out, const float2 *__restrict__ in,
+                                 const float2 *__restrict__ tab, int nel, unsigned inner, long long outer,
+                                 int accumulate, double coef) {
+  constexpr int nq = P + 1;
+  const int nin = nel + P;
+  const unsigned slice = (unsigned)(nel * nq) * inner;
+  const df cf = df_from(coef);
+  for (long long o = blockIdx.y; o < outer; o += gridDim.y) {
+    const float2 *src0 = in + (size_t)o * nin * inner;
+    float2 *dst0 = out + (size_t)o * slice;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < slice; i += gridDim.x * blockDim.x) {
+      const unsigned eq = i / inner, c = i - eq * inner, e = eq / nq;
+      const float2 *tb = tab + (size_t)eq * (P + 1);
+      const float2 *src = src0 + (size_t)e * inner + c;
+      df v = {0.f, 0.f};
+#pragma unroll
+      for (int a = 0; a <= P; ++a) v = df_fma(df_from2(__ldg(tb + a)), df_from2(src[(size_t)a * inner]), v);
+      if (accumulate) v = df_fma(cf, v, df_from2(dst0[i]));
+      else if (coef != 1.0) v = df_mul(cf, v);
+      dst0[i] = make_float2(v.hi, v.lo);
+    }
+  }
+}
+
+void launch_interp_df(cudaStream_t s, float2 *out, const float2 *in, const float2 *tab, int nel, int p,
+                      long long inner, long long outer, int accumulate, double coef) {
+  const long long slice = (long long)nel * (p + 1) * inner;
+  const int threads = 256;
+  dim3 g((unsigned)std::min<long long>((slice + threads - 1) / threads, 1024),
+         (unsigned)std::min<long long>(outer, 65535));
+  const unsigned in32 = (unsigned)inner;
+  switch (p) {
+    case 1: st_count_launch(); interp_df_kernel<1><<<g, threads, 0, s>>>(out, in, tab, nel, in32, outer, accumulate, coef); break;
+    case 2: st_count_launch(); interp_df_kernel<2><<<g, threads, 0, s>>>(out, in, tab, nel, in32, outer, accumulate, coef); break;
+    case 3: st_count_launch(); interp_df_kernel<3><<<g, threads, 0, s>>>(out, in, tab, nel, in32, outer, accumulate, coef); break;
+    default: st_count_launch(); interp_df_kernel<4><<<g, threads, 0, s>>>(out, in, tab, nel, in32, outer, accumulate, coef); break;
+  }
+}
+
+// A field at the spatial Gauss points (all time rows), double-float: x given
+// as pairs; deriv_dir selects the axis taking the second derivative (-1:
+// none); the result is written to dst, or added to it times coef.
+void spatial_to_qpts(st_handle *h, const float2 *x, int deriv_dir, float2 *dst, int accumulate, double coef) {
   cudaStream_t s = h->stream;
-  const double *cur = x;
+  const float2 *cur = x;
   long long dims[3] = {h->n[0], h->n[1], h->n[2]};
   int ping = 0;
   for (int l = 0; l < h->d; ++l) {
     long long inner = 1, outer = h->Nt;
     for (int m = 0; m < l; ++m) inner *= h->Q[m];
     for (int m = l + 1; m < h->d; ++m) outer *= dims[m];
-    double *out = (l == h->d - 1) ? dst : h->W64[ping];
-    const double *tab = (l == deriv_dir) ? h->B2q[l] : h->Bq[l];
-    launch_interp_fwd<double>(s, out, cur, tab, h->nel[l], h->p, h->nq, inner, outer);
+    const bool last = l == h->d - 1;
+    float2 *out = last ? dst : reinterpret_cast<float2 *>(h->W64[ping]);
+    const float2 *tab = (l == deriv_dir) ? h->B2q2[l] : h->Bq2[l];
+    launch_interp_df(s, out, cur, tab, h->nel[l], h->p, inner, outer, last ? accumulate : 0, last ? coef : 1.0);
     cur = out;
     ping ^= 1;
   }
-  return dst;
 }
 
 }  // namespace
 
 st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bool want_stats) {
   cudaStream_t s = h->stream;
-  // fields at spatial Gauss points: u, sum_l D_ll d_ll u, w
-  spatial_to_qpts(h, u, -1, h->U0);
-  for (int l = 0; l < h->d; ++l) {
-    spatial_to_qpts(h, u, l, h->Wq0);   // temporarily the second-derivative field
-    launch_axpby64(s, h->L0, h->Wq0, h->desc.D[l], l == 0 ? 0.0 : 1.0, h->NtQs);
-  }
-  spatial_to_qpts(h, w, -1, h->Wq0);
+  // fields at spatial Gauss points as double-float pairs: u, sum_l D_ll d_ll u, w
+  // (u and w split into pairs first; the FP64 field buffers hold the pairs)
+  float2 *u2 = reinterpret_cast<float2 *>(h->t64a), *w2 = reinterpret_cast<float2 *>(h->t64b);
+  st_count_launch(); d2df_kernel<<<grid_for(h->Ndof), 256, 0, s>>>(u2, u, h->Ndof);
+  st_count_launch(); d2df_kernel<<<grid_for(h->Ndof), 256, 0, s>>>(w2, w, h->Ndof);
+  float2 *U0 = reinterpret_cast<float2 *>(h->U0), *L0 = reinterpret_cast<float2 *>(h->L0);
+  float2 *W0 = reinterpret_cast<float2 *>(h->Wq0);
+  spatial_to_qpts(h, u2, -1, U0, 0, 1.0);
+  for (int l = 0; l < h->d; ++l) spatial_to_qpts(h, u2, l, L0, l > 0 ? 1 : 0, h->desc.D[l]);
+  spatial_to_qpts(h, w2, -1, W0, 0, 1.0);
   if (want_stats) {
     st_count_launch(); zero_ull_kernel<<<grid_for((long long)h->nel_t * h->Nel_s), 256, 0, s>>>(h->emax, (long long)h->nel_t * h->Nel_s);
     st_count_launch(); zero_ull_kernel<<<1, 32, 0, s>>>((unsigned long long *)h->stats, 4);
@@ -645,7 +695,7 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   IonicArgs a;
   a.D = h->desc;
   a.g = geom(h);
-  a.U0 = h->U0; a.L0 = h->L0; a.W0 = h->Wq0;
+  a.U0 = U0; a.L0 = L0; a.W0 = W0;
   a.bt = h->bt; a.xt = h->xt; a.bprod = h->bprod;
   a.bt2 = h->bt2; a.bprod2 = h->bprod2;
   a.Nt = h->Nt; a.nel_t = h->nel_t;

@@ -57,6 +57,7 @@ struct st_handle {
   double *Mb[3] = {}, *Kb[3] = {}, *Mtb = nullptr, *Wtb = nullptr;
   float *Mb32[3] = {}, *Kb32[3] = {}, *Mtb32 = nullptr, *Wtb32 = nullptr;
   double *Bq[3] = {}, *B2q[3] = {}, *wqs[3] = {};   // spatial tables [e][q][a], weights [e*nq+q]
+  float2 *Bq2[3] = {}, *B2q2[3] = {};                 // the same tables as double-float pairs
   float *Bq32[3] = {};
   double *bt = nullptr;       // time tables [k][e][q][a], k = 0..p
   double *wt = nullptr;       // time weights [e*nq+q]
