@@ -468,16 +468,37 @@ __global__ void band_stream_kernel(T *__restrict__ out, TiledTerms<T> tt, int n,
   }
 }
 
+// One row of an interpolation table (P+1 values) in shared memory, aligned so
+// that rows of 2 or 4 values are read with one vector access.
+template <typename T, int N>
+struct __align__((N == 4 ? 4 : N == 2 ? 2 : 1) * sizeof(T)) TabRow {
+  T v[N];
+};
+
+// Runs of elements per block of the strided interpolation passes (shorter
+// runs give more independent blocks; every run rereads P neighbours).
+constexpr int kRunFwd = 8, kRunBwd = 16;
+
+// Coefficients -> Gauss points along a strided axis: thread = column c of
+// one outer slice o, block = a run of elements.  The run's table rows are
+// staged in shared memory; the coefficients of the next U elements are
+// loaded before their outputs are formed.
 template <typename T, int P>
-__global__ void ifwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab, int nel,
-                                   long long inner, long long outer, int nruns) {
-  constexpr int nq = P + 1, U = 8;
+__global__ void __launch_bounds__(256) ifwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in,
+                                                          const T *__restrict__ tab, int nel, long long inner,
+                                                          long long outer, int nruns) {
+  constexpr int nq = P + 1, U = 8, RUN = kRunFwd;
+  __shared__ TabRow<T, P + 1> st[RUN * nq];
   const int nin = nel + P, nout = nel * nq;
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= inner) return;
   for (long long yr = blockIdx.y; yr < outer * nruns; yr += gridDim.y) {
     const long long o = yr / nruns;
-    const int e0 = (int)(yr - o * nruns) * kRun, e1 = min(nel, e0 + kRun);
+    const int e0 = (int)(yr - o * nruns) * RUN, e1 = min(nel, e0 + RUN);
+    __syncthreads();   // the previous run's rows are no longer read
+    for (int i = threadIdx.x; i < (e1 - e0) * nq * (P + 1); i += blockDim.x)
+      st[i / (P + 1)].v[i % (P + 1)] = __ldg(tab + (size_t)e0 * nq * (P + 1) + i);
+    __syncthreads();
+    if (c >= inner) continue;
     const T *src = in + o * nin * inner + c;
     T *dst = out + o * nout * inner + c;
     T w[P + 1];
@@ -496,10 +517,10 @@ __global__ void ifwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in
         w[P] = nx[u];
 #pragma unroll
         for (int q = 0; q < nq; ++q) {
-          const T *tb = tab + ((size_t)e * nq + q) * (P + 1);
+          const TabRow<T, P + 1> tb = st[(e - e0) * nq + q];
           T sacc = T(0);
 #pragma unroll
-          for (int a = 0; a <= P; ++a) sacc += __ldg(tb + a) * w[a];
+          for (int a = 0; a <= P; ++a) sacc += tb.v[a] * w[a];
           dst[((long long)e * nq + q) * inner] = sacc;
         }
       }
@@ -507,44 +528,57 @@ __global__ void ifwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in
   }
 }
 
+// Gauss points -> coefficients along a strided axis (transpose of the pass
+// above): thread = column c, block = a run of output coefficients; the
+// elements touching the run are swept in batches of UE whose Gauss values
+// (and, when accumulating, the old outputs) are loaded together.
 template <typename T, int P>
-__global__ void ibwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in, const T *__restrict__ tab, int nel,
-                                   long long inner, long long outer, int nruns, int accumulate) {
-  constexpr int nq = P + 1, UE = 4;   // elements whose Gauss values are loaded together
+__global__ void __launch_bounds__(256) ibwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in,
+                                                          const T *__restrict__ tab, int nel, long long inner,
+                                                          long long outer, int nruns, int accumulate) {
+  constexpr int nq = P + 1, UE = 4, RUN = kRunBwd;
+  __shared__ TabRow<T, P + 1> st[(RUN + P) * nq];
   const int nin = nel * nq, nout = nel + P;
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= inner) return;
   for (long long yr = blockIdx.y; yr < outer * nruns; yr += gridDim.y) {
     const long long o = yr / nruns;
-    const int i0 = (int)(yr - o * nruns) * kRun, i1 = min(nout, i0 + kRun);
+    const int i0 = (int)(yr - o * nruns) * RUN, i1 = min(nout, i0 + RUN);
+    const int ea = max(0, i0 - P), eb = min(nel - 1, i1 - 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (eb - ea + 1) * nq * (P + 1); i += blockDim.x)
+      st[i / (P + 1)].v[i % (P + 1)] = __ldg(tab + (size_t)ea * nq * (P + 1) + i);
+    __syncthreads();
+    if (c >= inner) continue;
     const T *src = in + o * nin * inner + c;
     T *dst = out + o * nout * inner + c;
     T acc[P + 1];   // acc[a]: coefficient e + a while element e is processed
 #pragma unroll
     for (int a = 0; a <= P; ++a) acc[a] = T(0);
-    const int ea = max(0, i0 - P), eb = min(nel - 1, i1 - 1);
     for (int e0 = ea; e0 <= eb; e0 += UE) {
-      T z[UE][nq];
+      T z[UE][nq], yo[UE];
 #pragma unroll
-      for (int u = 0; u < UE; ++u)
+      for (int u = 0; u < UE; ++u) {
+        const bool ok = e0 + u <= eb;
 #pragma unroll
-        for (int q = 0; q < nq; ++q) z[u][q] = (e0 + u <= eb) ? src[((long long)(e0 + u) * nq + q) * inner] : T(0);
+        for (int q = 0; q < nq; ++q) z[u][q] = ok ? src[((long long)(e0 + u) * nq + q) * inner] : T(0);
+        yo[u] = (accumulate && ok && e0 + u >= i0) ? dst[(long long)(e0 + u) * inner] : T(0);
+      }
 #pragma unroll
       for (int u = 0; u < UE; ++u) {
         const int e = e0 + u;
         if (e > eb) break;
+        TabRow<T, P + 1> r[nq];
+#pragma unroll
+        for (int q = 0; q < nq; ++q) r[q] = st[(e - ea) * nq + q];
 #pragma unroll
         for (int a = 0; a <= P; ++a) {
           T sacc = T(0);
 #pragma unroll
-          for (int q = 0; q < nq; ++q) sacc += __ldg(tab + ((size_t)e * nq + q) * (P + 1) + a) * z[u][q];
+          for (int q = 0; q < nq; ++q) sacc += r[q].v[a] * z[u][q];
           acc[a] += sacc;
         }
         // coefficient e receives nothing from later elements
-        if (e >= i0) {
-          long long idx = (long long)e * inner;
-          dst[idx] = accumulate ? dst[idx] + acc[0] : acc[0];
-        }
+        if (e >= i0) dst[(long long)e * inner] = accumulate ? yo[u] + acc[0] : acc[0];
 #pragma unroll
         for (int a = 0; a < P; ++a) acc[a] = acc[a + 1];
         acc[P] = T(0);
@@ -690,7 +724,8 @@ void launch_tiled(cudaStream_t s, T *out, const TiledTerms<T> &tt, int nin, int 
   } else {
     int bx = (int)std::min<long long>(256, (inner + 31) / 32 * 32);
     long long gx = (inner + bx - 1) / bx;
-    int nruns = OP == OP_FWD ? (nin - P + kRun - 1) / kRun : (nout + kRun - 1) / kRun;
+    int nruns = OP == OP_FWD ? (nin - P + kRunFwd - 1) / kRunFwd
+                : OP == OP_BWD ? (nout + kRunBwd - 1) / kRunBwd : (nout + kRun - 1) / kRun;
     long long gy = std::min<long long>(outer * nruns, 65535);
     dim3 grid((unsigned)gx, (unsigned)gy);
     if (OP == OP_BAND)
@@ -1116,162 +1151,151 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>(), xband_min_blocks<T,
   }
 }
 
-// Kronecker part of the operator for d = 2 (Sec. 3.1.1),
-//   y = C_m (W_t (x) M_y (x) M_x) x + (M_t (x) (D_x M_y (x) K_x + D_y K_y (x) M_x)) x,
-// in two passes: the time bands first (xW = W_t x, xM = M_t x, one read of x),
-// then every time slice in the plane.
-// Time pass: one thread per (spatial index j, run of time steps), a register
-// window of x along time; the two band rows of each step come from shared
-// memory (broadcast reads).  Bands [i][k] = A(i, i-P+k).
-template <typename T, int P>
-__global__ void __launch_bounds__(256) time_band2_kernel(T *__restrict__ xW, T *__restrict__ xM, const T *__restrict__ x,
-                                                         const T *__restrict__ Wt, const T *__restrict__ Mt, int Nt,
-                                                         long long Ns, int run) {
-  constexpr int B = 2 * P + 1, U = 8;
-  __shared__ __align__(16) T rows[64][16];   // [step in run][W_t row (8) | M_t row (8)]
-  const int it0 = blockIdx.y * run, it1 = min(Nt, it0 + run);
-  for (int e = threadIdx.x; e < (it1 - it0) * 16; e += blockDim.x) {
-    const int r = e >> 4, c = e & 15, i = it0 + r;
-    const int k = c & 7;
-    T v = T(0);
-    if (k < B) {
-      const int jc = i - P + k;
-      if (jc >= 0 && jc < Nt) v = (c < 8 ? Wt : Mt)[(size_t)i * B + k];
-    }
-    rows[r][c] = v;
-  }
-  __syncthreads();
-  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (j >= Ns) return;
-  T w[B];
-#pragma unroll
-  for (int k = 0; k < B - 1; ++k) {
-    const int it = it0 - P + k;
-    w[k + 1] = (it >= 0 && it < Nt) ? x[(long long)it * Ns + j] : T(0);
-  }
-  for (int ib = it0; ib < it1; ib += U) {
-    T nx[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int it = ib + u + P;
-      nx[u] = (ib + u < it1 && it < Nt) ? x[(long long)it * Ns + j] : T(0);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = ib + u;
-      if (i >= it1) break;
-#pragma unroll
-      for (int k = 0; k < B - 1; ++k) w[k] = w[k + 1];
-      w[B - 1] = nx[u];
-      const T *rw = rows[i - it0];
-      T sw = T(0), sm = T(0);
-#pragma unroll
-      for (int k = 0; k < B; ++k) {
-        sw += rw[k] * w[k];
-        sm += rw[8 + k] * w[k];
-      }
-      xW[(long long)i * Ns + j] = sw;
-      xM[(long long)i * Ns + j] = sm;
-    }
-  }
+// Two values combined by one paired multiply-add: (a.x b.x + c.x, a.y b.y + c.y).
+// FP32 pairs issue as one packed instruction (two FMAs per issue slot); FP64
+// pairs are two scalar FMAs.
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rc, rd;\n\t"
+      "mov.b64 ra, {%2, %3};\n\t"
+      "mov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\t"
+      "mov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
 }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename T> struct Pair;
+template <> struct Pair<float> {
+  typedef float2 type;
+  static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+};
+template <> struct Pair<double> {
+  typedef double2 type;
+  static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+};
 
-// Plane pass: block = (32-column strip, time slice).  Stages xW, xM of the
-// strip with a P-column halo, applies the x bands (r1 = C_m M_x xW + D_x K_x xM,
-// r2 = M_x xM) into shared memory, then the y bands:
-//   y = M_y r1 + D_y K_y r2   (written, or added to y).
-// Shared memory: ny * (2 (32 + 2P) + 2 * 32 + 2 (2P+1)) values.
+// Kronecker part of the operator for d = 2 (Sec. 3.1.1),
+//   y = C_m (W_t (x) M_y (x) M_x) x + (M_t (x) (D_x M_y (x) K_x + D_y K_y (x) M_x)) x
+//     = M_y r1 + D_y K_y r2,   r1 = C_m M_x xW + D_x K_x xM,  r2 = M_x xM,
+// with xW = W_t x and xM = M_t x, in one pass.  Block = (32-column strip,
+// time slice t):
+//  1. (xW, xM) of the strip with a P-column halo, as pairs in shared memory,
+//     from the 2P+1 planes of x around t (x is read from L2 by the blocks of
+//     neighbouring slices; each plane comes from HBM about once);
+//  2. the x bands in place (a warp owns whole rows; each lane one column);
+//  3. the y bands down each column from a sliding register window.
+// Every product of two bands' pairs is one paired multiply-add.  Bands
+// [i][k] = A(i, i-P+k).  Shared memory: ny (32 + 2P + 2P + 1) pairs.
 template <typename T, int P>
-__global__ void __launch_bounds__(256) plane_kron_kernel(T *__restrict__ y, const T *__restrict__ xW,
-                                                         const T *__restrict__ xM, const T *__restrict__ Mx,
-                                                         const T *__restrict__ Kx, const T *__restrict__ My,
-                                                         const T *__restrict__ Ky, int nx, int ny, T Cm, T Dx, T Dy,
-                                                         int accumulate) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *__restrict__ y, const T *__restrict__ x,
+                                                     const T *__restrict__ Wt, const T *__restrict__ Mt,
+                                                     const T *__restrict__ Mx, const T *__restrict__ Kx,
+                                                     const T *__restrict__ My, const T *__restrict__ Ky, int nx, int ny,
+                                                     int Nt, T Cm, T Dx, T Dy) {
+  typedef typename Pair<T>::type T2;
   constexpr int B = 2 * P + 1, SW = 32, HW = SW + 2 * P;
-  extern __shared__ __align__(16) unsigned char pk_raw[];
-  T *iW = reinterpret_cast<T *>(pk_raw);   // [ny][HW]; after the row pass r1 in columns P..P+SW-1
-  T *iM = iW + (size_t)ny * HW;            // [ny][HW]; after the row pass r2 in columns P..P+SW-1
-  T *by = iM + (size_t)ny * HW;            // [ny][2B]: M_y row, D_y K_y row
-  const int cx0 = blockIdx.x * SW;
-  const long long plane = (long long)nx * ny;
-  const long long base = (long long)blockIdx.y * plane;
+  extern __shared__ __align__(16) unsigned char k2_raw[];
+  T2 *S = reinterpret_cast<T2 *>(k2_raw);   // [ny][HW]: (xW, xM); after the x pass (r1, r2) in columns P..P+SW-1
+  T2 *by = S + (size_t)ny * HW;             // [ny][B]: (M_y, D_y K_y) row pairs
+  const int t = blockIdx.y, cx0 = blockIdx.x * SW;
+  const long long Ns = (long long)nx * ny;
   const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5, nrg = blockDim.x >> 5;
-  // stage the strip with asynchronous copies (all in flight at once); halo
-  // columns outside the plane are zero
-  for (int r = rg; r < ny; r += nrg) {
-    const T *rw = xW + base + (long long)r * nx, *rm = xM + base + (long long)r * nx;
-    for (int c = lane; c < HW; c += 32) {
-      const int cx = cx0 - P + c;
-      if (cx >= 0 && cx < nx) {
-        cp_async_elem(iW + (size_t)r * HW + c, rw + cx);
-        cp_async_elem(iM + (size_t)r * HW + c, rm + cx);
-      } else {
-        iW[(size_t)r * HW + c] = T(0);
-        iM[(size_t)r * HW + c] = T(0);
-      }
-    }
-  }
-  cp_async_commit();
+  // row t of W_t and M_t as pairs; only the planes klo..khi exist
+  const int klo = max(0, P - t), khi = min(B - 1, Nt - 1 - t + P);
+  T2 tw[B];
+#pragma unroll
+  for (int k = 0; k < B; ++k)
+    tw[k] = (k >= klo && k <= khi) ? Pair<T>::make(Wt[(size_t)t * B + k], Mt[(size_t)t * B + k]) : Pair<T>::make(0, 0);
   for (int e = threadIdx.x; e < ny * B; e += blockDim.x) {
     const int r = e / B, k = e - r * B, rr = r - P + k;
     const bool ok = rr >= 0 && rr < ny;
-    by[(size_t)r * 2 * B + k] = ok ? My[e] : T(0);
-    by[(size_t)r * 2 * B + B + k] = ok ? Dy * Ky[e] : T(0);
+    by[e] = ok ? Pair<T>::make(My[e], Dy * Ky[e]) : Pair<T>::make(0, 0);
   }
-  cp_async_wait<0>();
+  // 1. time bands of the strip (halo columns outside the plane are zero);
+  // UE elements a round, all their loads issued before any product
+  constexpr int UE = 4;
+  const long long pofs = (long long)(t - P) * Ns;   // offset of plane t-P (negative near the start)
+  const int nel = ny * HW;
+  for (int e0 = threadIdx.x; e0 < nel; e0 += UE * blockDim.x) {
+    T v[UE][B];
+#pragma unroll
+    for (int u = 0; u < UE; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int r = e / HW, c = e - r * HW, cx = cx0 - P + c;
+      const bool ok = e < nel && cx >= 0 && cx < nx;
+      const long long o = pofs + (long long)r * nx + cx;
+#pragma unroll
+      for (int k = 0; k < B; ++k) v[u][k] = (ok && k >= klo && k <= khi) ? __ldg(x + (o + (long long)k * Ns)) : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < UE; ++u) {
+      const int e = e0 + u * blockDim.x;
+      T2 acc = Pair<T>::make(0, 0);
+#pragma unroll
+      for (int k = 0; k < B; ++k) acc = pfma(tw[k], Pair<T>::make(v[u][k], v[u][k]), acc);
+      if (e < nel) S[e] = acc;
+    }
+  }
   __syncthreads();
-  const int c = lane;
-  const int cx = cx0 + c;
-  T mx[B], kx[B];
+  // 2. x bands in place: all reads of a row precede the writes of its centre
+  const int c = lane, cx = cx0 + c;
+  T2 mx[B];
+  T kx[B];
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const bool ok = cx < nx && cx - P + k >= 0 && cx - P + k < nx;
-    mx[k] = ok ? Mx[(size_t)cx * B + k] : T(0);
+    const T m = ok ? Mx[(size_t)cx * B + k] : T(0);
+    mx[k] = Pair<T>::make(m, m);
     kx[k] = ok ? Kx[(size_t)cx * B + k] : T(0);
   }
-  // row pass in place: a warp owns whole rows; all its reads of a row precede
-  // the writes of the results into the row's centre columns
   for (int r = rg; r < ny; r += nrg) {
-    T *pw = iW + (size_t)r * HW + c, *pm = iM + (size_t)r * HW + c;
-    T a = T(0), b = T(0), m2 = T(0);
+    T2 *row = S + (size_t)r * HW + c;
+    T2 a = Pair<T>::make(0, 0);   // (M_x xW, M_x xM)
+    T b = T(0);                   // K_x xM
 #pragma unroll
     for (int k = 0; k < B; ++k) {
-      a += mx[k] * pw[k];
-      b += kx[k] * pm[k];
-      m2 += mx[k] * pm[k];
+      const T2 v = row[k];
+      a = pfma(mx[k], v, a);
+      b = fma(kx[k], v.y, b);
     }
     __syncwarp();
-    pw[P] = Cm * a + Dx * b;
-    pm[P] = m2;
+    row[P] = Pair<T>::make(Cm * a.x + Dx * b, a.y);
     __syncwarp();
   }
-  const T *r1 = iW + P, *r2 = iM + P;   // row stride HW
   __syncthreads();
   if (cx >= nx) return;
-  // column pass: each thread a contiguous run of rows, r1 and r2 in a sliding
-  // register window (every staged value read once)
+  // 3. y bands: each warp a contiguous run of rows, (r1, r2) of rows r-P..r+P
+  // in registers
+  const T2 *R = S + P + c;   // row stride HW
   const int per = (ny + nrg - 1) / nrg, ra = rg * per, rb = min(ny, ra + per);
   if (ra >= rb) return;
-  T w1[B], w2[B];
+  T2 w[B];
 #pragma unroll
   for (int k = 0; k < B - 1; ++k) {
     const int rr = ra - P + k;
-    const bool ok = rr >= 0 && rr < ny;
-    w1[k + 1] = ok ? r1[(size_t)rr * HW + c] : T(0);
-    w2[k + 1] = ok ? r2[(size_t)rr * HW + c] : T(0);
+    w[k + 1] = (rr >= 0 && rr < ny) ? R[(size_t)rr * HW] : Pair<T>::make(0, 0);
   }
-  for (int r = ra; r < rb; ++r) {
+  T *yo = y + (long long)t * Ns + (long long)ra * nx + cx;
+  for (int r0 = ra; r0 < rb; r0 += B) {
 #pragma unroll
-    for (int k = 0; k < B - 1; ++k) { w1[k] = w1[k + 1]; w2[k] = w2[k + 1]; }
-    const int rn = r + P;
-    w1[B - 1] = rn < ny ? r1[(size_t)rn * HW + c] : T(0);
-    w2[B - 1] = rn < ny ? r2[(size_t)rn * HW + c] : T(0);
-    const T *br = by + (size_t)r * 2 * B;
-    T v = T(0);
+    for (int u = 0; u < B; ++u) {
+      const int r = r0 + u;
+      if (r >= rb) break;
 #pragma unroll
-    for (int k = 0; k < B; ++k) v += br[k] * w1[k] + br[B + k] * w2[k];
-    const long long idx = base + (long long)r * nx + cx;
-    y[idx] = accumulate ? y[idx] + v : v;
+      for (int k = 0; k < B - 1; ++k) w[k] = w[k + 1];
+      w[B - 1] = r + P < ny ? R[(size_t)(r + P) * HW] : Pair<T>::make(0, 0);
+      const T2 *br = by + (size_t)r * B;
+      T2 acc = Pair<T>::make(0, 0);
+#pragma unroll
+      for (int k = 0; k < B; ++k) acc = pfma(br[k], w[k], acc);
+      *yo = acc.x + acc.y;
+      yo += nx;
+    }
   }
 }
 
@@ -1986,29 +2010,24 @@ bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, co
 }
 
 template <typename T>
-bool launch_kron2d(cudaStream_t s, T *y, T *xW, T *xM, const T *x, const T *Wt, const T *Mt, const T *Mx,
-                   const T *Kx, const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx,
-                   double Dy) {
-  const size_t sh = (size_t)ny * (2 * (32 + 2 * p) + 2 * (2 * p + 1)) * sizeof(T);
-  if (sh > 200 * 1024 || p > 4) return false;
-  const long long Ns = (long long)nx * ny;
-  const int run = 32;
-  dim3 g1((unsigned)((Ns + 255) / 256), (unsigned)((Nt + run - 1) / run));
-  dim3 g2((unsigned)((nx + 31) / 32), (unsigned)Nt);
-  auto go = [&](auto k1, auto k2, int P) {
+bool launch_kron2d(cudaStream_t s, T *y, const T *x, const T *Wt, const T *Mt, const T *Mx, const T *Kx, const T *My,
+                   const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx, double Dy) {
+  const size_t sh = (size_t)ny * ((32 + 2 * p) + (2 * p + 1)) * 2 * sizeof(T);
+  if (sh > 200 * 1024 || p > 4 || Nt > 65535) return false;
+  dim3 g((unsigned)((nx + 31) / 32), (unsigned)Nt);
+  auto go = [&](auto k, int P) {
     static bool attr[5] = {false, false, false, false, false};
     if (!attr[P]) {
-      cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr[P] = true;
     }
-    st_count_launch(); k1<<<g1, 256, 0, s>>>(xW, xM, x, Wt, Mt, Nt, Ns, run);
-    st_count_launch(); k2<<<g2, 256, sh, s>>>(y, xW, xM, Mx, Kx, My, Ky, nx, ny, (T)Cm, (T)Dx, (T)Dy, 0);
+    st_count_launch(); k<<<g, 256, sh, s>>>(y, x, Wt, Mt, Mx, Kx, My, Ky, nx, ny, Nt, (T)Cm, (T)Dx, (T)Dy);
   };
   switch (p) {
-    case 1: go(time_band2_kernel<T, 1>, plane_kron_kernel<T, 1>, 1); break;
-    case 2: go(time_band2_kernel<T, 2>, plane_kron_kernel<T, 2>, 2); break;
-    case 3: go(time_band2_kernel<T, 3>, plane_kron_kernel<T, 3>, 3); break;
-    default: go(time_band2_kernel<T, 4>, plane_kron_kernel<T, 4>, 4); break;
+    case 1: go(kron2d_kernel<T, 1>, 1); break;
+    case 2: go(kron2d_kernel<T, 2>, 2); break;
+    case 3: go(kron2d_kernel<T, 3>, 3); break;
+    default: go(kron2d_kernel<T, 4>, 4); break;
   }
   return true;
 }
@@ -2219,8 +2238,8 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
                                      long long, bool);                                                \
   template void launch_qband_apply<T>(cudaStream_t, T *, const T *, const float *, const float *, int, \
                                       long long, int);                                                  \
-  template bool launch_kron2d<T>(cudaStream_t, T *, T *, T *, const T *, const T *, const T *, const T *, \
-                                 const T *, const T *, const T *, int, int, int, int, double, double,   \
+  template bool launch_kron2d<T>(cudaStream_t, T *, const T *, const T *, const T *, const T *, const T *, \
+                                 const T *, const T *, int, int, int, int, double, double,              \
                                  double);                                                              \
   template bool launch_xband_fused<T>(cudaStream_t, T *, const T *, const float *, const float *,       \
                                       const T *, int, int, long long, int, int *);                      \
