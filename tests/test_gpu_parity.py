@@ -155,6 +155,29 @@ def test_lowrank_long_time(P):
     s.close()
 
 
+@pytest.mark.parametrize("kind", ["picard", "newton"])
+def test_apply_tiny_mesh(P, kind):
+    """A 2D mesh of 1 x 2 elements with p = 1 (6 coefficients per time slice, 3
+    time functions): one 32-column strip far wider than the plane, time bands
+    cut at both ends.  FP64 and FP32 operator as in the cases above."""
+    c = dict(d=2, p=1, n_el=[1, 2], n_el_t=3)
+    desc = problem(c, nonlinear=kind)
+    o = Oracle(desc)
+    u, w = iterate(o, 2)
+    A, _ = o.linearization(u, w, kind)
+    s = solver(P, desc)
+    du, dw = dev(u), dev(w)
+    s.ionic(ptr(du), ptr(dw))
+    x = W.random_vector(o.st.N_dof, seed=5)
+    dx, dy = dev(x), empty(o.st.N_dof)
+    s.apply(ptr(dx), ptr(dy), P.ST_FP64)
+    assert rel(host(dy), A @ x) < 1e-12
+    dx32, dy32 = dev(x, np.float32), empty(o.st.N_dof, "float32")
+    s.apply(ptr(dx32), ptr(dy32), P.ST_MIXED)
+    assert rel(host(dy32), A @ x) < 2e-5
+    s.close()
+
+
 @pytest.mark.parametrize("c", CASES, ids=IDS)
 def test_precond(P, c):
     desc = problem(c)
