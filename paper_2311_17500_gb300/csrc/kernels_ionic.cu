@@ -653,6 +653,94 @@ void launch_interp_df(cudaStream_t s, float2 *out, const float2 *in, const float
   }
 }
 
+// The three fields of the ionic model in two dimensions by sum factorization,
+// every input read once per pass, double-float.  One axis, inner extent
+// `inner` (1 for x), tables B (values) and B2 (second derivatives):
+//  first pass (x):  o0 = B i0,  o1 = B2 i0,  o2 = B i1      (i0 = u, i1 = w)
+//  last pass (y):   o0 = B i0,  o1 = c1 B i1 + c2 B2 i0,  o2 = B i2
+// so that with i0 = B_x u, i1 = B2_x u, i2 = B_x w the outputs are u,
+// D_x d_xx u + D_y d_yy u and w at the spatial Gauss points.
+// Grid y runs over the outer index, grid x over one outer slice.
+template <int P, bool LAST>
+__global__ void fields_interp_kernel(float2 *__restrict__ o0, float2 *__restrict__ o1, float2 *__restrict__ o2,
+                                     const float2 *__restrict__ i0, const float2 *__restrict__ i1,
+                                     const float2 *__restrict__ i2, const float2 *__restrict__ tb,
+                                     const float2 *__restrict__ tb2, int nel, unsigned inner, long long outer,
+                                     double c1, double c2) {
+  constexpr int nq = P + 1;
+  const int nin = nel + P;
+  const unsigned slice = (unsigned)(nel * nq) * inner;
+  const df d1 = df_from(c1), d2 = df_from(c2);
+  for (long long o = blockIdx.y; o < outer; o += gridDim.y) {
+    const size_t ibase = (size_t)o * nin * inner, obase = (size_t)o * slice;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < slice; i += gridDim.x * blockDim.x) {
+      const unsigned eq = i / inner, c = i - eq * inner, e = eq / nq;
+      const size_t src = ibase + (size_t)e * inner + c;
+      df s0 = {0.f, 0.f}, s1 = s0, s2 = s0, s3 = s0;
+#pragma unroll
+      for (int a = 0; a <= P; ++a) {
+        const df b = df_from2(__ldg(tb + (size_t)eq * nq + a)), b2 = df_from2(__ldg(tb2 + (size_t)eq * nq + a));
+        const size_t k = src + (size_t)a * inner;
+        const df x0 = df_from2(i0[k]), x1 = df_from2(i1[k]);
+        s0 = df_fma(b, x0, s0);
+        s1 = df_fma(b2, x0, s1);
+        s2 = df_fma(b, x1, s2);
+        if (LAST) s3 = df_fma(b, df_from2(i2[k]), s3);
+      }
+      const size_t d = obase + i;
+      o0[d] = make_float2(s0.hi, s0.lo);
+      if (LAST) {
+        const df l = df_fma(d1, s2, df_mul(d2, s1));
+        o1[d] = make_float2(l.hi, l.lo);
+        o2[d] = make_float2(s3.hi, s3.lo);
+      } else {
+        o1[d] = make_float2(s1.hi, s1.lo);
+        o2[d] = make_float2(s2.hi, s2.lo);
+      }
+    }
+  }
+}
+
+template <bool LAST>
+void launch_fields_interp(cudaStream_t s, int p, float2 *o0, float2 *o1, float2 *o2, const float2 *i0,
+                          const float2 *i1, const float2 *i2, const float2 *tb, const float2 *tb2, int nel,
+                          long long inner, long long outer, double c1, double c2) {
+  const long long slice = (long long)nel * (p + 1) * inner;
+  const int threads = 256;
+  dim3 g((unsigned)std::min<long long>((slice + threads - 1) / threads, 1024),
+         (unsigned)std::min<long long>(outer, 65535));
+  const unsigned in32 = (unsigned)inner;
+  switch (p) {
+    case 1: st_count_launch(); fields_interp_kernel<1, LAST><<<g, threads, 0, s>>>(o0, o1, o2, i0, i1, i2, tb, tb2, nel, in32, outer, c1, c2); break;
+    case 2: st_count_launch(); fields_interp_kernel<2, LAST><<<g, threads, 0, s>>>(o0, o1, o2, i0, i1, i2, tb, tb2, nel, in32, outer, c1, c2); break;
+    case 3: st_count_launch(); fields_interp_kernel<3, LAST><<<g, threads, 0, s>>>(o0, o1, o2, i0, i1, i2, tb, tb2, nel, in32, outer, c1, c2); break;
+    default: st_count_launch(); fields_interp_kernel<4, LAST><<<g, threads, 0, s>>>(o0, o1, o2, i0, i1, i2, tb, tb2, nel, in32, outer, c1, c2); break;
+  }
+}
+
+// The 2D fields through the two passes above when the three x-pass results
+// fit in the two Gauss-point work buffers; false (nothing launched) if not.
+bool fields_to_qpts_2d(st_handle *h, const float2 *u2, const float2 *w2, float2 *U0, float2 *L0, float2 *W0) {
+  if (h->d != 2) return false;
+  const long long sz = h->Nt * h->n[1] * h->Q[0];   // one x-pass result [N_t][n_y][Q_x]
+  const long long cap = h->NtQs;                      // pairs per work buffer
+  float2 *B0 = reinterpret_cast<float2 *>(h->W64[0]), *B1 = reinterpret_cast<float2 *>(h->W64[1]);
+  float2 *X[3];
+  if (3 * sz <= cap) {
+    X[0] = B0; X[1] = B0 + sz; X[2] = B0 + 2 * sz;
+  } else if (2 * sz <= cap) {
+    X[0] = B0; X[1] = B0 + sz; X[2] = B1;
+  } else {
+    return false;
+  }
+  cudaStream_t s = h->stream;
+  launch_fields_interp<false>(s, h->p, X[0], X[1], X[2], u2, w2, nullptr, h->Bq2[0], h->B2q2[0], h->nel[0], 1,
+                              h->Nt * h->n[1], 1.0, 1.0);
+  launch_fields_interp<true>(s, h->p, U0, L0, W0, X[0], X[1], X[2], h->Bq2[1], h->B2q2[1], h->nel[1], h->Q[0],
+                             h->Nt, h->desc.D[0], h->desc.D[1]);
+  return true;
+}
+
 // A field at the spatial Gauss points (all time rows), double-float: x given
 // as pairs; deriv_dir selects the axis taking the second derivative (-1:
 // none); the result is written to dst, or added to it times coef.
@@ -685,9 +773,11 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   st_count_launch(); d2df_kernel<<<grid_for(h->Ndof), 256, 0, s>>>(w2, w, h->Ndof);
   float2 *U0 = reinterpret_cast<float2 *>(h->U0), *L0 = reinterpret_cast<float2 *>(h->L0);
   float2 *W0 = reinterpret_cast<float2 *>(h->Wq0);
-  spatial_to_qpts(h, u2, -1, U0, 0, 1.0);
-  for (int l = 0; l < h->d; ++l) spatial_to_qpts(h, u2, l, L0, l > 0 ? 1 : 0, h->desc.D[l]);
-  spatial_to_qpts(h, w2, -1, W0, 0, 1.0);
+  if (!fields_to_qpts_2d(h, u2, w2, U0, L0, W0)) {
+    spatial_to_qpts(h, u2, -1, U0, 0, 1.0);
+    for (int l = 0; l < h->d; ++l) spatial_to_qpts(h, u2, l, L0, l > 0 ? 1 : 0, h->desc.D[l]);
+    spatial_to_qpts(h, w2, -1, W0, 0, 1.0);
+  }
   if (want_stats) {
     st_count_launch(); zero_ull_kernel<<<grid_for((long long)h->nel_t * h->Nel_s), 256, 0, s>>>(h->emax, (long long)h->nel_t * h->Nel_s);
     st_count_launch(); zero_ull_kernel<<<1, 32, 0, s>>>((unsigned long long *)h->stats, 4);
