@@ -224,24 +224,54 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
     close_column(c);
   };
   std::vector<double> acol(m + 1);
-  int j = 0;
-  for (; j < m; ++j) {
-    T *uj = V + (long long)j * ld, *w = V + (long long)(j + 1) * ld, *zj = Z + (long long)j * ld;
+  // Iterations are enqueued one ahead of the host: iteration j+1 goes to the
+  // stream before the coefficients of iteration j are read back (into one of
+  // two pinned slots), unless the residual estimate extrapolated from the
+  // last two columns says iteration j may end the cycle.  An iteration
+  // launched past the end of the cycle only writes basis columns that are
+  // not used.
+  const int nhh = (int)hh.size();
+  const size_t slot = (size_t)nhh + 1;   // coefficients, then the tensor-core error flag
+  auto launch_iter = [&](int jj) -> st_status {
+    T *uj = V + (long long)jj * ld, *w = V + (long long)(jj + 1) * ld, *zj = Z + (long long)jj * ld;
     ST_TRY(precond_T<T>(h, uj, zj));
     ST_TRY(apply_T<T>(h, zj, w));
     {
       // delayed CGS2: one dot pass of [V_0..V_{j-1}, u_j, w] against (u_j, w),
       // one update pass writing v_j and u_{j+1}
       double vb = (double)N * sizeof(T);
-      ProfScope ps(h, PROF_ARNOLDI, vb * (2.0 * (j + 2) + 2.0), 8.0 * (j + 2) * (double)N);
-      launch_multi_dot2<T>(s, hd, V, ld, j + 2, uj, w, N, scratch);
-      launch_dcgs2_update<T>(s, V, ld, j, hd, N, sc, reinterpret_cast<T *>(h->gs_coef));
+      ProfScope ps(h, PROF_ARNOLDI, vb * (2.0 * (jj + 2) + 2.0), 8.0 * (jj + 2) * (double)N);
+      launch_multi_dot2<T>(s, hd, V, ld, jj + 2, uj, w, N, scratch);
+      launch_dcgs2_update<T>(s, V, ld, jj, hd, N, sc, reinterpret_cast<T *>(h->gs_coef));
     }
-    ST_CUDA(cudaMemcpyAsync(hh.data(), hd, hh.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    double *hs = h->red_host + (size_t)(jj & 1) * slot;
+    ST_CUDA(cudaMemcpyAsync(hs, hd, nhh * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaMemcpyAsync(hs + nhh, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaEventRecord(h->arn_ev[jj & 1], s));
+    return ST_OK;
+  };
+  std::vector<double> resv(1, beta);   // residual estimate after c finished columns
+  ST_TRY(launch_iter(0));
+  int launched = 1;
+  int j = 0;
+  for (; j < m; ++j) {
+    if (launched == j + 1 && j + 1 < m) {
+      bool ahead = true;
+      if (j >= 2 && resv.size() >= (size_t)j) {
+        const double r1 = resv[j - 1], r2 = resv[j - 2];
+        ahead = r2 > 0.0 && r1 * (r1 / r2) > 2.0 * tol * beta;
+      }
+      if (ahead) {
+        ST_TRY(launch_iter(j + 1));
+        ++launched;
+      }
+    }
+    ST_CUDA(cudaEventSynchronize(h->arn_ev[j & 1]));
+    const double *hs = h->red_host + (size_t)(j & 1) * slot;
     int tc_flag = 0;
-    ST_CUDA(cudaMemcpyAsync(&tc_flag, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-    ST_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(&tc_flag, hs + nhh, sizeof(int));
     if (tc_flag) return ST_ERR_TIMEOUT;
+    std::copy(hs, hs + nhh, hh.begin());
     const double nu = hh[2 * (m + 2)], gam = hh[2 * (m + 2) + 1], sw = hh[2 * (m + 2) + 2];
     if (!std::isfinite(nu) || !std::isfinite(gam) || !std::isfinite(sw)) return ST_ERR_NAN;
     if (j == 0) {
@@ -249,11 +279,16 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
     } else {
       for (int i = 0; i < j; ++i) acol[i] = hh[2 * i];
       finish_column(j, acol.data(), nu);
+      resv.push_back(res);
       if (res <= tol * beta || nu == 0.0) { k = j; done = true; break; }
     }
     for (int i = 0; i < j; ++i) bprev[i] = hh[2 * i + 1];
     gprev = gam;
     sprev = sw;
+    if (launched == j + 1 && j + 1 < m) {
+      ST_TRY(launch_iter(j + 1));
+      ++launched;
+    }
   }
   if (!done) {
     // the last column: reorthogonalization dots of u_m alone
@@ -684,6 +719,8 @@ st_status st_destroy(st_handle *h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (void *p : h->allocs) cudaFree(p);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->arn_ev)
+    if (e) cudaEventDestroy(e);
   if (h->red_host) cudaFreeHost(h->red_host);
   delete h;
   return ST_OK;
@@ -847,6 +884,14 @@ static st_status setup_impl(st_handle *h) {
   h->t32b = dalloc<float>(h, h->Ndof, &e);
   h->d32 = dalloc<float>(h, h->Ndof, &e);
   h->hcol = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
+  // pinned host slots for the Arnoldi coefficients (two iterations in flight)
+  // and the events that mark their arrival
+  if (cudaMallocHost(&h->red_host, 2 * (size_t)(2 * (h->m + 2) + 4) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    h->red_host = nullptr;
+    return ST_ERR_OOM;
+  }
+  for (int i = 0; i < 2; ++i) ST_CUDA(cudaEventCreateWithFlags(&h->arn_ev[i], cudaEventDisableTiming));
   h->gs_coef = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
   if (e != ST_OK) return e;
   {

@@ -117,7 +117,8 @@ struct st_handle {
   float *K32[7] = {};
   double *U0 = nullptr, *L0 = nullptr, *Wq0 = nullptr;   // ionic fields at spatial qpts [Nt][Qs]
   double *red = nullptr;       // reduction scratch (device)
-  double *red_host = nullptr;  // pinned host mirror
+  double *red_host = nullptr;  // pinned host slots of the Arnoldi coefficients (two iterations)
+  cudaEvent_t arn_ev[2] = {nullptr, nullptr};   // arrival of each slot
   // Krylov
   int m = 0;
   long long ldv = 0;          // Krylov basis leading dimension (16-byte aligned rows)
