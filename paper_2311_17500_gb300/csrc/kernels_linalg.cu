@@ -7,6 +7,7 @@
 #include "st_internal.h"
 #include "dev_sync.cuh"
 #include "df.cuh"
+#include "pdl.cuh"
 
 namespace {
 
@@ -487,6 +488,8 @@ template <typename T, int P>
 __global__ void __launch_bounds__(256) ifwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in,
                                                           const T *__restrict__ tab, int nel, long long inner,
                                                           long long outer, int nruns) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
   constexpr int nq = P + 1, U = 8, RUN = kRunFwd;
   __shared__ TabRow<T, P + 1> st[RUN * nq];
   const int nin = nel + P, nout = nel * nq;
@@ -536,6 +539,8 @@ template <typename T, int P>
 __global__ void __launch_bounds__(256) ibwd_stream_kernel(T *__restrict__ out, const T *__restrict__ in,
                                                           const T *__restrict__ tab, int nel, long long inner,
                                                           long long outer, int nruns, int accumulate) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
   constexpr int nq = P + 1, UE = 4, RUN = kRunBwd;
   __shared__ TabRow<T, P + 1> st[(RUN + P) * nq];
   const int nin = nel * nq, nout = nel + P;
@@ -731,9 +736,9 @@ void launch_tiled(cudaStream_t s, T *out, const TiledTerms<T> &tt, int nin, int 
     if (OP == OP_BAND)
       band_stream_kernel<T, P><<<grid, bx, 0, s>>>(out, tt, nout, inner, outer, nruns, acc);
     else if (OP == OP_FWD)
-      ifwd_stream_kernel<T, P><<<grid, bx, 0, s>>>(out, tt.in[0], tt.tab[0], nin - P, inner, outer, nruns);
+      pdl_launch(ifwd_stream_kernel<T, P>, grid, dim3(bx), 0, s, out, tt.in[0], tt.tab[0], nin - P, inner, outer, nruns);
     else
-      ibwd_stream_kernel<T, P><<<grid, bx, 0, s>>>(out, tt.in[0], tt.tab[0], nout - P, inner, outer, nruns, acc);
+      pdl_launch(ibwd_stream_kernel<T, P>, grid, dim3(bx), 0, s, out, tt.in[0], tt.tab[0], nout - P, inner, outer, nruns, acc);
   }
 }
 
@@ -930,6 +935,8 @@ __global__ void __launch_bounds__(xband_max_threads<T, P>(), xband_min_blocks<T,
     }
     __syncthreads();
   }
+  pdl_trigger();
+  pdl_wait();   // the table and barriers above are set up before the previous kernel ends
   long long gbase = 0;   // steps issued by this block before the current segment
   for (long long blk = blockIdx.x; blk < rows * nseg; blk += gridDim.x) {
     const long long o = blk % rows;
@@ -1216,6 +1223,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *
     const bool ok = rr >= 0 && rr < ny;
     by[e] = ok ? Pair<T>::make(My[e], Dy * Ky[e]) : Pair<T>::make(0, 0);
   }
+  pdl_trigger();
+  pdl_wait();   // the band rows above are staged before the previous kernel ends
   // 1. time bands of the strip (halo columns outside the plane are zero);
   // UE elements a round, all their loads issued before any product
   constexpr int UE = 4;
@@ -1386,6 +1395,8 @@ __global__ void __launch_bounds__(256) gemm_kernel(T *__restrict__ C, const T *_
 template <typename T, int P, int U>
 __global__ void __launch_bounds__(128) tline_lu_kernel(T *__restrict__ z, const T *__restrict__ r,
                                                        const T *__restrict__ lu, int Nt, long long Ns) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
   const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (j >= Ns) return;
   constexpr int B = 2 * P + 1;
@@ -1590,6 +1601,8 @@ __global__ void __launch_bounds__(256) mdot_kernel(double *__restrict__ partial,
 // stride pattern and a fixed shuffle tree combines them (deterministic).
 __global__ void reduce_blocks_kernel(double *__restrict__ out, const double *__restrict__ partial, int nblocks,
                                      int nv) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
   int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   int lane = threadIdx.x & 31;
   if (i >= nv) return;
@@ -1664,6 +1677,8 @@ template <typename T, int G>
 __global__ void __launch_bounds__(256) mdot2_kernel(double *__restrict__ partial, const T *__restrict__ V,
                                                     long long ldv, int nv, const T *__restrict__ x1,
                                                     const T *__restrict__ x2, long long n) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
   typedef V16<T> X;
   typedef typename X::type VT;
   constexpr int W = X::W;
@@ -1750,6 +1765,8 @@ __global__ void __launch_bounds__(256) mdot2_kernel(double *__restrict__ partial
 template <typename T>
 __global__ void __launch_bounds__(256) dcgs2_coef_kernel(T *__restrict__ coef, double *__restrict__ sc,
                                                          const double *__restrict__ D, int j) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
   __shared__ double part[3][8];
   __shared__ double scal[2];
   double sa2 = 0.0, sab = 0.0, sb2 = 0.0;
@@ -1793,6 +1810,8 @@ __global__ void __launch_bounds__(256) dcgs2_coef_kernel(T *__restrict__ coef, d
 template <typename T>
 __global__ void __launch_bounds__(256) dcgs2_update_kernel(T *__restrict__ V, long long ldv, int j,
                                                            const T *__restrict__ coef, long long n) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
   typedef V16<T> X;
   typedef typename X::type VT;
   constexpr int W = X::W;
@@ -1990,9 +2009,13 @@ bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, co
   auto go = [&](auto kern, int P) {
     const int NB = sizeof(T) == 8 ? 2 : 1;
     size_t sh = (size_t)S * NB * (P + 1) * threads * (P + 1) * sizeof(float) + (size_t)S * threads * sizeof(T);
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+      attr = true;
+    }
     st_count_launch();
-    kern<<<blocks, threads, sh, s>>>(Y1, X1, bhi, blo, tab, nel, Nt, rows, seglen, err);
+    pdl_launch(kern, dim3(blocks), dim3(threads), sh, s, Y1, X1, bhi, blo, tab, nel, Nt, rows, seglen, err);
   };
   // bulk band copies need 16-byte aligned slices: Q_x a multiple of 4 floats
   const bool bulk = (nel * (p + 1)) % 4 == 0 && ((uintptr_t)bhi % 16) == 0 && (!blo || ((uintptr_t)blo % 16) == 0);
@@ -2021,7 +2044,7 @@ bool launch_kron2d(cudaStream_t s, T *y, const T *x, const T *Wt, const T *Mt, c
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr[P] = true;
     }
-    st_count_launch(); k<<<g, 256, sh, s>>>(y, x, Wt, Mt, Mx, Kx, My, Ky, nx, ny, Nt, (T)Cm, (T)Dx, (T)Dy);
+    st_count_launch(); pdl_launch(k, g, dim3(256), sh, s, y, x, Wt, Mt, Mx, Kx, My, Ky, nx, ny, Nt, (T)Cm, (T)Dx, (T)Dy);
   };
   switch (p) {
     case 1: go(kron2d_kernel<T, 1>, 1); break;
@@ -2086,10 +2109,10 @@ void launch_tline_lu_solve(cudaStream_t s, T *z, const T *r, const T *lu, int Nt
   constexpr int U = sizeof(T) == 4 ? 16 : 8;
   const unsigned blocks = (unsigned)((Ns + 127) / 128);
   switch (p) {
-    case 1: st_count_launch(); tline_lu_kernel<T, 1, U><<<blocks, 128, 0, s>>>(z, r, lu, Nt, Ns); break;
-    case 2: st_count_launch(); tline_lu_kernel<T, 2, U><<<blocks, 128, 0, s>>>(z, r, lu, Nt, Ns); break;
-    case 3: st_count_launch(); tline_lu_kernel<T, 3, U><<<blocks, 128, 0, s>>>(z, r, lu, Nt, Ns); break;
-    default: st_count_launch(); tline_lu_kernel<T, 4, U><<<blocks, 128, 0, s>>>(z, r, lu, Nt, Ns); break;
+    case 1: st_count_launch(); pdl_launch(tline_lu_kernel<T, 1, U>, dim3(blocks), dim3(128), 0, s, z, r, lu, Nt, Ns); break;
+    case 2: st_count_launch(); pdl_launch(tline_lu_kernel<T, 2, U>, dim3(blocks), dim3(128), 0, s, z, r, lu, Nt, Ns); break;
+    case 3: st_count_launch(); pdl_launch(tline_lu_kernel<T, 3, U>, dim3(blocks), dim3(128), 0, s, z, r, lu, Nt, Ns); break;
+    default: st_count_launch(); pdl_launch(tline_lu_kernel<T, 4, U>, dim3(blocks), dim3(128), 0, s, z, r, lu, Nt, Ns); break;
   }
 }
 
@@ -2128,16 +2151,16 @@ void launch_multi_dot2(cudaStream_t s, double *out, const T *V, long long ldv, i
   long long cap = std::max<long long>(1, n / (V16<T>::W * 256 * 2));
   int bx = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(want, cap), kDotBlocks));
   dim3 grid(bx, groups);
-  st_count_launch(); mdot2_kernel<T, G><<<grid, 256, 0, s>>>(scratch, V, ldv, nv, x1, x2, n);
-  st_count_launch(); reduce_blocks_kernel<<<(2 * nv + 3) / 4, 128, 0, s>>>(out, scratch, bx, 2 * nv);
+  st_count_launch(); pdl_launch(mdot2_kernel<T, G>, grid, dim3(256), 0, s, scratch, V, ldv, nv, x1, x2, n);
+  st_count_launch(); pdl_launch(reduce_blocks_kernel, dim3((2 * nv + 3) / 4), dim3(128), 0, s, out, (const double *)scratch, bx, 2 * nv);
 }
 
 template <typename T>
 void launch_dcgs2_update(cudaStream_t s, T *V, long long ldv, int j, const double *D, long long n, double *sc,
                          T *coef) {
   long long nvec = n / V16<T>::W;
-  st_count_launch(); dcgs2_coef_kernel<T><<<1, 256, 0, s>>>(coef, sc, D, j);
-  st_count_launch(); dcgs2_update_kernel<T><<<grid_for(std::max<long long>(nvec, 1)), kThreads, 0, s>>>(V, ldv, j, coef, n);
+  st_count_launch(); pdl_launch(dcgs2_coef_kernel<T>, dim3(1), dim3(256), 0, s, coef, sc, D, j);
+  st_count_launch(); pdl_launch(dcgs2_update_kernel<T>, dim3(grid_for(std::max<long long>(nvec, 1))), dim3(kThreads), 0, s, V, ldv, j, (const T *)coef, n);
 }
 
 template <typename T>
@@ -2149,6 +2172,8 @@ void launch_scale_copy(cudaStream_t s, T *y, const T *x, double alpha, long long
 // one warp per row, no index division.
 __global__ void pad_rows_kernel(float *__restrict__ out, const float *__restrict__ in, long long rows, long long n,
                                 long long stride) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
   const int lane = threadIdx.x & 31;
   const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -2161,7 +2186,7 @@ __global__ void pad_rows_kernel(float *__restrict__ out, const float *__restrict
 
 void launch_pad_rows(cudaStream_t s, float *out, const float *in, long long rows, long long n, long long stride) {
   long long blocks = std::min<long long>((rows + 7) / 8, 152LL * 32);
-  st_count_launch(); pad_rows_kernel<<<(unsigned)std::max<long long>(blocks, 1), 256, 0, s>>>(out, in, rows, n, stride);
+  st_count_launch(); pdl_launch(pad_rows_kernel, dim3((unsigned)std::max<long long>(blocks, 1)), dim3(256), 0, s, out, in, rows, n, stride);
 }
 
 void launch_axpby64(cudaStream_t s, double *y, const double *x, double a, double b, long long n) {

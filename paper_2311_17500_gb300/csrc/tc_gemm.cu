@@ -32,6 +32,7 @@
 #include <cudaTypedefs.h>
 #include "st_internal.h"
 #include "dev_sync.cuh"
+#include "pdl.cuh"
 
 namespace {
 
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(256) tc_xform_tma_kernel(const __grid_constant
   __shared__ uint32_t tmem_slot;
   __shared__ int fail;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  pdl_trigger();
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
                  "r"(x.ncols_tmem)
@@ -172,6 +174,7 @@ __global__ void __launch_bounds__(256) tc_xform_tma_kernel(const __grid_constant
               "r"(sB + (uint32_t)c * bbytes_chunk),
           "l"((uint64_t)&tmB), "r"(c * kTcKC), "r"(0), "r"(smem_u32(&bfull))
           : "memory");
+    pdl_wait();   // X is written by the previous kernel (M above is constant)
     for (long long q = 0; q < njobs; ++q) {
       const int st = (int)(q % S);
       const long long u = q / S;
@@ -225,6 +228,7 @@ __global__ void __launch_bounds__(256) tc_xform_tma_kernel(const __grid_constant
     }
   } else if (warp >= 4) {
     // ---- epilogue: warp w reads TMEM lanes 32 (w - 4) .. +31
+    pdl_wait();   // the output may still be read by the previous kernel
     const int lw = warp - 4;
     for (long long i = 0; i < my_tiles; ++i) {
       const int acc = (int)(i & 1);
@@ -423,7 +427,7 @@ st_status launch_tc_xform(cudaStream_t s, float *out, const float *X, long long 
     x.ncols_tmem = tc_ncols(Npad, 2);
     int grid = (int)std::min<long long>(ntiles, 152);
     st_count_launch();
-    tc_xform_tma_kernel<S><<<grid, 256, need_tma, s>>>(tmX, tmB, x);
+    ST_CUDA(pdl_launch(tc_xform_tma_kernel<S>, dim3(grid), dim3(256), need_tma, s, tmX, tmB, x));
     ST_CUDA(cudaGetLastError());
     return ST_OK;
   }
