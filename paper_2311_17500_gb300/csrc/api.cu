@@ -407,7 +407,9 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   // --- Kronecker part
   const bool plane2 = h->d == 2;
   ProfScope *pk = new ProfScope(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_KRON, vec * (h->d == 1 ? 7 : plane2 ? 2 : 19));
-  if (plane2 && launch_kron2d<T>(s, y, x, P::Wt(h), P::Mt(h), P::Mb(h, 0), P::Kb(h, 0),
+  // (FP64: x is split into double-float pairs in a Kronecker work buffer,
+  // unused on this path)
+  if (plane2 && launch_kron2d<T>(s, y, x, P::K(h, 0), P::Wt(h), P::Mt(h), P::Mb(h, 0), P::Kb(h, 0),
                                  P::Mb(h, 1), P::Kb(h, 1), (int)nx, (int)ny, (int)Nt, p, D.C_m, D.D[0], D.D[1])) {
     delete pk;
     pk = nullptr;

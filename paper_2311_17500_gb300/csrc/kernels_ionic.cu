@@ -482,21 +482,73 @@ __global__ void d2df_kernel(float2 *__restrict__ out, const double *__restrict__
 // Eq. tildeS added to the reaction band) in double-float arithmetic on the
 // (high, low) pairs; Tr and Cq come split into pairs.
 template <int RMAX>
-__global__ void su_band_update_kernel(float *__restrict__ bhi, float *__restrict__ blo,
-                                      const float2 *__restrict__ Tr, const float2 *__restrict__ Cq, int r0, int R,
-                                      long long Mrows, long long Qs) {
-  // blockIdx.y strides over the band rows m, x over the spatial points q
-  for (long long m = blockIdx.y; m < Mrows; m += gridDim.y)
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Qs; q += (long long)gridDim.x * blockDim.x) {
-    const long long idx = m * Qs + q;
-    df v = {bhi[idx], blo[idx]};
+__global__ void __launch_bounds__(256) su_band_update_kernel(float *__restrict__ bhi, float *__restrict__ blo,
+                                                             const float2 *__restrict__ Tr,
+                                                             const float2 *__restrict__ Cq, int r0, int R,
+                                                             long long Mrows, long long Qs) {
+  // thread = 4 consecutive spatial points q (their rank coefficients stay in
+  // registers), blockIdx.y strides over the band rows m, two rows at a time
+  const long long q0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * 4;
+  if (q0 >= Qs) return;
+  const int nr = min(RMAX, R - r0);
+  const bool vec = (Qs % 4) == 0;   // rows start on 16-byte boundaries
+  const int nu = (int)min(4LL, Qs - q0);
+  df c[RMAX][4];
 #pragma unroll
-    for (int rr = 0; rr < RMAX; ++rr) {
-      const int r = r0 + rr;
-      if (r < R) v = df_fma(df_from2(__ldg(Tr + (long long)r * Mrows + m)), df_from2(__ldg(Cq + (long long)r * Qs + q)), v);
+  for (int rr = 0; rr < RMAX; ++rr)
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      c[rr][u] = (rr < nr && u < nu) ? df_from2(Cq[(long long)(r0 + rr) * Qs + q0 + u]) : df{0.f, 0.f};
+  auto update = [&](long long m, float (&h)[4], float (&l)[4]) {
+    df t[RMAX];
+#pragma unroll
+    for (int rr = 0; rr < RMAX; ++rr)
+      t[rr] = rr < nr ? df_from2(__ldg(Tr + (long long)(r0 + rr) * Mrows + m)) : df{0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      df v = {h[u], l[u]};
+#pragma unroll
+      for (int rr = 0; rr < RMAX; ++rr)
+        if (rr < nr) v = df_fma(t[rr], c[rr][u], v);
+      h[u] = v.hi;
+      l[u] = v.lo;
     }
-    bhi[idx] = v.hi;
-    blo[idx] = v.lo;
+  };
+  auto load = [&](long long idx, float (&h)[4], float (&l)[4]) {
+    if (vec) {
+      const float4 a = *reinterpret_cast<const float4 *>(bhi + idx), b = *reinterpret_cast<const float4 *>(blo + idx);
+      h[0] = a.x; h[1] = a.y; h[2] = a.z; h[3] = a.w;
+      l[0] = b.x; l[1] = b.y; l[2] = b.z; l[3] = b.w;
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        h[u] = u < nu ? bhi[idx + u] : 0.f;
+        l[u] = u < nu ? blo[idx + u] : 0.f;
+      }
+    }
+  };
+  auto store = [&](long long idx, const float (&h)[4], const float (&l)[4]) {
+    if (vec) {
+      *reinterpret_cast<float4 *>(bhi + idx) = make_float4(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<float4 *>(blo + idx) = make_float4(l[0], l[1], l[2], l[3]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (u < nu) { bhi[idx + u] = h[u]; blo[idx + u] = l[u]; }
+    }
+  };
+  const long long step = gridDim.y;
+  for (long long m = blockIdx.y; m < Mrows; m += 2 * step) {
+    const long long m2 = m + step;
+    float h0[4], l0[4], h1[4], l1[4];
+    load(m * Qs + q0, h0, l0);
+    if (m2 < Mrows) load(m2 * Qs + q0, h1, l1);
+    update(m, h0, l0);
+    store(m * Qs + q0, h0, l0);
+    if (m2 < Mrows) {
+      update(m2, h1, l1);
+      store(m2 * Qs + q0, h1, l1);
+    }
   }
 }
 
@@ -933,13 +985,18 @@ st_status su_band_add(st_handle *h) {
   float2 *Tr2 = h->Tr2;
   st_count_launch(); d2df_kernel<<<grid_for((long long)R * h->Qs), 256, 0, s>>>(Cq2, Cq, (long long)R * h->Qs);
   st_count_launch(); d2df_kernel<<<grid_for((long long)R * Mrows), 256, 0, s>>>(Tr2, h->Tr, (long long)R * Mrows);
-  const dim3 g2((unsigned)std::min<long long>((h->Qs + 255) / 256, 64), (unsigned)std::min<long long>(Mrows, 128));
+  // thread = 4 spatial points; about 8 blocks per SM in all
+  const long long gx = (h->Qs + 1023) / 1024;
+  const dim3 g2((unsigned)gx, (unsigned)std::max<long long>(1, std::min<long long>(Mrows, (152LL * 8 + gx - 1) / gx)));
   (void)total;
-  for (int r0 = 0; r0 < R; r0 += 16) {
-    if (R - r0 <= 8) {
-      st_count_launch(); su_band_update_kernel<8><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+  for (int r0 = 0; r0 < R; r0 += 8) {
+    const int left = R - r0;
+    if (left <= 2) {
+      st_count_launch(); su_band_update_kernel<2><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+    } else if (left <= 4) {
+      st_count_launch(); su_band_update_kernel<4><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
     } else {
-      st_count_launch(); su_band_update_kernel<16><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+      st_count_launch(); su_band_update_kernel<8><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
     }
   }
   ST_CUDA(cudaGetLastError());

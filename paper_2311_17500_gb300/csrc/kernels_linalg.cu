@@ -1173,17 +1173,39 @@ __device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
       : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
   return d;
 }
-__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c) {
-  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
-}
+// FP64 pairs are computed in double-float arithmetic (GB300's FP64 rate is
+// 1/64 of FP32): a pair of double-float values and two df multiply-adds.
+struct df2 {
+  df x, y;
+};
+__device__ __forceinline__ df2 pfma(df2 a, df2 b, df2 c) { return {df_fma(a.x, b.x, c.x), df_fma(a.y, b.y, c.y)}; }
+
+// Pair<T>: the pair type of the Kronecker kernel, its compute type ct and
+// the conversions and scalar operations in ct.
 template <typename T> struct Pair;
 template <> struct Pair<float> {
   typedef float2 type;
+  typedef float ct;
+  typedef float src;   // x as read by the Kronecker kernel
+  static __device__ __forceinline__ float load(float v) { return v; }
   static __device__ __forceinline__ float2 make(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ float from(float v) { return v; }
+  static __device__ __forceinline__ float to(float v) { return v; }
+  static __device__ __forceinline__ float mul(float a, float b) { return a * b; }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return fmaf(a, b, c); }
+  static __device__ __forceinline__ float add(float a, float b) { return a + b; }
 };
 template <> struct Pair<double> {
-  typedef double2 type;
-  static __device__ __forceinline__ double2 make(double a, double b) { return make_double2(a, b); }
+  typedef df2 type;
+  typedef df ct;
+  typedef float2 src;   // x pre-split into double-float pairs (no FP64 work per read)
+  static __device__ __forceinline__ df load(float2 v) { return {v.x, v.y}; }
+  static __device__ __forceinline__ df2 make(df a, df b) { return {a, b}; }
+  static __device__ __forceinline__ df from(double v) { return df_from(v); }
+  static __device__ __forceinline__ double to(df v) { return df_to(v); }
+  static __device__ __forceinline__ df mul(df a, df b) { return df_mul(a, b); }
+  static __device__ __forceinline__ df fma(df a, df b, df c) { return df_fma(a, b, c); }
+  static __device__ __forceinline__ df add(df a, df b) { return df_add(a, b); }
 };
 
 // Kronecker part of the operator for d = 2 (Sec. 3.1.1),
@@ -1199,12 +1221,16 @@ template <> struct Pair<double> {
 // Every product of two bands' pairs is one paired multiply-add.  Bands
 // [i][k] = A(i, i-P+k).  Shared memory: ny (32 + 2P + 2P + 1) pairs.
 template <typename T, int P>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *__restrict__ y, const T *__restrict__ x,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *__restrict__ y, const typename Pair<T>::src *__restrict__ x,
                                                      const T *__restrict__ Wt, const T *__restrict__ Mt,
                                                      const T *__restrict__ Mx, const T *__restrict__ Kx,
                                                      const T *__restrict__ My, const T *__restrict__ Ky, int nx, int ny,
                                                      int Nt, T Cm, T Dx, T Dy) {
-  typedef typename Pair<T>::type T2;
+  typedef Pair<T> PT;
+  typedef typename PT::type T2;
+  typedef typename PT::ct CT;
+  const CT z0 = PT::from(T(0));
+  const T2 zz = PT::make(z0, z0);
   constexpr int B = 2 * P + 1, SW = 32, HW = SW + 2 * P;
   extern __shared__ __align__(16) unsigned char k2_raw[];
   T2 *S = reinterpret_cast<T2 *>(k2_raw);   // [ny][HW]: (xW, xM); after the x pass (r1, r2) in columns P..P+SW-1
@@ -1217,11 +1243,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *
   T2 tw[B];
 #pragma unroll
   for (int k = 0; k < B; ++k)
-    tw[k] = (k >= klo && k <= khi) ? Pair<T>::make(Wt[(size_t)t * B + k], Mt[(size_t)t * B + k]) : Pair<T>::make(0, 0);
+    tw[k] = (k >= klo && k <= khi) ? PT::make(PT::from(Wt[(size_t)t * B + k]), PT::from(Mt[(size_t)t * B + k])) : zz;
   for (int e = threadIdx.x; e < ny * B; e += blockDim.x) {
     const int r = e / B, k = e - r * B, rr = r - P + k;
     const bool ok = rr >= 0 && rr < ny;
-    by[e] = ok ? Pair<T>::make(My[e], Dy * Ky[e]) : Pair<T>::make(0, 0);
+    by[e] = ok ? PT::make(PT::from(My[e]), PT::from(Dy * Ky[e])) : zz;
   }
   pdl_trigger();
   pdl_wait();   // the band rows above are staged before the previous kernel ends
@@ -1231,7 +1257,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *
   const long long pofs = (long long)(t - P) * Ns;   // offset of plane t-P (negative near the start)
   const int nel = ny * HW;
   for (int e0 = threadIdx.x; e0 < nel; e0 += UE * blockDim.x) {
-    T v[UE][B];
+    typename PT::src v[UE][B];
 #pragma unroll
     for (int u = 0; u < UE; ++u) {
       const int e = e0 + u * blockDim.x;
@@ -1239,14 +1265,18 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *
       const bool ok = e < nel && cx >= 0 && cx < nx;
       const long long o = pofs + (long long)r * nx + cx;
 #pragma unroll
-      for (int k = 0; k < B; ++k) v[u][k] = (ok && k >= klo && k <= khi) ? __ldg(x + (o + (long long)k * Ns)) : T(0);
+      for (int k = 0; k < B; ++k)
+        v[u][k] = (ok && k >= klo && k <= khi) ? __ldg(x + (o + (long long)k * Ns)) : typename PT::src{};
     }
 #pragma unroll
     for (int u = 0; u < UE; ++u) {
       const int e = e0 + u * blockDim.x;
-      T2 acc = Pair<T>::make(0, 0);
+      T2 acc = zz;
 #pragma unroll
-      for (int k = 0; k < B; ++k) acc = pfma(tw[k], Pair<T>::make(v[u][k], v[u][k]), acc);
+      for (int k = 0; k < B; ++k) {
+        const CT cv = PT::load(v[u][k]);
+        acc = pfma(tw[k], PT::make(cv, cv), acc);
+      }
       if (e < nel) S[e] = acc;
     }
   }
@@ -1254,26 +1284,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *
   // 2. x bands in place: all reads of a row precede the writes of its centre
   const int c = lane, cx = cx0 + c;
   T2 mx[B];
-  T kx[B];
+  CT kx[B];
 #pragma unroll
   for (int k = 0; k < B; ++k) {
     const bool ok = cx < nx && cx - P + k >= 0 && cx - P + k < nx;
-    const T m = ok ? Mx[(size_t)cx * B + k] : T(0);
-    mx[k] = Pair<T>::make(m, m);
-    kx[k] = ok ? Kx[(size_t)cx * B + k] : T(0);
+    const CT m = PT::from(ok ? Mx[(size_t)cx * B + k] : T(0));
+    mx[k] = PT::make(m, m);
+    kx[k] = PT::from(ok ? Kx[(size_t)cx * B + k] : T(0));
   }
+  const CT cm = PT::from(Cm), dx = PT::from(Dx);
   for (int r = rg; r < ny; r += nrg) {
     T2 *row = S + (size_t)r * HW + c;
-    T2 a = Pair<T>::make(0, 0);   // (M_x xW, M_x xM)
-    T b = T(0);                   // K_x xM
+    T2 a = zz;   // (M_x xW, M_x xM)
+    CT b = z0;   // K_x xM
 #pragma unroll
     for (int k = 0; k < B; ++k) {
       const T2 v = row[k];
       a = pfma(mx[k], v, a);
-      b = fma(kx[k], v.y, b);
+      b = PT::fma(kx[k], v.y, b);
     }
     __syncwarp();
-    row[P] = Pair<T>::make(Cm * a.x + Dx * b, a.y);
+    row[P] = PT::make(PT::fma(cm, a.x, PT::mul(dx, b)), a.y);
     __syncwarp();
   }
   __syncthreads();
@@ -1287,7 +1318,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *
 #pragma unroll
   for (int k = 0; k < B - 1; ++k) {
     const int rr = ra - P + k;
-    w[k + 1] = (rr >= 0 && rr < ny) ? R[(size_t)rr * HW] : Pair<T>::make(0, 0);
+    w[k + 1] = (rr >= 0 && rr < ny) ? R[(size_t)rr * HW] : zz;
   }
   T *yo = y + (long long)t * Ns + (long long)ra * nx + cx;
   for (int r0 = ra; r0 < rb; r0 += B) {
@@ -1297,12 +1328,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) kron2d_kernel(T *
       if (r >= rb) break;
 #pragma unroll
       for (int k = 0; k < B - 1; ++k) w[k] = w[k + 1];
-      w[B - 1] = r + P < ny ? R[(size_t)(r + P) * HW] : Pair<T>::make(0, 0);
+      w[B - 1] = r + P < ny ? R[(size_t)(r + P) * HW] : zz;
       const T2 *br = by + (size_t)r * B;
-      T2 acc = Pair<T>::make(0, 0);
+      T2 acc = zz;
 #pragma unroll
       for (int k = 0; k < B; ++k) acc = pfma(br[k], w[k], acc);
-      *yo = acc.x + acc.y;
+      *yo = PT::to(PT::add(acc.x, acc.y));
       yo += nx;
     }
   }
@@ -2032,19 +2063,42 @@ bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, co
   return true;
 }
 
+// x split into double-float pairs for the FP64 instance of the Kronecker
+// kernel (one conversion per value instead of one per read).
+__global__ void split_df_kernel(float2 *__restrict__ out, const double *__restrict__ in, long long n) {
+  pdl_trigger();
+  pdl_wait();   // x is written by the previous kernel, out may still be read by it
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const df v = df_from(in[i]);
+    out[i] = make_float2(v.hi, v.lo);
+  }
+}
+
 template <typename T>
-bool launch_kron2d(cudaStream_t s, T *y, const T *x, const T *Wt, const T *Mt, const T *Mx, const T *Kx, const T *My,
-                   const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx, double Dy) {
+bool launch_kron2d(cudaStream_t s, T *y, const T *x, void *split, const T *Wt, const T *Mt, const T *Mx,
+                   const T *Kx, const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx,
+                   double Dy) {
   const size_t sh = (size_t)ny * ((32 + 2 * p) + (2 * p + 1)) * 2 * sizeof(T);
   if (sh > 200 * 1024 || p > 4 || Nt > 65535) return false;
   dim3 g((unsigned)((nx + 31) / 32), (unsigned)Nt);
+  const typename Pair<T>::src *xs;
+  if constexpr (sizeof(T) == 8) {
+    const long long n = (long long)Nt * nx * ny;
+    float2 *sp = reinterpret_cast<float2 *>(split);
+    st_count_launch();
+    pdl_launch(split_df_kernel, dim3((unsigned)std::min<long long>((n + 255) / 256, 152LL * 16)), dim3(256), 0, s, sp,
+               reinterpret_cast<const double *>(x), n);
+    xs = sp;
+  } else {
+    xs = x;
+  }
   auto go = [&](auto k, int P) {
     static bool attr[5] = {false, false, false, false, false};
     if (!attr[P]) {
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
       attr[P] = true;
     }
-    st_count_launch(); pdl_launch(k, g, dim3(256), sh, s, y, x, Wt, Mt, Mx, Kx, My, Ky, nx, ny, Nt, (T)Cm, (T)Dx, (T)Dy);
+    st_count_launch(); pdl_launch(k, g, dim3(256), sh, s, y, xs, Wt, Mt, Mx, Kx, My, Ky, nx, ny, Nt, (T)Cm, (T)Dx, (T)Dy);
   };
   switch (p) {
     case 1: go(kron2d_kernel<T, 1>, 1); break;
@@ -2263,8 +2317,8 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
                                      long long, bool);                                                \
   template void launch_qband_apply<T>(cudaStream_t, T *, const T *, const float *, const float *, int, \
                                       long long, int);                                                  \
-  template bool launch_kron2d<T>(cudaStream_t, T *, const T *, const T *, const T *, const T *, const T *, \
-                                 const T *, const T *, int, int, int, int, double, double,              \
+  template bool launch_kron2d<T>(cudaStream_t, T *, const T *, void *, const T *, const T *, const T *,  \
+                                 const T *, const T *, const T *, int, int, int, int, double, double,   \
                                  double);                                                              \
   template bool launch_xband_fused<T>(cudaStream_t, T *, const T *, const float *, const float *,       \
                                       const T *, int, int, long long, int, int *);                      \

@@ -194,8 +194,11 @@ void launch_qband_apply(cudaStream_t s, T *z, const T *x, const float *bhi, cons
 // Kronecker part of the operator for d = 2 (time pass into xW, xM, then the
 // plane pass into y); false when a plane column does not fit shared memory.
 template <typename T>
-bool launch_kron2d(cudaStream_t s, T *y, const T *x, const T *Wt, const T *Mt, const T *Mx, const T *Kx,
-                   const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx, double Dy);
+// 2D Kronecker part; for FP64, `split` is scratch of N_t n_y n_x float pairs
+// (x split into double-float pairs), unused for FP32.
+bool launch_kron2d(cudaStream_t s, T *y, const T *x, void *split, const T *Wt, const T *Mt, const T *Mx,
+                   const T *Kx, const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx,
+                   double Dy);
 // Largest block (threads) of the fused x pass for this element size and degree.
 int xband_fused_limit(size_t elem, int p);
 template <typename T>
