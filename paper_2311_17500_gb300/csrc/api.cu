@@ -404,12 +404,20 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   long long nx = h->n[0], ny = h->n[1], nz = h->n[2], Nt = h->Nt, Ns = h->Ns;
   const double sz = sizeof(T);
   const double vec = (double)h->Ndof * sz;
+  // FP64 with d >= 2: x as double-float pairs (in the second Gauss-point work
+  // buffer, which the reaction part below only overwrites after its first
+  // pass), read by the 2D Kronecker kernel and the first interpolation pass
+  const bool fused = h->d >= 2 && (h->nel[0] + p + 31) / 32 * 32 <= xband_fused_limit(sizeof(T), p);
+  float2 *xs = nullptr;
+  if (sizeof(T) == 8 && (h->d == 2 || fused)) {
+    xs = reinterpret_cast<float2 *>(h->W64[1]);
+    ProfScope ps(h, PROF_APPLY64, 3.0 * (double)h->Ndof * sizeof(double));
+    launch_split_df(s, xs, reinterpret_cast<const double *>(x), h->Ndof);
+  }
   // --- Kronecker part
   const bool plane2 = h->d == 2;
   ProfScope *pk = new ProfScope(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_KRON, vec * (h->d == 1 ? 7 : plane2 ? 2 : 19));
-  // (FP64: x is split into double-float pairs in a Kronecker work buffer,
-  // unused on this path)
-  if (plane2 && launch_kron2d<T>(s, y, x, P::K(h, 0), P::Wt(h), P::Mt(h), P::Mb(h, 0), P::Kb(h, 0),
+  if (plane2 && launch_kron2d<T>(s, y, x, xs, P::Wt(h), P::Mt(h), P::Mb(h, 0), P::Kb(h, 0),
                                  P::Mb(h, 1), P::Kb(h, 1), (int)nx, (int)ny, (int)Nt, p, D.C_m, D.D[0], D.D[1])) {
     delete pk;
     pk = nullptr;
@@ -468,7 +476,50 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
   long long nd[3] = {h->n[0], h->n[1], h->n[2]};
   const T *cur = x;
   int ping = 0;
-  if (h->d >= 2 && (h->nel[0] + p + 31) / 32 * 32 <= xband_fused_limit(sizeof(T), p)) {
+  if (fused && sizeof(T) == 8) {
+    // the FP64 operator on double-float pairs from the split x to the last
+    // backward pass (no FP64 instruction per value); passes as below
+    const float2 *cur2 = xs;
+    for (int l = h->d - 1; l >= 1; --l) {
+      long long inner = 1, outer = Nt;
+      for (int k = 0; k < l; ++k) inner *= nd[k];
+      for (int k = l + 1; k < h->d; ++k) outer *= qd[k];
+      float2 *out2 = reinterpret_cast<float2 *>(P::W(h, ping));
+      ProfScope ps(h, PROF_APPLY64, sz * (double)outer * inner * (h->n[l] + (double)h->Q[l]));
+      launch_interp_fwd_pairs(s, out2, cur2, h->Bq2[l], h->nel[l], p, inner, outer);
+      cur2 = out2;
+      ping ^= 1;
+    }
+    long long rows = 1;
+    for (int k = 1; k < h->d; ++k) rows *= qd[k];
+    float2 *Y2 = reinterpret_cast<float2 *>(P::W(h, ping));
+    {
+      ProfScope ps(h, PROF_APPLY64, sz * ((double)(p + 1) * h->NtQs + 2.0 * (double)Nt * rows * nx));
+      launch_xband_fused<float2>(s, Y2, cur2, h->band32, h->band_lo, h->Bq2[0], h->nel[0], (int)Nt, rows, p,
+                                 h->tc_err);
+    }
+    cur2 = Y2;
+    ping ^= 1;
+    for (int l = 1; l < h->d; ++l) {
+      long long inner = 1, outer = Nt;
+      for (int k = 0; k < l; ++k) inner *= nd[k];
+      for (int k = l + 1; k < h->d; ++k) outer *= qd[k];
+      const bool last = l == h->d - 1;
+      ProfScope ps(h, PROF_APPLY64, sz * (double)outer * inner * (h->n[l] * (last ? 2.0 : 1.0) + (double)h->Q[l]));
+      if (last) {
+        launch_interp_bwd_pairs<double>(s, reinterpret_cast<double *>(y), cur2, h->Bq2[l], h->nel[l], p, inner,
+                                        outer, true);
+      } else {
+        float2 *out2 = reinterpret_cast<float2 *>(P::W(h, ping));
+        launch_interp_bwd_pairs<float2>(s, out2, cur2, h->Bq2[l], h->nel[l], p, inner, outer, false);
+        cur2 = out2;
+        ping ^= 1;
+      }
+    }
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+  }
+  if (fused) {
     // the other axes to their Gauss points (last axis first), x kept in
     // coefficients; then the fused x pass; then the other axes back, the
     // last one accumulated onto the Kronecker part

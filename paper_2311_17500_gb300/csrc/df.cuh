@@ -92,5 +92,8 @@ template <> __device__ __forceinline__ df ct_from<df>(float v) { return {v, 0.f}
 template <typename CT> __device__ __forceinline__ CT ct_from(double v);
 template <> __device__ __forceinline__ float ct_from<float>(double v) { return (float)v; }
 template <> __device__ __forceinline__ df ct_from<df>(double v) { return df_from(v); }
+template <typename CT> __device__ __forceinline__ CT ct_from(float2 v);
+template <> __device__ __forceinline__ df ct_from<df>(float2 v) { return {v.x, v.y}; }
 __device__ __forceinline__ void ct_store(float *p, float v) { *p = v; }
 __device__ __forceinline__ void ct_store(double *p, df v) { *p = df_to(v); }
+__device__ __forceinline__ void ct_store(float2 *p, df v) { *p = make_float2(v.hi, v.lo); }

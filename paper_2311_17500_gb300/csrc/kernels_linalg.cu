@@ -603,6 +603,128 @@ __global__ void __launch_bounds__(256) ibwd_stream_kernel(T *__restrict__ out, c
   }
 }
 
+// The two passes above for the FP64 operator on double-float pairs: input
+// and (forward) output as (high, low) float pairs, arithmetic in double-float,
+// so no FP64 instruction is spent per value.  The backward pass writes pairs,
+// or FP64 (optionally accumulated) for the last axis.
+__device__ __forceinline__ df ld_df(const float2 *p) { const float2 v = *p; return {v.x, v.y}; }
+__device__ __forceinline__ df ld_df(const double *p) { return df_from(*p); }
+
+template <int P>
+__global__ void __launch_bounds__(256) ifwd_pairs_kernel(float2 *__restrict__ out, const float2 *__restrict__ in,
+                                                         const float2 *__restrict__ tab, int nel, long long inner,
+                                                         long long outer, int nruns) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
+  constexpr int nq = P + 1, U = 8, RUN = kRunFwd;
+  __shared__ TabRow<float2, P + 1> st[RUN * nq];
+  const int nin = nel + P, nout = nel * nq;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (long long yr = blockIdx.y; yr < outer * nruns; yr += gridDim.y) {
+    const long long o = yr / nruns;
+    const int e0 = (int)(yr - o * nruns) * RUN, e1 = min(nel, e0 + RUN);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (e1 - e0) * nq * (P + 1); i += blockDim.x)
+      st[i / (P + 1)].v[i % (P + 1)] = __ldg(tab + (size_t)e0 * nq * (P + 1) + i);
+    __syncthreads();
+    if (c >= inner) continue;
+    const float2 *src = in + o * nin * inner + c;
+    float2 *dst = out + o * nout * inner + c;
+    df w[P + 1];
+#pragma unroll
+    for (int a = 0; a < P; ++a) w[a + 1] = ld_df(src + (long long)(e0 + a) * inner);
+    for (int eb = e0; eb < e1; eb += U) {
+      df nx[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) nx[u] = (eb + u < e1) ? ld_df(src + (long long)(eb + u + P) * inner) : df{0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int e = eb + u;
+        if (e >= e1) break;
+#pragma unroll
+        for (int a = 0; a < P; ++a) w[a] = w[a + 1];
+        w[P] = nx[u];
+#pragma unroll
+        for (int q = 0; q < nq; ++q) {
+          const TabRow<float2, P + 1> tb = st[(e - e0) * nq + q];
+          df sacc = {0.f, 0.f};
+#pragma unroll
+          for (int a = 0; a <= P; ++a) sacc = df_fma(df{tb.v[a].x, tb.v[a].y}, w[a], sacc);
+          dst[((long long)e * nq + q) * inner] = make_float2(sacc.hi, sacc.lo);
+        }
+      }
+    }
+  }
+}
+
+template <int P, typename TO>
+__global__ void __launch_bounds__(256) ibwd_pairs_kernel(TO *__restrict__ out, const float2 *__restrict__ in,
+                                                         const float2 *__restrict__ tab, int nel, long long inner,
+                                                         long long outer, int nruns, int accumulate) {
+  pdl_trigger();
+  pdl_wait();   // inputs and outputs are shared with the previous kernel
+  constexpr int nq = P + 1, UE = 4, RUN = kRunBwd;
+  __shared__ TabRow<float2, P + 1> st[(RUN + P) * nq];
+  const int nin = nel * nq, nout = nel + P;
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const df zero = {0.f, 0.f};
+  for (long long yr = blockIdx.y; yr < outer * nruns; yr += gridDim.y) {
+    const long long o = yr / nruns;
+    const int i0 = (int)(yr - o * nruns) * RUN, i1 = min(nout, i0 + RUN);
+    const int ea = max(0, i0 - P), eb = min(nel - 1, i1 - 1);
+    __syncthreads();
+    for (int i = threadIdx.x; i < (eb - ea + 1) * nq * (P + 1); i += blockDim.x)
+      st[i / (P + 1)].v[i % (P + 1)] = __ldg(tab + (size_t)ea * nq * (P + 1) + i);
+    __syncthreads();
+    if (c >= inner) continue;
+    const float2 *src = in + o * nin * inner + c;
+    TO *dst = out + o * nout * inner + c;
+    df acc[P + 1];   // acc[a]: coefficient e + a while element e is processed
+#pragma unroll
+    for (int a = 0; a <= P; ++a) acc[a] = zero;
+    for (int e0 = ea; e0 <= eb; e0 += UE) {
+      df z[UE][nq], yo[UE];
+#pragma unroll
+      for (int u = 0; u < UE; ++u) {
+        const bool ok = e0 + u <= eb;
+#pragma unroll
+        for (int q = 0; q < nq; ++q) z[u][q] = ok ? ld_df(src + ((long long)(e0 + u) * nq + q) * inner) : zero;
+        yo[u] = (accumulate && ok && e0 + u >= i0) ? ld_df(dst + (long long)(e0 + u) * inner) : zero;
+      }
+#pragma unroll
+      for (int u = 0; u < UE; ++u) {
+        const int e = e0 + u;
+        if (e > eb) break;
+        TabRow<float2, P + 1> r[nq];
+#pragma unroll
+        for (int q = 0; q < nq; ++q) r[q] = st[(e - ea) * nq + q];
+#pragma unroll
+        for (int a = 0; a <= P; ++a) {
+          df sacc = zero;
+#pragma unroll
+          for (int q = 0; q < nq; ++q) sacc = df_fma(df{r[q].v[a].x, r[q].v[a].y}, z[u][q], sacc);
+          acc[a] = df_add(acc[a], sacc);
+        }
+        // coefficient e receives nothing from later elements
+        if (e >= i0) ct_store(dst + (long long)e * inner, accumulate ? df_add(yo[u], acc[0]) : acc[0]);
+#pragma unroll
+        for (int a = 0; a < P; ++a) acc[a] = acc[a + 1];
+        acc[P] = zero;
+      }
+    }
+    // coefficients eb+1 .. i1-1 (only past the last element); acc[0] is eb+1
+    for (int i = eb + 1; i < i1; ++i) {
+      if (i >= i0) {
+        TO *p = dst + (long long)i * inner;
+        ct_store(p, accumulate ? df_add(ld_df(p), acc[0]) : acc[0]);
+      }
+#pragma unroll
+      for (int a = 0; a < P; ++a) acc[a] = acc[a + 1];
+      acc[P] = zero;
+    }
+  }
+}
+
 // Fastest-axis passes: a block stages rb whole rows in shared memory
 // (coalesced), and each thread keeps the weights of its output positions in
 // registers across the rows of the block.
@@ -895,6 +1017,7 @@ constexpr long long kXbWaitLimit = 1ll << 22;
 
 template <typename T> struct XbandCT { typedef float type; };
 template <> struct XbandCT<double> { typedef df type; };
+template <> struct XbandCT<float2> { typedef df type; };   // double-float pairs in and out
 
 template <typename T, int P>
 constexpr int xband_min_blocks() { return (sizeof(T) == 8 && P <= 3) ? 2 : 1; }
@@ -2009,6 +2132,42 @@ void launch_interp_bwd(cudaStream_t s, T *out, const T *in, const T *tab, int ne
   launch_tiled_p<T, OP_BWD>(s, p, out, tt, nel * (p + 1), nel + p, inner, outer, accumulate);
 }
 
+void launch_interp_fwd_pairs(cudaStream_t s, float2 *out, const float2 *in, const float2 *tab, int nel, int p,
+                             long long inner, long long outer) {
+  const int bx = (int)std::min<long long>(256, (inner + 31) / 32 * 32);
+  const long long gx = (inner + bx - 1) / bx;
+  const int nruns = (nel + kRunFwd - 1) / kRunFwd;
+  dim3 grid((unsigned)gx, (unsigned)std::min<long long>(outer * nruns, 65535));
+  st_count_launch();
+  switch (p) {
+    case 1: pdl_launch(ifwd_pairs_kernel<1>, grid, dim3(bx), 0, s, out, in, tab, nel, inner, outer, nruns); break;
+    case 2: pdl_launch(ifwd_pairs_kernel<2>, grid, dim3(bx), 0, s, out, in, tab, nel, inner, outer, nruns); break;
+    case 3: pdl_launch(ifwd_pairs_kernel<3>, grid, dim3(bx), 0, s, out, in, tab, nel, inner, outer, nruns); break;
+    default: pdl_launch(ifwd_pairs_kernel<4>, grid, dim3(bx), 0, s, out, in, tab, nel, inner, outer, nruns); break;
+  }
+}
+
+template <typename TO>
+void launch_interp_bwd_pairs(cudaStream_t s, TO *out, const float2 *in, const float2 *tab, int nel, int p,
+                             long long inner, long long outer, bool accumulate) {
+  const int bx = (int)std::min<long long>(256, (inner + 31) / 32 * 32);
+  const long long gx = (inner + bx - 1) / bx;
+  const int nruns = (nel + p + kRunBwd - 1) / kRunBwd;
+  dim3 grid((unsigned)gx, (unsigned)std::min<long long>(outer * nruns, 65535));
+  const int acc = accumulate ? 1 : 0;
+  st_count_launch();
+  switch (p) {
+    case 1: pdl_launch(ibwd_pairs_kernel<1, TO>, grid, dim3(bx), 0, s, out, in, tab, nel, inner, outer, nruns, acc); break;
+    case 2: pdl_launch(ibwd_pairs_kernel<2, TO>, grid, dim3(bx), 0, s, out, in, tab, nel, inner, outer, nruns, acc); break;
+    case 3: pdl_launch(ibwd_pairs_kernel<3, TO>, grid, dim3(bx), 0, s, out, in, tab, nel, inner, outer, nruns, acc); break;
+    default: pdl_launch(ibwd_pairs_kernel<4, TO>, grid, dim3(bx), 0, s, out, in, tab, nel, inner, outer, nruns, acc); break;
+  }
+}
+template void launch_interp_bwd_pairs<float2>(cudaStream_t, float2 *, const float2 *, const float2 *, int, int,
+                                              long long, long long, bool);
+template void launch_interp_bwd_pairs<double>(cudaStream_t, double *, const float2 *, const float2 *, int, int,
+                                              long long, long long, bool);
+
 template <typename T>
 void launch_qband_apply(cudaStream_t s, T *z, const T *x, const float *bhi, const float *blo, int Nt, long long Qs,
                         int p) {
@@ -2075,23 +2234,15 @@ __global__ void split_df_kernel(float2 *__restrict__ out, const double *__restri
 }
 
 template <typename T>
-bool launch_kron2d(cudaStream_t s, T *y, const T *x, void *split, const T *Wt, const T *Mt, const T *Mx,
+bool launch_kron2d(cudaStream_t s, T *y, const T *x, const void *split, const T *Wt, const T *Mt, const T *Mx,
                    const T *Kx, const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx,
                    double Dy) {
   const size_t sh = (size_t)ny * ((32 + 2 * p) + (2 * p + 1)) * 2 * sizeof(T);
   if (sh > 200 * 1024 || p > 4 || Nt > 65535) return false;
   dim3 g((unsigned)((nx + 31) / 32), (unsigned)Nt);
   const typename Pair<T>::src *xs;
-  if constexpr (sizeof(T) == 8) {
-    const long long n = (long long)Nt * nx * ny;
-    float2 *sp = reinterpret_cast<float2 *>(split);
-    st_count_launch();
-    pdl_launch(split_df_kernel, dim3((unsigned)std::min<long long>((n + 255) / 256, 152LL * 16)), dim3(256), 0, s, sp,
-               reinterpret_cast<const double *>(x), n);
-    xs = sp;
-  } else {
-    xs = x;
-  }
+  if constexpr (sizeof(T) == 8) xs = reinterpret_cast<const float2 *>(split);
+  else xs = x;
   auto go = [&](auto k, int P) {
     static bool attr[5] = {false, false, false, false, false};
     if (!attr[P]) {
@@ -2107,6 +2258,12 @@ bool launch_kron2d(cudaStream_t s, T *y, const T *x, void *split, const T *Wt, c
     default: go(kron2d_kernel<T, 4>, 4); break;
   }
   return true;
+}
+
+void launch_split_df(cudaStream_t s, float2 *out, const double *in, long long n) {
+  st_count_launch();
+  pdl_launch(split_df_kernel, dim3((unsigned)std::max<long long>(1, std::min<long long>((n + 255) / 256, 152LL * 16))),
+             dim3(256), 0, s, out, in, n);
 }
 
 template <typename T>
@@ -2317,8 +2474,9 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
                                      long long, bool);                                                \
   template void launch_qband_apply<T>(cudaStream_t, T *, const T *, const float *, const float *, int, \
                                       long long, int);                                                  \
-  template bool launch_kron2d<T>(cudaStream_t, T *, const T *, void *, const T *, const T *, const T *,  \
-                                 const T *, const T *, const T *, int, int, int, int, double, double,   \
+  template bool launch_kron2d<T>(cudaStream_t, T *, const T *, const void *, const T *, const T *,        \
+                                 const T *, const T *, const T *, const T *, int, int, int, int, double, \
+                                 double,                                                              \
                                  double);                                                              \
   template bool launch_xband_fused<T>(cudaStream_t, T *, const T *, const float *, const float *,       \
                                       const T *, int, int, long long, int, int *);                      \
@@ -2337,4 +2495,6 @@ void launch_gemm64(cudaStream_t s, double *C, const double *A, const double *X, 
                                        double *, T *);
 INST(float)
 INST(double)
+template bool launch_xband_fused<float2>(cudaStream_t, float2 *, const float2 *, const float *, const float *,
+                                          const float2 *, int, int, long long, int, int *);
 #undef INST

@@ -194,11 +194,20 @@ void launch_qband_apply(cudaStream_t s, T *z, const T *x, const float *bhi, cons
 // Kronecker part of the operator for d = 2 (time pass into xW, xM, then the
 // plane pass into y); false when a plane column does not fit shared memory.
 template <typename T>
-// 2D Kronecker part; for FP64, `split` is scratch of N_t n_y n_x float pairs
-// (x split into double-float pairs), unused for FP32.
-bool launch_kron2d(cudaStream_t s, T *y, const T *x, void *split, const T *Wt, const T *Mt, const T *Mx,
+// 2D Kronecker part; for FP64, `split` holds x as double-float pairs
+// (N_t n_y n_x float pairs, see launch_split_df), unused for FP32.
+bool launch_kron2d(cudaStream_t s, T *y, const T *x, const void *split, const T *Wt, const T *Mt, const T *Mx,
                    const T *Kx, const T *My, const T *Ky, int nx, int ny, int Nt, int p, double Cm, double Dx,
                    double Dy);
+// FP64 operator on double-float pairs: x split into (high, low) float pairs,
+// and the strided interpolation passes with pair input (forward: pair output;
+// backward: pair output, or FP64 output, optionally accumulated).
+void launch_split_df(cudaStream_t s, float2 *out, const double *in, long long n);
+void launch_interp_fwd_pairs(cudaStream_t s, float2 *out, const float2 *in, const float2 *tab, int nel, int p,
+                             long long inner, long long outer);
+template <typename TO>
+void launch_interp_bwd_pairs(cudaStream_t s, TO *out, const float2 *in, const float2 *tab, int nel, int p,
+                             long long inner, long long outer, bool accumulate);
 // Largest block (threads) of the fused x pass for this element size and degree.
 int xband_fused_limit(size_t elem, int p);
 template <typename T>
