@@ -859,6 +859,29 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   return ST_OK;
 }
 
+// C[m][c] = sum_k A[k][m] X[k][c] for the columns c0 <= c < min(c0 + 8, nc)
+// (A: K x M row-major, X: K x nc, C: M x nc): one thread per m, the few
+// columns in registers, X read by every thread of a warp at once.  For the
+// tall, narrow products of the low-rank step a tiled GEMM would compute
+// mostly padding.
+__global__ void skinny_atx_kernel(double *__restrict__ C, const double *__restrict__ A, const double *__restrict__ X,
+                                  long long M, int nc, int c0, int K) {
+  const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (m >= M) return;
+  const int n = min(8, nc - c0);
+  double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int k = 0; k < K; ++k) {
+    const double a = A[(long long)k * M + m];
+    const double *xr = X + (long long)k * nc + c0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      if (c < n) acc[c] = fma(a, __ldg(xr + c), acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    if (c < n) C[m * nc + c0 + c] = acc[c];
+}
+
 st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
   cudaStream_t s = h->stream;
   const st_problem_desc &D = h->desc;
@@ -954,7 +977,10 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
   for (int r = 0; r < R; ++r) sig[r] = std::sqrt(std::max(lam[r], 0.0));
   ST_CUDA(cudaMemcpyAsync(h->sr, sig.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
   // V = Theta^T U_R diag(1/sigma): (N_s x R)
-  launch_gemm64(s, h->Vr, h->theta, h->Ur, (int)h->Ns, R, Nt, 1, h->Ns, R, 1, R, 1, 1.0, 0.0);
+  for (int c0 = 0; c0 < R; c0 += 8) {
+    st_count_launch();
+    skinny_atx_kernel<<<(unsigned)((h->Ns + 127) / 128), 128, 0, s>>>(h->Vr, h->theta, h->Ur, h->Ns, R, c0, Nt);
+  }
   st_count_launch(); scale_cols_kernel<<<grid_for(h->Ns * R), 256, 0, s>>>(h->Vr, h->sr, R, h->Ns);
   ST_CUDA(cudaGetLastError());
   return ST_OK;

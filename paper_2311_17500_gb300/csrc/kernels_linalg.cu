@@ -2342,7 +2342,11 @@ void launch_multi_dot(cudaStream_t s, double *out, const T *V, long long ldv, in
   long long cap = std::max<long long>(1, n / (V16<T>::W * 256 * 8));
   int bx = (int)std::max<long long>(1, std::min<long long>(std::min<long long>(want, cap), kDotBlocks));
   dim3 grid(bx, groups);
-  st_count_launch(); mdot_kernel<T, G><<<grid, 256, 0, s>>>(scratch, V, ldv, nv, w, n);
+  // a single product (norms) takes the one-row instance: no repeated loads
+  // of the same row and one accumulator per thread
+  st_count_launch();
+  if (nv == 1) mdot_kernel<T, 1><<<grid, 256, 0, s>>>(scratch, V, ldv, nv, w, n);
+  else mdot_kernel<T, G><<<grid, 256, 0, s>>>(scratch, V, ldv, nv, w, n);
   st_count_launch(); reduce_blocks_kernel<<<(nv + 3) / 4, 128, 0, s>>>(out, scratch, bx, nv);
 }
 
