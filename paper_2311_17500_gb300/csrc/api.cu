@@ -861,6 +861,16 @@ static st_status setup_impl(st_handle *h) {
   }
   ST_TRY(upload<double>(h, &h->wt, hs.tdir.wq));
   ST_TRY(upload<double>(h, &h->xt, hs.tdir.xq));
+  {
+    // stimulus windows of each time quadrature point ([t0, t1), as in the
+    // source assembly)
+    std::vector<int> tm(hs.tdir.xq.size(), 0);
+    if (D.source_kind == ST_SRC_STIM)
+      for (size_t i = 0; i < tm.size(); ++i)
+        for (int b = 0; b < D.n_stim; ++b)
+          if (hs.tdir.xq[i] >= D.stim[b].t0 && hs.tdir.xq[i] < D.stim[b].t1) tm[i] |= 1 << b;
+    ST_TRY(upload_i(h, &h->tmask, tm));
+  }
   ST_TRY(upload<double>(h, &h->tauq, hs.tau_q));
   ST_TRY(upload<double>(h, &h->wlu, hs.wlu));
   {

@@ -94,6 +94,8 @@ struct IonicArgs {
   const double *bt, *xt;        // time tables: values/derivatives, points
   const double *bprod;          // [e][qt][pair]: w_t b_i b_{i+k} for the band pairs (i, k), k <= P - i
   const float2 *bt2, *bprod2;   // the same tables as double-float pairs (bt for k = 0, 1)
+  const int *tmask;             // [e*nq+qt]: bit b set if time point (e, qt) lies in stimulus window b
+  float2 amp2[ST_MAX_STIM];     // stimulus amplitudes as double-float pairs
   int Nt, nel_t;
   long long Qs, Nel_s;
   int kind;                     // ST_PICARD: C_r, ST_NEWTON: C_J
@@ -181,15 +183,20 @@ __global__ void __launch_bounds__(128, P <= 3 ? 4 : 2) ionic_tline_kernel(IonicA
           lap = df_fma(v0, cl[j], lap);
           w = df_fma(v0, cw[j], w);
         }
-        double f = 0.0;
-        const double t = a.xt[e * nq + qt];
+        df fd = zero;
         if (stim) {
-          for (int b = 0; b < a.D.n_stim; ++b)
-            if (((inbox >> b) & 1u) && t >= a.D.stim[b].t0 && t < a.D.stim[b].t1) f += a.D.stim[b].amp;
+          // boxes containing this point whose time window holds this time
+          // point, their amplitudes summed in box order
+          unsigned act = inbox & (unsigned)__ldg(a.tmask + e * nq + qt);
+          while (act) {
+            const int b = __ffs(act) - 1;
+            act &= act - 1;
+            fd = df_add(fd, df_from2(a.amp2[b]));
+          }
         } else if (a.D.source_kind != ST_SRC_ZERO) {
-          f = source_at(a.D, sp.x, t);
+          const double f = source_at(a.D, sp.x, a.xt[e * nq + qt]);
+          if (f != 0.0) fd = df_from(f);
         }
-        const df fd = f == 0.0 ? zero : df_from(f);
         // C_r = c1 (u - a)(u - 1) + c2 w = c1 ((u - (1 + a)) u + a) + c2 w
         const df c2w = df_mul(c2, w);
         const df Cr = df_fma(c1, df_fma(df_sub(u, apl), u, aa), c2w);
@@ -840,6 +847,12 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   a.U0 = U0; a.L0 = L0; a.W0 = W0;
   a.bt = h->bt; a.xt = h->xt; a.bprod = h->bprod;
   a.bt2 = h->bt2; a.bprod2 = h->bprod2;
+  a.tmask = h->tmask;
+  for (int b = 0; b < ST_MAX_STIM; ++b) {
+    const double v = b < h->desc.n_stim ? h->desc.stim[b].amp : 0.0;
+    const float hi = (float)v;
+    a.amp2[b] = make_float2(hi, (float)(v - (double)hi));
+  }
   a.Nt = h->Nt; a.nel_t = h->nel_t;
   a.Qs = h->Qs; a.Nel_s = h->Nel_s;
   a.kind = kind;

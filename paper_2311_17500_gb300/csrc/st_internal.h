@@ -62,6 +62,7 @@ struct st_handle {
   double *bt = nullptr;       // time tables [k][e][q][a], k = 0..p
   double *wt = nullptr;       // time weights [e*nq+q]
   double *xt = nullptr;       // time points [e*nq+q]
+  int *tmask = nullptr;       // [e*nq+q]: bit b set if the time point lies in stimulus window b
   double *xs[3] = {};         // spatial points per direction [e*nq+q]
   double *tauq = nullptr;     // [l-1][e][q]
   double *bprod = nullptr;    // [e][q][pair] w_t b_i b_{i+k}, pairs (i, k) with k <= p - i
