@@ -665,9 +665,6 @@ GeomArgs geom(st_handle *h) {
   return g;
 }
 
-// coefficient tensor [N_t][n_z][n_y][n_x] -> values at spatial Gauss points
-// [N_t][Q_z][Q_y][Q_x]; `deriv_dir` selects the direction that uses the second
-// derivative table (-1: values only).  Uses both FP64 work buffers.
 // One spatial axis from coefficients to Gauss points in double-float:
 // out[o][e*nq+g][c] (= or += coef *) sum_a tab[e][g][a] in[o][e+a][c].
 // Grid y runs over o, grid x over the (e*nq+g, c) outputs of one o slice, so
@@ -800,9 +797,11 @@ bool fields_to_qpts_2d(st_handle *h, const float2 *u2, const float2 *w2, float2 
   return true;
 }
 
-// A field at the spatial Gauss points (all time rows), double-float: x given
-// as pairs; deriv_dir selects the axis taking the second derivative (-1:
-// none); the result is written to dst, or added to it times coef.
+// A field at the spatial Gauss points (all time rows), double-float: the
+// coefficient tensor [N_t][n_z][n_y][n_x] as pairs to [N_t][Q_z][Q_y][Q_x];
+// deriv_dir selects the axis taking the second derivative (-1: none); the
+// result is written to dst, or added to it times coef.  Intermediate axes use
+// both Gauss-point work buffers.
 void spatial_to_qpts(st_handle *h, const float2 *x, int deriv_dir, float2 *dst, int accumulate, double coef) {
   cudaStream_t s = h->stream;
   const float2 *cur = x;
