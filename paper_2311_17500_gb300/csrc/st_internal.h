@@ -139,6 +139,21 @@ struct st_handle {
   size_t ev_used = 0;
 };
 
+// Opts `kernel` in to `bytes` of dynamic shared memory on the current device.
+// The attribute is per device, so each call site keeps a mask of the devices
+// it has set up, and a repeated call on the same device does nothing.
+template <typename K>
+inline cudaError_t smem_optin(K kernel, int bytes, unsigned long long &devices_done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (devices_done & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) devices_done |= bit;
+  return e;
+}
+
 // Stage categories of the optional per-stage timing.
 enum {
   PROF_KRON = 0,      // banded Kronecker passes of the operator

@@ -419,11 +419,8 @@ st_status launch_tc_xform(cudaStream_t s, float *out, const float *X, long long 
   CUtensorMap tmX, tmB;
   if (need_tma <= 200 * 1024 && aligned && encode_2d(&tmX, X, nb, R, in_stride, kTcKC, kTcRows) &&
       encode_2d(&tmB, Mpad, Kpad, Npad, Kpad, kTcKC, Npad)) {
-    static bool attr = false;
-    if (!attr) {
-      ST_CUDA(cudaFuncSetAttribute(tc_xform_tma_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 210 * 1024));
-      attr = true;
-    }
+    static unsigned long long attr = 0;
+    ST_CUDA(smem_optin(tc_xform_tma_kernel<S>, 210 * 1024, attr));
     x.ncols_tmem = tc_ncols(Npad, 2);
     int grid = (int)std::min<long long>(ntiles, 152);
     st_count_launch();
@@ -436,11 +433,8 @@ st_status launch_tc_xform(cudaStream_t s, float *out, const float *X, long long 
   int max_ctas = 512 / x.ncols_tmem;
   size_t floor_bytes = (size_t)(227 * 1024) / (size_t)(max_ctas + 1) + 1024;
   size_t sh = std::max(need, floor_bytes);
-  static bool attr_set = false;
-  if (!attr_set) {
-    ST_CUDA(cudaFuncSetAttribute(tc_xform_staged_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  static unsigned long long attr_set = 0;
+  ST_CUDA(smem_optin(tc_xform_staged_kernel, 200 * 1024, attr_set));
   int grid = (int)std::min<long long>(ntiles, 152LL * max_ctas);
   st_count_launch();
   tc_xform_staged_kernel<<<grid, 128, sh, s>>>(x);
