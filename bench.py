@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--scale", default=None, help="nx,ny,nt element counts (smaller case, e.g. for profiling)")
+    ap.add_argument("--serve", action="store_true",
+                    help="the serving stream instead of the single workload (latency p50/p99, DoF/s)")
+    ap.add_argument("--requests", type=int, default=256, help="--serve: requests in the stream")
+    ap.add_argument("--rate", type=float, default=3.0, help="--serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--slots", type=int, default=8, help="--serve: requests in flight at most")
     return ap.parse_args()
 
 
@@ -376,10 +381,83 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """The serving stream: seeded 2D requests (p in {2,3}, 32..256 elements per
+    direction, 64..512 time elements, D log-uniform, a stimulus at a uniform
+    position) arriving as a Poisson stream.  A request is st_setup and one
+    fixed-point step (GMRES-IR to relative residual 1e-8) from u = w = 0, on its
+    own stream; admission is first come, first served under 85 % of the free
+    device memory and a slot limit.  One JSON line: unknowns per second over the
+    makespan, and arrival-to-completion latency percentiles."""
+    import torch
+    import workloads as W
+    from paper_2311_17500_gb300 import build as B
+    B.build()
+    import paper_2311_17500_gb300 as P
+    from paper_2311_17500_gb300 import serve
+    P.load()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    reqs = W.serving_requests(n_req=args.requests, seed=4, rate=args.rate)
+
+    def desc_of(r):
+        d = dict(r["desc"])
+        d.update(max_fp=1, rtol=1e-8, gmres_m=150, max_it=3000)
+        return d
+
+    runner, footprint = serve.gpu_runner(desc_of), serve.gpu_footprint(desc_of)
+    # library, tensor-core self-test and caches warmed outside the timed stream
+    warm = dict(reqs[0], desc=dict(reqs[0]["desc"], n_el=[16, 16], n_el_t=16))
+    runner(warm)
+    torch.cuda.synchronize()
+    free, _total = torch.cuda.mem_get_info()
+    budget = int(0.85 * free)
+    eng = serve.Engine(runner, footprint, budget, args.slots)
+    with Clocks(local) as ck:
+        recs = eng.run(reqs)
+    torch.cuda.synchronize()
+    out = serve.summary(recs, n_dofs=lambda r: r["result"]["n_dof"])
+    n_dof = [W.n_dofs(desc_of(r)) for r in reqs]
+    errors = {}
+    for r in recs:
+        if r["status"] in ("failed", "rejected"):
+            errors[r["error"]] = errors.get(r["error"], 0) + 1
+            if len(errors) == 1 and errors[r["error"]] == 1:
+                d = desc_of(reqs[r["id"]])
+                print(f"request {r['id']} ({d['p']}, {d['n_el']}, {d['n_el_t']}): {r['error']}", file=sys.stderr)
+    iters = [r["result"]["stats"]["total_gmres"] for r in recs if r["status"] == "done"]
+    line = {
+        "metric": "serving stream: unknowns/s over the makespan and arrival-to-completion latency p50/p99",
+        "value": out.get("dof_per_s"), "unit": "DoF/s", "n_gpus": 1, "higher_is_better": True,
+        "latency_ms": {"p50": 1e3 * out["p50_s"], "p99": 1e3 * out["p99_s"], "mean": 1e3 * out["mean_s"]}
+        if out["done"] else None,
+        "service_ms_mean": 1e3 * out["service_mean_s"] if out["done"] else None,
+        "makespan_s": out.get("makespan_s"),
+        "requests": out["requests"], "done": out["done"], "failed": out["failed"], "rejected": out["rejected"],
+        "errors": dict(sorted(errors.items(), key=lambda kv: -kv[1])[:5]),
+        "failed_shapes": [[desc_of(reqs[r["id"]])["p"]] + desc_of(reqs[r["id"]])["n_el"] +
+                          [desc_of(reqs[r["id"]])["n_el_t"]] for r in recs if r["status"] == "failed"][:12],
+        "dtype": "f32+df64+f64", "data": "synthetic",
+        "config": {"workload": f"serving stream: {args.requests} seeded 2D requests, p in {{2,3}}, 32..256 "
+                               f"elements per direction, 64..512 time elements, D log-uniform in [2e-4,2e-3], "
+                               f"Poisson arrivals at {args.rate}/s; a request = set-up + one fixed-point step "
+                               f"to rel.res 1e-8 from u = w = 0",
+                   "unknowns_per_request": {"min": min(n_dof), "median": int(sorted(n_dof)[len(n_dof) // 2]),
+                                            "max": max(n_dof)},
+                   "slots": args.slots, "budget_gb": budget / 1e9, "peak_admitted_gb": eng.peak_bytes / 1e9,
+                   "gmres_iters_mean": (sum(iters) / len(iters)) if iters else None},
+        "clocks": ck.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -26,7 +26,7 @@ GET = dict(theta_hat=0, lowrank_s=1, lowrank_u=2, lowrank_v=3, tau_q=4, fd_eig=5
 EXPORTS = ["st_footprint", "st_setup", "st_destroy", "st_error_string", "st_get_dims", "st_ionic",
            "st_linearize", "st_apply", "st_precond", "st_linsolve", "st_wupdate", "st_rhs", "st_solve",
            "st_get", "st_profile", "st_profile_read", "st_launch_count",
-           "st_tc_selftest", "st_wupdate_static"]
+           "st_tc_selftest", "st_wupdate_static", "st_last_cuda_error"]
 STAGES = ["kron", "interp", "qband", "fd_gemm", "fd_lu", "arnoldi", "ionic", "lowrank", "apply64"]
 
 
@@ -106,8 +106,10 @@ def load(path=None):
     lib.st_tc_selftest.argtypes = [P(i), P(ctypes.c_double)]
     lib.st_launch_count.argtypes = []
     lib.st_launch_count.restype = ctypes.c_longlong
+    lib.st_last_cuda_error.argtypes = []
+    lib.st_last_cuda_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("st_error_string", "st_launch_count"):
+        if name not in ("st_error_string", "st_launch_count", "st_last_cuda_error"):
             getattr(lib, name).restype = i
     _lib = lib
     return lib
@@ -151,7 +153,12 @@ def make_desc(desc):
 
 def _check(code, what):
     if code != ST_OK:
-        msg = load().st_error_string(code).decode()
+        lib = load()
+        msg = lib.st_error_string(code).decode()
+        if code in (ST_ERR_CUDA, ST_ERR_OOM):
+            detail = lib.st_last_cuda_error().decode()
+            if detail:
+                msg += ": " + detail
         raise StError(code, f"{what} failed ({msg})")
 
 

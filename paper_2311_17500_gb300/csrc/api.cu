@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 #include "st_internal.h"
@@ -326,6 +327,16 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
 // ---------------------------------------------------------------- internals
 static std::atomic<long long> g_launches{0};
 void st_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// the CUDA error behind the last ST_ERR_CUDA / ST_ERR_OOM, per thread
+static thread_local char g_cuda_detail[256] = "";
+void st_note_cuda_error(cudaError_t e, const char *file, int line) {
+  const char *base = file;
+  for (const char *c = file; *c; ++c)
+    if (*c == '/') base = c + 1;
+  std::snprintf(g_cuda_detail, sizeof(g_cuda_detail), "%s (%d) at %s:%d", cudaGetErrorName(e), (int)e, base, line);
+}
+const char *st_cuda_detail() { return g_cuda_detail; }
 static cudaEvent_t prof_event(st_handle *h) {
   if (h->ev_used == h->ev_pool.size()) {
     cudaEvent_t e;
@@ -742,6 +753,8 @@ template st_status precond_T<float>(st_handle *, const float *, float *);
 
 // ---------------------------------------------------------------- C ABI
 extern "C" {
+
+const char *st_last_cuda_error(void) { return st_cuda_detail(); }
 
 const char *st_error_string(st_status s) {
   switch (s) {

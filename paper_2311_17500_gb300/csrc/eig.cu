@@ -689,7 +689,7 @@ st_status gram_top_eigs(st_handle *h, const double *G, int n, double tr, double 
   const int kmax = std::min(n, 192);
   size_t shb = (size_t)(n + kmax + 2) * sizeof(double);
   if (shb > 200 * 1024) return ST_ERR_NOT_CONVERGED;
-  static unsigned long long attr = 0;
+  static std::atomic<unsigned long long> attr{0};
   smem_optin(lanczos_kernel, 200 * 1024, attr);
   double *Q = h->eig_work;                       // (kmax + 1) x n
   double *ab = Q + (size_t)(kmax + 1) * n;       // alpha[kmax], beta[kmax]

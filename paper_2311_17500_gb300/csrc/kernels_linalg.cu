@@ -2199,7 +2199,7 @@ bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, co
   auto go = [&](auto kern, int P) {
     const int NB = sizeof(T) == 8 ? 2 : 1;
     size_t sh = (size_t)S * NB * (P + 1) * threads * (P + 1) * sizeof(float) + (size_t)S * threads * sizeof(T);
-    static unsigned long long attr = 0;
+    static std::atomic<unsigned long long> attr{0};
     smem_optin(kern, 200 * 1024, attr);
     st_count_launch();
     pdl_launch(kern, dim3(blocks), dim3(threads), sh, s, Y1, X1, bhi, blo, tab, nel, Nt, rows, seglen, err);
@@ -2241,7 +2241,7 @@ bool launch_kron2d(cudaStream_t s, T *y, const T *x, const void *split, const T 
   if constexpr (sizeof(T) == 8) xs = reinterpret_cast<const float2 *>(split);
   else xs = x;
   auto go = [&](auto k, int P) {
-    static unsigned long long attr[5] = {0, 0, 0, 0, 0};
+    static std::atomic<unsigned long long> attr[5] = {{0}, {0}, {0}, {0}, {0}};
     smem_optin(k, 200 * 1024, attr[P]);
     st_count_launch(); pdl_launch(k, g, dim3(256), sh, s, y, xs, Wt, Mt, Mx, Kx, My, Ky, nx, ny, Nt, (T)Cm, (T)Dx, (T)Dy);
   };

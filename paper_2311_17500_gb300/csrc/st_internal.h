@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 #include <vector>
@@ -143,14 +144,14 @@ struct st_handle {
 // The attribute is per device, so each call site keeps a mask of the devices
 // it has set up, and a repeated call on the same device does nothing.
 template <typename K>
-inline cudaError_t smem_optin(K kernel, int bytes, unsigned long long &devices_done) {
+inline cudaError_t smem_optin(K kernel, int bytes, std::atomic<unsigned long long> &devices_done) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   const unsigned long long bit = 1ull << (dev & 63);
-  if (devices_done & bit) return cudaSuccess;
+  if (devices_done.load(std::memory_order_acquire) & bit) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e == cudaSuccess) devices_done |= bit;
+  if (e == cudaSuccess) devices_done.fetch_or(bit, std::memory_order_release);
   return e;
 }
 
@@ -178,10 +179,18 @@ struct ProfScope {
 };
 
 // ---------------------------------------------------------------- helpers
+// Records the CUDA error behind an ST_ERR_CUDA / ST_ERR_OOM return, per calling
+// thread (read back with st_last_cuda_error).
+void st_note_cuda_error(cudaError_t e, const char *file, int line);
+const char *st_cuda_detail();
+
 #define ST_CUDA(call)                                                  \
   do {                                                                 \
     cudaError_t _e = (call);                                           \
-    if (_e != cudaSuccess) return _e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA; \
+    if (_e != cudaSuccess) {                                           \
+      st_note_cuda_error(_e, __FILE__, __LINE__);                      \
+      return _e == cudaErrorMemoryAllocation ? ST_ERR_OOM : ST_ERR_CUDA; \
+    }                                                                  \
   } while (0)
 
 #define ST_TRY(call)                    \

@@ -24,7 +24,9 @@
 // Every mbarrier wait is bounded: a wait that gives up sets the error flag,
 // the role stops, the CTA frees its tensor memory and returns.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -369,20 +371,26 @@ __global__ void __launch_bounds__(128) tc_xform_staged_kernel(XformArgs x) {
   if (threadIdx.x == 0 && fail) atomicExch(x.err, 1);
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+// The driver's tensor-map encoder, looked up once (thread-safe static
+// initialization; null if the driver does not provide it).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p) {
+      cudaGetLastError();
+      return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+    }
+    return (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }();
+  return fn;
+}
 
 bool encode_2d(CUtensorMap *m, const float *ptr, long long inner, long long outer, long long stride_elems,
                int box_inner, int box_outer) {
-  if (!g_encode) {
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-      cudaGetLastError();
-      return false;
-    }
-    g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  }
+  const PFN_cuTensorMapEncodeTiled_v12000 g_encode = tensor_map_encoder();
+  if (!g_encode) return false;
   cuuint64_t gdim[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
   cuuint64_t gstride[1] = {(cuuint64_t)stride_elems * sizeof(float)};
   cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
@@ -419,7 +427,7 @@ st_status launch_tc_xform(cudaStream_t s, float *out, const float *X, long long 
   CUtensorMap tmX, tmB;
   if (need_tma <= 200 * 1024 && aligned && encode_2d(&tmX, X, nb, R, in_stride, kTcKC, kTcRows) &&
       encode_2d(&tmB, Mpad, Kpad, Npad, Kpad, kTcKC, Npad)) {
-    static unsigned long long attr = 0;
+    static std::atomic<unsigned long long> attr{0};
     ST_CUDA(smem_optin(tc_xform_tma_kernel<S>, 210 * 1024, attr));
     x.ncols_tmem = tc_ncols(Npad, 2);
     int grid = (int)std::min<long long>(ntiles, 152);
@@ -433,7 +441,7 @@ st_status launch_tc_xform(cudaStream_t s, float *out, const float *X, long long 
   int max_ctas = 512 / x.ncols_tmem;
   size_t floor_bytes = (size_t)(227 * 1024) / (size_t)(max_ctas + 1) + 1024;
   size_t sh = std::max(need, floor_bytes);
-  static unsigned long long attr_set = 0;
+  static std::atomic<unsigned long long> attr_set{0};
   ST_CUDA(smem_optin(tc_xform_staged_kernel, 200 * 1024, attr_set));
   int grid = (int)std::min<long long>(ntiles, 152LL * max_ctas);
   st_count_launch();
@@ -443,8 +451,9 @@ st_status launch_tc_xform(cudaStream_t s, float *out, const float *X, long long 
 }
 
 namespace {
-int g_tc_state = 0;
+std::atomic<int> g_tc_state{0};
 double g_tc_err = 0.0;
+std::mutex g_tc_mutex;   // one self-test at a time (handles may be set up from several threads)
 
 // host-side deterministic fill (linear congruential, values in [-1, 1))
 void fill(std::vector<float> &v, unsigned seed) {
@@ -461,16 +470,22 @@ void fill(std::vector<float> &v, unsigned seed) {
 // 16), with a padded input row stride and a padded output as in the
 // preconditioner.
 int tc_state(cudaStream_t s, double *err_out) {
-  if (g_tc_state != 0) {
+  if (g_tc_state.load() != 0) {
+    std::lock_guard<std::mutex> lk(g_tc_mutex);
     if (err_out) *err_out = g_tc_err;
-    return g_tc_state;
+    return g_tc_state.load();
+  }
+  std::lock_guard<std::mutex> lk(g_tc_mutex);
+  if (g_tc_state.load() != 0) {   // another thread finished the test meanwhile
+    if (err_out) *err_out = g_tc_err;
+    return g_tc_state.load();
   }
   int dev = 0, major = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   if (major != 10) {
     g_tc_state = -1;
-    return g_tc_state;
+    return -1;
   }
   const int nb = 131, nj = 131, T = 27, ld = 132;
   const long long Aa = 37, R = T * Aa, Apad = 40;
@@ -522,7 +537,8 @@ int tc_state(cudaStream_t s, double *err_out) {
   }
   cudaFree(dX); cudaFree(dXc); cudaFree(dM); cudaFree(dMp); cudaFree(d1); cudaFree(d2); cudaFree(derr);
   g_tc_err = err;
-  g_tc_state = (ok && err < 5e-3) ? 1 : -1;
+  const int state = (ok && err < 5e-3) ? 1 : -1;
+  g_tc_state = state;
   if (err_out) *err_out = err;
-  return g_tc_state;
+  return state;
 }
