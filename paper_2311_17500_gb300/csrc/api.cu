@@ -326,15 +326,58 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
 
 // ---------------------------------------------------------------- internals
 static std::atomic<long long> g_launches{0};
-void st_count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
-// the CUDA error behind the last ST_ERR_CUDA / ST_ERR_OOM, per thread
-static thread_local char g_cuda_detail[256] = "";
-void st_note_cuda_error(cudaError_t e, const char *file, int line) {
+namespace {
+// Source positions of this thread's launches: the last one, and the one after
+// which a CUDA error was first found pending (cleared once the error is gone).
+struct LaunchNote {
+  const char *file = nullptr;
+  int line = 0;
+  cudaError_t err = cudaSuccess;
+  const char *efile = nullptr;
+  int eline = 0;
+};
+thread_local LaunchNote g_launch_note;
+
+const char *base_name(const char *file) {
   const char *base = file;
   for (const char *c = file; *c; ++c)
     if (*c == '/') base = c + 1;
-  std::snprintf(g_cuda_detail, sizeof(g_cuda_detail), "%s (%d) at %s:%d", cudaGetErrorName(e), (int)e, base, line);
+  return base;
+}
+}  // namespace
+
+void st_count_launch_at(const char *file, int line) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  LaunchNote &n = g_launch_note;
+  const cudaError_t e = cudaPeekAtLastError();
+  if (e == cudaSuccess) {
+    n.err = cudaSuccess;
+  } else if (n.err == cudaSuccess && n.file) {
+    n.err = e;
+    n.efile = n.file;
+    n.eline = n.line;
+  }
+  n.file = file;
+  n.line = line;
+}
+
+// the CUDA error behind the last ST_ERR_CUDA / ST_ERR_OOM, per thread
+static thread_local char g_cuda_detail[320] = "";
+void st_note_cuda_error(cudaError_t e, const char *file, int line) {
+  LaunchNote &n = g_launch_note;
+  if (n.err == e && n.efile) {
+    std::snprintf(g_cuda_detail, sizeof(g_cuda_detail), "%s (%d) at %s:%d, pending since the launch at %s:%d",
+                  cudaGetErrorName(e), (int)e, base_name(file), line, base_name(n.efile), n.eline);
+  } else if (n.file) {
+    std::snprintf(g_cuda_detail, sizeof(g_cuda_detail), "%s (%d) at %s:%d, last launch at %s:%d",
+                  cudaGetErrorName(e), (int)e, base_name(file), line, base_name(n.file), n.line);
+  } else {
+    std::snprintf(g_cuda_detail, sizeof(g_cuda_detail), "%s (%d) at %s:%d", cudaGetErrorName(e), (int)e,
+                  base_name(file), line);
+  }
+  n.err = cudaSuccess;
+  n.efile = nullptr;
 }
 const char *st_cuda_detail() { return g_cuda_detail; }
 static cudaEvent_t prof_event(st_handle *h) {

@@ -2196,25 +2196,27 @@ bool launch_xband_fused(cudaStream_t s, T *Y1, const T *X1, const float *bhi, co
   nseg = (Nt + seglen - 1) / seglen;
   unsigned blocks = (unsigned)std::min<long long>(rows * nseg, 1LL << 30);
   constexpr int S = sizeof(T) == 4 ? 4 : 3;
-  auto go = [&](auto kern, int P) {
+  // every instance has the same function type, so this lambda has one
+  // instantiation per T: the opt-in masks are kept per instance (P, BULK)
+  auto go = [&](auto kern, int P, bool bulk_kern) {
     const int NB = sizeof(T) == 8 ? 2 : 1;
     size_t sh = (size_t)S * NB * (P + 1) * threads * (P + 1) * sizeof(float) + (size_t)S * threads * sizeof(T);
-    static std::atomic<unsigned long long> attr{0};
-    smem_optin(kern, 200 * 1024, attr);
+    static std::atomic<unsigned long long> attr[10] = {};
+    smem_optin(kern, 200 * 1024, attr[2 * P + (bulk_kern ? 1 : 0)]);
     st_count_launch();
     pdl_launch(kern, dim3(blocks), dim3(threads), sh, s, Y1, X1, bhi, blo, tab, nel, Nt, rows, seglen, err);
   };
   // bulk band copies need 16-byte aligned slices: Q_x a multiple of 4 floats
   const bool bulk = (nel * (p + 1)) % 4 == 0 && ((uintptr_t)bhi % 16) == 0 && (!blo || ((uintptr_t)blo % 16) == 0);
   switch (p * 2 + (bulk ? 1 : 0)) {
-    case 2: go(xband_fused_kernel<T, 1, S, false>, 1); break;
-    case 3: go(xband_fused_kernel<T, 1, S, true>, 1); break;
-    case 4: go(xband_fused_kernel<T, 2, S, false>, 2); break;
-    case 5: go(xband_fused_kernel<T, 2, S, true>, 2); break;
-    case 6: go(xband_fused_kernel<T, 3, S, false>, 3); break;
-    case 7: go(xband_fused_kernel<T, 3, S, true>, 3); break;
-    case 8: go(xband_fused_kernel<T, 4, S, false>, 4); break;
-    default: go(xband_fused_kernel<T, 4, S, true>, 4); break;
+    case 2: go(xband_fused_kernel<T, 1, S, false>, 1, false); break;
+    case 3: go(xband_fused_kernel<T, 1, S, true>, 1, true); break;
+    case 4: go(xband_fused_kernel<T, 2, S, false>, 2, false); break;
+    case 5: go(xband_fused_kernel<T, 2, S, true>, 2, true); break;
+    case 6: go(xband_fused_kernel<T, 3, S, false>, 3, false); break;
+    case 7: go(xband_fused_kernel<T, 3, S, true>, 3, true); break;
+    case 8: go(xband_fused_kernel<T, 4, S, false>, 4, false); break;
+    default: go(xband_fused_kernel<T, 4, S, true>, 4, true); break;
   }
   return true;
 }

@@ -304,5 +304,10 @@ template <typename T>
 st_status precond_T(st_handle *h, const T *r, T *z);
 
 void *st_alloc(st_handle *h, size_t bytes, st_status *err);
-// Process-wide count of kernel launches issued by this library.
-void st_count_launch();
+// Process-wide count of kernel launches issued by this library, called just
+// before each launch with the launch's source position.  An error found
+// pending at that point (a launch refused by the runtime, or a runtime call
+// after it) is attributed, per thread, to the launch before; the detail behind
+// a later ST_ERR_CUDA names it.
+void st_count_launch_at(const char *file, int line);
+#define st_count_launch() st_count_launch_at(__FILE__, __LINE__)
