@@ -184,8 +184,8 @@ def test_apply_wide_x_every_fused_instance(P):
     slices by bulk copy), then p = 2 with Q_x a multiple of 4 (bulk copy) and
     not (plain loads).  Each instance of that kernel needs its own opt-in; the
     operators as in the cases above."""
-    for c in (dict(d=2, p=3, n_el=[120, 2], n_el_t=3), dict(d=2, p=2, n_el=[200, 2], n_el_t=3),
-              dict(d=2, p=2, n_el=[199, 2], n_el_t=3)):
+    for c in (dict(d=2, p=3, n_el=[120, 2], n_el_t=3), dict(d=2, p=2, n_el=[196, 2], n_el_t=3),
+              dict(d=2, p=2, n_el=[194, 2], n_el_t=3)):
         desc = problem(c)
         o = Oracle(desc)
         u, w = iterate(o, 2)
