@@ -10,7 +10,7 @@
   tolerance eps (Eq. tol), and theta at the Gauss points as the
   (d+1)-linear interpolant on the Greville grid (Sec. 3.1).
 
-Readings where the paper is silent (listed in the design doc): tau is the
+Readings where the paper is silent: tau is the
 minimum-norm solution in the scaled coefficients c_k / h_t^(2k-1); the support
 extension is taken literally with the underlying b-hat index in time; the
 L-infinity norms are maxima over Gauss points; Theta = 1 when the denominator
