@@ -32,11 +32,24 @@ def _compile(src):
     cmd = [nvcc(), *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3",
            "-I" + INCLUDE, "-I" + CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
     if src.endswith(".cu"):
-        cmd[1:1] = ["-x", "cu"]
+        cmd[1:1] = ["-x", "cu", "-Xptxas", "-v"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{res.stdout}\n{res.stderr}")
+    if src.endswith(".cu"):
+        # registers and static shared memory of every kernel (ptxas report),
+        # read by the CPU launch audit in tests/
+        with open(resources_path(src), "w") as f:
+            f.write(res.stderr)
     return obj
+
+
+def resources_path(src):
+    return os.path.join(OBJDIR, os.path.splitext(src)[0] + ".resources.txt")
+
+
+def objects():
+    return [os.path.join(OBJDIR, os.path.splitext(s)[0] + ".o") for s in SOURCES]
 
 
 def build(force=False, verbose=False):

@@ -1,0 +1,109 @@
+"""Host-side launch logic of the library, audited on the CPU.
+
+The library's objects are linked against a stand-in CUDA runtime that runs no
+kernel (tests/launch_audit/fake_cudart.cpp).  st_setup and st_solve are then
+driven over a sequence of problem shapes in one process, and every kernel
+launch is checked against GB300 limits: block and grid extents, dynamic
+shared memory against the kernel's own limit (48 KB unless it opted in),
+shared memory per block, registers per block (from the ptxas report of the
+build), cluster size.  Every copy and memset is checked against its
+allocation, and every tensor map against the encoder's rules.
+
+One process runs every shape because shared-memory opt-ins are per process:
+the sequence starts with p = 3 and then moves to p = 2 wide-x shapes. That
+order once left p = 2 instances of the fused x pass without their opt-in.
+"""
+
+import json
+import os
+import re
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+AUDIT = os.path.join(ROOT, "tests", "launch_audit")
+
+# p, n_el per spatial direction, n_el_t: p = 1..4, d = 1..3, tiny and ragged
+# meshes, x axes wide enough for every fused-pass width, long time axes, and
+# the serving order of the shapes (p = 3 first, then p = 2 wide x)
+SHAPES = ["3,16,16,16", "3,120,33,64", "2,194,33,64", "2,216,33,64", "2,150,33,64", "3,254,40,16",
+          "2,255,32,16", "1,300,20,16", "4,200,20,16", "2,5,4,6", "3,4,5,5", "1,6,5,7", "4,6,5,7", "2,1,2,3",
+          "2,8,8,512", "2,7,9", "3,40,20", "2,3,4,3,4", "3,8,8,8,16", "4,10,10,10,8", "1,20,20,20,8",
+          "2,200,8,8,8"]
+
+
+def _have_tools():
+    nvcc = shutil.which("nvcc") or (os.path.exists("/usr/local/cuda/bin/nvcc") and "/usr/local/cuda/bin/nvcc")
+    return bool(nvcc) and shutil.which("g++") is not None and os.path.exists("/usr/local/cuda/include/cuda.h")
+
+
+@pytest.fixture(scope="module")
+def audit_env():
+    if not _have_tools():
+        pytest.skip("nvcc, g++ or the CUDA headers are missing")
+    from paper_2311_17500_gb300 import build as B
+    B.build()
+    cu = [s for s in B.SOURCES if s.endswith(".cu")]
+    if not all(os.path.exists(B.resources_path(s)) for s in cu):
+        B.build(force=True)
+    out = os.path.join(B.OBJDIR, "audit")
+    os.makedirs(out, exist_ok=True)
+    lib = os.path.join(out, "libst_audit.so")
+    subprocess.run([B.nvcc(), *B.ARCH, "-shared", "-o", lib, *B.objects(), "-cudart", "shared"], check=True,
+                   capture_output=True)
+    rt = os.path.join(out, "libcudart.so.13")
+    subprocess.run(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-I/usr/local/cuda/include",
+                    "-Wl,-soname,libcudart.so.13", "-Wl,--version-script=" + os.path.join(AUDIT, "cudart.map"),
+                    os.path.join(AUDIT, "fake_cudart.cpp"), "-o", rt], check=True, capture_output=True)
+    table = os.path.join(out, "resources.txt")
+    with open(table, "w") as f:
+        for s in cu:
+            kernel = None
+            for line in open(B.resources_path(s)):
+                m = re.search(r"Compiling entry function '(\S+)'", line)
+                if m:
+                    kernel = m.group(1)
+                    continue
+                m = re.search(r"Used (\d+) registers", line)
+                if m and kernel:
+                    sm = re.search(r"(\d+) bytes smem", line)
+                    f.write(f"{kernel} {m.group(1)} {sm.group(1) if sm else 0}\n")
+                    kernel = None
+    return dict(lib=lib, dir=out, table=table)
+
+
+def run(audit_env, shapes, **extra):
+    env = dict(os.environ, LD_LIBRARY_PATH=audit_env["dir"], AUDIT_RESOURCES=audit_env["table"],
+               AUDIT_LOG=os.path.join(audit_env["dir"], "launches.log"), **extra)
+    res = subprocess.run([sys.executable, os.path.join(AUDIT, "run_shapes.py"), audit_env["lib"], *shapes],
+                         env=env, capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stderr[-3000:]
+    rows = [json.loads(line) for line in res.stdout.splitlines() if line.startswith("{")]
+    assert [r["shape"] for r in rows] == list(shapes)
+    log = open(env["AUDIT_LOG"]).read()
+    return rows, log
+
+
+def test_every_launch_within_limits(audit_env):
+    rows, log = run(audit_env, SHAPES)
+    bad = [line for line in log.splitlines() if line.startswith("VIOLATION")]
+    assert not bad, "\n".join(bad[:10])
+    for r in rows:
+        assert r["violations"] == 0, r
+        # set-up, linearization, both operators, the preconditioner and Arnoldi ran
+        assert r["launches"] >= 60, r
+        assert r["error"] is None or "CUDA error" not in r["error"], r
+    # the tensor-core transforms and their tensor maps were audited too
+    assert "tc_xform" in log and "tensor map" in log
+
+
+def test_audit_sees_a_missing_opt_in(audit_env):
+    """With opt-ins ignored, the kernels that need more than 48 KB of dynamic
+    shared memory are refused: the audit can see the failure it guards against."""
+    rows, log = run(audit_env, ["3,120,33,64", "2,194,33,64"], AUDIT_IGNORE_OPTIN="1")
+    assert sum(r["violations"] for r in rows) > 0
+    assert "no opt-in" in log
+    assert any(r["error"] and "pending since the launch at" in r["error"] for r in rows)
