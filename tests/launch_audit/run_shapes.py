@@ -2,7 +2,10 @@
 against a library linked to the launch-auditing stand-in runtime (see
 fake_cudart.cpp); prints one JSON line per shape.
 
-usage: run_shapes.py LIBRARY SHAPE...   with SHAPE = p,n_el_x[,n_el_y[,n_el_z]],n_el_t
+usage: run_shapes.py [--concurrent K] LIBRARY SHAPE...
+       with SHAPE = p,n_el_x[,n_el_y[,n_el_z]],n_el_t
+With --concurrent K the shapes go through the serving engine instead, with
+K requests in flight on K threads, each with its own handle.
 """
 
 import ctypes
@@ -17,34 +20,59 @@ import workloads as W  # noqa: E402
 from paper_2311_17500_gb300 import _lib as L  # noqa: E402
 
 
+def describe(base, shape):
+    v = [int(a) for a in shape.split(",")]
+    p, n_el, n_el_t = v[0], v[1:-1], v[-1]
+    d = len(n_el)
+    box = base["source"]["boxes"][0]
+    desc = dict(base, d=d, p=p, n_el=n_el, n_el_t=n_el_t, D=[base["D"][0]] * d, max_fp=1, gmres_m=8,
+                max_it=16, rtol=1e-8)
+    desc["source"] = dict(base["source"], boxes=[dict(box, lo=[0.05] * d, hi=[0.15] * d)])
+    return desc
+
+
+def solve_once(rt, desc):
+    """st_setup + st_solve; the error text, or None."""
+    n = W.n_dofs(desc)
+    try:
+        s = L.Solver(desc, 0)
+        u, w = rt.audit_alloc(8 * n), rt.audit_alloc(8 * n)
+        ctypes.memset(u, 0, 8 * n)
+        ctypes.memset(w, 0, 8 * n)
+        try:
+            s.solve(u, w, allow_unconverged=True)
+        finally:
+            s.close()
+    except Exception as e:  # values read back are not results: a NaN exit is expected
+        return str(e)
+    return None
+
+
 def main():
-    L.load(sys.argv[1])
+    args = sys.argv[1:]
+    concurrent = 0
+    if args[0] == "--concurrent":
+        concurrent, args = int(args[1]), args[2:]
+    L.load(args[0])
     rt = ctypes.CDLL("libcudart.so.13")
     rt.audit_alloc.restype = ctypes.c_void_p
     rt.audit_alloc.argtypes = [ctypes.c_size_t]
     rt.audit_violations.restype = ctypes.c_longlong
     rt.audit_launches.restype = ctypes.c_longlong
     base = W.serving_requests(n_req=1, seed=21)[0]["desc"]
-    for shape in sys.argv[2:]:
-        v = [int(a) for a in shape.split(",")]
-        p, n_el, n_el_t = v[0], v[1:-1], v[-1]
-        d = len(n_el)
-        box = base["source"]["boxes"][0]
-        desc = dict(base, d=d, p=p, n_el=n_el, n_el_t=n_el_t, D=[base["D"][0]] * d, max_fp=1, gmres_m=8,
-                    max_it=16, rtol=1e-8)
-        desc["source"] = dict(base["source"], boxes=[dict(box, lo=[0.05] * d, hi=[0.15] * d)])
-        n = W.n_dofs(desc)
+    if concurrent:
+        from paper_2311_17500_gb300 import serve
+        reqs = [dict(id=i, arrival=0.0, desc=describe(base, sh)) for i, sh in enumerate(args[1:])]
+        eng = serve.Engine(lambda r: solve_once(rt, r["desc"]), lambda r: 1, budget_bytes=concurrent,
+                           max_slots=concurrent)
+        recs = eng.run(reqs)
+        for sh, rec in zip(args[1:], recs):
+            print(json.dumps(dict(shape=sh, status=rec["status"], error=rec["result"])), flush=True)
+        print(json.dumps(dict(violations=rt.audit_violations(), launches=rt.audit_launches())), flush=True)
+        return
+    for shape in args[1:]:
         v0, l0 = rt.audit_violations(), rt.audit_launches()
-        err = None
-        try:
-            s = L.Solver(desc, 0)
-            u, w = rt.audit_alloc(8 * n), rt.audit_alloc(8 * n)
-            ctypes.memset(u, 0, 8 * n)
-            ctypes.memset(w, 0, 8 * n)
-            s.solve(u, w, allow_unconverged=True)
-            s.close()
-        except Exception as e:  # values read back are not results: a NaN exit is expected
-            err = str(e)
+        err = solve_once(rt, describe(base, shape))
         print(json.dumps(dict(shape=shape, violations=rt.audit_violations() - v0,
                               launches=rt.audit_launches() - l0, error=err)), flush=True)
 

@@ -107,3 +107,24 @@ def test_audit_sees_a_missing_opt_in(audit_env):
     assert sum(r["violations"] for r in rows) > 0
     assert "no opt-in" in log
     assert any(r["error"] and "pending since the launch at" in r["error"] for r in rows)
+
+
+def test_requests_in_flight_together(audit_env):
+    """The serving engine with four requests in flight on four threads, each
+    with its own handle (shared state of the library: the tensor-core
+    self-test, the opt-in masks, the per-thread error detail)."""
+    shapes = ["3,16,16,16", "2,194,33,64", "3,120,33,64", "2,216,33,64", "2,5,4,6", "3,4,5,5,5", "1,30,30,16",
+              "4,20,20,8"]
+    env = dict(os.environ, LD_LIBRARY_PATH=audit_env["dir"], AUDIT_RESOURCES=audit_env["table"],
+               AUDIT_LOG=os.path.join(audit_env["dir"], "launches_concurrent.log"))
+    res = subprocess.run([sys.executable, os.path.join(AUDIT, "run_shapes.py"), "--concurrent", "4",
+                          audit_env["lib"], *shapes], env=env, capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stderr[-3000:]
+    rows = [json.loads(line) for line in res.stdout.splitlines() if line.startswith("{")]
+    per_request, total = rows[:-1], rows[-1]
+    assert [r["shape"] for r in per_request] == shapes
+    for r in per_request:
+        assert r["status"] == "done", r
+        assert r["error"] is None or "CUDA error" not in r["error"], r
+    assert total["violations"] == 0
+    assert total["launches"] >= 60 * len(shapes)
