@@ -21,13 +21,29 @@ from paper_2311_17500_gb300 import _lib as L  # noqa: E402
 
 
 def describe(base, shape):
-    v = [int(a) for a in shape.split(",")]
+    """SHAPE[:option...], options fp64 (FP64 GMRES), newton, galerkin, symmetric
+    (support extension), wzero (w fixed at zero)."""
+    sizes, *opts = shape.split(":")
+    v = [int(a) for a in sizes.split(",")]
     p, n_el, n_el_t = v[0], v[1:-1], v[-1]
     d = len(n_el)
     box = base["source"]["boxes"][0]
     desc = dict(base, d=d, p=p, n_el=n_el, n_el_t=n_el_t, D=[base["D"][0]] * d, max_fp=1, gmres_m=8,
                 max_it=16, rtol=1e-8)
     desc["source"] = dict(base["source"], boxes=[dict(box, lo=[0.05] * d, hi=[0.15] * d)])
+    for o in opts:
+        if o == "fp64":
+            desc["precision"] = "fp64"
+        elif o == "newton":
+            desc["nonlinear"] = "newton"
+        elif o == "galerkin":
+            desc["stabilization"] = "galerkin"
+        elif o == "symmetric":
+            desc["suppext"] = "symmetric"
+        elif o == "wzero":
+            desc["fix_w_zero"] = True
+        else:
+            raise ValueError("unknown option " + o)
     return desc
 
 

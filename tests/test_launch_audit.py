@@ -28,11 +28,13 @@ AUDIT = os.path.join(ROOT, "tests", "launch_audit")
 
 # p, n_el per spatial direction, n_el_t: p = 1..4, d = 1..3, tiny and ragged
 # meshes, x axes wide enough for every fused-pass width, long time axes, and
-# the serving order of the shapes (p = 3 first, then p = 2 wide x)
+# the serving order of the shapes (p = 3 first, then p = 2 wide x); then FP64 GMRES, Newton,
+# Galerkin, the symmetric support extension and w fixed at zero
 SHAPES = ["3,16,16,16", "3,120,33,64", "2,194,33,64", "2,216,33,64", "2,150,33,64", "3,254,40,16",
           "2,255,32,16", "1,300,20,16", "4,200,20,16", "2,5,4,6", "3,4,5,5", "1,6,5,7", "4,6,5,7", "2,1,2,3",
           "2,8,8,512", "2,7,9", "3,40,20", "2,3,4,3,4", "3,8,8,8,16", "4,10,10,10,8", "1,20,20,20,8",
-          "2,200,8,8,8"]
+          "2,200,8,8,8", "3,16,16,16:fp64", "2,194,33,64:fp64:newton", "3,120,33,64:newton",
+          "2,8,8,8,16:fp64", "2,9,7,12:galerkin", "3,9,7,12:symmetric:wzero", "1,40,12:fp64"]
 
 
 def _have_tools():
