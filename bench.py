@@ -54,7 +54,8 @@ def parse():
     ap.add_argument("--serve", action="store_true",
                     help="the serving stream instead of the single workload (latency p50/p99, DoF/s)")
     ap.add_argument("--requests", type=int, default=256, help="--serve: requests in the stream")
-    ap.add_argument("--rate", type=float, default=3.0, help="--serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="--serve: Poisson arrival rate (requests/s); 0 = 0.8 x the measured saturated rate")
     ap.add_argument("--slots", type=int, default=8, help="--serve: requests in flight at most")
     return ap.parse_args()
 
@@ -388,7 +389,12 @@ def run_serve(args):
     fixed-point step (GMRES-IR to relative residual 1e-8) from u = w = 0, on its
     own stream; admission is first come, first served under 85 % of the free
     device memory and a slot limit.  One JSON line: unknowns per second over the
-    makespan, and arrival-to-completion latency percentiles."""
+    makespan, and arrival-to-completion latency percentiles.
+
+    With --rate 0 (the default) the arrival rate is set from the stream
+    itself: a first pass serves every request at once (all arrive at t = 0),
+    which gives the saturated throughput in requests/s; the timed pass then
+    runs the same requests as a Poisson stream at 0.8 of that rate."""
     import torch
     import workloads as W
     from paper_2311_17500_gb300 import build as B
@@ -398,7 +404,13 @@ def run_serve(args):
     P.load()
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    reqs = W.serving_requests(n_req=args.requests, seed=4, rate=args.rate)
+    # arrivals drawn at rate 1 and scaled: every rate gives the same requests
+    unit = W.serving_requests(n_req=args.requests, seed=4, rate=1.0)
+
+    def at_rate(rate):
+        return [dict(r, arrival=(r["arrival"] / rate if rate else 0.0)) for r in unit]
+
+    reqs = unit
 
     def desc_of(r):
         d = dict(r["desc"])
@@ -412,6 +424,19 @@ def run_serve(args):
     torch.cuda.synchronize()
     free, _total = torch.cuda.mem_get_info()
     budget = int(0.85 * free)
+    saturated = None
+    rate = args.rate
+    if not rate > 0:
+        recs0 = serve.Engine(runner, footprint, budget, args.slots).run(at_rate(0.0))
+        torch.cuda.synchronize()
+        out0 = serve.summary(recs0, n_dofs=lambda r: r["result"]["n_dof"])
+        if not out0["done"]:
+            raise RuntimeError("no request of the saturated pass completed: %s" % recs0[0]["error"])
+        rate = 0.8 * out0["done"] / out0["makespan_s"]
+        saturated = {"requests_per_s": out0["done"] / out0["makespan_s"], "dof_per_s": out0.get("dof_per_s"),
+                     "makespan_s": out0["makespan_s"], "done": out0["done"], "failed": out0["failed"],
+                     "rejected": out0["rejected"]}
+    reqs = at_rate(rate)
     eng = serve.Engine(runner, footprint, budget, args.slots)
     with Clocks(local) as ck:
         recs = eng.run(reqs)
@@ -440,10 +465,13 @@ def run_serve(args):
         "dtype": "f32+df64+f64", "data": "synthetic",
         "config": {"workload": f"serving stream: {args.requests} seeded 2D requests, p in {{2,3}}, 32..256 "
                                f"elements per direction, 64..512 time elements, D log-uniform in [2e-4,2e-3], "
-                               f"Poisson arrivals at {args.rate}/s; a request = set-up + one fixed-point step "
+                               f"Poisson arrivals at {rate:.3g}/s; a request = set-up + one fixed-point step "
                                f"to rel.res 1e-8 from u = w = 0",
                    "unknowns_per_request": {"min": min(n_dof), "median": int(sorted(n_dof)[len(n_dof) // 2]),
                                             "max": max(n_dof)},
+                   "arrival_rate_per_s": rate,
+                   "rate_rule": "given" if args.rate > 0 else "0.8 x saturated throughput of the same requests",
+                   "saturated": saturated,
                    "slots": args.slots, "budget_gb": budget / 1e9, "peak_admitted_gb": eng.peak_bytes / 1e9,
                    "gmres_iters_mean": (sum(iters) / len(iters)) if iters else None},
         "clocks": ck.summary(),

@@ -135,3 +135,14 @@ def test_serving_stream_is_seeded_and_in_range():
         assert 2e-4 <= d["D"][0] <= 2e-3 and d["D"][0] == d["D"][1]
         box = d["source"]["boxes"][0]
         assert 0.0 <= box["lo"][0] <= 0.9 and box["hi"][0] == pytest.approx(box["lo"][0] + 0.1)
+
+
+def test_arrival_rate_scales_the_same_requests():
+    """Exponential gaps scale with 1/rate and the shapes do not depend on the
+    rate, so a stream can be replayed at a rate measured from its own
+    saturated pass."""
+    one = W.serving_requests(n_req=32, seed=4, rate=1.0)
+    for rate in (0.5, 3.0, 17.0):
+        r = W.serving_requests(n_req=32, seed=4, rate=rate)
+        assert [a["desc"] for a in r] == [a["desc"] for a in one]
+        assert np.allclose([a["arrival"] * rate for a in r], [a["arrival"] for a in one], rtol=1e-12)
