@@ -136,8 +136,13 @@ void *allocate(size_t n, bool dev) {
   const size_t sz = (n + 255) / 256 * 256 + 256;
   void *p = aligned_alloc(256, sz);
   if (!p) return nullptr;
+  // AUDIT_FILL_BYTES bounds the filled prefix of an allocation, so that
+  // full-size problems fit in host memory (untouched pages stay unmapped)
+  static const size_t fill_limit = getenv("AUDIT_FILL_BYTES") ? strtoull(getenv("AUDIT_FILL_BYTES"), nullptr, 10)
+                                                               : ~size_t(0);
   unsigned long long *q = static_cast<unsigned long long *>(p);
-  for (size_t i = 0; i < sz / 8; ++i) q[i] = kFill;
+  const size_t nfill = (sz < fill_limit ? sz : fill_limit) / 8;
+  for (size_t i = 0; i < nfill; ++i) q[i] = kFill;
   std::lock_guard<std::mutex> lk(mu);
   allocs[(uintptr_t)p] = Alloc{n, dev};
   return p;
