@@ -14,6 +14,11 @@ A-hat, the tau invariant, the w elimination, the rest state, the low-rank
 tolerance, convergence rates against closed-form solutions and the spatially
 uniform ODE limit.  Parity is unpinned for the full nonlinear Spline-Upwind
 wave runs, which only the oracle itself defines.
+
+For problems too large to assemble, `rows` evaluates selected rows of the
+operators and of the load vector over the supports of their test functions.
+That uses the same tables and Gauss rule as the assembly, and the rows equal
+the assembled ones on small meshes (tests/test_oracle_rows.py).
 """
 
 from .solve import Oracle  # noqa: F401
