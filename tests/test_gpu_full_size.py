@@ -60,3 +60,26 @@ def test_full_size_sampled_rows():
     assert out["rel_res"] <= 1e-8
     SR.check_solution(st, desc, rows, inp, f_rows, np.linalg.norm(fh), host(dsol), 1e-8)
     s.close()
+
+
+def test_newton_workload_full_size():
+    """The Newton workload at its full size (2D, p = 2, 16 x 16 x 32 elements,
+    10,692 unknowns, FP64): three nonlinear steps from u = w = 0 on both sides,
+    against the oracle's assembled solves.  The SU ranks of the three steps
+    are 1, 1 and 2; the oracle's tails at the cut are 0.03 to 0.12 and 1.26
+    to 100 of the tolerance, far from a tie."""
+    torch_cuda()
+    from oracle import Oracle
+    P = library()
+    desc = W.config("c1_newton_2d")
+    desc.update(max_fp=3, delta=0.0, rtol=1e-13, gmres_m=80)
+    o = Oracle(desc)
+    u_ref, w_ref, hist = o.solve(max_fp=3)
+    s = P.Solver(desc, stream())
+    u, w = empty(o.st.N_dof), empty(o.st.N_dof)
+    st = s.solve(ptr(u), ptr(w), allow_unconverged=True)
+    assert st["fp_iters"] == 3
+    assert st["rank"] == hist[-1]["rank"]
+    for got, ref in ((host(u), u_ref), (host(w), w_ref)):
+        assert np.abs(got - ref).max() <= 1e-9 * np.abs(ref).max()
+    s.close()
