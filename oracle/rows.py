@@ -7,8 +7,9 @@ function is removed, Sec. 2).  It involves only the space-time elements in
 the support of v_i: (p+1) time elements times (p+1)^d spatial elements.
 Evaluating those elements' Gauss-point integrands from the coefficient
 vectors gives the row exactly as the assembled matrix of `SpaceTime.assemble`
-does.  The same Gauss rule is used, with the same tables, so a full-size
-problem never assembles or stores a space-time array.
+does: the same Gauss rule and the same tables, restricted to those elements
+(local_table, local_glob), so a full-size problem never assembles or stores a
+space-time array.
 
 Operators are given as terms (coef_fn, kt_test, ks_test, kt_trial, ks_trial)
 like `SpaceTime.assemble`'s, with coef_fn(et, es) returning the integrand
@@ -21,6 +22,35 @@ Test infrastructure only: nothing in the product path imports this package.
 import numpy as np
 
 from . import model
+
+
+def local_table(st, ks, es):
+    """The spatial basis table of `SpaceTime.stab` for the spatial elements es
+    only: T[e, qs, ls] = prod_l vals_l[k_l][e_l, q_l, local_l(e_l)[a_l]], with
+    es, qs and ls colexicographic (direction 0 fastest)."""
+    es = np.asarray(es)
+    tab = None
+    rem = es.copy()
+    for l, dr in enumerate(st.sdirs):
+        e_l = rem % dr.n_el
+        rem = rem // dr.n_el
+        loc = np.array([dr.local[e] for e in e_l])                     # (E, p+1)
+        t_l = dr.vals[ks[l]][e_l[:, None], :, loc].transpose(0, 2, 1)  # (E, nq, p+1)
+        if tab is None:
+            tab = t_l
+        else:
+            E, Q, A = tab.shape
+            tab = np.einsum('eqa,epb->epqba', tab, t_l).reshape(E, t_l.shape[1] * Q, t_l.shape[2] * A)
+    return tab
+
+
+def local_glob(st, et, es):
+    """Global dof of (a_t, l_s) on the elements (et, es), -1 where the removed
+    first time function would be: (len(es), p+1, L_s)."""
+    it = st.tglob[et]
+    g = it[None, :, None] * st.N_s + st.sglob[es][:, None, :]
+    g[:, it < 0, :] = -1
+    return g
 
 
 def support(st, i):
@@ -36,9 +66,9 @@ def local_field(st, vec, et, es, kt=0, ks=None):
     """Derivative (kt in time, ks per spatial direction) of the spline with
     coefficients `vec` at the Gauss points of (et, es): (len(es), nq_t, nq_s)."""
     ks = (0,) * st.d if ks is None else tuple(ks)
-    g = st.glob(et)[es]                                         # (E, p+1, L_s)
+    g = local_glob(st, et, es)                                  # (E, p+1, L_s)
     c = np.where(g >= 0, vec[np.maximum(g, 0)], 0.0)
-    return np.einsum('eal,ta,eql->etq', c, st.ttab[kt][et], st.stab(ks)[es])
+    return np.einsum('eal,ta,eql->etq', c, st.ttab[kt][et], local_table(st, ks, es))
 
 
 def apply_rows(st, terms, rows, x):
@@ -50,13 +80,13 @@ def apply_rows(st, terms, rows, x):
         for et in ets:
             a_i = int(np.nonzero(st.tglob[et] == it)[0][0])
             l_i = np.array([int(np.nonzero(st.sglob[e] == i_s)[0][0]) for e in ess])
-            g = st.glob(et)[ess]
+            g = local_glob(st, et, ess)
             xl = np.where(g >= 0, x[np.maximum(g, 0)], 0.0)         # (E, p+1, L_s)
             wt = st.tdir.wq[et]
             for coef_fn, kti, ksi, ktj, ksj in terms:
                 W = coef_fn(et, ess) * wt[None, :, None] * st.ws[ess][:, None, :]
-                Si = st.stab(ksi)[ess, :, :][np.arange(len(ess)), :, l_i]     # (E, nq_s)
-                trial = np.einsum('tb,eqm,ebm->etq', st.ttab[ktj][et], st.stab(ksj)[ess], xl)
+                Si = local_table(st, ksi, ess)[np.arange(len(ess)), :, l_i]      # (E, nq_s)
+                trial = np.einsum('tb,eqm,ebm->etq', st.ttab[ktj][et], local_table(st, ksj, ess), xl)
                 acc += np.einsum('etq,t,eq,etq->', W, st.ttab[kti][et][:, a_i], Si, trial)
         out[r] = acc
     return out
@@ -72,7 +102,7 @@ def load_rows(st, coef_fn, rows, kt=0, ks=None):
             a_i = int(np.nonzero(st.tglob[et] == it)[0][0])
             l_i = np.array([int(np.nonzero(st.sglob[e] == i_s)[0][0]) for e in ess])
             W = coef_fn(et, ess) * st.tdir.wq[et][None, :, None] * st.ws[ess][:, None, :]
-            Si = st.stab(ks)[ess, :, :][np.arange(len(ess)), :, l_i]
+            Si = local_table(st, ks, ess)[np.arange(len(ess)), :, l_i]
             out[r] += np.einsum('etq,t,eq->', W, st.ttab[kt][et][:, a_i], Si)
     return out
 

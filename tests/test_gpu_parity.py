@@ -178,31 +178,6 @@ def test_apply_tiny_mesh(P, kind):
     s.close()
 
 
-def test_apply_wide_x_every_fused_instance(P):
-    """Wide x axes, in one process, for which the fused x pass of the FP64
-    operator takes more than 48 KB of dynamic shared memory: p = 3 (band
-    slices by bulk copy), then p = 2 with Q_x a multiple of 4 (bulk copy) and
-    not (plain loads).  Each instance of that kernel needs its own opt-in; the
-    operators as in the cases above."""
-    for c in (dict(d=2, p=3, n_el=[120, 2], n_el_t=3), dict(d=2, p=2, n_el=[196, 2], n_el_t=3),
-              dict(d=2, p=2, n_el=[194, 2], n_el_t=3)):
-        desc = problem(c)
-        o = Oracle(desc)
-        u, w = iterate(o, 2)
-        A, _ = o.linearization(u, w, "picard")
-        s = solver(P, desc)
-        du, dw = dev(u), dev(w)
-        s.ionic(ptr(du), ptr(dw))
-        x = W.random_vector(o.st.N_dof, seed=5)
-        dx, dy = dev(x), empty(o.st.N_dof)
-        s.apply(ptr(dx), ptr(dy), P.ST_FP64)
-        assert rel(host(dy), A @ x) < 1e-12, c
-        dx32, dy32 = dev(x, np.float32), empty(o.st.N_dof, "float32")
-        s.apply(ptr(dx32), ptr(dy32), P.ST_MIXED)
-        assert rel(host(dy32), A @ x) < 2e-5, c
-        s.close()
-
-
 @pytest.mark.parametrize("c", CASES, ids=IDS)
 def test_precond(P, c):
     desc = problem(c)

@@ -50,24 +50,3 @@ def test_served_solutions_equal_standalone_solves():
     out = serve.summary(recs, n_dofs=lambda r: r["result"]["n_dof"])
     assert out["done"] == len(reqs) and out["p99_s"] >= out["p50_s"] > 0.0
     torch.cuda.synchronize()
-
-
-def test_wide_x_solves_in_one_process():
-    """Solves in the order that the serving stream met them: a p = 3 request
-    first, then p = 2 requests whose fused x pass of the FP64 operator needs
-    more than 48 KB of shared memory (224 threads, Q_x not a multiple of 4 and
-    a multiple of 4).  Every instance of that kernel needs its own opt-in;
-    with one opt-in per element type the p = 2 solves failed with a CUDA
-    error.  One fixed-point step each, small in y and time."""
-    from tests.gpu_helpers import empty, host, ptr, stream
-    P = library()
-    base = W.serving_requests(n_req=1, seed=21)[0]["desc"]
-    for p, nx in ((3, 120), (2, 194), (2, 216)):
-        desc = dict(base, p=p, n_el=[nx, 8], n_el_t=8, max_fp=1, gmres_m=60)
-        n = W.n_dofs(desc)
-        s = P.Solver(desc, stream())
-        u, w = empty(n), empty(n)
-        st = s.solve(ptr(u), ptr(w), allow_unconverged=True)
-        assert st["fp_iters"] == 1, (p, nx)
-        assert np.all(np.isfinite(host(u))) and np.abs(host(u)).max() > 0.0, (p, nx)
-        s.close()

@@ -75,3 +75,14 @@ def test_full_size_checks_on_a_small_mesh():
     bad[rows[len(rows) // 2]] *= 1.0 + 1e-9
     with pytest.raises(AssertionError):
         SR.check_apply(st, desc, rows, inp, bad, 1e-12)
+
+
+@pytest.mark.parametrize("c", CASES, ids=[f"d{c['d']}p{c['p']}" for c in CASES])
+def test_local_tables_equal_the_global_ones(c):
+    from oracle.spacetime import SpaceTime
+    st = SpaceTime(problem(c))
+    es = np.arange(st.N_el_s)[::2]
+    for ks in [(0,) * st.d] + [st.unit(l, k) for l in range(st.d) for k in (1, 2)]:
+        assert np.array_equal(OR.local_table(st, ks, es), st.stab(ks)[es])
+    for et in range(st.n_el_t):
+        assert np.array_equal(OR.local_glob(st, et, es), st.glob(et)[es])
