@@ -457,6 +457,7 @@ def run_serve(args):
         "latency_ms": {"p50": 1e3 * out["p50_s"], "p99": 1e3 * out["p99_s"], "mean": 1e3 * out["mean_s"]}
         if out["done"] else None,
         "service_ms_mean": 1e3 * out["service_mean_s"] if out["done"] else None,
+        "queue_ms": {"p50": 1e3 * out["queue_p50_s"], "p99": 1e3 * out["queue_p99_s"]} if out["done"] else None,
         "makespan_s": out.get("makespan_s"),
         "requests": out["requests"], "done": out["done"], "failed": out["failed"], "rejected": out["rejected"],
         "errors": dict(sorted(errors.items(), key=lambda kv: -kv[1])[:5]),

@@ -102,17 +102,20 @@ class Engine:
 
 
 def summary(records, n_dofs=None):
-    """Latency percentiles (arrival to completion) and throughput of a run."""
+    """Latency percentiles (arrival to completion), time waiting for admission
+    (arrival to admission) and throughput of a run."""
     ok = [r for r in records if r["status"] == "done"]
     lat = np.array([r["done"] - r["arrival"] for r in ok], dtype=float)
     svc = np.array([r["done"] - r["admitted"] for r in ok], dtype=float)
+    wait = np.array([r["admitted"] - r["arrival"] for r in ok], dtype=float)
     out = dict(requests=len(records), done=len(ok),
                failed=sum(r["status"] == "failed" for r in records),
                rejected=sum(r["status"] == "rejected" for r in records))
     if len(ok):
         makespan = max(r["done"] for r in ok) - min(r["arrival"] for r in records)
         out.update(p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
-                   mean_s=float(lat.mean()), service_mean_s=float(svc.mean()), makespan_s=float(makespan))
+                   mean_s=float(lat.mean()), service_mean_s=float(svc.mean()), makespan_s=float(makespan),
+                   queue_p50_s=float(np.percentile(wait, 50)), queue_p99_s=float(np.percentile(wait, 99)))
         if n_dofs is not None:
             units = sum(n_dofs(r) for r in ok)
             out["dof_per_s"] = float(units / makespan) if makespan > 0 else None

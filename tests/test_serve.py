@@ -114,6 +114,9 @@ def test_summary_percentiles_and_throughput():
     assert out["p50_s"] == pytest.approx(np.percentile(lat, 50))
     assert out["p99_s"] == pytest.approx(np.percentile(lat, 99))
     assert out["makespan_s"] == pytest.approx(1.9)
+    wait = np.array([0.1 * i for i in range(10)])
+    assert out["queue_p50_s"] == pytest.approx(np.percentile(wait, 50))
+    assert out["queue_p99_s"] == pytest.approx(np.percentile(wait, 99))
     assert out["dof_per_s"] == pytest.approx(1000 / 1.9)
 
 
