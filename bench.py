@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0,
                     help="--serve: Poisson arrival rate (requests/s); 0 = 0.8 x the measured saturated rate")
     ap.add_argument("--slots", type=int, default=8, help="--serve: requests in flight at most")
+    ap.add_argument("--serve-requests", type=int, default=64,
+                    help="requests of the short serving pass in the default run (0: none)")
     return ap.parse_args()
 
 
@@ -348,6 +350,17 @@ def run_ours(args):
                 "rel_res": f_st["rel_res"], "setup_s": setup64, "speedup_mixed_vs_fp64": fm / ms_step}
         s64.close()
 
+    serving = None
+    if ws == 1 and args.serve_requests > 0:
+        # the serving stream, shortened: latency percentiles beside the step
+        # throughput; a failure here is reported in the line, never fatal
+        try:
+            f = serving_pass(args.serve_requests, 0.0, args.slots, local, clocks=False)
+            serving = {k: f[k] for k in ("value", "unit", "latency_ms", "queue_ms", "service_ms_mean", "requests",
+                                         "done", "failed", "rejected", "errors", "config")}
+        except Exception as e:  # noqa: BLE001
+            serving = {"error": f"{type(e).__name__}: {e}"}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline()
@@ -375,6 +388,7 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -382,35 +396,28 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_serve(args):
+def serving_pass(n_requests, rate, slots, local, clocks=True):
     """The serving stream: seeded 2D requests (p in {2,3}, 32..256 elements per
     direction, 64..512 time elements, D log-uniform, a stimulus at a uniform
     position) arriving as a Poisson stream.  A request is st_setup and one
     fixed-point step (GMRES-IR to relative residual 1e-8) from u = w = 0, on its
     own stream; admission is first come, first served under 85 % of the free
-    device memory and a slot limit.  One JSON line: unknowns per second over the
-    makespan, and arrival-to-completion latency percentiles.
+    device memory and a slot limit.  Returns the fields of the JSON line:
+    unknowns per second over the makespan, arrival-to-completion latency
+    percentiles, admission waits and the workload.
 
-    With --rate 0 (the default) the arrival rate is set from the stream
-    itself: a first pass serves every request at once (all arrive at t = 0),
-    which gives the saturated throughput in requests/s; the timed pass then
-    runs the same requests as a Poisson stream at 0.8 of that rate."""
+    With rate 0 the arrival rate is set from the stream itself: a first pass
+    serves every request at once (all arrive at t = 0), which gives the
+    saturated throughput in requests/s; the timed pass then runs the same
+    requests as a Poisson stream at 0.8 of that rate."""
     import torch
     import workloads as W
-    from paper_2311_17500_gb300 import build as B
-    B.build()
-    import paper_2311_17500_gb300 as P
     from paper_2311_17500_gb300 import serve
-    P.load()
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
     # arrivals drawn at rate 1 and scaled: every rate gives the same requests
-    unit = W.serving_requests(n_req=args.requests, seed=4, rate=1.0)
+    unit = W.serving_requests(n_req=n_requests, seed=4, rate=1.0)
 
-    def at_rate(rate):
-        return [dict(r, arrival=(r["arrival"] / rate if rate else 0.0)) for r in unit]
-
-    reqs = unit
+    def at_rate(r):
+        return [dict(q, arrival=(q["arrival"] / r if r else 0.0)) for q in unit]
 
     def desc_of(r):
         d = dict(r["desc"])
@@ -419,15 +426,14 @@ def run_serve(args):
 
     runner, footprint = serve.gpu_runner(desc_of), serve.gpu_footprint(desc_of)
     # library, tensor-core self-test and caches warmed outside the timed stream
-    warm = dict(reqs[0], desc=dict(reqs[0]["desc"], n_el=[16, 16], n_el_t=16))
-    runner(warm)
+    runner(dict(unit[0], desc=dict(unit[0]["desc"], n_el=[16, 16], n_el_t=16)))
     torch.cuda.synchronize()
     free, _total = torch.cuda.mem_get_info()
     budget = int(0.85 * free)
     saturated = None
-    rate = args.rate
-    if not rate > 0:
-        recs0 = serve.Engine(runner, footprint, budget, args.slots).run(at_rate(0.0))
+    given = rate > 0
+    if not given:
+        recs0 = serve.Engine(runner, footprint, budget, slots).run(at_rate(0.0))
         torch.cuda.synchronize()
         out0 = serve.summary(recs0, n_dofs=lambda r: r["result"]["n_dof"])
         if not out0["done"]:
@@ -437,8 +443,12 @@ def run_serve(args):
                      "makespan_s": out0["makespan_s"], "done": out0["done"], "failed": out0["failed"],
                      "rejected": out0["rejected"]}
     reqs = at_rate(rate)
-    eng = serve.Engine(runner, footprint, budget, args.slots)
-    with Clocks(local) as ck:
+    eng = serve.Engine(runner, footprint, budget, slots)
+    if clocks:
+        with Clocks(local) as ck:
+            recs = eng.run(reqs)
+    else:
+        ck = None
         recs = eng.run(reqs)
     torch.cuda.synchronize()
     out = serve.summary(recs, n_dofs=lambda r: r["result"]["n_dof"])
@@ -451,9 +461,8 @@ def run_serve(args):
                 d = desc_of(reqs[r["id"]])
                 print(f"request {r['id']} ({d['p']}, {d['n_el']}, {d['n_el_t']}): {r['error']}", file=sys.stderr)
     iters = [r["result"]["stats"]["total_gmres"] for r in recs if r["status"] == "done"]
-    line = {
-        "metric": "serving stream: unknowns/s over the makespan and arrival-to-completion latency p50/p99",
-        "value": out.get("dof_per_s"), "unit": "DoF/s", "n_gpus": 1, "higher_is_better": True,
+    fields = {
+        "value": out.get("dof_per_s"), "unit": "DoF/s",
         "latency_ms": {"p50": 1e3 * out["p50_s"], "p99": 1e3 * out["p99_s"], "mean": 1e3 * out["mean_s"]}
         if out["done"] else None,
         "service_ms_mean": 1e3 * out["service_mean_s"] if out["done"] else None,
@@ -463,20 +472,35 @@ def run_serve(args):
         "errors": dict(sorted(errors.items(), key=lambda kv: -kv[1])[:5]),
         "failed_shapes": [[desc_of(reqs[r["id"]])["p"]] + desc_of(reqs[r["id"]])["n_el"] +
                           [desc_of(reqs[r["id"]])["n_el_t"]] for r in recs if r["status"] == "failed"][:12],
-        "dtype": "f32+df64+f64", "data": "synthetic",
-        "config": {"workload": f"serving stream: {args.requests} seeded 2D requests, p in {{2,3}}, 32..256 "
+        "config": {"workload": f"serving stream: {n_requests} seeded 2D requests, p in {{2,3}}, 32..256 "
                                f"elements per direction, 64..512 time elements, D log-uniform in [2e-4,2e-3], "
                                f"Poisson arrivals at {rate:.3g}/s; a request = set-up + one fixed-point step "
                                f"to rel.res 1e-8 from u = w = 0",
                    "unknowns_per_request": {"min": min(n_dof), "median": int(sorted(n_dof)[len(n_dof) // 2]),
                                             "max": max(n_dof)},
                    "arrival_rate_per_s": rate,
-                   "rate_rule": "given" if args.rate > 0 else "0.8 x saturated throughput of the same requests",
+                   "rate_rule": "given" if given else "0.8 x saturated throughput of the same requests",
                    "saturated": saturated,
-                   "slots": args.slots, "budget_gb": budget / 1e9, "peak_admitted_gb": eng.peak_bytes / 1e9,
+                   "slots": slots, "budget_gb": budget / 1e9, "peak_admitted_gb": eng.peak_bytes / 1e9,
                    "gmres_iters_mean": (sum(iters) / len(iters)) if iters else None},
-        "clocks": ck.summary(),
     }
+    if ck is not None:
+        fields["clocks"] = ck.summary()
+    return fields
+
+
+def run_serve(args):
+    """The serving stream alone (see serving_pass): one JSON line."""
+    import torch
+    from paper_2311_17500_gb300 import build as B
+    B.build()
+    import paper_2311_17500_gb300 as P
+    P.load()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    fields = serving_pass(args.requests, args.rate, args.slots, local)
+    line = {"metric": "serving stream: unknowns/s over the makespan and arrival-to-completion latency p50/p99",
+            "n_gpus": 1, "higher_is_better": True, "dtype": "f32+df64+f64", "data": "synthetic", **fields}
     if rank == 0:
         print(json.dumps(line))
 
