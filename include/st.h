@@ -124,7 +124,10 @@ typedef struct {
 } st_stats;
 
 /* Device bytes st_setup would allocate for this description (admission
- * control for the serving loop).  ST_ERR_ARG on an invalid description. */
+ * control for the serving loop): an upper bound on the bytes that st_setup
+ * and the later calls request from cudaMalloc for this handle (the runtime's
+ * rounding of each allocation is not included).  ST_ERR_ARG on an invalid
+ * description. */
 st_status st_footprint(const st_problem_desc *desc, size_t *bytes);
 
 /* Build a solver for `desc`: the 1D spline data of Sec. 2 and Sec. 3.1

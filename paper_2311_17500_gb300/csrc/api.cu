@@ -66,8 +66,13 @@ Sizes plan(const st_problem_desc &D) {
   // 1D data (generous)
   b += (size_t)(6 * z.nmax * z.B + 4 * z.nmax * z.nmax) * (d8 + f4) + (size_t)z.Qt * (z.p + 2) * z.nq * d8 * 4;
   b += (size_t)(3 * z.nmax * z.nq * z.nq * 4) * d8;
+  // rows padded to a multiple of 4 (FP32 LU and the tensor-core transforms)
+  const size_t nxp = (size_t)(z.n[0] + 3) / 4 * 4;
+  const size_t Ns_pad = (size_t)z.Ns / z.n[0] * nxp;
+  size_t np = (size_t)z.Nt;
+  for (int l = 0; l < z.d; ++l) np *= (size_t)(z.n[l] + 3) / 4 * 4;
   b += (size_t)z.Ns * d8;                                          // mu
-  b += (size_t)z.Nt * z.B * z.Ns * (d8 + f4);                      // LU per eigen-index
+  b += (size_t)z.Nt * z.B * (z.Ns * d8 + Ns_pad * f4);             // LU per eigen-index (FP64, padded FP32)
   b += (size_t)(z.p + 1) * z.NtQs * (f4 + f4);                     // bands (high + low parts)
   b += (size_t)z.Ndof * d8 * 9;                                    // f, theta, FP64 vectors
   b += (size_t)z.Ndof * f4 * 4;                                    // FP32 vectors
@@ -77,10 +82,12 @@ Sizes plan(const st_problem_desc &D) {
   b += (size_t)z.NtQs * d8 * 5;                                    // two work buffers + ionic fields
   b += (size_t)z.NtQs * f4 * 2;
   b += (size_t)z.Ndof * (d8 + f4) * 7;                             // Kronecker temporaries
-  b += (size_t)z.Ndof * f4 * 4;                                    // padded transform buffers
+  b += 2 * (std::max<size_t>(np, 2 * (size_t)z.Ndof) + 64) * f4;   // padded transform buffers
   if (D.precision == ST_FP64) b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * d8;
   else b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * f4;
-  b += (size_t)(608 * (2 * z.m + 56) + 4096) * d8;
+  b += (size_t)(608 * (2 * z.m + 56) + 4096) * d8;                 // reduction scratch
+  b += 2 * (size_t)(2 * (z.m + 2) + 8) * d8 + 256;                 // Hessenberg column, DCGS2 coefficients, flags
+  b += 64 * 1024;   // small tables: 1D data of tiny meshes (one element at least each), Gauss-point hats
   z.bytes = b;
   return z;
 }

@@ -49,6 +49,7 @@ std::map<const void *, int> dyn_limit;                    // opt-ins
 thread_local cudaError_t last_error = cudaSuccess;
 FILE *logf = nullptr;
 long long n_launch = 0, n_violation = 0;
+long long device_bytes = 0, device_peak = 0;   // cudaMalloc'd and not yet freed
 
 void init() {
   if (logf) return;
@@ -145,6 +146,11 @@ void *allocate(size_t n, bool dev) {
   for (size_t i = 0; i < nfill; ++i) q[i] = kFill;
   std::lock_guard<std::mutex> lk(mu);
   allocs[(uintptr_t)p] = Alloc{n, dev};
+  if (dev) {
+    if (logf) fprintf(logf, "alloc %zu\n", n);
+    device_bytes += (long long)n;
+    if (device_bytes > device_peak) device_peak = device_bytes;
+  }
   return p;
 }
 
@@ -293,6 +299,7 @@ cudaError_t cudaFree(void *p) {
     violation("free of an unknown pointer");
     return fail(cudaErrorInvalidValue);
   }
+  if (it->second.dev) device_bytes -= (long long)it->second.size;
   allocs.erase(it);
   free(p);
   return cudaSuccess;
@@ -375,6 +382,14 @@ cudaError_t cudaGetDriverEntryPointByVersion(const char *sym, void **fn, unsigne
 // read by the driver script
 long long audit_violations(void) { return n_violation; }
 long long audit_launches(void) { return n_launch; }
+// device bytes allocated and not freed; the peak since the last reset
+long long audit_device_bytes(void) { return device_bytes; }
+long long audit_device_peak_reset(void) {
+  std::lock_guard<std::mutex> lk(mu);
+  const long long p = device_peak;
+  device_peak = device_bytes;
+  return p;
+}
 void *audit_alloc(size_t n) {
   void *p = nullptr;
   cudaMalloc(&p, n);

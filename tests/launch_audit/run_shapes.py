@@ -75,6 +75,8 @@ def main():
     rt.audit_alloc.argtypes = [ctypes.c_size_t]
     rt.audit_violations.restype = ctypes.c_longlong
     rt.audit_launches.restype = ctypes.c_longlong
+    rt.audit_device_bytes.restype = ctypes.c_longlong
+    rt.audit_device_peak_reset.restype = ctypes.c_longlong
     base = W.serving_requests(n_req=1, seed=21)[0]["desc"]
     if concurrent:
         from paper_2311_17500_gb300 import serve
@@ -88,9 +90,16 @@ def main():
         return
     for shape in args[1:]:
         v0, l0 = rt.audit_violations(), rt.audit_launches()
-        err = solve_once(rt, describe(base, shape))
+        desc = describe(base, shape)
+        b0 = rt.audit_device_bytes()
+        rt.audit_device_peak_reset()
+        err = solve_once(rt, desc)
+        # device bytes the handle held at its peak (set-up and solve; the two
+        # solution vectors are allocated through the same runtime)
+        peak = rt.audit_device_peak_reset() - b0
         print(json.dumps(dict(shape=shape, violations=rt.audit_violations() - v0,
-                              launches=rt.audit_launches() - l0, error=err)), flush=True)
+                              launches=rt.audit_launches() - l0, error=err, peak_bytes=peak,
+                              footprint=L.footprint(desc) + 2 * 8 * W.n_dofs(desc))), flush=True)
 
 
 if __name__ == "__main__":

@@ -102,6 +102,20 @@ def test_every_launch_within_limits(audit_env):
     assert "tc_xform" in log and "tensor map" in log
 
 
+def test_footprint_bounds_what_a_handle_allocates(audit_env):
+    """The serving loop admits a request by st_footprint (plus its two
+    solution vectors): that figure must not be below what set-up and solve
+    allocate on the device, or admission over-commits device memory.  A
+    first small problem takes the once-per-process tensor-core self-test, whose
+    buffers belong to no handle."""
+    rows, _ = run(audit_env, ["2,2,2,3"] + SHAPES + ["1,1,1,1", "4,1,1,1", "1,1,1,1,1", "4,1,1,1,1"])
+    for r in rows[1:]:
+        assert r["peak_bytes"] > 0, r
+        assert r["peak_bytes"] <= r["footprint"], r
+        # and not so far above it that admission turns requests away for nothing
+        assert r["footprint"] <= 1.25 * r["peak_bytes"] + (1 << 20), r
+
+
 def test_audit_sees_a_missing_opt_in(audit_env):
     """With opt-ins ignored, the kernels that need more than 48 KB of dynamic
     shared memory are refused: the audit can see the failure it guards against."""
