@@ -148,9 +148,11 @@ const char *st_error_string(st_status s);
 
 /* Diagnostics, no counterpart in the paper: the CUDA error behind the last
  * ST_ERR_CUDA or ST_ERR_OOM returned to the calling thread, as
- * "<error name> (<code>) at <file>:<line>", or "" if there was none.  The
- * string is owned by the library and stays valid until the thread's next
- * such error. */
+ * "<error name> (<code>) at <file>:<line>", followed by ", pending since the
+ * launch at <file>:<line>" when the error was already pending before a later
+ * launch (a launch the runtime refused), else by ", last launch at
+ * <file>:<line>"; "" if there was none.  The string is owned by the library
+ * and stays valid until the thread's next such error. */
 const char *st_last_cuda_error(void);
 
 st_status st_get_dims(const st_handle *h, st_dims *out);
