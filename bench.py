@@ -433,7 +433,8 @@ def serving_pass(n_requests, rate, slots, local, clocks=True):
     saturated = None
     given = rate > 0
     if not given:
-        recs0 = serve.Engine(runner, footprint, budget, slots).run(at_rate(0.0))
+        recs0 = serve.Engine(runner, footprint, budget, slots,
+                             retryable=serve.device_memory_exhausted).run(at_rate(0.0))
         torch.cuda.synchronize()
         out0 = serve.summary(recs0, n_dofs=lambda r: r["result"]["n_dof"])
         if not out0["done"]:
@@ -443,7 +444,7 @@ def serving_pass(n_requests, rate, slots, local, clocks=True):
                      "makespan_s": out0["makespan_s"], "done": out0["done"], "failed": out0["failed"],
                      "rejected": out0["rejected"]}
     reqs = at_rate(rate)
-    eng = serve.Engine(runner, footprint, budget, slots)
+    eng = serve.Engine(runner, footprint, budget, slots, retryable=serve.device_memory_exhausted)
     if clocks:
         with Clocks(local) as ck:
             recs = eng.run(reqs)
@@ -469,6 +470,7 @@ def serving_pass(n_requests, rate, slots, local, clocks=True):
         "queue_ms": {"p50": 1e3 * out["queue_p50_s"], "p99": 1e3 * out["queue_p99_s"]} if out["done"] else None,
         "makespan_s": out.get("makespan_s"),
         "requests": out["requests"], "done": out["done"], "failed": out["failed"], "rejected": out["rejected"],
+        "retries": sum(r["retries"] for r in recs),
         "errors": dict(sorted(errors.items(), key=lambda kv: -kv[1])[:5]),
         "failed_shapes": [[desc_of(reqs[r["id"]])["p"]] + desc_of(reqs[r["id"]])["n_el"] +
                           [desc_of(reqs[r["id"]])["n_el_t"]] for r in recs if r["status"] == "failed"][:12],

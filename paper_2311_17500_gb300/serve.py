@@ -25,9 +25,16 @@ import numpy as np
 
 
 class Engine:
-    """First-come first-served admission under a byte budget and a slot limit."""
+    """First-come first-served admission under a byte budget and a slot limit.
 
-    def __init__(self, run_request, footprint, budget_bytes, max_slots, clock=time.perf_counter):
+    A request whose run raises an exception that `retryable` accepts (device
+    memory exhausted by something outside the budget, for instance) goes back
+    to the head of the queue, at most `max_retries` times.  It is admitted
+    again only after another request has completed, and only while other
+    requests are in flight; otherwise it is recorded as failed."""
+
+    def __init__(self, run_request, footprint, budget_bytes, max_slots, clock=time.perf_counter,
+                 retryable=None, max_retries=2):
         if max_slots < 1:
             raise ValueError("max_slots must be at least 1")
         self.run_request = run_request
@@ -35,6 +42,8 @@ class Engine:
         self.budget = int(budget_bytes)
         self.max_slots = int(max_slots)
         self.clock = clock
+        self.retryable = retryable or (lambda exc: False)
+        self.max_retries = int(max_retries)
 
     def run(self, requests):
         """Serve `requests` (dicts with "id", "arrival" and "desc"); returns one
@@ -43,12 +52,16 @@ class Engine:
         records = {}
         for r in pending:
             records[r["id"]] = dict(id=r["id"], arrival=float(r["arrival"]), footprint=int(self.footprint(r)),
-                                    status="pending", admitted=None, done=None, result=None, error=None)
+                                    status="pending", admitted=None, done=None, result=None, error=None,
+                                    retries=0)
+        by_id = {r["id"]: r for r in pending}
+        retry_after = {}      # request id -> completions count at its failure
         queue = []            # arrived, not yet admitted (FIFO)
         active = {}           # future -> request id
         used = 0
         peak = 0
         nxt = 0
+        completions = 0
         t0 = self.clock()
         with cf.ThreadPoolExecutor(max_workers=self.max_slots) as pool:
             while nxt < len(pending) or queue or active:
@@ -70,6 +83,9 @@ class Engine:
                         continue
                     if used + rec["footprint"] > self.budget:
                         break
+                    if head["id"] in retry_after and completions <= retry_after[head["id"]]:
+                        break         # a retry waits for memory to be released
+                    retry_after.pop(head["id"], None)
                     queue.pop(0)
                     used += rec["footprint"]
                     peak = max(peak, used)
@@ -92,9 +108,18 @@ class Engine:
                     rec["done"] = self.clock() - t0
                     exc = fut.exception()
                     if exc is None:
+                        completions += 1
                         rec["status"] = "done"
                         rec["result"] = fut.result()
+                    elif self.retryable(exc) and rec["retries"] < self.max_retries and active:
+                        rec["retries"] += 1
+                        rec["status"] = "queued"
+                        rec["done"] = None
+                        rec["error"] = "%s: %s" % (type(exc).__name__, exc)
+                        retry_after[rid] = completions
+                        queue.insert(0, by_id[rid])
                     else:
+                        completions += 1
                         rec["status"] = "failed"
                         rec["error"] = "%s: %s" % (type(exc).__name__, exc)
         self.peak_bytes = peak
@@ -139,6 +164,15 @@ def gpu_footprint(desc_of):
         desc = desc_of(req)
         return int(L.footprint(desc)) + 2 * 8 * n_unknowns(desc)
     return fp
+
+
+def device_memory_exhausted(exc):
+    """True for the library's ST_ERR_OOM and for torch's out-of-memory error:
+    the request can run once memory held elsewhere is released."""
+    from . import _lib as L
+    if isinstance(exc, L.StError):
+        return exc.code == L.ST_ERR_OOM
+    return type(exc).__name__ == "OutOfMemoryError"
 
 
 def gpu_runner(desc_of, keep_solution=False, device=None):

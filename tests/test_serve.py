@@ -149,3 +149,64 @@ def test_arrival_rate_scales_the_same_requests():
         r = W.serving_requests(n_req=32, seed=4, rate=rate)
         assert [a["desc"] for a in r] == [a["desc"] for a in one]
         assert np.allclose([a["arrival"] * rate for a in r], [a["arrival"] for a in one], rtol=1e-12)
+
+
+class Transient(RuntimeError):
+    pass
+
+
+def test_retryable_failure_runs_again_after_a_completion():
+    # request 1 fails once (as if device memory were held elsewhere) while 0 runs
+    reqs = stream(3, 0.0, 0.02, [10])
+    calls = {}
+    lock = threading.Lock()
+
+    def run(req):
+        with lock:
+            calls[req["id"]] = calls.get(req["id"], 0) + 1
+            first = calls[req["id"]] == 1
+        if req["id"] == 1 and first:
+            raise Transient("out of memory")
+        time.sleep(req["work"])
+        return dict(ok=req["id"])
+
+    eng = serve.Engine(run, fp_of, budget_bytes=100, max_slots=3, retryable=lambda e: isinstance(e, Transient))
+    recs = eng.run(reqs)
+    assert [r["status"] for r in recs] == ["done"] * 3
+    assert recs[1]["retries"] == 1 and calls[1] == 2
+    assert recs[0]["retries"] == 0 and recs[2]["retries"] == 0
+
+
+def test_retryable_failure_alone_is_a_failure():
+    reqs = stream(1, 0.0, 0.0, [10])
+
+    def run(req):
+        raise Transient("out of memory")
+
+    recs = serve.Engine(run, fp_of, budget_bytes=100, max_slots=2,
+                        retryable=lambda e: isinstance(e, Transient)).run(reqs)
+    assert recs[0]["status"] == "failed" and recs[0]["retries"] == 0
+
+
+def test_retries_are_bounded():
+    reqs = stream(2, 0.0, 0.01, [10])
+    calls = {1: 0}
+
+    def run(req):
+        if req["id"] == 1:
+            calls[1] += 1
+            raise Transient("out of memory")
+        time.sleep(0.05)
+        return dict(ok=0)
+
+    recs = serve.Engine(run, fp_of, budget_bytes=100, max_slots=2, max_retries=2,
+                        retryable=lambda e: isinstance(e, Transient)).run(reqs)
+    assert recs[0]["status"] == "done"
+    assert recs[1]["status"] == "failed" and recs[1]["retries"] <= 2 and calls[1] == recs[1]["retries"] + 1
+
+
+def test_out_of_memory_is_retryable():
+    from paper_2311_17500_gb300 import _lib as L
+    assert serve.device_memory_exhausted(L.StError(L.ST_ERR_OOM, "st_setup failed"))
+    assert not serve.device_memory_exhausted(L.StError(L.ST_ERR_CUDA, "st_solve failed"))
+    assert not serve.device_memory_exhausted(ValueError("x"))
