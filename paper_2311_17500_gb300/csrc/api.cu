@@ -2,6 +2,7 @@
 // nonlinear loop of the space-time IgA monodomain solver (include/st.h).
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -415,7 +416,9 @@ ProfScope::~ProfScope() {
 
 void *st_alloc(st_handle *h, size_t bytes, st_status *err) {
   void *p = nullptr;
-  if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+  const size_t n = std::max<size_t>(bytes, 16);
+  const cudaError_t e = h->pooled ? cudaMallocAsync(&p, n, h->stream) : cudaMalloc(&p, n);
+  if (e != cudaSuccess) {
     cudaGetLastError();
     *err = ST_ERR_OOM;
     return nullptr;
@@ -423,6 +426,54 @@ void *st_alloc(st_handle *h, size_t bytes, st_status *err) {
   h->allocs.push_back(p);
   return p;
 }
+
+namespace {
+// Page-locked host slots of the Arnoldi coefficients, reused across handles:
+// allocating and freeing page-locked memory per handle would synchronize the
+// device each time.  One slot holds 2 (2 (m + 2) + 4) doubles for m <= 500.
+constexpr size_t kPinnedSlot = 16384;
+static_assert(2 * (2 * (500 + 2) + 4) * sizeof(double) <= kPinnedSlot, "pinned slot too small for m = 500");
+std::mutex g_pinned_mutex;
+std::vector<void *> g_pinned_free;
+
+double *pinned_acquire() {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mutex);
+    if (!g_pinned_free.empty()) {
+      void *p = g_pinned_free.back();
+      g_pinned_free.pop_back();
+      return static_cast<double *>(p);
+    }
+  }
+  void *p = nullptr;
+  if (cudaHostAlloc(&p, kPinnedSlot, cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<double *>(p);
+}
+
+void pinned_release(void *p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mutex);
+  g_pinned_free.push_back(p);
+}
+
+// Whether the device has stream-ordered memory pools (checked once per device).
+bool pools_supported(int dev) {
+  static std::atomic<unsigned long long> known{0}, yes{0};
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (known.load(std::memory_order_acquire) & bit) return (yes.load(std::memory_order_acquire) & bit) != 0;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMemoryPoolsSupported, dev) != cudaSuccess) {
+    cudaGetLastError();
+    v = 0;
+  }
+  if (v) yes.fetch_or(bit, std::memory_order_release);
+  known.fetch_or(bit, std::memory_order_release);
+  return v != 0;
+}
+}  // namespace
 
 template <typename T> struct Prec;
 template <> struct Prec<double> {
@@ -832,12 +883,19 @@ st_status st_footprint(const st_problem_desc *desc, size_t *bytes) {
 st_status st_destroy(st_handle *h) {
   if (!h) return ST_OK;
   cudaSetDevice(h->dev);
-  if (h->stream) cudaStreamSynchronize(h->stream);
-  for (void *p : h->allocs) cudaFree(p);
+  cudaStreamSynchronize(h->stream);
+  if (h->pooled) {
+    // freed in stream order, then waited for on this stream alone, so the
+    // memory is back in the pool when the call returns
+    for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
+    cudaStreamSynchronize(h->stream);
+  } else {
+    for (void *p : h->allocs) cudaFree(p);
+  }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   for (cudaEvent_t e : h->arn_ev)
     if (e) cudaEventDestroy(e);
-  if (h->red_host) cudaFreeHost(h->red_host);
+  pinned_release(h->red_host);
   delete h;
   return ST_OK;
 }
@@ -1012,11 +1070,8 @@ static st_status setup_impl(st_handle *h) {
   h->hcol = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
   // pinned host slots for the Arnoldi coefficients (two iterations in flight)
   // and the events that mark their arrival
-  if (cudaMallocHost(&h->red_host, 2 * (size_t)(2 * (h->m + 2) + 4) * sizeof(double)) != cudaSuccess) {
-    cudaGetLastError();
-    h->red_host = nullptr;
-    return ST_ERR_OOM;
-  }
+  h->red_host = pinned_acquire();
+  if (!h->red_host) return ST_ERR_OOM;
   for (int i = 0; i < 2; ++i) ST_CUDA(cudaEventCreateWithFlags(&h->arn_ev[i], cudaEventDisableTiming));
   h->gs_coef = dalloc<double>(h, (size_t)2 * (h->m + 2) + 8, &e);
   if (e != ST_OK) return e;
@@ -1073,6 +1128,7 @@ st_status st_setup(const st_problem_desc *desc, void *cuda_stream, st_handle **o
   h->desc = *desc;
   h->stream = (cudaStream_t)cuda_stream;
   cudaGetDevice(&h->dev);
+  h->pooled = pools_supported(h->dev);
   st_status s = setup_impl(h);
   if (s != ST_OK) {
     st_destroy(h);

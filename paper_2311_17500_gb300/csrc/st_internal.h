@@ -132,6 +132,10 @@ struct st_handle {
   double *hcol = nullptr;      // device [2*(m+2)] Arnoldi coefficients
   double *gs_coef = nullptr;   // 2 (m + 2) values: Gram-Schmidt update coefficients (FP64 or FP32)
   std::vector<void *> allocs;
+  // allocations come from the device's stream-ordered memory pool (allocated
+  // and freed in the order of the handle's stream): freeing them then waits
+  // for this stream only, where cudaFree would wait for the whole device
+  bool pooled = false;
   // optional per-stage timing (CUDA events on the handle's stream)
   bool prof_on = false;
   struct ProfRec { int cat; cudaEvent_t a, b; double bytes, flops; };

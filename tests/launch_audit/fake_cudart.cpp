@@ -273,6 +273,7 @@ cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr a, int) {
     case cudaDevAttrComputeCapabilityMinor: *v = 3; break;
     case cudaDevAttrMultiProcessorCount: *v = 152; break;
     case cudaDevAttrMaxSharedMemoryPerBlockOptin: *v = (int)kMaxSmemPerBlock; break;
+    case cudaDevAttrMemoryPoolsSupported: *v = 1; break;
     default: *v = 0;
   }
   return cudaSuccess;
@@ -305,6 +306,10 @@ cudaError_t cudaFree(void *p) {
   return cudaSuccess;
 }
 cudaError_t cudaFreeHost(void *p) { return cudaFree(p); }
+// stream-ordered allocation: the same host memory (no kernel runs, so stream
+// order is the call order)
+cudaError_t cudaMallocAsync(void **p, size_t n, cudaStream_t) { return cudaMalloc(p, n); }
+cudaError_t cudaFreeAsync(void *p, cudaStream_t) { return cudaFree(p); }
 cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind k) { return copy(d, s, n, k); }
 cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind k, cudaStream_t) {
   return copy(d, s, n, k);
