@@ -8,7 +8,9 @@
 // cudaFuncSetAttribute), static + dynamic shared memory against the 227 KB
 // per-block maximum, registers per block against the 64 K register file, and
 // cluster size.  Every copy and memset is checked against the allocation it
-// touches, and every tiled tensor map against the encoder's rules (16-byte
+// touches, and stream-ordered allocations (cudaMallocAsync) against the
+// stream of each copy, memset and free; every tiled tensor map against the
+// encoder's rules (16-byte
 // base and strides, box extents 1..256, inner box a multiple of 16 bytes and
 // at most 128 bytes under 128-byte swizzling).  A launch that breaks a limit
 // is refused with the error the runtime gives for it, as the real runtime
@@ -41,6 +43,8 @@ std::mutex mu;
 struct Alloc {
   size_t size;
   bool dev;
+  bool ordered = false;           // from cudaMallocAsync: usable in the order of `stream`
+  cudaStream_t stream = nullptr;
 };
 std::map<uintptr_t, Alloc> allocs;
 std::map<const void *, std::string> names;                // host stub -> kernel name
@@ -77,6 +81,21 @@ bool inside_device(const void *p, size_t n) {
   if (it == allocs.begin()) return false;
   --it;
   return it->second.dev && a >= it->first && a + n <= it->first + it->second.size;
+}
+
+const Alloc *find(const void *p) {
+  const uintptr_t a = (uintptr_t)p;
+  auto it = allocs.upper_bound(a);
+  if (it == allocs.begin()) return nullptr;
+  --it;
+  return (a >= it->first && a < it->first + it->second.size + 256) ? &it->second : nullptr;
+}
+
+// a stream-ordered allocation touched by an operation on another stream (or
+// by a synchronous call, which runs on the legacy stream)
+bool wrong_stream(const void *p, cudaStream_t s) {
+  const Alloc *a = find(p);
+  return a && a->dev && a->ordered && a->stream != s;
 }
 
 cudaError_t fail(cudaError_t e) {
@@ -154,9 +173,15 @@ void *allocate(size_t n, bool dev) {
   return p;
 }
 
-cudaError_t copy(void *dst, const void *src, size_t n, cudaMemcpyKind k) {
+cudaError_t copy(void *dst, const void *src, size_t n, cudaMemcpyKind k, cudaStream_t stream) {
   std::lock_guard<std::mutex> lk(mu);
   init();
+  if ((k != cudaMemcpyHostToDevice && wrong_stream(src, stream)) ||
+      (k != cudaMemcpyDeviceToHost && wrong_stream(dst, stream))) {
+    char b[200];
+    snprintf(b, sizeof b, "copy on another stream than its stream-ordered allocation: dst %p src %p", dst, src);
+    violation(b);
+  }
   bool ok = true;
   if (k == cudaMemcpyHostToDevice) ok = inside_device(dst, n);
   else if (k == cudaMemcpyDeviceToHost) ok = inside_device(src, n);
@@ -308,14 +333,32 @@ cudaError_t cudaFree(void *p) {
 cudaError_t cudaFreeHost(void *p) { return cudaFree(p); }
 // stream-ordered allocation: the same host memory (no kernel runs, so stream
 // order is the call order)
-cudaError_t cudaMallocAsync(void **p, size_t n, cudaStream_t) { return cudaMalloc(p, n); }
-cudaError_t cudaFreeAsync(void *p, cudaStream_t) { return cudaFree(p); }
-cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind k) { return copy(d, s, n, k); }
-cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind k, cudaStream_t) {
-  return copy(d, s, n, k);
+cudaError_t cudaMallocAsync(void **p, size_t n, cudaStream_t st) {
+  const cudaError_t e = cudaMalloc(p, n);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(mu);
+    Alloc &a = allocs[(uintptr_t)*p];
+    a.ordered = true;
+    a.stream = st;
+  }
+  return e;
+}
+cudaError_t cudaFreeAsync(void *p, cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    init();
+    const Alloc *a = find(p);
+    if (a && !a->ordered) violation("cudaFreeAsync of memory from cudaMalloc");
+    if (wrong_stream(p, st)) violation("cudaFreeAsync on another stream than the allocation's");
+  }
+  return cudaFree(p);
+}
+cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind k) { return copy(d, s, n, k, nullptr); }
+cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind k, cudaStream_t st) {
+  return copy(d, s, n, k, st);
 }
 cudaError_t cudaMemcpy2DAsync(void *d, size_t dpitch, const void *s, size_t spitch, size_t w, size_t h,
-                              cudaMemcpyKind k, cudaStream_t) {
+                              cudaMemcpyKind k, cudaStream_t st) {
   if (w > dpitch || w > spitch) {
     std::lock_guard<std::mutex> lk(mu);
     init();
@@ -323,14 +366,15 @@ cudaError_t cudaMemcpy2DAsync(void *d, size_t dpitch, const void *s, size_t spit
     return fail(cudaErrorInvalidPitchValue);
   }
   for (size_t r = 0; r < h; ++r) {
-    cudaError_t e = copy(static_cast<char *>(d) + r * dpitch, static_cast<const char *>(s) + r * spitch, w, k);
+    cudaError_t e = copy(static_cast<char *>(d) + r * dpitch, static_cast<const char *>(s) + r * spitch, w, k, st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
-cudaError_t cudaMemset(void *p, int v, size_t n) {
+static cudaError_t set(void *p, int v, size_t n, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(mu);
   init();
+  if (wrong_stream(p, st)) violation("memset on another stream than its stream-ordered allocation");
   if (!inside_device(p, n)) {
     violation("memset outside its allocation");
     return fail(cudaErrorInvalidValue);
@@ -338,7 +382,8 @@ cudaError_t cudaMemset(void *p, int v, size_t n) {
   memset(p, v, n);
   return cudaSuccess;
 }
-cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t) { return cudaMemset(p, v, n); }
+cudaError_t cudaMemset(void *p, int v, size_t n) { return set(p, v, n, nullptr); }
+cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t st) { return set(p, v, n, st); }
 cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaEventCreate(cudaEvent_t *e) {
   *e = reinterpret_cast<cudaEvent_t>(malloc(8));

@@ -47,11 +47,13 @@ def describe(base, shape):
     return desc
 
 
-def solve_once(rt, desc):
-    """st_setup + st_solve; the error text, or None."""
+def solve_once(rt, desc, stream=0x1000):
+    """st_setup + st_solve on `stream` (any non-zero value names a stream of
+    its own: the stand-in runtime never dereferences it); the error text, or
+    None."""
     n = W.n_dofs(desc)
     try:
-        s = L.Solver(desc, 0)
+        s = L.Solver(desc, stream)
         u, w = rt.audit_alloc(8 * n), rt.audit_alloc(8 * n)
         ctypes.memset(u, 0, 8 * n)
         ctypes.memset(w, 0, 8 * n)
@@ -81,7 +83,8 @@ def main():
     if concurrent:
         from paper_2311_17500_gb300 import serve
         reqs = [dict(id=i, arrival=0.0, desc=describe(base, sh)) for i, sh in enumerate(args[1:])]
-        eng = serve.Engine(lambda r: solve_once(rt, r["desc"]), lambda r: 1, budget_bytes=concurrent,
+        eng = serve.Engine(lambda r: solve_once(rt, r["desc"], stream=0x1000 + 16 * r["id"]), lambda r: 1,
+                           budget_bytes=concurrent,
                            max_slots=concurrent)
         recs = eng.run(reqs)
         for sh, rec in zip(args[1:], recs):
