@@ -103,7 +103,14 @@ cudaError_t fail(cudaError_t e) {
   return e;
 }
 
-cudaError_t audit_launch(const void *fn, dim3 g, dim3 b, size_t dyn, int cluster) {
+// AUDIT_FORBID_NULL_STREAM: every caller passes a stream of its own, so a
+// launch or an asynchronous copy on the legacy stream ignored it
+bool forbid_null_stream() {
+  static const bool f = getenv("AUDIT_FORBID_NULL_STREAM") != nullptr;
+  return f;
+}
+
+cudaError_t audit_launch(const void *fn, dim3 g, dim3 b, size_t dyn, int cluster, cudaStream_t stream) {
   std::lock_guard<std::mutex> lk(mu);
   init();
   ++n_launch;
@@ -148,6 +155,7 @@ cudaError_t audit_launch(const void *fn, dim3 g, dim3 b, size_t dyn, int cluster
     violation(std::string("cluster size: ") + desc);
     e = cudaErrorInvalidValue;
   }
+  if (stream == nullptr && forbid_null_stream()) violation(std::string("launch on the legacy stream: ") + desc);
   if (e != cudaSuccess) last_error = e;
   return e;
 }
@@ -265,15 +273,15 @@ cudaError_t __cudaGetKernel(cudaKernel_t *k, const void *fn) {
   *k = (cudaKernel_t)fn;
   return cudaSuccess;
 }
-cudaError_t __cudaLaunchKernel(cudaKernel_t k, dim3 g, dim3 b, void **, size_t smem, cudaStream_t) {
-  return audit_launch((const void *)k, g, b, smem, 1);
+cudaError_t __cudaLaunchKernel(cudaKernel_t k, dim3 g, dim3 b, void **, size_t smem, cudaStream_t st) {
+  return audit_launch((const void *)k, g, b, smem, 1, st);
 }
 cudaError_t cudaLaunchKernelExC(const cudaLaunchConfig_t *c, const void *fn, void **) {
   int cluster = 1;
   for (unsigned i = 0; i < c->numAttrs; ++i)
     if (c->attrs[i].id == cudaLaunchAttributeClusterDimension)
       cluster = (int)(c->attrs[i].val.clusterDim.x * c->attrs[i].val.clusterDim.y * c->attrs[i].val.clusterDim.z);
-  return audit_launch(fn, c->gridDim, c->blockDim, c->dynamicSmemBytes, cluster);
+  return audit_launch(fn, c->gridDim, c->blockDim, c->dynamicSmemBytes, cluster, c->stream);
 }
 cudaError_t cudaFuncSetAttribute(const void *fn, cudaFuncAttribute a, int v) {
   std::lock_guard<std::mutex> lk(mu);
@@ -355,6 +363,11 @@ cudaError_t cudaFreeAsync(void *p, cudaStream_t st) {
 }
 cudaError_t cudaMemcpy(void *d, const void *s, size_t n, cudaMemcpyKind k) { return copy(d, s, n, k, nullptr); }
 cudaError_t cudaMemcpyAsync(void *d, const void *s, size_t n, cudaMemcpyKind k, cudaStream_t st) {
+  if (st == nullptr && forbid_null_stream()) {
+    std::lock_guard<std::mutex> lk(mu);
+    init();
+    violation("asynchronous copy on the legacy stream");
+  }
   return copy(d, s, n, k, st);
 }
 cudaError_t cudaMemcpy2DAsync(void *d, size_t dpitch, const void *s, size_t spitch, size_t w, size_t h,
@@ -383,7 +396,14 @@ static cudaError_t set(void *p, int v, size_t n, cudaStream_t st) {
   return cudaSuccess;
 }
 cudaError_t cudaMemset(void *p, int v, size_t n) { return set(p, v, n, nullptr); }
-cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t st) { return set(p, v, n, st); }
+cudaError_t cudaMemsetAsync(void *p, int v, size_t n, cudaStream_t st) {
+  if (st == nullptr && forbid_null_stream()) {
+    std::lock_guard<std::mutex> lk(mu);
+    init();
+    violation("asynchronous memset on the legacy stream");
+  }
+  return set(p, v, n, st);
+}
 cudaError_t cudaStreamSynchronize(cudaStream_t) { return cudaSuccess; }
 cudaError_t cudaEventCreate(cudaEvent_t *e) {
   *e = reinterpret_cast<cudaEvent_t>(malloc(8));

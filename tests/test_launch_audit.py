@@ -7,7 +7,10 @@ launch is checked against GB300 limits: block and grid extents, dynamic
 shared memory against the kernel's own limit (48 KB unless it opted in),
 shared memory per block, registers per block (from the ptxas report of the
 build), cluster size.  Every copy and memset is checked against its
-allocation, and every tensor map against the encoder's rules.
+allocation, and every tensor map against the encoder's rules.  Each handle
+gets a stream of its own, so no launch or asynchronous copy may use the legacy
+stream, and the stream-ordered allocations are checked against the streams of
+their copies, memsets and frees.
 
 One process runs every shape because shared-memory opt-ins are per process:
 the sequence starts with p = 3 and then moves to p = 2 wide-x shapes. That
@@ -90,7 +93,8 @@ def run(audit_env, shapes, **extra):
 
 
 def test_every_launch_within_limits(audit_env):
-    rows, log = run(audit_env, SHAPES)
+    # every handle gets a stream of its own: nothing may run on the legacy stream
+    rows, log = run(audit_env, SHAPES, AUDIT_FORBID_NULL_STREAM="1")
     bad = [line for line in log.splitlines() if line.startswith("VIOLATION")]
     assert not bad, "\n".join(bad[:10])
     for r in rows:
@@ -132,7 +136,7 @@ def test_requests_in_flight_together(audit_env):
     shapes = ["3,16,16,16", "2,194,33,64", "3,120,33,64", "2,216,33,64", "2,5,4,6", "3,4,5,5,5", "1,30,30,16",
               "4,20,20,8"]
     env = dict(os.environ, LD_LIBRARY_PATH=audit_env["dir"], AUDIT_RESOURCES=audit_env["table"],
-               AUDIT_LOG=os.path.join(audit_env["dir"], "launches_concurrent.log"))
+               AUDIT_LOG=os.path.join(audit_env["dir"], "launches_concurrent.log"), AUDIT_FORBID_NULL_STREAM="1")
     res = subprocess.run([sys.executable, os.path.join(AUDIT, "run_shapes.py"), "--concurrent", "4",
                           audit_env["lib"], *shapes], env=env, capture_output=True, text=True, timeout=900)
     assert res.returncode == 0, res.stderr[-3000:]
