@@ -9,7 +9,9 @@
 // per-block maximum, registers per block against the 64 K register file, and
 // cluster size.  Every copy and memset is checked against the allocation it
 // touches, and stream-ordered allocations (cudaMallocAsync) against the
-// stream of each copy, memset and free; every tiled tensor map against the
+// stream of each copy, memset and free; every pointer argument of a launch
+// (from the kernel's demangled signature) against the device allocations;
+// every tiled tensor map against the
 // encoder's rules (16-byte
 // base and strides, box extents 1..256, inner box a multiple of 16 bytes and
 // at most 128 bytes under 128-byte swizzling).  A launch that breaks a limit
@@ -49,10 +51,11 @@ struct Alloc {
 std::map<uintptr_t, Alloc> allocs;
 std::map<const void *, std::string> names;                // host stub -> kernel name
 std::map<std::string, std::pair<int, int>> resources;     // kernel name -> (registers, static smem)
+std::map<std::string, std::string> pointer_params;       // kernel name -> 'P' (pointer) / 'S' per parameter
 std::map<const void *, int> dyn_limit;                    // opt-ins
 thread_local cudaError_t last_error = cudaSuccess;
 FILE *logf = nullptr;
-long long n_launch = 0, n_violation = 0;
+long long n_launch = 0, n_violation = 0, n_pointer_checks = 0;
 long long device_bytes = 0, device_peak = 0;   // cudaMalloc'd and not yet freed
 
 void init() {
@@ -66,6 +69,12 @@ void init() {
     std::string name;
     int r, s;
     while (in >> name >> r >> s) resources[name] = {r, s};
+  }
+  const char *g = getenv("AUDIT_SIGNATURES");
+  if (g) {
+    std::ifstream in(g);
+    std::string name, kinds;
+    while (in >> name >> kinds) pointer_params[name] = kinds;
   }
 }
 
@@ -110,11 +119,29 @@ bool forbid_null_stream() {
   return f;
 }
 
-cudaError_t audit_launch(const void *fn, dim3 g, dim3 b, size_t dyn, int cluster, cudaStream_t stream) {
+cudaError_t audit_launch(const void *fn, dim3 g, dim3 b, size_t dyn, int cluster, cudaStream_t stream,
+                         void **args) {
   std::lock_guard<std::mutex> lk(mu);
   init();
   ++n_launch;
   const std::string name = names.count(fn) ? names[fn] : std::string("(unregistered)");
+  // every pointer parameter (of a known signature) must be null or point into
+  // a device allocation
+  auto sig = pointer_params.find(name);
+  if (args && sig != pointer_params.end()) {
+    for (size_t i = 0; i < sig->second.size(); ++i) {
+      if (sig->second[i] != 'P') continue;
+      const void *p = *static_cast<void *const *>(args[i]);
+      ++n_pointer_checks;
+      const Alloc *a = p ? find(p) : nullptr;
+      if (p && !(a && a->dev)) {
+        char b2[400];
+        snprintf(b2, sizeof b2, "pointer argument %zu of launch %lld %s outside every device allocation: %p", i,
+                 n_launch, name.c_str(), p);
+        violation(b2);
+      }
+    }
+  }
   int regs = 0, st = 0;
   auto r = resources.find(name);
   if (r != resources.end()) {
@@ -273,15 +300,15 @@ cudaError_t __cudaGetKernel(cudaKernel_t *k, const void *fn) {
   *k = (cudaKernel_t)fn;
   return cudaSuccess;
 }
-cudaError_t __cudaLaunchKernel(cudaKernel_t k, dim3 g, dim3 b, void **, size_t smem, cudaStream_t st) {
-  return audit_launch((const void *)k, g, b, smem, 1, st);
+cudaError_t __cudaLaunchKernel(cudaKernel_t k, dim3 g, dim3 b, void **args, size_t smem, cudaStream_t st) {
+  return audit_launch((const void *)k, g, b, smem, 1, st, args);
 }
-cudaError_t cudaLaunchKernelExC(const cudaLaunchConfig_t *c, const void *fn, void **) {
+cudaError_t cudaLaunchKernelExC(const cudaLaunchConfig_t *c, const void *fn, void **args) {
   int cluster = 1;
   for (unsigned i = 0; i < c->numAttrs; ++i)
     if (c->attrs[i].id == cudaLaunchAttributeClusterDimension)
       cluster = (int)(c->attrs[i].val.clusterDim.x * c->attrs[i].val.clusterDim.y * c->attrs[i].val.clusterDim.z);
-  return audit_launch(fn, c->gridDim, c->blockDim, c->dynamicSmemBytes, cluster, c->stream);
+  return audit_launch(fn, c->gridDim, c->blockDim, c->dynamicSmemBytes, cluster, c->stream, args);
 }
 cudaError_t cudaFuncSetAttribute(const void *fn, cudaFuncAttribute a, int v) {
   std::lock_guard<std::mutex> lk(mu);
@@ -452,6 +479,7 @@ cudaError_t cudaGetDriverEntryPointByVersion(const char *sym, void **fn, unsigne
 // read by the driver script
 long long audit_violations(void) { return n_violation; }
 long long audit_launches(void) { return n_launch; }
+long long audit_pointer_checks(void) { return n_pointer_checks; }
 // device bytes allocated and not freed; the peak since the last reset
 long long audit_device_bytes(void) { return device_bytes; }
 long long audit_device_peak_reset(void) {

@@ -79,6 +79,7 @@ def main():
     rt.audit_launches.restype = ctypes.c_longlong
     rt.audit_device_bytes.restype = ctypes.c_longlong
     rt.audit_device_peak_reset.restype = ctypes.c_longlong
+    rt.audit_pointer_checks.restype = ctypes.c_longlong
     base = W.serving_requests(n_req=1, seed=21)[0]["desc"]
     if concurrent:
         from paper_2311_17500_gb300 import serve
@@ -102,7 +103,8 @@ def main():
         peak = rt.audit_device_peak_reset() - b0
         print(json.dumps(dict(shape=shape, violations=rt.audit_violations() - v0,
                               launches=rt.audit_launches() - l0, error=err, peak_bytes=peak,
-                              footprint=L.footprint(desc) + 2 * 8 * W.n_dofs(desc))), flush=True)
+                              footprint=L.footprint(desc) + 2 * 8 * W.n_dofs(desc),
+                              pointer_checks=rt.audit_pointer_checks())), flush=True)
 
 
 if __name__ == "__main__":

@@ -77,11 +77,58 @@ def audit_env():
                     sm = re.search(r"(\d+) bytes smem", line)
                     f.write(f"{kernel} {m.group(1)} {sm.group(1) if sm else 0}\n")
                     kernel = None
-    return dict(lib=lib, dir=out, table=table)
+    sigs = os.path.join(out, "signatures.txt")
+    write_signatures(table, sigs)
+    return dict(lib=lib, dir=out, table=table, sigs=sigs)
+
+
+def parameter_kinds(demangled):
+    """'P' (pointer) or 'S' (anything else) per parameter of a demangled
+    function signature such as 'void f<float, 2>(float*, float const*, int)'."""
+    if not demangled.endswith(")"):
+        return None
+    depth, start = 0, None
+    for i in range(len(demangled) - 1, -1, -1):
+        c = demangled[i]
+        if c == ")":
+            depth += 1
+        elif c == "(":
+            depth -= 1
+            if depth == 0:
+                start = i
+                break
+    if start is None:
+        return None
+    params, depth, cur = [], 0, ""
+    for c in demangled[start + 1:-1]:
+        if c in "<(":
+            depth += 1
+        elif c in ">)":
+            depth -= 1
+        if c == "," and depth == 0:
+            params.append(cur.strip())
+            cur = ""
+        else:
+            cur += c
+    if cur.strip():
+        params.append(cur.strip())
+    return "".join("P" if p.endswith("*") else "S" for p in params)
+
+
+def write_signatures(table, path):
+    """Pointer parameters of every kernel, from its demangled name (c++filt)."""
+    names = [line.split()[0] for line in open(table) if line.strip()]
+    res = subprocess.run(["c++filt"], input="\n".join(names), capture_output=True, text=True, check=True)
+    with open(path, "w") as f:
+        for name, dem in zip(names, res.stdout.splitlines()):
+            kinds = parameter_kinds(dem.strip())
+            if kinds:
+                f.write(f"{name} {kinds}\n")
 
 
 def run(audit_env, shapes, **extra):
     env = dict(os.environ, LD_LIBRARY_PATH=audit_env["dir"], AUDIT_RESOURCES=audit_env["table"],
+               AUDIT_SIGNATURES=audit_env["sigs"],
                AUDIT_LOG=os.path.join(audit_env["dir"], "launches.log"), **extra)
     res = subprocess.run([sys.executable, os.path.join(AUDIT, "run_shapes.py"), audit_env["lib"], *shapes],
                          env=env, capture_output=True, text=True, timeout=900)
@@ -102,8 +149,10 @@ def test_every_launch_within_limits(audit_env):
         # set-up, linearization, both operators, the preconditioner and Arnoldi ran
         assert r["launches"] >= 60, r
         assert r["error"] is None or "CUDA error" not in r["error"], r
-    # the tensor-core transforms and their tensor maps were audited too
+    # the tensor-core transforms and their tensor maps were audited too, and the
+    # pointer arguments of the launches
     assert "tc_xform" in log and "tensor map" in log
+    assert rows[-1]["pointer_checks"] >= 10 * sum(r["launches"] for r in rows) // 10 > 0
 
 
 def test_footprint_bounds_what_a_handle_allocates(audit_env):
@@ -136,6 +185,7 @@ def test_requests_in_flight_together(audit_env):
     shapes = ["3,16,16,16", "2,194,33,64", "3,120,33,64", "2,216,33,64", "2,5,4,6", "3,4,5,5,5", "1,30,30,16",
               "4,20,20,8"]
     env = dict(os.environ, LD_LIBRARY_PATH=audit_env["dir"], AUDIT_RESOURCES=audit_env["table"],
+               AUDIT_SIGNATURES=audit_env["sigs"],
                AUDIT_LOG=os.path.join(audit_env["dir"], "launches_concurrent.log"), AUDIT_FORBID_NULL_STREAM="1")
     res = subprocess.run([sys.executable, os.path.join(AUDIT, "run_shapes.py"), "--concurrent", "4",
                           audit_env["lib"], *shapes], env=env, capture_output=True, text=True, timeout=900)
@@ -167,3 +217,45 @@ def test_audit_sees_a_stream_ordered_allocation_used_elsewhere(audit_env):
     rt.cudaMemsetAsync(p, 0, 4096, ctypes.c_void_p(0x2000))
     assert rt.audit_violations() == v0 + 1
     rt.cudaFreeAsync(p, ctypes.c_void_p(0x1000))
+
+
+CHECKER = r'''
+import ctypes, sys
+rt = ctypes.CDLL(sys.argv[1])
+rt.audit_violations.restype = ctypes.c_longlong
+class Dim3(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_uint), ("y", ctypes.c_uint), ("z", ctypes.c_uint)]
+class Config(ctypes.Structure):
+    _fields_ = [("grid", Dim3), ("block", Dim3), ("smem", ctypes.c_size_t), ("stream", ctypes.c_void_p),
+                ("attrs", ctypes.c_void_p), ("nattrs", ctypes.c_uint)]
+host_fn = ctypes.create_string_buffer(8)
+rt.__cudaRegisterFunction(None, host_fn, None, b"probe_kernel", -1, None, None, None, None, None)
+dev = ctypes.c_void_p()
+rt.cudaMalloc(ctypes.byref(dev), ctypes.c_size_t(256))
+def launch(ptr):
+    p = ctypes.c_void_p(ptr)
+    n = ctypes.c_int(3)
+    args = (ctypes.c_void_p * 2)(ctypes.cast(ctypes.byref(p), ctypes.c_void_p), ctypes.cast(ctypes.byref(n), ctypes.c_void_p))
+    cfg = Config(Dim3(1, 1, 1), Dim3(32, 1, 1), 0, None, None, 0)
+    rt.cudaLaunchKernelExC(ctypes.byref(cfg), host_fn, args)
+v0 = rt.audit_violations()
+launch(dev.value + 64)
+launch(0)
+v1 = rt.audit_violations()
+launch(ctypes.addressof(host_fn))
+print(v1 - v0, rt.audit_violations() - v1)
+'''
+
+
+def test_audit_sees_a_pointer_outside_the_device_allocations(audit_env, tmp_path):
+    """A launch whose pointer parameter points into no device allocation is
+    flagged; a pointer into an allocation, or null, is not."""
+    sigs = tmp_path / "sigs.txt"
+    sigs.write_text("probe_kernel PS\n")
+    script = tmp_path / "probe.py"
+    script.write_text(CHECKER)
+    env = dict(os.environ, AUDIT_SIGNATURES=str(sigs), AUDIT_LOG=str(tmp_path / "log.txt"))
+    res = subprocess.run([sys.executable, str(script), os.path.join(audit_env["dir"], "libcudart.so.13")],
+                         env=env, capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, res.stderr
+    assert res.stdout.split() == ["0", "1"]
