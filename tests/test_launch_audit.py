@@ -200,23 +200,35 @@ def test_requests_in_flight_together(audit_env):
     assert total["launches"] >= 60 * len(shapes)
 
 
-def test_audit_sees_a_stream_ordered_allocation_used_elsewhere(audit_env):
-    """The stand-in runtime flags a copy or memset of stream-ordered memory on
-    another stream than the one it was allocated on."""
-    import ctypes
-    rt = ctypes.CDLL(os.path.join(audit_env["dir"], "libcudart.so.13"))
-    rt.audit_violations.restype = ctypes.c_longlong
-    rt.cudaMallocAsync.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_void_p]
-    rt.cudaMemsetAsync.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]
-    rt.cudaFreeAsync.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
-    p = ctypes.c_void_p()
-    assert rt.cudaMallocAsync(ctypes.byref(p), 4096, ctypes.c_void_p(0x1000)) == 0
-    v0 = rt.audit_violations()
-    assert rt.cudaMemsetAsync(p, 0, 4096, ctypes.c_void_p(0x1000)) == 0
-    assert rt.audit_violations() == v0
-    rt.cudaMemsetAsync(p, 0, 4096, ctypes.c_void_p(0x2000))
-    assert rt.audit_violations() == v0 + 1
-    rt.cudaFreeAsync(p, ctypes.c_void_p(0x1000))
+STREAM_PROBE = r'''
+import ctypes, sys
+rt = ctypes.CDLL(sys.argv[1])
+rt.audit_violations.restype = ctypes.c_longlong
+rt.cudaMallocAsync.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_void_p]
+rt.cudaMemsetAsync.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p]
+rt.cudaFreeAsync.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+p = ctypes.c_void_p()
+assert rt.cudaMallocAsync(ctypes.byref(p), 4096, ctypes.c_void_p(0x1000)) == 0
+v0 = rt.audit_violations()
+rt.cudaMemsetAsync(p, 0, 4096, ctypes.c_void_p(0x1000))
+v1 = rt.audit_violations()
+rt.cudaMemsetAsync(p, 0, 4096, ctypes.c_void_p(0x2000))
+print(v1 - v0, rt.audit_violations() - v1)
+rt.cudaFreeAsync(p, ctypes.c_void_p(0x1000))
+'''
+
+
+def test_audit_sees_a_stream_ordered_allocation_used_elsewhere(audit_env, tmp_path):
+    """The stand-in runtime flags a memset of stream-ordered memory on another
+    stream than the one it was allocated on.  (A process of its own: one that
+    has loaded the real runtime would resolve the same library name to it.)"""
+    script = tmp_path / "stream_probe.py"
+    script.write_text(STREAM_PROBE)
+    env = dict(os.environ, AUDIT_LOG=str(tmp_path / "log.txt"))
+    res = subprocess.run([sys.executable, str(script), os.path.join(audit_env["dir"], "libcudart.so.13")],
+                         env=env, capture_output=True, text=True, timeout=120)
+    assert res.returncode == 0, res.stderr
+    assert res.stdout.split() == ["0", "1"]
 
 
 CHECKER = r'''
