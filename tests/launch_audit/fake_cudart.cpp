@@ -8,13 +8,12 @@
 // cudaFuncSetAttribute), static + dynamic shared memory against the 227 KB
 // per-block maximum, registers per block against the 64 K register file, and
 // cluster size.  Every copy and memset is checked against the allocation it
-// touches, and stream-ordered allocations (cudaMallocAsync) against the
-// stream of each copy, memset and free; every pointer argument of a launch
-// (from the kernel's demangled signature) against the device allocations;
-// every tiled tensor map against the
-// encoder's rules (16-byte
-// base and strides, box extents 1..256, inner box a multiple of 16 bytes and
-// at most 128 bytes under 128-byte swizzling).  A launch that breaks a limit
+// touches, stream-ordered allocations (cudaMallocAsync) against the stream of
+// each copy, memset and free, every pointer argument of a launch (from the
+// kernel's demangled signature) against the device allocations, and every
+// tiled tensor map against the encoder's rules (16-byte base and strides, box
+// extents 1..256, inner box a multiple of 16 bytes and at most 128 bytes under
+// 128-byte swizzling).  A launch that breaks a limit
 // is refused with the error the runtime gives for it, as the real runtime
 // would, and recorded.
 //
