@@ -5,7 +5,8 @@ fake_cudart.cpp); prints one JSON line per shape.
 usage: run_shapes.py [--concurrent K] LIBRARY SHAPE...
        with SHAPE = p,n_el_x[,n_el_y[,n_el_z]],n_el_t
 With --concurrent K the shapes go through the serving engine instead, with
-K requests in flight on K threads, each with its own handle.
+K requests in flight on K threads, each with its own handle.  With --api every
+entry point of the C ABI runs once per shape.
 """
 
 import ctypes
@@ -66,11 +67,56 @@ def solve_once(rt, desc, stream=0x1000):
     return None
 
 
+def exercise_api(rt, desc, stream=0x1000):
+    """Every entry point of the C ABI once on one handle (garbage values: only
+    the launches, copies and allocations are of interest); the error texts."""
+    n = W.n_dofs(desc)
+    errors = []
+
+    def call(name, fn):
+        try:
+            return fn()
+        except Exception as e:  # values read back are not results
+            errors.append(f"{name}: {e}")
+            return None
+
+    dev = {k: rt.audit_alloc(8 * n) for k in ("u", "w", "w2", "f", "x", "y", "sol")}
+    for k in dev:
+        ctypes.memset(dev[k], 0, 8 * n)
+    s = call("setup", lambda: L.Solver(desc, stream))
+    if s is None:
+        return errors
+    call("rhs", lambda: s.rhs(dev["f"]))
+    info = call("ionic", lambda: s.ionic(dev["u"], dev["w"])) or {}
+    call("linearize", lambda: s.linearize(dev["u"], dev["w"], "newton", keep_theta=True))
+    for prec in (L.ST_FP64, L.ST_MIXED):
+        call("apply", lambda: s.apply(dev["x"], dev["y"], prec))
+        call("precond", lambda: s.precond(dev["x"], dev["y"], prec))
+    call("linsolve", lambda: s.linsolve(dev["f"], dev["sol"], allow_unconverged=True))
+    call("wupdate", lambda: s.wupdate(dev["u"], dev["w2"]))
+    call("profile", lambda: s.profile(True))
+    call("apply (profiled)", lambda: s.apply(dev["x"], dev["y"], L.ST_MIXED))
+    call("profile_read", lambda: s.profile_read())
+    call("profile off", lambda: s.profile(False))
+    rank = int(info.get("rank", 0))
+    d = s.dims
+    for what, count in (("theta_hat", n), ("fd_eig", sum(d["n"][:desc["d"]])), ("lowrank_s", rank),
+                        ("lowrank_u", d["N_t"] * rank), ("lowrank_v", d["N_s"] * rank),
+                        ("tau_q", desc["p"] * desc["n_el_t"] * (desc["p"] + 1))):
+        call("get " + what, lambda: s.get(what, count))
+    call("close", s.close)
+    call("wupdate_static", lambda: L.wupdate_static(desc, dev["u"], dev["w2"], stream))
+    return errors
+
+
 def main():
     args = sys.argv[1:]
     concurrent = 0
+    api = False
     if args[0] == "--concurrent":
         concurrent, args = int(args[1]), args[2:]
+    if args[0] == "--api":
+        api, args = True, args[1:]
     L.load(args[0])
     rt = ctypes.CDLL("libcudart.so.13")
     rt.audit_alloc.restype = ctypes.c_void_p
@@ -91,6 +137,13 @@ def main():
         for sh, rec in zip(args[1:], recs):
             print(json.dumps(dict(shape=sh, status=rec["status"], error=rec["result"])), flush=True)
         print(json.dumps(dict(violations=rt.audit_violations(), launches=rt.audit_launches())), flush=True)
+        return
+    if api:
+        for shape in args[1:]:
+            v0, l0 = rt.audit_violations(), rt.audit_launches()
+            errs = exercise_api(rt, describe(base, shape))
+            print(json.dumps(dict(shape=shape, violations=rt.audit_violations() - v0,
+                                  launches=rt.audit_launches() - l0, errors=errs)), flush=True)
         return
     for shape in args[1:]:
         v0, l0 = rt.audit_violations(), rt.audit_launches()

@@ -271,3 +271,23 @@ def test_audit_sees_a_pointer_outside_the_device_allocations(audit_env, tmp_path
                          env=env, capture_output=True, text=True, timeout=120)
     assert res.returncode == 0, res.stderr
     assert res.stdout.split() == ["0", "1"]
+
+
+def test_every_entry_point(audit_env):
+    """Every entry point of the C ABI once per shape (right-hand side,
+    linearizations, both operators and preconditioners, the linear solve, the
+    w-updates with and without a handle, the per-stage timing, the internal
+    arrays): every launch, copy and pointer within the limits, no CUDA error."""
+    shapes = ["3,16,16,16", "2,194,33,64", "2,5,4,6", "1,6,7", "2,3,4,3,4", "4,6,5,7", "3,120,33,64:fp64"]
+    env = dict(os.environ, LD_LIBRARY_PATH=audit_env["dir"], AUDIT_RESOURCES=audit_env["table"],
+               AUDIT_SIGNATURES=audit_env["sigs"], AUDIT_FORBID_NULL_STREAM="1",
+               AUDIT_LOG=os.path.join(audit_env["dir"], "launches_api.log"))
+    res = subprocess.run([sys.executable, os.path.join(AUDIT, "run_shapes.py"), "--api", audit_env["lib"], *shapes],
+                         env=env, capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stderr[-3000:]
+    rows = [json.loads(line) for line in res.stdout.splitlines() if line.startswith("{")]
+    assert [r["shape"] for r in rows] == shapes
+    for r in rows:
+        assert r["violations"] == 0, r
+        assert r["launches"] >= 100, r
+        assert not [e for e in r["errors"] if "CUDA error" in e or "out of memory" in e], r
