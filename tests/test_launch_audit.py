@@ -291,3 +291,19 @@ def test_every_entry_point(audit_env):
         assert r["violations"] == 0, r
         assert r["launches"] >= 100, r
         assert not [e for e in r["errors"] if "CUDA error" in e or "out of memory" in e], r
+
+
+def test_serving_stream_in_arrival_order(audit_env):
+    """The 256 requests of the serving stream, in arrival order, in one
+    process (the order in which the fused pass's instances first ran when a
+    shared-memory opt-in was missing): no launch refused, no CUDA error, and
+    st_footprint above every handle's allocations.  Device memory is filled
+    only in its first MiB so that the large requests fit in host memory."""
+    import workloads as W
+    reqs = W.serving_requests(n_req=256, seed=4, rate=1.0)
+    shapes = [f'{r["desc"]["p"]},{r["desc"]["n_el"][0]},{r["desc"]["n_el"][1]},{r["desc"]["n_el_t"]}' for r in reqs]
+    rows, _ = run(audit_env, shapes, AUDIT_FORBID_NULL_STREAM="1", AUDIT_FILL_BYTES=str(1 << 20))
+    assert sum(r["violations"] for r in rows) == 0
+    for r in rows:
+        assert r["error"] is None or "CUDA error" not in r["error"], r
+        assert r["peak_bytes"] <= r["footprint"], r
