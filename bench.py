@@ -204,6 +204,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_linear_solve(solver, u2, w2, stream, reps):
+    """Time of one linear solve to relative residual 1e-8 (st_linsolve) with
+    the linearization frozen at the saved iterate (u2, w2) and x0 = u2; the
+    right-hand side is f.  Mean of `reps` solves after one untimed solve."""
+    import torch
+    n = u2.numel()
+    f = torch.zeros(n, dtype=torch.float64, device="cuda")
+    x = torch.empty_like(f)
+    solver.rhs(f.data_ptr())
+    solver.linearize(u2.data_ptr(), w2.data_ptr(), "picard")
+    out = None
+    times = []
+    for k in range(reps + 1):
+        x.copy_(u2)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        out = solver.linsolve(f.data_ptr(), x.data_ptr(), allow_unconverged=True)
+        ev1.record(stream)
+        ev1.synchronize()
+        if k > 0:
+            times.append(ev0.elapsed_time(ev1))
+    ms = sum(times) / len(times)
+    return {"ms": ms, "dof_per_s": n / (ms / 1000.0), "gmres_iters": out["gmres_iters"],
+            "outer_iters": out["outer_iters"], "rel_res": out["rel_res"]}
+
+
 def run_ours(args):
     import torch
     import workloads as W
@@ -333,6 +360,12 @@ def run_ours(args):
         em = sum(e_ms) / len(e_ms)
         e2e = {"value": ws * N / (em / 1000.0), "unit": "DoF/s", "h2d_bytes_per_step": 2 * 8 * N,
                "d2h_bytes_per_step": 2 * 8 * N}
+    # the linear solve alone, mixed and FP64, at the same frozen linearization
+    linear = {}
+    try:
+        linear["mixed"] = time_linear_solve(s, u2, w2, stream, max(3, args.steps // 2))
+    except Exception as e:  # noqa: BLE001 (reported in the line, never fatal)
+        linear["mixed"] = {"error": f"{type(e).__name__}: {e}"}
     s.close()
 
     fp64 = None
@@ -348,6 +381,12 @@ def run_ours(args):
         fm = sum(f_ms) / len(f_ms)
         fp64 = {"value": N / (fm / 1000.0), "ms_per_step": fm, "gmres_iters": f_st["gmres_iters"],
                 "rel_res": f_st["rel_res"], "setup_s": setup64, "speedup_mixed_vs_fp64": fm / ms_step}
+        try:
+            linear["fp64"] = time_linear_solve(s64, u2, w2, stream, 1)
+            if "ms" in linear.get("mixed", {}):
+                linear["speedup_mixed_vs_fp64"] = linear["fp64"]["ms"] / linear["mixed"]["ms"]
+        except Exception as e:  # noqa: BLE001
+            linear["fp64"] = {"error": f"{type(e).__name__}: {e}"}
         s64.close()
 
     serving = None
@@ -385,6 +424,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": roof,
         "fp64": fp64,
+        "linear_solve": linear,
         "e2e": e2e,
         "clocks": clocks,
         "cpu_baseline": cpu,
