@@ -1,4 +1,4 @@
-"""Host flow of bench.py's serving pass on the CPU: the device calls are
+"""Host flows of bench.py on the CPU (the serving pass, the linear-solve timing): the device calls are
 replaced by host fakes (a runner that sleeps in proportion to a request's
 unknowns), so the saturated pass, the rate rule and the fields of the JSON
 line are checked without a GPU."""
@@ -43,3 +43,54 @@ def test_serving_pass_fields_and_rate_rule(monkeypatch):
     assert cfg["peak_admitted_gb"] * 1e9 <= cfg["budget_gb"] * 1e9 + 1
     given = bench.serving_pass(6, 50.0, 2, 0, clocks=False)
     assert given["config"]["rate_rule"] == "given" and given["config"]["saturated"] is None
+
+
+def test_linear_solve_timing_flow(monkeypatch):
+    """bench.time_linear_solve on the CPU: device tensors and events replaced
+    by host fakes; the frozen linearization is taken once, every solve starts
+    from the saved iterate, and the untimed first solve is left out."""
+    torch = pytest.importorskip("torch")
+    sys.path.insert(0, ROOT)
+    import bench
+
+    zeros = torch.zeros
+    monkeypatch.setattr(torch, "zeros", lambda *a, **k: zeros(*a, **{x: v for x, v in k.items() if x != "device"}))
+
+    class Event:
+        clock = [0.0]
+
+        def __init__(self, enable_timing=False):
+            self.t = None
+
+        def record(self, stream=None):
+            Event.clock[0] += 1.0
+            self.t = Event.clock[0]
+
+        def synchronize(self):
+            pass
+
+        def elapsed_time(self, other):
+            return other.t - self.t
+
+    monkeypatch.setattr(torch.cuda, "Event", Event)
+
+    class Solver:
+        def __init__(self):
+            self.calls = []
+
+        def rhs(self, f):
+            self.calls.append("rhs")
+
+        def linearize(self, u, w, kind):
+            self.calls.append(("linearize", kind))
+
+        def linsolve(self, b, x, allow_unconverged=False):
+            self.calls.append("linsolve")
+            return dict(gmres_iters=11, outer_iters=2, rel_res=3e-9)
+
+    u2 = torch.arange(5, dtype=torch.float64)
+    s = Solver()
+    out = bench.time_linear_solve(s, u2, u2 * 0, None, 3)
+    assert s.calls == ["rhs", ("linearize", "picard")] + ["linsolve"] * 4
+    assert out["ms"] == pytest.approx(1.0) and out["dof_per_s"] == pytest.approx(5 / 1e-3)
+    assert out["gmres_iters"] == 11 and out["outer_iters"] == 2 and out["rel_res"] == 3e-9
