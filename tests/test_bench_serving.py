@@ -1,7 +1,7 @@
-"""Host flows of bench.py on the CPU (the serving pass, the linear-solve timing): the device calls are
-replaced by host fakes (a runner that sleeps in proportion to a request's
-unknowns), so the saturated pass, the rate rule and the fields of the JSON
-line are checked without a GPU."""
+"""Host flows of bench.py on the CPU: the serving pass and the linear-solve
+timing.  The device calls are replaced by host fakes (a runner that sleeps in
+proportion to a request's unknowns, host events), so the saturated pass, the
+rate rule and the fields of the JSON line are checked without a GPU."""
 
 import os
 import sys
