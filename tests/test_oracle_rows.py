@@ -86,3 +86,23 @@ def test_local_tables_equal_the_global_ones(c):
         assert np.array_equal(OR.local_table(st, ks, es), st.stab(ks)[es])
     for et in range(st.n_el_t):
         assert np.array_equal(OR.local_glob(st, et, es), st.glob(et)[es])
+
+
+@pytest.mark.parametrize("name", ["c2_aniso_2d", "c3_cube_3d"])
+def test_full_size_oracle_side_runs(name):
+    """The oracle's part of the full-size GPU checks at the workloads' real
+    sizes (4.43 M and 37.1 M unknowns): the sampled rows of f, of both
+    operators and of the preconditioner come out finite, in seconds, and the
+    rows hit the stimulus."""
+    from oracle.spacetime import SpaceTime
+    from tests import sampled_rows as SR
+    desc = W.config(name)
+    desc.update(stabilization="galerkin", precision="mixed")
+    st = SpaceTime(desc)
+    rows = SR.sample_rows(st, desc, seed=5)
+    inp = SR.linearization_inputs(st.N_dof)
+    f = OR.load_rows(st, OR.source_fn(st, desc), rows)
+    y = OR.apply_rows(st, OR.picard_galerkin_terms(st, desc, inp["u"], inp["w"]), rows, inp["x"])
+    z = OR.apply_rows(st, OR.precond_terms(st, desc), rows, inp["r"])
+    assert np.all(np.isfinite(f)) and np.all(np.isfinite(y)) and np.all(np.isfinite(z))
+    assert np.abs(f).max() > 0.0 and np.abs(y).max() > 0.0
