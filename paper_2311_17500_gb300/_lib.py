@@ -133,7 +133,7 @@ def make_desc(desc):
         raise ValueError("too many stimulus boxes")
     c.n_stim = len(boxes)
     for k, bx in enumerate(boxes):
-        for l in range(c.d):
+        for l in range(min(c.d, 3)):   # d > 3 is left to the library to reject
             c.stim[k].lo[l] = bx["lo"][l]
             c.stim[k].hi[l] = bx["hi"][l]
         c.stim[k].t0, c.stim[k].t1, c.stim[k].amp = bx["t0"], bx["t1"], bx["amp"]

@@ -45,3 +45,27 @@ def test_binding_struct_matches_header_field_order():
         for part in f.split(","):
             names.append(re.sub(r"\[.*\]", "", part).strip())
     assert names == [n for n, _ in StProblemDesc._fields_]
+
+
+def test_footprint_validates_and_grows():
+    """st_footprint is pure host logic: it rejects invalid descriptions with
+    ST_ERR_ARG and grows with every size that allocates (no GPU needed)."""
+    import workloads as W
+    from paper_2311_17500_gb300 import _lib as L
+    from paper_2311_17500_gb300 import build
+    build.build()
+    base = W.config("c1_newton_2d")
+    fp = L.footprint(base)
+    assert fp > 0
+    four_d = dict(d=4, n_el=[16] * 4, D=[1e-3] * 4,
+                  source=dict(kind="stim", boxes=[W.stim_box([0] * 4, [0.1] * 4, 0, 1, 1)]))
+    for bad in (dict(p=0), dict(p=5), four_d, dict(n_el=[0, 16]), dict(n_el_t=0), dict(T=-1.0),
+                dict(D=[0.0, 1e-3]), dict(gmres_m=0), dict(gmres_m=501), dict(rtol=0.0), dict(alpha=1.5),
+                dict(max_fp=0), dict(eps_theta=-0.1)):
+        desc = dict(base, **bad)
+        with pytest.raises(L.StError) as e:
+            L.footprint(desc)
+        assert e.value.code == L.ST_ERR_ARG, bad
+    for grow in (dict(n_el_t=64), dict(n_el=[32, 16]), dict(n_el=[16, 32]), dict(gmres_m=200), dict(p=3)):
+        assert L.footprint(dict(base, **grow)) > fp, grow
+    assert L.footprint(dict(base, precision="fp64")) > L.footprint(dict(base, precision="mixed"))
