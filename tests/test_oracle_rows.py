@@ -68,7 +68,7 @@ def test_full_size_checks_on_a_small_mesh():
     A = o.operator(model.reaction_coef(desc, fl["u"], fl["w"]))
     SR.check_apply(st, desc, rows, inp, A @ inp["x"], 1e-12)
     z = spla.spsolve(o.precond_matrix().tocsc(), inp["r"])
-    SR.check_precond(st, desc, rows, inp, z, 1e-9)
+    SR.check_precond(st, desc, rows, inp, z, 1e-9)   # exact solve: far below SR.PRECOND_RESIDUAL_TOL
     x = spla.spsolve(A.tocsc(), f)
     SR.check_solution(st, desc, rows, inp, f_rows, np.linalg.norm(f), x, 1e-8)
     bad = A @ inp["x"]
