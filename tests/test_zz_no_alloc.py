@@ -1,7 +1,7 @@
 """The allocation-free w-update (st_wupdate_static) against st_wupdate.
 
-The file name keeps it last in collection, so it also runs after every other
-GPU test has used the device.  Two calls in a row on different problems (the
+The file name keeps it late in collection, after the parity, serving and
+tensor-core tests have used the device.  Two calls in a row on different problems (the
 second overwrites the fixed device scratch with other bands), then a problem
 that fills the scratch exactly; each result is compared with st_wupdate on a
 handle set up from the same description, at the tolerance of the FP64
