@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--rate", type=float, default=0.0,
                     help="--serve: Poisson arrival rate (requests/s); 0 = 0.8 x the measured saturated rate")
     ap.add_argument("--slots", type=int, default=8, help="--serve: requests in flight at most")
+    ap.add_argument("--serve-log", default=None, help="--serve: write one JSON line per request to this file")
     ap.add_argument("--serve-requests", type=int, default=64,
                     help="requests of the short serving pass in the default run (0: none)")
     return ap.parse_args()
@@ -436,7 +437,7 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def serving_pass(n_requests, rate, slots, local, clocks=True):
+def serving_pass(n_requests, rate, slots, local, clocks=True, log_path=None):
     """The serving stream: seeded 2D requests (p in {2,3}, 32..256 elements per
     direction, 64..512 time elements, D log-uniform, a stimulus at a uniform
     position) arriving as a Poisson stream.  A request is st_setup and one
@@ -502,6 +503,16 @@ def serving_pass(n_requests, rate, slots, local, clocks=True):
                 d = desc_of(reqs[r["id"]])
                 print(f"request {r['id']} ({d['p']}, {d['n_el']}, {d['n_el_t']}): {r['error']}", file=sys.stderr)
     iters = [r["result"]["stats"]["total_gmres"] for r in recs if r["status"] == "done"]
+    if log_path:
+        # one JSON line per request: its shape, its times and how it ended
+        with open(log_path, "w") as f:
+            for r in recs:
+                d = desc_of(reqs[r["id"]])
+                f.write(json.dumps({"id": r["id"], "p": d["p"], "n_el": d["n_el"], "n_el_t": d["n_el_t"],
+                                    "n_dof": W.n_dofs(d), "arrival_s": r["arrival"], "admitted_s": r["admitted"],
+                                    "done_s": r["done"], "status": r["status"], "retries": r["retries"],
+                                    "gmres": (r["result"] or {}).get("stats", {}).get("total_gmres"),
+                                    "error": r["error"]}) + "\n")
     fields = {
         "value": out.get("dof_per_s"), "unit": "DoF/s",
         "latency_ms": {"p50": 1e3 * out["p50_s"], "p99": 1e3 * out["p99_s"], "mean": 1e3 * out["mean_s"]}
@@ -540,7 +551,7 @@ def run_serve(args):
     P.load()
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
-    fields = serving_pass(args.requests, args.rate, args.slots, local)
+    fields = serving_pass(args.requests, args.rate, args.slots, local, log_path=args.serve_log)
     line = {"metric": "serving stream: unknowns/s over the makespan and arrival-to-completion latency p50/p99",
             "n_gpus": 1, "higher_is_better": True, "dtype": "f32+df64+f64", "data": "synthetic", **fields}
     if rank == 0:

@@ -12,7 +12,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def test_serving_pass_fields_and_rate_rule(monkeypatch):
+def test_serving_pass_fields_and_rate_rule(monkeypatch, tmp_path):
     torch = pytest.importorskip("torch")
     sys.path.insert(0, ROOT)
     import bench
@@ -30,7 +30,13 @@ def test_serving_pass_fields_and_rate_rule(monkeypatch):
     monkeypatch.setattr(serve, "gpu_footprint", lambda desc_of: (lambda r: 1 << 20))
     monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
     monkeypatch.setattr(torch.cuda, "mem_get_info", lambda *a, **k: (64 << 20, 128 << 20))
-    f = bench.serving_pass(12, 0.0, 4, 0, clocks=False)
+    log = tmp_path / "requests.jsonl"
+    f = bench.serving_pass(12, 0.0, 4, 0, clocks=False, log_path=str(log))
+    import json
+    lines = [json.loads(x) for x in log.read_text().splitlines()]
+    assert [x["id"] for x in lines] == list(range(12))
+    assert all(x["status"] == "done" and x["done_s"] >= x["admitted_s"] >= 0.0 for x in lines)
+    assert all(x["n_dof"] == W.n_dofs(dict(x, d=2)) for x in lines)
     cfg = f["config"]
     assert f["done"] == 12 and f["failed"] == 0 and f["rejected"] == 0
     sat = cfg["saturated"]
