@@ -10,7 +10,10 @@ instead of blocking the queue.  Each admitted request runs in a worker
 thread on its own CUDA stream (the library's entry points release the GIL,
 so the kernels of the requests in flight overlap on the device); its memory
 is returned to the budget when it completes.  A request whose run raises is
-recorded as failed and its memory is returned as well.
+recorded as failed and its memory is returned as well; one that ran out of
+device memory held outside the budget may go back to the head of the queue
+instead (see Engine).  A record's "error" keeps the last failure, also for a
+request that completed after a retry.
 
 The engine itself is plain Python and device-agnostic: `run_request` does the
 work of one request and `footprint` sizes it.  `gpu_runner` and
