@@ -138,6 +138,11 @@ cudaError_t audit_launch(const void *fn, dim3 g, dim3 b, size_t dyn, int cluster
         snprintf(b2, sizeof b2, "pointer argument %zu of launch %lld %s outside every device allocation: %p", i,
                  n_launch, name.c_str(), p);
         violation(b2);
+      } else if (a && a->ordered && a->stream != stream) {
+        char b2[400];
+        snprintf(b2, sizeof b2, "pointer argument %zu of launch %lld %s: stream-ordered memory of another stream",
+                 i, n_launch, name.c_str());
+        violation(b2);
       }
     }
   }

@@ -244,24 +244,32 @@ host_fn = ctypes.create_string_buffer(8)
 rt.__cudaRegisterFunction(None, host_fn, None, b"probe_kernel", -1, None, None, None, None, None)
 dev = ctypes.c_void_p()
 rt.cudaMalloc(ctypes.byref(dev), ctypes.c_size_t(256))
-def launch(ptr):
+def launch(ptr, stream=None):
     p = ctypes.c_void_p(ptr)
     n = ctypes.c_int(3)
     args = (ctypes.c_void_p * 2)(ctypes.cast(ctypes.byref(p), ctypes.c_void_p), ctypes.cast(ctypes.byref(n), ctypes.c_void_p))
-    cfg = Config(Dim3(1, 1, 1), Dim3(32, 1, 1), 0, None, None, 0)
+    cfg = Config(Dim3(1, 1, 1), Dim3(32, 1, 1), 0, stream, None, 0)
     rt.cudaLaunchKernelExC(ctypes.byref(cfg), host_fn, args)
 v0 = rt.audit_violations()
 launch(dev.value + 64)
 launch(0)
 v1 = rt.audit_violations()
 launch(ctypes.addressof(host_fn))
-print(v1 - v0, rt.audit_violations() - v1)
+v2 = rt.audit_violations()
+rt.cudaMallocAsync.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_size_t, ctypes.c_void_p]
+pooled = ctypes.c_void_p()
+rt.cudaMallocAsync(ctypes.byref(pooled), 256, ctypes.c_void_p(0x1000))
+launch(pooled.value, 0x1000)
+v3 = rt.audit_violations()
+launch(pooled.value, 0x2000)
+print(v1 - v0, v2 - v1, v3 - v2, rt.audit_violations() - v3)
 '''
 
 
 def test_audit_sees_a_pointer_outside_the_device_allocations(audit_env, tmp_path):
     """A launch whose pointer parameter points into no device allocation is
-    flagged; a pointer into an allocation, or null, is not."""
+    flagged, and so is one on another stream than its stream-ordered memory; a
+    pointer into an allocation, or null, is not."""
     sigs = tmp_path / "sigs.txt"
     sigs.write_text("probe_kernel PS\n")
     script = tmp_path / "probe.py"
@@ -270,7 +278,7 @@ def test_audit_sees_a_pointer_outside_the_device_allocations(audit_env, tmp_path
     res = subprocess.run([sys.executable, str(script), os.path.join(audit_env["dir"], "libcudart.so.13")],
                          env=env, capture_output=True, text=True, timeout=120)
     assert res.returncode == 0, res.stderr
-    assert res.stdout.split() == ["0", "1"]
+    assert res.stdout.split() == ["0", "1", "0", "1"]
 
 
 def test_every_entry_point(audit_env):
