@@ -152,7 +152,7 @@ def test_every_launch_within_limits(audit_env):
     # the tensor-core transforms and their tensor maps were audited too, and the
     # pointer arguments of the launches
     assert "tc_xform" in log and "tensor map" in log
-    assert rows[-1]["pointer_checks"] >= 10 * sum(r["launches"] for r in rows) // 10 > 0
+    assert rows[-1]["pointer_checks"] >= sum(r["launches"] for r in rows) > 0   # every kernel takes a pointer
 
 
 def test_footprint_bounds_what_a_handle_allocates(audit_env):
