@@ -137,7 +137,10 @@ st_status st_footprint(const st_problem_desc *desc, size_t *bytes);
  * C_m W_t + (mu_j + a c1) M_t per spatial eigenvalue mu_j (Sec. 3.2,
  * Eq. preconditioner, with the conductivity scaling of each direction), and the
  * right-hand side f of Eq. (rhsfun).  `cuda_stream` is a cudaStream_t (NULL =
- * legacy default stream).  On success *out owns every device buffer. */
+ * legacy default stream).  On success *out owns every device buffer.  The
+ * handle belongs to the device current at this call: every later call on it
+ * runs there, whatever device the calling thread has current, and restores
+ * the thread's device on return. */
 st_status st_setup(const st_problem_desc *desc, void *cuda_stream, st_handle **out);
 
 /* Release every resource of the handle (NULL is accepted). */

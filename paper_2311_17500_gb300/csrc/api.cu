@@ -333,6 +333,21 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
 }  // namespace
 
 // ---------------------------------------------------------------- internals
+namespace {
+// A handle's entry points run on the handle's device, whatever device the
+// calling thread has current; the thread's device is restored on return.
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess) prev = cur;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+}  // namespace
+
 static std::atomic<long long> g_launches{0};
 
 namespace {
@@ -882,20 +897,22 @@ st_status st_footprint(const st_problem_desc *desc, size_t *bytes) {
 
 st_status st_destroy(st_handle *h) {
   if (!h) return ST_OK;
-  cudaSetDevice(h->dev);
-  cudaStreamSynchronize(h->stream);
-  if (h->pooled) {
-    // freed in stream order, then waited for on this stream alone, so the
-    // memory is back in the pool when the call returns
-    for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
+  {
+    DeviceScope ds(h->dev);
     cudaStreamSynchronize(h->stream);
-  } else {
-    for (void *p : h->allocs) cudaFree(p);
+    if (h->pooled) {
+      // freed in stream order, then waited for on this stream alone, so the
+      // memory is back in the pool when the call returns
+      for (void *p : h->allocs) cudaFreeAsync(p, h->stream);
+      cudaStreamSynchronize(h->stream);
+    } else {
+      for (void *p : h->allocs) cudaFree(p);
+    }
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->arn_ev)
+      if (e) cudaEventDestroy(e);
+    pinned_release(h->red_host);
   }
-  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
-  for (cudaEvent_t e : h->arn_ev)
-    if (e) cudaEventDestroy(e);
-  pinned_release(h->red_host);
   delete h;
   return ST_OK;
 }
@@ -1142,6 +1159,7 @@ st_status st_linearize(st_handle *h, const double *u, const double *w, int kind,
                        st_ionic_info *info) {
   if (!h || !u || !w) return ST_ERR_ARG;
   if (kind != ST_PICARD && kind != ST_NEWTON) return ST_ERR_ARG;
+  DeviceScope ds(h->dev);
   bool su = h->desc.stabilization == ST_SU;
   bool stats = !keep_theta;
   {
@@ -1183,6 +1201,7 @@ st_status st_ionic(st_handle *h, const double *u, const double *w, st_ionic_info
 st_status st_apply(st_handle *h, int prec, const void *x, void *y) {
   if (!h || !x || !y || x == y) return ST_ERR_ARG;
   if (!h->have_lin) return ST_ERR_STATE;
+  DeviceScope ds(h->dev);
   if (prec == ST_FP64) return apply_T<double>(h, (const double *)x, (double *)y);
   if (prec == ST_MIXED) return apply_T<float>(h, (const float *)x, (float *)y);
   return ST_ERR_ARG;
@@ -1190,6 +1209,7 @@ st_status st_apply(st_handle *h, int prec, const void *x, void *y) {
 
 st_status st_precond(st_handle *h, int prec, const void *r, void *z) {
   if (!h || !r || !z) return ST_ERR_ARG;
+  DeviceScope ds(h->dev);
   if (prec == ST_FP64) return precond_T<double>(h, (const double *)r, (double *)z);
   if (prec == ST_MIXED) return precond_T<float>(h, (const float *)r, (float *)z);
   return ST_ERR_ARG;
@@ -1197,12 +1217,14 @@ st_status st_precond(st_handle *h, int prec, const void *r, void *z) {
 
 st_status st_rhs(st_handle *h, double *f) {
   if (!h || !f) return ST_ERR_ARG;
+  DeviceScope ds(h->dev);
   ST_CUDA(cudaMemcpyAsync(f, h->f64, h->Ndof * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   return ST_OK;
 }
 
 st_status st_wupdate(st_handle *h, const double *u, double *w) {
   if (!h || !u || !w || u == w) return ST_ERR_ARG;
+  DeviceScope ds(h->dev);
   return wupdate_run(h, u, w);
 }
 
@@ -1221,6 +1243,7 @@ st_status st_wupdate_static(const st_problem_desc *desc, const double *u, double
 st_status st_linsolve(st_handle *h, const double *b, double *x, st_stats *stats) {
   if (!h || !b || !x) return ST_ERR_ARG;
   if (!h->have_lin) return ST_ERR_STATE;
+  DeviceScope ds(h->dev);
   cudaStream_t s = h->stream;
   const st_problem_desc &D = h->desc;
   long long N = h->Ndof;
@@ -1268,6 +1291,7 @@ st_status st_linsolve(st_handle *h, const double *b, double *x, st_stats *stats)
 
 st_status st_solve(st_handle *h, double *u, double *w, st_stats *stats) {
   if (!h || !u || !w) return ST_ERR_ARG;
+  DeviceScope ds(h->dev);
   cudaStream_t s = h->stream;
   const st_problem_desc &D = h->desc;
   long long N = h->Ndof;
@@ -1335,6 +1359,7 @@ st_status st_tc_selftest(int *usable, double *max_rel_err) {
 
 st_status st_profile(st_handle *h, int enable) {
   if (!h) return ST_ERR_ARG;
+  DeviceScope ds(h->dev);
   ST_CUDA(cudaStreamSynchronize(h->stream));
   h->prof.clear();
   h->ev_used = 0;
@@ -1344,6 +1369,7 @@ st_status st_profile(st_handle *h, int enable) {
 
 st_status st_profile_read(st_handle *h, int cat, double *ms, double *bytes, double *flops, long long *launches) {
   if (!h || cat < 0 || cat >= PROF_NCAT || !ms || !bytes || !flops || !launches) return ST_ERR_ARG;
+  DeviceScope ds(h->dev);
   ST_CUDA(cudaStreamSynchronize(h->stream));
   double t = 0.0, b = 0.0, f = 0.0;
   long long n = 0;
@@ -1359,6 +1385,7 @@ st_status st_profile_read(st_handle *h, int cat, double *ms, double *bytes, doub
 
 st_status st_get(st_handle *h, int what, void *dst, size_t bytes) {
   if (!h || !dst) return ST_ERR_ARG;
+  DeviceScope ds(h->dev);
   cudaStream_t s = h->stream;
   size_t need = 0;
   const void *src = nullptr;

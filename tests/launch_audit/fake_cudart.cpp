@@ -46,7 +46,9 @@ struct Alloc {
   bool dev;
   bool ordered = false;           // from cudaMallocAsync: usable in the order of `stream`
   cudaStream_t stream = nullptr;
+  int device = 0;                 // the device current when it was allocated
 };
+thread_local int current_device = 0;
 std::map<uintptr_t, Alloc> allocs;
 std::map<const void *, std::string> names;                // host stub -> kernel name
 std::map<std::string, std::pair<int, int>> resources;     // kernel name -> (registers, static smem)
@@ -138,6 +140,11 @@ cudaError_t audit_launch(const void *fn, dim3 g, dim3 b, size_t dyn, int cluster
         snprintf(b2, sizeof b2, "pointer argument %zu of launch %lld %s outside every device allocation: %p", i,
                  n_launch, name.c_str(), p);
         violation(b2);
+      } else if (a && a->device != current_device) {
+        char b2[400];
+        snprintf(b2, sizeof b2, "pointer argument %zu of launch %lld %s: memory of device %d, launch on device %d",
+                 i, n_launch, name.c_str(), a->device, current_device);
+        violation(b2);
       } else if (a && a->ordered && a->stream != stream) {
         char b2[400];
         snprintf(b2, sizeof b2, "pointer argument %zu of launch %lld %s: stream-ordered memory of another stream",
@@ -203,7 +210,9 @@ void *allocate(size_t n, bool dev) {
   const size_t nfill = (sz < fill_limit ? sz : fill_limit) / 8;
   for (size_t i = 0; i < nfill; ++i) q[i] = kFill;
   std::lock_guard<std::mutex> lk(mu);
-  allocs[(uintptr_t)p] = Alloc{n, dev};
+  Alloc rec{n, dev};
+  rec.device = current_device;
+  allocs[(uintptr_t)p] = rec;
   if (dev) {
     if (logf) fprintf(logf, "alloc %zu\n", n);
     device_bytes += (long long)n;
@@ -343,10 +352,14 @@ cudaError_t cudaDeviceGetAttribute(int *v, cudaDeviceAttr a, int) {
   return cudaSuccess;
 }
 cudaError_t cudaGetDevice(int *d) {
-  *d = 0;
+  *d = current_device;
   return cudaSuccess;
 }
-cudaError_t cudaSetDevice(int) { return cudaSuccess; }
+cudaError_t cudaSetDevice(int d) {
+  if (d < 0 || d > 7) return fail(cudaErrorInvalidDevice);
+  current_device = d;
+  return cudaSuccess;
+}
 cudaError_t cudaMalloc(void **p, size_t n) {
   *p = allocate(n, true);
   return *p ? cudaSuccess : fail(cudaErrorMemoryAllocation);

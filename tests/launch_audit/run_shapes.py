@@ -6,7 +6,9 @@ usage: run_shapes.py [--concurrent K] LIBRARY SHAPE...
        with SHAPE = p,n_el_x[,n_el_y[,n_el_z]],n_el_t
 With --concurrent K the shapes go through the serving engine instead, with
 K requests in flight on K threads, each with its own handle.  With --api every
-entry point of the C ABI runs once per shape.
+entry point of the C ABI runs once per shape.  With --other-device D the
+calling thread has device D current during st_solve (the handle was set up
+on device 0).
 """
 
 import ctypes
@@ -48,20 +50,29 @@ def describe(base, shape):
     return desc
 
 
-def solve_once(rt, desc, stream=0x1000):
+def solve_once(rt, desc, stream=0x1000, other_device=None):
     """st_setup + st_solve on `stream` (any non-zero value names a stream of
-    its own: the stand-in runtime never dereferences it); the error text, or
-    None."""
+    its own: the stand-in runtime never dereferences it); with other_device,
+    the calling thread has that device current during st_solve.  The error
+    text, or None."""
     n = W.n_dofs(desc)
     try:
         s = L.Solver(desc, stream)
         u, w = rt.audit_alloc(8 * n), rt.audit_alloc(8 * n)
         ctypes.memset(u, 0, 8 * n)
         ctypes.memset(w, 0, 8 * n)
+        if other_device is not None:
+            rt.cudaSetDevice(other_device)
         try:
             s.solve(u, w, allow_unconverged=True)
         finally:
             s.close()
+            if other_device is not None:
+                cur = ctypes.c_int(-1)
+                rt.cudaGetDevice(ctypes.byref(cur))
+                rt.cudaSetDevice(0)
+                if cur.value != other_device:
+                    return "the calling thread's device was not restored"
     except Exception as e:  # values read back are not results: a NaN exit is expected
         return str(e)
     return None
@@ -117,6 +128,9 @@ def main():
         concurrent, args = int(args[1]), args[2:]
     if args[0] == "--api":
         api, args = True, args[1:]
+    other = None
+    if args[0] == "--other-device":
+        other, args = int(args[1]), args[2:]
     L.load(args[0])
     rt = ctypes.CDLL("libcudart.so.13")
     rt.audit_alloc.restype = ctypes.c_void_p
@@ -150,7 +164,7 @@ def main():
         desc = describe(base, shape)
         b0 = rt.audit_device_bytes()
         rt.audit_device_peak_reset()
-        err = solve_once(rt, desc)
+        err = solve_once(rt, desc, other_device=other)
         # device bytes the handle held at its peak (set-up and solve; the two
         # solution vectors are allocated through the same runtime)
         peak = rt.audit_device_peak_reset() - b0

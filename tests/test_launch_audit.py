@@ -315,3 +315,20 @@ def test_serving_stream_in_arrival_order(audit_env):
     for r in rows:
         assert r["error"] is None or "CUDA error" not in r["error"], r
         assert r["peak_bytes"] <= r["footprint"], r
+
+
+def test_entry_points_run_on_the_handles_device(audit_env):
+    """A handle set up on device 0 and driven from a thread with device 1
+    current: every launch still finds its memory on its own device, and the
+    thread's device is restored on return."""
+    env = dict(os.environ, LD_LIBRARY_PATH=audit_env["dir"], AUDIT_RESOURCES=audit_env["table"],
+               AUDIT_SIGNATURES=audit_env["sigs"], AUDIT_LOG=os.path.join(audit_env["dir"], "launches_dev.log"))
+    shapes = ["3,16,16,16", "2,194,33,64", "2,3,4,3,4"]
+    res = subprocess.run([sys.executable, os.path.join(AUDIT, "run_shapes.py"), "--other-device", "1",
+                          audit_env["lib"], *shapes], env=env, capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stderr[-3000:]
+    rows = [json.loads(line) for line in res.stdout.splitlines() if line.startswith("{")]
+    assert [r["shape"] for r in rows] == shapes
+    for r in rows:
+        assert r["violations"] == 0, r
+        assert r["error"] is None or ("CUDA error" not in r["error"] and "restored" not in r["error"]), r
