@@ -156,8 +156,9 @@ class Transient(RuntimeError):
 
 
 def test_retryable_failure_runs_again_after_a_completion():
-    # request 1 fails once (as if device memory were held elsewhere) while 0 runs
-    reqs = stream(3, 0.0, 0.02, [10])
+    # request 1 fails once (as if device memory were held elsewhere) while 0
+    # runs; the others run long enough for that failure to be seen first
+    reqs = stream(3, 0.0, 0.3, [10])
     calls = {}
     lock = threading.Lock()
 
@@ -196,7 +197,7 @@ def test_retries_are_bounded():
         if req["id"] == 1:
             calls[1] += 1
             raise Transient("out of memory")
-        time.sleep(0.05)
+        time.sleep(0.3)
         return dict(ok=0)
 
     recs = serve.Engine(run, fp_of, budget_bytes=100, max_slots=2, max_retries=2,
