@@ -4,7 +4,6 @@ limit of a spatially uniform stimulus."""
 
 import numpy as np
 import pytest
-import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from oracle import Oracle
