@@ -78,7 +78,7 @@ def solve_once(rt, desc, stream=0x1000, other_device=None):
     return None
 
 
-def exercise_api(rt, desc, stream=0x1000):
+def exercise_api(rt, desc, stream=0x1000, other_device=None):
     """Every entry point of the C ABI once on one handle (garbage values: only
     the launches, copies and allocations are of interest); the error texts."""
     n = W.n_dofs(desc)
@@ -97,6 +97,8 @@ def exercise_api(rt, desc, stream=0x1000):
     s = call("setup", lambda: L.Solver(desc, stream))
     if s is None:
         return errors
+    if other_device is not None:
+        rt.cudaSetDevice(other_device)
     call("rhs", lambda: s.rhs(dev["f"]))
     info = call("ionic", lambda: s.ionic(dev["u"], dev["w"])) or {}
     call("linearize", lambda: s.linearize(dev["u"], dev["w"], "newton", keep_theta=True))
@@ -116,21 +118,28 @@ def exercise_api(rt, desc, stream=0x1000):
                         ("tau_q", desc["p"] * desc["n_el_t"] * (desc["p"] + 1))):
         call("get " + what, lambda: s.get(what, count))
     call("close", s.close)
+    if other_device is not None:
+        cur = ctypes.c_int(-1)
+        rt.cudaGetDevice(ctypes.byref(cur))
+        if cur.value != other_device:
+            errors.append("the calling thread's device was not restored")
+        rt.cudaSetDevice(0)   # the handle-free call runs on the caller's device, where its buffers are
     call("wupdate_static", lambda: L.wupdate_static(desc, dev["u"], dev["w2"], stream))
     return errors
 
 
 def main():
     args = sys.argv[1:]
-    concurrent = 0
-    api = False
-    if args[0] == "--concurrent":
-        concurrent, args = int(args[1]), args[2:]
-    if args[0] == "--api":
-        api, args = True, args[1:]
-    other = None
-    if args[0] == "--other-device":
-        other, args = int(args[1]), args[2:]
+    concurrent, api, other = 0, False, None
+    while args[0].startswith("--"):
+        if args[0] == "--concurrent":
+            concurrent, args = int(args[1]), args[2:]
+        elif args[0] == "--api":
+            api, args = True, args[1:]
+        elif args[0] == "--other-device":
+            other, args = int(args[1]), args[2:]
+        else:
+            raise SystemExit("unknown option " + args[0])
     L.load(args[0])
     rt = ctypes.CDLL("libcudart.so.13")
     rt.audit_alloc.restype = ctypes.c_void_p
@@ -155,7 +164,7 @@ def main():
     if api:
         for shape in args[1:]:
             v0, l0 = rt.audit_violations(), rt.audit_launches()
-            errs = exercise_api(rt, describe(base, shape))
+            errs = exercise_api(rt, describe(base, shape), other_device=other)
             print(json.dumps(dict(shape=shape, violations=rt.audit_violations() - v0,
                                   launches=rt.audit_launches() - l0, errors=errs)), flush=True)
         return

@@ -332,3 +332,12 @@ def test_entry_points_run_on_the_handles_device(audit_env):
     for r in rows:
         assert r["violations"] == 0, r
         assert r["error"] is None or ("CUDA error" not in r["error"] and "restored" not in r["error"]), r
+    # and every other entry point the same way
+    res = subprocess.run([sys.executable, os.path.join(AUDIT, "run_shapes.py"), "--api", "--other-device", "1",
+                          audit_env["lib"], *shapes], env=env, capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stderr[-3000:]
+    rows = [json.loads(line) for line in res.stdout.splitlines() if line.startswith("{")]
+    assert [r["shape"] for r in rows] == shapes
+    for r in rows:
+        assert r["violations"] == 0, r
+        assert not [e for e in r["errors"] if "CUDA error" in e or "restored" in e], r
