@@ -18,7 +18,8 @@
  *     handle owns all of its workspaces.
  *   - Work is enqueued on the stream passed to st_setup.  Calls that return
  *     host scalars (st_ionic, st_linsolve, st_solve, st_get) synchronize it;
- *     st_apply, st_precond, st_wupdate and st_rhs are asynchronous.
+ *     st_apply, st_precond, st_wupdate and st_rhs are asynchronous
+ *     (st_wupdate_static is not: see there).
  *   - Errors are returned as st_status, never by aborting.  After ST_ERR_CUDA
  *     the handle must be destroyed; after any other error it stays usable.
  *   - A handle is not thread-safe; separate handles are independent.
@@ -212,9 +213,16 @@ st_status st_wupdate(st_handle *h, const double *u_dev, double *w_dev);
  * desc: the problem (only d, p, n_el, n_el_t, T, b, d_e are used; the whole
  * description must pass the checks of st_setup).  u_dev, w_dev: device
  * vectors of N_dof FP64 values in the layout above, u_dev != w_dev; w_dev is
- * overwritten.  cuda_stream: the stream the work is enqueued on (asynchronous;
- * 0 = legacy default stream).  Result: the same values as st_wupdate on a
- * handle set up from the same description.
+ * overwritten.  cuda_stream: the stream the work is enqueued on (0 = legacy
+ * default stream).  Result: the same values as st_wupdate on a handle set up
+ * from the same description.
+ *
+ * Synchronization: the call is not fully asynchronous.  The two bands are
+ * copied from ordinary (pageable) host memory that the call owns only while
+ * it runs; a copy from pageable memory first waits for the work already
+ * queued on cuda_stream, so the call returns only after that earlier work
+ * has finished and the bands have been handed to the device.  The w kernel
+ * itself is queued behind the copies and may still be running on return.
  *
  * Memory: no device memory is allocated (no cudaMalloc, cudaFree or
  * allocating library call).  The two time bands M_t and LU(W_t + b d_e M_t),

@@ -8,4 +8,4 @@ binding; it has no CPU fallback.
 
 from ._lib import (Solver, footprint, load, make_desc, StError, wupdate_static,  # noqa: F401
                    ST_FP64, ST_MIXED, ST_PICARD, ST_NEWTON, EXPORTS,
-                   ST_ERR_CAPACITY, ST_WUPDATE_STATIC_CAPACITY)
+                   ST_ERR_CAPACITY, ST_ERR_NAN, ST_ERR_NOT_CONVERGED, ST_WUPDATE_STATIC_CAPACITY)

@@ -311,6 +311,24 @@ int band_lu_inplace(double *a, int n, int p) {
   return 0;
 }
 
+namespace {
+// M_t, W_t on X_t and the banded LU of W_t + b d_e M_t (the time matrix of the
+// w-system, Eq. lin_sys_L) for the time direction `td`: the one definition
+// shared by the handle set-up and the handle-free w-update.
+st_status time_bands(const Dir1D &td, const st_problem_desc &d, std::vector<double> &Mt, std::vector<double> &Wt,
+                     std::vector<double> &wlu) {
+  const int p = d.p;
+  Mt = band_matrix(td, 0, 0, 1);
+  Wt = band_matrix(td, 0, 1, 1);   // row i tests b_i, column j carries b_j'
+  const int Nt = td.n - 1;
+  const int B = 2 * p + 1;
+  wlu.assign((size_t)Nt * B, 0.0);
+  for (size_t i = 0; i < wlu.size(); ++i) wlu[i] = Wt[i] + d.b * d.d_e * Mt[i];
+  if (band_lu_inplace(wlu.data(), Nt, p) != 0) return ST_ERR_BREAKDOWN;
+  return ST_OK;
+}
+}  // namespace
+
 st_status host_setup(const st_problem_desc &d, HostSetup &hs) {
   int p = d.p;
   for (int l = 0; l < d.d; ++l) {
@@ -319,29 +337,15 @@ st_status host_setup(const st_problem_desc &d, HostSetup &hs) {
     hs.K[l] = band_matrix(hs.sdir[l], 1, 1, 0);
   }
   build_dir(hs.tdir, d.n_el_t, p, d.T, p);
-  hs.Mt = band_matrix(hs.tdir, 0, 0, 1);
-  hs.Wt = band_matrix(hs.tdir, 0, 1, 1);   // row i tests b_i, column j carries b_j'
   if (!tau_setup(hs.tdir, hs.tau_q)) return ST_ERR_BREAKDOWN;
-  int Nt = hs.tdir.n - 1;
-  int B = 2 * p + 1;
-  hs.wlu.assign((size_t)Nt * B, 0.0);
-  for (size_t i = 0; i < hs.wlu.size(); ++i) hs.wlu[i] = hs.Wt[i] + d.b * d.d_e * hs.Mt[i];
-  if (band_lu_inplace(hs.wlu.data(), Nt, p) != 0) return ST_ERR_BREAKDOWN;
-  return ST_OK;
+  return time_bands(hs.tdir, d, hs.Mt, hs.Wt, hs.wlu);
 }
 
-// Time bands only (M_t and the banded LU of W_t + b d_e M_t), with the same
-// arithmetic as host_setup; used by the handle-free w-update.
+// Time bands only (M_t and the banded LU of W_t + b d_e M_t); used by the
+// handle-free w-update.
 st_status host_time_bands(const st_problem_desc &d, std::vector<double> &Mt, std::vector<double> &wlu) {
-  int p = d.p;
   Dir1D td;
-  build_dir(td, d.n_el_t, p, d.T, p);
-  Mt = band_matrix(td, 0, 0, 1);
-  std::vector<double> Wt = band_matrix(td, 0, 1, 1);
-  int Nt = td.n - 1;
-  int B = 2 * p + 1;
-  wlu.assign((size_t)Nt * B, 0.0);
-  for (size_t i = 0; i < wlu.size(); ++i) wlu[i] = Wt[i] + d.b * d.d_e * Mt[i];
-  if (band_lu_inplace(wlu.data(), Nt, p) != 0) return ST_ERR_BREAKDOWN;
-  return ST_OK;
+  build_dir(td, d.n_el_t, d.p, d.T, d.p);
+  std::vector<double> Wt;
+  return time_bands(td, d, Mt, Wt, wlu);
 }

@@ -58,6 +58,7 @@ thread_local cudaError_t last_error = cudaSuccess;
 FILE *logf = nullptr;
 long long n_launch = 0, n_violation = 0, n_pointer_checks = 0;
 long long device_bytes = 0, device_peak = 0;   // cudaMalloc'd and not yet freed
+long long n_alloc_calls = 0;   // allocations and frees of any kind (device, page-locked, stream-ordered)
 
 void init() {
   if (logf) return;
@@ -210,6 +211,7 @@ void *allocate(size_t n, bool dev) {
   const size_t nfill = (sz < fill_limit ? sz : fill_limit) / 8;
   for (size_t i = 0; i < nfill; ++i) q[i] = kFill;
   std::lock_guard<std::mutex> lk(mu);
+  ++n_alloc_calls;
   Alloc rec{n, dev};
   rec.device = current_device;
   allocs[(uintptr_t)p] = rec;
@@ -378,6 +380,7 @@ cudaError_t cudaFree(void *p) {
     return fail(cudaErrorInvalidValue);
   }
   if (it->second.dev) device_bytes -= (long long)it->second.size;
+  ++n_alloc_calls;
   allocs.erase(it);
   free(p);
   return cudaSuccess;
@@ -499,6 +502,11 @@ long long audit_launches(void) { return n_launch; }
 long long audit_pointer_checks(void) { return n_pointer_checks; }
 // device bytes allocated and not freed; the peak since the last reset
 long long audit_device_bytes(void) { return device_bytes; }
+// allocation and free calls so far (a caller brackets a call with two reads)
+long long audit_alloc_calls(void) {
+  std::lock_guard<std::mutex> lk(mu);
+  return n_alloc_calls;
+}
 long long audit_device_peak_reset(void) {
   std::lock_guard<std::mutex> lk(mu);
   const long long p = device_peak;

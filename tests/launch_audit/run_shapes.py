@@ -124,7 +124,10 @@ def exercise_api(rt, desc, stream=0x1000, other_device=None):
         if cur.value != other_device:
             errors.append("the calling thread's device was not restored")
         rt.cudaSetDevice(0)   # the handle-free call runs on the caller's device, where its buffers are
+    a0 = rt.audit_alloc_calls()
     call("wupdate_static", lambda: L.wupdate_static(desc, dev["u"], dev["w2"], stream))
+    if rt.audit_alloc_calls() != a0:
+        errors.append("wupdate_static allocated or freed memory")
     return errors
 
 
@@ -149,6 +152,7 @@ def main():
     rt.audit_device_bytes.restype = ctypes.c_longlong
     rt.audit_device_peak_reset.restype = ctypes.c_longlong
     rt.audit_pointer_checks.restype = ctypes.c_longlong
+    rt.audit_alloc_calls.restype = ctypes.c_longlong
     base = W.serving_requests(n_req=1, seed=21)[0]["desc"]
     if concurrent:
         from paper_2311_17500_gb300 import serve

@@ -285,7 +285,8 @@ def test_every_entry_point(audit_env):
     """Every entry point of the C ABI once per shape (right-hand side,
     linearizations, both operators and preconditioners, the linear solve, the
     w-updates with and without a handle, the per-stage timing, the internal
-    arrays): every launch, copy and pointer within the limits, no CUDA error."""
+    arrays): every launch, copy and pointer within the limits, no CUDA error,
+    and no allocation or free of any kind inside the handle-free w-update."""
     shapes = ["3,16,16,16", "2,194,33,64", "2,5,4,6", "1,6,7", "2,3,4,3,4", "4,6,5,7", "3,120,33,64:fp64"]
     env = dict(os.environ, LD_LIBRARY_PATH=audit_env["dir"], AUDIT_RESOURCES=audit_env["table"],
                AUDIT_SIGNATURES=audit_env["sigs"], AUDIT_FORBID_NULL_STREAM="1",
@@ -299,6 +300,7 @@ def test_every_entry_point(audit_env):
         assert r["violations"] == 0, r
         assert r["launches"] >= 100, r
         assert not [e for e in r["errors"] if "CUDA error" in e or "out of memory" in e], r
+        assert "wupdate_static allocated or freed memory" not in r["errors"], r
 
 
 def test_serving_stream_in_arrival_order(audit_env):

@@ -147,3 +147,75 @@ def test_newton_residual_vanishes_at_solution():
     w_fix = o.w_update(u)
     r = o.F - o.operator(o.st.const(0.0)) @ u - o.ionic_load(u, w_fix)
     assert np.abs(r).max() < 1e-10 * np.abs(o.F).max()
+
+
+def test_jacobian_coef_is_the_u_derivative_of_the_ionic_current():
+    """C_J (the Newton coefficient of the u-equation) is d/du of
+    I_ion(u, w) = c1 u (u - a)(u - 1) + c2 u w of eq. 3.1.  Checked three
+    ways that do not retype the formula: a centred difference of I_ion at
+    random (u, w); the slopes of the cubic at its three roots 0, a and 1,
+    which are the products of the differences to the other two roots; and
+    the w-dependence, d/dw of C_J = c2 = d/dw of I_ion / u."""
+    from oracle import model
+    desc = W.base_desc()
+    desc.update(W.DIMENSIONAL_RM)
+    a, c1, c2 = desc["a"], desc["c1"], desc["c2"]
+    rng = np.random.Generator(np.random.PCG64(3))
+    u = rng.uniform(-0.5, 1.5, 200)
+    w = rng.uniform(-0.2, 1.0, 200)
+    h = 1e-5
+    fd = (model.ionic_current(desc, u + h, w) - model.ionic_current(desc, u - h, w)) / (2 * h)
+    cj = model.jacobian_coef(desc, u, w)
+    # the centred difference of a cubic is exact up to c1 h^2 and rounding
+    assert np.abs(cj - fd).max() <= c1 * h * h + 1e-8 * np.abs(cj).max()
+    for root, slope in ((0.0, (0.0 - a) * (0.0 - 1.0)), (a, (a - 0.0) * (a - 1.0)), (1.0, (1.0 - 0.0) * (1.0 - a))):
+        wz = np.zeros(1)
+        assert abs(model.jacobian_coef(desc, np.array([root]), wz)[0] - c1 * slope) <= 1e-13 * c1
+        assert abs(model.ionic_current(desc, np.array([root]), wz)[0]) <= 1e-15 * c1
+    dw = (model.jacobian_coef(desc, u, w + 0.25) - model.jacobian_coef(desc, u, w)) / 0.25
+    assert np.abs(dw - c2).max() <= 1e-12 * c2
+    # C_J = C_r + u dC_r/du: the Picard coefficient is I_ion / u
+    nz = np.abs(u) > 1e-3
+    assert np.abs(model.reaction_coef(desc, u, w)[nz] * u[nz] - model.ionic_current(desc, u, w)[nz]).max() < 1e-12
+
+
+def _newton_errors(monkeypatch=None, coef=None):
+    """Distances max|u_k - u*| of the oracle's Newton iterates to its converged
+    solution, on a 1D Galerkin problem with w held at zero (so the u-equation
+    is the whole system and Newton on it is exact Newton)."""
+    from oracle import model
+    desc = W.base_desc(d=1, p=2, n_el=[6], n_el_t=8, T=6.0, D=[1e-2], stabilization="galerkin",
+                       nonlinear="newton", fix_w_zero=True, delta=0.0,
+                       source=dict(kind="stim", boxes=[W.stim_box([0.0], [0.4], 0.0, 1.0, 0.6)]))
+    if coef is not None:
+        monkeypatch.setattr(model, "jacobian_coef", coef)
+    _, _, hist = Oracle(desc).solve(max_fp=12, record=True)
+    us = [np.zeros_like(hist[0]["u"])] + [h["u"] for h in hist]
+    ref = us[-1]
+    return np.array([np.abs(x - ref).max() for x in us[:-1]])
+
+
+def test_newton_converges_quadratically(monkeypatch):
+    """With the true derivative the error squares each step once it is small:
+    e_{k+1} <= K e_k^2 with one K over the last steps before round-off, and
+    the contraction e_{k+1}/e_k falls towards zero.  A coefficient with a
+    term dropped (the c1 a part of C_J, a plausible slip) still converges to
+    the same solution, but only linearly: the same test rejects it."""
+    e = _newton_errors()
+    live = [k for k in range(len(e) - 1) if e[k + 1] > 1e-12 and e[k] < 1e-1]
+    assert len(live) >= 2, e
+    ratio2 = [e[k + 1] / e[k] ** 2 for k in live]
+    assert max(ratio2) < 50.0, e
+    assert e[live[-1] + 1] / e[live[-1]] < 1e-2, e
+
+    from oracle import model
+    true = model.jacobian_coef
+
+    def dropped(desc, u, w):
+        return true(desc, u, w) - desc["c1"] * desc["a"]
+
+    bad = _newton_errors(monkeypatch, dropped)
+    live_b = [k for k in range(len(bad) - 1) if bad[k + 1] > 1e-12 and bad[k] < 1e-1]
+    assert live_b, bad
+    assert max(bad[k + 1] / bad[k] ** 2 for k in live_b) > 50.0 or \
+        bad[live_b[-1] + 1] / bad[live_b[-1]] >= 1e-2, bad
