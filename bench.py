@@ -4,20 +4,25 @@
 One step = one pass of the whole hot path: one fixed-point iteration of
 Sec. 3.1 (ionic quadrature, Theta-hat, low rank, reaction + SU bands, the
 preconditioned GMRES solve of A u = f to true relative residual 1e-8, the
-w-update, relaxation and the stopping norm), on the 2D anisotropic workload
-(p = 3, 128 x 128 spatial x 256 time elements, 4,427,538 unknowns), starting
-every step from the same saved iterate k = 2.  The set-up (1D data,
-eigendecompositions, LU factors) runs once per problem and is reported apart.
+w-update, relaxation and the stopping norm), starting every step from the
+same saved iterate k = 2.  The default workload is the largest configuration
+that fits one GB300: the 3D cube (p = 2, 64^3 spatial x 128 time elements,
+37,086,984 unknowns, mixed precision); --workload c2_aniso_2d selects the 2D
+anisotropic one (p = 3, 128 x 128 x 256 elements, 4,427,538 unknowns).  The
+set-up (1D data, eigendecompositions, LU factors) runs once per problem and
+is reported apart.
 
 Output: one JSON line (rank 0).  `value` is unknowns per second of the mixed
 FP32/FP64 path with inputs resident on the device; `fp64` gives the FP64 path
 on the same step; `e2e` measures the same step through the C ABI from pinned
-host buffers, copies included; `roofline` reports the dominant kernel (the
-fused reaction/SU pass) against the measured HBM bandwidth, with every
-stage's time and bandwidth beside it; `cpu_baseline` times
-the CPU oracle on a bounded sample of the same workload.
+host buffers, copies included; `roofline` reports the FP32 operator apply
+(the hot kernel group of every GMRES iteration) against the measured HBM
+bandwidth, counting the method's algorithmic bytes (x in, y out, u^k and w^k
+in: 16 bytes per unknown), with every stage's time and bandwidth beside it;
+`cpu_baseline` times the CPU oracle on a bounded sample of the same workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload c3_cube_3d|c2_aniso_2d]
 """
 
 import argparse
@@ -31,13 +36,22 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "c2_aniso_2d"
-# DRAM bytes (read + write) per launch of the fused reaction/SU kernel from an
-# ncu capture of the same kernel build (a 96x96x192 case, scaled to the full
-# launch by its Gauss point-steps); cleared whenever that kernel changes,
-# until it is captured again.
-TRAFFIC_PER_LAUNCH = {"c2_aniso_2d": 1.2355e9}
-CPU_SAMPLE = dict(n_el=[12, 12], n_el_t=24)
+WORKLOAD = "c3_cube_3d"
+# DRAM bytes (read + write) of one FP32 operator apply (all of its kernels)
+# from an ncu capture of the same build, per workload; absent until captured,
+# and removed whenever one of those kernels changes.
+TRAFFIC_PER_APPLY = {}
+# bounded CPU samples of each workload (same physics, fewer elements): the
+# cpu_baseline of our line (one step, about 10 s of oracle work) and each step
+# of the reference arm (a few seconds, so that its whole run stays short)
+CPU_SAMPLES = {"c3_cube_3d": dict(n_el=[6, 6, 6], n_el_t=12),
+               "c2_aniso_2d": dict(n_el=[12, 12], n_el_t=24)}
+REF_SAMPLES = {"c3_cube_3d": dict(n_el=[5, 5, 5], n_el_t=10),
+               "c2_aniso_2d": dict(n_el=[12, 12], n_el_t=24)}
+# algorithmic bytes of one FP32 operator apply per unknown (the method's
+# compulsory traffic): x read and y written, u^k and w^k read for the exact
+# reaction coefficient at the Gauss points, 4 bytes each
+APPLY_BYTES_PER_DOF = 16.0
 
 
 def parse():
@@ -46,6 +60,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(CPU_SAMPLES))
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -139,18 +154,23 @@ def cpu_oracle_step(desc_sample):
     return json.loads(res.stdout.strip().splitlines()[-1])
 
 
-def cpu_sample_desc():
+def cpu_sample_desc(samples=None):
     import workloads as W
-    d = W.config(WORKLOAD, scale=CPU_SAMPLE)
+    d = W.config(WORKLOAD, scale=(samples or CPU_SAMPLES)[WORKLOAD])
     d["max_fp"] = 1
     return d
+
+
+def sample_shape(samples=None):
+    c = (samples or CPU_SAMPLES)[WORKLOAD]
+    return "x".join(str(v) for v in c["n_el"]) + f"x{c['n_el_t']}"
 
 
 def cpu_baseline():
     out = cpu_oracle_step(cpu_sample_desc())
     return {"value": out["n_dof"] / out["seconds"], "unit": "DoF/s", "cores": 1, "kind": "oracle",
-            "sample": f"one fixed-point step from u=w=0 of the same physics on {CPU_SAMPLE['n_el'][0]}x"
-                      f"{CPU_SAMPLE['n_el'][1]}x{CPU_SAMPLE['n_el_t']} elements ({out['n_dof']} DoF): "
+            "sample": f"one fixed-point step from u=w=0 of the same physics on {sample_shape()} "
+                      f"elements ({out['n_dof']} DoF): "
                       f"sparse space-time assembly + SuperLU direct solve, {out['seconds']:.1f} s"}
 
 
@@ -179,8 +199,15 @@ def dist_env():
 
 
 def workload_name(desc):
-    return (f"{WORKLOAD}: 2D unit square, p=3, {desc['n_el'][0]}x{desc['n_el'][1]} x {desc['n_el_t']} elements, "
-            f"D=diag(1e-3,2.5e-4), seeded corner stimulus, SU, Picard step from saved iterate k=2")
+    d = desc["d"]
+    dom = "unit square" if d == 2 else "unit cube" if d == 3 else "unit interval"
+    D = desc["D"]
+    dstr = f"D={D[0]:g} I" if len(set(D)) == 1 else "D=diag(" + ",".join(f"{v:g}" for v in D) + ")"
+    stim = {"c2_aniso_2d": "seeded corner stimulus", "c3_cube_3d": "planar stimulus x<0.05"}.get(WORKLOAD, "stimulus")
+    return (f"{WORKLOAD}: {d}D {dom}, p={desc['p']}, " + "x".join(str(v) for v in desc["n_el"]) +
+            f" x {desc['n_el_t']} elements, {dstr}, {stim}, "
+            f"{desc['stabilization'].upper() if desc['stabilization'] == 'su' else 'Galerkin'}, "
+            f"Picard step from saved iterate k=2")
 
 
 # the metric of both arms (ours and the reference arm's oracle)
@@ -192,7 +219,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    desc = cpu_sample_desc()
+    desc = cpu_sample_desc(REF_SAMPLES)
     times = []
     n_dof = None
     for k in range(args.warmup + args.steps):
@@ -207,7 +234,7 @@ def run_reference(args):
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(W.config(WORKLOAD)),
-                       "sample": f"each step: the same physics on {CPU_SAMPLE['n_el']} x {CPU_SAMPLE['n_el_t']} "
+                       "sample": f"each step: the same physics on {sample_shape(REF_SAMPLES)} "
                                  f"elements ({n_dof} DoF), one fixed-point step from u = w = 0"},
             "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle",
                              "sample": "CPU FP64 oracle: sparse assembly + SuperLU, one fixed-point step"},
@@ -266,9 +293,9 @@ def run_ours(args):
 
     desc = W.config(WORKLOAD)
     if args.scale:
-        nx, ny, nt = (int(v) for v in args.scale.split(","))
-        desc["n_el"] = [nx, ny]
-        desc["n_el_t"] = nt
+        vals = [int(v) for v in args.scale.split(",")]
+        desc["n_el"] = vals[:-1]
+        desc["n_el_t"] = vals[-1]
     desc["max_fp"] = 1
     desc["rtol"] = 1e-8
     desc["gmres_m"] = 150
@@ -330,19 +357,28 @@ def run_ours(args):
     ms_step, value = whole_job(ms_local, N, dist, "cuda")
     st_last = stats[-1]
 
-    # roofline of the dominant kernel: the fused reaction/SU pass (stage
-    # "qband": one launch per FP32 operator application), HBM-bound; its
-    # algorithmic bytes per launch are the time band once, the x-coefficient
-    # rows in and out once.  Every stage's achieved bandwidth is listed too.
+    # roofline of the FP32 operator apply, the kernel group every GMRES
+    # iteration runs (stages kron + interp + qband; one qband launch per
+    # apply): the method's algorithmic bytes (APPLY_BYTES_PER_DOF per
+    # unknown) over the event-timed duration of those stages.  The bytes the
+    # kernels actually stream (stored time bands at the spatial Gauss points,
+    # sum-factorization intermediates) are reported beside it as `streamed`.
     hbm, bf16, src = peaks
-    rec = prof["qband"]
-    achieved = rec["bytes"] / (rec["ms"] / 1000.0) / 1e9 if rec["ms"] > 0 else 0.0
-    per_launch = rec["bytes"] / max(rec["launches"], 1)
-    roof = {"bound": "hbm", "kernel": "xband_fused_kernel<float,3> (stage qband)", "achieved": achieved,
-            "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": TRAFFIC_PER_LAUNCH.get(WORKLOAD) if args.scale is None else None,
-            "algorithmic_bytes_per_launch": per_launch, "peak_source": src,
-            "share_of_step": rec["ms"] / sum(ptimes), "launches": rec["launches"],
+    applies = max(prof["qband"]["launches"], 1)
+    t_apply = sum(prof[k]["ms"] for k in ("kron", "interp", "qband")) / applies
+    alg = APPLY_BYTES_PER_DOF * N
+    achieved = alg / (t_apply / 1000.0) / 1e9 if t_apply > 0 else 0.0
+    streamed = sum(prof[k]["bytes"] for k in ("kron", "interp", "qband")) / applies
+    traffic = TRAFFIC_PER_APPLY.get(WORKLOAD) if args.scale is None else None
+    roof = {"bound": "hbm", "kernel": "FP32 operator apply (kron + interp + xband_fused; stages kron, interp, qband)",
+            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": traffic, "algorithmic_bytes_per_launch": alg,
+            "algorithmic_bytes_rule": f"{APPLY_BYTES_PER_DOF:g} B per unknown: x in, y out, u^k and w^k in (FP32)",
+            "apply_ms": t_apply, "applies": applies,
+            "streamed_bytes_per_apply": streamed,
+            "streamed_over_algorithmic": streamed / alg,
+            "peak_source": src,
+            "share_of_step": t_apply * applies / sum(ptimes),
             "profiled_ms_per_step": sum(ptimes) / len(ptimes),
             "stages_ms_per_step": {k: v["ms"] / len(ptimes) for k, v in prof.items()},
             "stages_gbs": {k: (v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] > 0 and v["bytes"] > 0 else None)
@@ -423,7 +459,7 @@ def run_ours(args):
         "dtype": "f32+df64+f64", "data": "synthetic",
         "config": {"workload": workload_name(desc),
                    "N_dof": N, "precision": "mixed: FP32 inner GMRES(150) + FP64 refinement",
-                   "l2": "inputs larger than L2 (time bands alone 1.08 GB FP32)",
+                   "l2": "inputs larger than L2 (vectors of %.0f MB FP32 and the stored time bands)" % (4 * N / 1e6),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "setup_s": setup_s},
         "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
@@ -566,7 +602,9 @@ def run_serve(args):
 
 
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = args.workload
     if args.impl == "reference":
         run_reference(args)
     elif args.serve:

@@ -17,12 +17,14 @@
     - the mixed-precision solve, through the residual f - A x.  Every row of it
       is bounded by the residual norm, which the solve brings below
       1e-8 ||f||.
-  The large problems use the Galerkin operator: the SU term needs Theta-hat
-  from maxima over all Gauss points and a global SVD, which the oracle cannot
-  form at these sizes.  With or without that term, the same kernels run at
-  the same launch shapes, since it only changes the values of the time bands;
-  it is checked on the smaller meshes of test_gpu_parity.py and in full on the
-  Newton problem here.
+  These checks use the Galerkin operator.
+* The 2D problem again with its SU term, at a smooth seeded linearization (an
+  excitation front, workloads.wave_fields): the oracle evaluates the residual
+  one time element at a time (oracle/streamed.py) and forms Theta-hat, its
+  maxima and denominator, and the truncated SVD of Eq. (tol) at full size.
+  Checked: the maxima and denominator, every entry of Theta-hat, the rank and
+  the singular values, and sampled rows of both operators with the low-rank
+  SU term.
 """
 
 import numpy as np
@@ -31,6 +33,9 @@ import pytest
 import workloads as W
 from oracle import Oracle
 from oracle.spacetime import SpaceTime
+from oracle import rows as OR
+from oracle import streamed as S
+from oracle.stabilization import low_rank, tau_solve
 from tests import sampled_rows as SR
 from tests.gpu_helpers import dev, empty, host, library, ptr, rel, stream, torch_cuda
 
@@ -160,3 +165,50 @@ def test_2d_workload_full_size_sampled_rows():
 
 def test_3d_workload_full_size_sampled_rows():
     sampled_rows_at_full_size("c3_cube_3d")
+
+
+def test_2d_workload_full_size_su():
+    torch = torch_cuda()
+    P = library()
+    desc = W.config("c2_aniso_2d")
+    desc.update(precision="mixed")
+    torch.cuda.empty_cache()
+    free, _total = torch.cuda.mem_get_info()
+    need = P.footprint(desc) + 8 * 8 * W.n_dofs(desc)
+    if free < need:
+        pytest.skip(f"needs {need / 1e9:.0f} GB of device memory, {free / 1e9:.0f} GB free")
+    st = SpaceTime(desc)
+    n = st.N_dof
+    u, w = W.wave_fields(desc)
+    th, info = S.theta_hat(st, desc, u, w, desc["suppext"])
+    eps = desc["eps_theta"]
+    U, sv, V = low_rank(th, eps)
+    R = len(sv)
+    # no tie at the cut: the tails around it stay clear of eps ||Theta||_F
+    allsv = np.linalg.svd(th, compute_uv=False)
+    fro = np.sqrt(np.sum(allsv ** 2))
+    tail = np.sqrt(np.concatenate([np.cumsum((allsv ** 2)[::-1])[::-1], [0.0]]))
+    assert R >= 2 and tail[R - 1] > (1 + 1e-4) * eps * fro and tail[R] < (1 - 1e-4) * eps * fro
+    s = P.Solver(desc, stream())
+    du, dw = dev(u), dev(w)
+    g = s.ionic(ptr(du), ptr(dw))
+    for key in ("u_max", "ut_max", "r_max", "den"):
+        assert abs(g[key] - info[key]) <= 1e-12 * info[key], (key, g[key], info[key])
+    assert g["rank"] == R
+    thg = np.array(s.get("theta_hat", n)).reshape(st.N_t, st.N_s)
+    assert np.abs(thg - th).max() <= 1e-12
+    assert rel(np.array(s.get("lowrank_s", R)), sv) <= 1e-10
+    rows = SR.sample_rows(st, desc, seed=5)
+    _, tau_q = tau_solve(st)
+    terms = OR.picard_galerkin_terms(st, desc, u, w) + S.su_terms(st, desc, tau_q, U, sv, V)
+    x = W.random_vector(n, seed=13)
+    ref = OR.apply_rows(st, terms, rows, x)
+    dx, dy = dev(x), empty(n)
+    s.apply(ptr(dx), ptr(dy), P.ST_FP64)
+    y = host(dy)
+    assert np.abs(y[rows] - ref).max() <= 1e-12 * np.abs(y).max()
+    dx32, dy32 = dev(x, np.float32), empty(n, "float32")
+    s.apply(ptr(dx32), ptr(dy32), P.ST_MIXED)
+    y32 = host(dy32)
+    assert np.abs(y32[rows] - ref).max() <= 2e-5 * np.abs(y32).max()
+    s.close()

@@ -135,6 +135,29 @@ def n_dofs(desc):
     return n_s * (desc["n_el_t"] + p - 1)
 
 
+def wave_fields(desc, seed=7, speed=0.03, width=0.05):
+    """Smooth synthetic linearization inputs (u, w), coefficient vectors in the
+    layout [t][z][y][x]: an excitation front spreading from a seeded point.
+    Closed-form values on a uniform index grid (x_i = i / (n_l - 1), t_j =
+    (j + 1) T / N_t) are used directly as coefficients; nothing here evaluates a
+    basis function.  u = (1 + tanh((speed t - r) / width)) / 2 with r the
+    distance to the point, w = 0.3 times the same front five time units later."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    d, p = desc["d"], desc["p"]
+    n = [ne + p for ne in desc["n_el"]]
+    n_t = desc["n_el_t"] + p - 1
+    c = rng.uniform(0.0, 0.3, size=d)
+    axes = [np.linspace(0.0, 1.0, n[l]) for l in range(d)]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")              # (z, y, x) order
+    r2 = sum((grids[d - 1 - l] - c[l]) ** 2 for l in range(d))
+    r = np.sqrt(r2)[None]
+    t = (np.arange(n_t) + 1.0) * desc["T"] / n_t
+    t = t.reshape((n_t,) + (1,) * d)
+    u = 0.5 * (1.0 + np.tanh((speed * t - r) / width))
+    w = 0.3 * 0.5 * (1.0 + np.tanh((speed * (t - 5.0) - r) / width))
+    return u.reshape(-1), w.reshape(-1)
+
+
 def random_vector(n, seed, lo=-1.0, hi=1.0):
     """x ~ U(lo, hi) from numpy PCG64(seed), float64."""
     rng = np.random.Generator(np.random.PCG64(seed))
