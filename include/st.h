@@ -58,6 +58,30 @@ enum { ST_FP64 = 0, ST_MIXED = 1 };
  * symmetric union of neighbouring supports (xi_{i-p}, xi_{i+2p+1}) */
 enum { ST_SUPPEXT_LITERAL = 0, ST_SUPPEXT_SYMMETRIC = 1 };
 /* precision selector of st_apply / st_precond: ST_FP64 -> double*, ST_MIXED -> float* */
+/* form of the reaction + SU part of the operator (Sec. 3.1.1, Eq. lin_sys_A):
+ *  ST_FORM_BANDS: one symmetric time band per spatial Gauss point, assembled per
+ *                 linearization and streamed by every apply ((p+1)^(d+1) values
+ *                 per unknown of device memory);
+ *  ST_FORM_LEAN:  no stored bands: the reaction term is integrated at the
+ *                 space-time Gauss points from u^k, w^k inside the apply and the
+ *                 SU term of Eq. (tildeS) is kept as its rank-R factors
+ *                 (requires d >= 2 and n_el[0] + p <= 256);
+ *  ST_FORM_AUTO:  the lean form where it applies, else the band form. */
+enum { ST_FORM_AUTO = 0, ST_FORM_BANDS = 1, ST_FORM_LEAN = 2 };
+/* operator of the inner FP32 Krylov solve of the mixed mode (the Krylov
+ * vectors and the preconditioner stay FP32):
+ *  ST_INNER_FP32: the operator in FP32 arithmetic;
+ *  ST_INNER_DF:   the operator in double-float arithmetic (FP64 accuracy on the
+ *                 FP32 pipes), its input and output rounded to FP32.  An FP32
+ *                 operator has rounding errors of the size of the mass-matrix
+ *                 terms it sums; when the space-time system is ill conditioned
+ *                 (the B-spline mass matrices of d+1 directions), the inner
+ *                 correction then carries a relative error near kappa(A) u_32
+ *                 and the FP64 refinement contracts slowly;
+ *  ST_INNER_AUTO: FP32 first; from the first refinement step that reduces
+ *                 the true residual by less than a factor 20, double-float for
+ *                 the rest of the handle's life. */
+enum { ST_INNER_AUTO = 0, ST_INNER_FP32 = 1, ST_INNER_DF = 2 };
 
 #define ST_MAX_STIM 8
 
@@ -92,6 +116,8 @@ typedef struct {
   int gmres_m;           /* Krylov basis size (restart length) */
   double rtol;           /* target true relative residual ||f - A u|| / ||f|| */
   int max_it;            /* cap on total inner GMRES iterations per linear solve */
+  int operator_form;     /* ST_FORM_* */
+  int inner_op;          /* ST_INNER_* (mixed mode) */
 } st_problem_desc;
 
 typedef struct st_handle st_handle;

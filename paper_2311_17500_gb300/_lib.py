@@ -20,6 +20,8 @@ ST_GALERKIN, ST_SU = 0, 1
 ST_PICARD, ST_NEWTON = 0, 1
 ST_FP64, ST_MIXED = 0, 1
 ST_SUPPEXT = {"literal": 0, "symmetric": 1}
+ST_FORM = {"auto": 0, "bands": 1, "lean": 2}
+ST_INNER = {"auto": 0, "fp32": 1, "df": 2}
 ST_MAX_STIM = 8
 GET = dict(theta_hat=0, lowrank_s=1, lowrank_u=2, lowrank_v=3, tau_q=4, fd_eig=5, bands_1d=6)
 
@@ -44,7 +46,8 @@ class StProblemDesc(ctypes.Structure):
                 ("stabilization", ctypes.c_int), ("suppext", ctypes.c_int), ("eps_theta", ctypes.c_double),
                 ("nonlinear", ctypes.c_int), ("alpha", ctypes.c_double), ("delta", ctypes.c_double),
                 ("max_fp", ctypes.c_int), ("fix_w_zero", ctypes.c_int), ("precision", ctypes.c_int),
-                ("gmres_m", ctypes.c_int), ("rtol", ctypes.c_double), ("max_it", ctypes.c_int)]
+                ("gmres_m", ctypes.c_int), ("rtol", ctypes.c_double), ("max_it", ctypes.c_int),
+                ("operator_form", ctypes.c_int), ("inner_op", ctypes.c_int)]
 
 
 class StDims(ctypes.Structure):
@@ -148,6 +151,8 @@ def make_desc(desc):
     c.gmres_m = int(desc["gmres_m"])
     c.rtol = float(desc["rtol"])
     c.max_it = int(desc["max_it"])
+    c.operator_form = ST_FORM[desc.get("operator_form", "auto")]
+    c.inner_op = ST_INNER[desc.get("inner_op", "auto")]
     return c
 
 

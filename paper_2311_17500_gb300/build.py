@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libst.so")
 OBJDIR = os.path.join(HERE, "_build")
 
-SOURCES = ["setup_host.cpp", "kernels_linalg.cu", "kernels_ionic.cu", "eig.cu", "tc_gemm.cu", "api.cu"]
+SOURCES = ["setup_host.cpp", "kernels_linalg.cu", "kernels_ionic.cu", "kernels_lean.cu", "eig.cu", "tc_gemm.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

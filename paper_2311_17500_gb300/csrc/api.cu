@@ -21,8 +21,13 @@ struct Sizes {
   int Nt, nel_t, Qt;
   long long Ns, Ndof, Qs, Nel_s, NtQs;
   int m, nmax, cap;
+  bool lean;
+  long long rows_x, wcap;
   size_t bytes;
 };
+
+// The lean operator form applies to d >= 2 with an x row in one block.
+bool lean_applies(const st_problem_desc &D) { return D.d >= 2 && xlean_feasible(D.n_el[0], D.p); }
 
 st_status validate(const st_problem_desc *d) {
   if (!d) return ST_ERR_ARG;
@@ -41,6 +46,9 @@ st_status validate(const st_problem_desc *d) {
   if (d->gmres_m < 1 || d->gmres_m > 500 || !(d->rtol > 0) || d->max_it < 1) return ST_ERR_ARG;
   if (!(d->eps_theta >= 0) || !(d->alpha > 0) || d->alpha > 1 || !(d->delta >= 0) || d->max_fp < 1)
     return ST_ERR_ARG;
+  if (d->operator_form < ST_FORM_AUTO || d->operator_form > ST_FORM_LEAN) return ST_ERR_ARG;
+  if (d->inner_op < ST_INNER_AUTO || d->inner_op > ST_INNER_DF) return ST_ERR_ARG;
+  if (d->operator_form == ST_FORM_LEAN && !lean_applies(*d)) return ST_ERR_ARG;
   return ST_OK;
 }
 
@@ -62,6 +70,13 @@ Sizes plan(const st_problem_desc &D) {
   z.nmax = z.Nt;
   for (int l = 0; l < D.d; ++l) z.nmax = std::max(z.nmax, z.n[l]);
   z.cap = (int)std::min<long long>(z.Nt, z.Ns);
+  z.lean = D.operator_form == ST_FORM_LEAN || (D.operator_form == ST_FORM_AUTO && lean_applies(D));
+  z.rows_x = 1;
+  for (int l = 1; l < D.d; ++l) z.rows_x *= z.Q[l];
+  // values per Gauss-point work buffer: every spatial Gauss point of every time
+  // row in the band form; in the lean form the Gauss rows of the other axes
+  // with x in coefficients (the largest array of the apply), at least N_dof
+  z.wcap = z.lean ? std::max<long long>((long long)z.Nt * z.rows_x * z.n[0], z.Ndof) : z.NtQs;
   size_t b = 0;
   size_t d8 = sizeof(double), f4 = sizeof(float);
   // 1D data (generous)
@@ -74,14 +89,20 @@ Sizes plan(const st_problem_desc &D) {
   for (int l = 0; l < z.d; ++l) np *= (size_t)(z.n[l] + 3) / 4 * 4;
   b += (size_t)z.Ns * d8;                                          // mu
   b += (size_t)z.Nt * z.B * (z.Ns * d8 + Ns_pad * f4);             // LU per eigen-index (FP64, padded FP32)
-  b += (size_t)(z.p + 1) * z.NtQs * (f4 + f4);                     // bands (high + low parts)
+  if (z.lean) {
+    b += (size_t)z.wcap * d8 * 2;                                  // two work buffers (FP32 ones alias them)
+    b += (size_t)z.Nt * z.rows_x * z.n[0] * d8 * 2;                // u^k, w^k rows (pairs)
+    b += (size_t)z.cap * d8 + (size_t)z.Qt * d8;                   // rank scales, time weight pairs
+  } else {
+    b += (size_t)(z.p + 1) * z.NtQs * (f4 + f4);                   // bands (high + low parts)
+    b += (size_t)z.NtQs * d8 * 5;                                  // two work buffers + ionic fields
+    b += (size_t)z.NtQs * f4 * 2;
+  }
   b += (size_t)z.Ndof * d8 * 9;                                    // f, theta, FP64 vectors
   b += (size_t)z.Ndof * f4 * 4;                                    // FP32 vectors
   b += (size_t)z.nel_t * z.Nel_s * 8;                              // element maxima
   b += (size_t)z.Nt * z.Nt * d8 * 2 + (size_t)z.nmax * z.nmax * (12 * d8 + 2 * f4);
   b += (size_t)z.cap * (z.Nt + z.Ns + 1 + z.Qt + 2 * (z.p + 1) * z.Nt) * d8;
-  b += (size_t)z.NtQs * d8 * 5;                                    // two work buffers + ionic fields
-  b += (size_t)z.NtQs * f4 * 2;
   b += (size_t)z.Ndof * (d8 + f4) * 7;                             // Kronecker temporaries
   b += 2 * (std::max<size_t>(np, 2 * (size_t)z.Ndof) + 64) * f4;   // padded transform buffers
   if (D.precision == ST_FP64) b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * d8;
@@ -178,6 +199,20 @@ template <typename T> T *zbasis(st_handle *h);
 template <> double *zbasis<double>(st_handle *h) { return h->Z64; }
 template <> float *zbasis<float>(st_handle *h) { return h->Z32; }
 
+// The operator inside a Krylov cycle: the FP64 cycle applies it in FP64; the
+// FP32 cycle in FP32, or in double-float on its FP32 vectors (converted to
+// FP64 around the FP64 operator) when the handle's inner solve needs the
+// accuracy.
+template <typename T> st_status inner_apply(st_handle *h, const T *z, T *w);
+template <> st_status inner_apply<double>(st_handle *h, const double *z, double *w) { return apply_T<double>(h, z, w); }
+template <> st_status inner_apply<float>(st_handle *h, const float *z, float *w) {
+  if (!h->inner_df) return apply_T<float>(h, z, w);
+  launch_f2d(h->stream, h->z64, z, h->Ndof);
+  ST_TRY(apply_T<double>(h, h->z64, h->t64a));
+  launch_d2f(h->stream, w, h->t64a, 1.0, h->Ndof);
+  return ST_OK;
+}
+
 template <typename T>
 st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int *its, double *est) {
   cudaStream_t s = h->stream;
@@ -244,7 +279,7 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
   auto launch_iter = [&](int jj) -> st_status {
     T *uj = V + (long long)jj * ld, *w = V + (long long)(jj + 1) * ld, *zj = Z + (long long)jj * ld;
     ST_TRY(precond_T<T>(h, uj, zj));
-    ST_TRY(apply_T<T>(h, zj, w));
+    ST_TRY(inner_apply<T>(h, zj, w));
     {
       // delayed CGS2: one dot pass of [V_0..V_{j-1}, u_j, w] against (u_j, w),
       // one update pass writing v_j and u_{j+1}
@@ -518,6 +553,42 @@ template <> struct Prec<float> {
   static const float *lu(st_handle *h) { return h->lu32; }
 };
 
+LeanTerms lean_terms(st_handle *h) {
+  LeanTerms L;
+  const st_problem_desc &D = h->desc;
+  L.exact = 1;
+  L.U1 = h->U1;
+  L.W1 = h->W1;
+  L.bt = h->bt2;   // k = 0 block of [k][e][gt][a]
+  L.wt = h->wt2;
+  for (int l = 0; l < 3; ++l) {
+    L.ws[l] = h->wqs[l];
+    L.hi[l] = h->hat_i_s[l];
+    L.hl[l] = h->hat_l_s[l];
+    L.n[l] = h->n[l];
+    L.Q[l] = h->Q[l];
+  }
+  L.Rt = D.stabilization == ST_SU ? h->rank : 0;
+  L.V = h->Vr;
+  L.cf = h->cfr;
+  L.Tb = h->Tr2;
+  L.newton = h->lin_kind == ST_NEWTON;
+  L.c1 = D.c1; L.c2 = D.c2; L.a = D.a;
+  L.d = h->d; L.p = h->p; L.nel = h->nel[0]; L.Nt = h->Nt; L.nel_t = h->nel_t;
+  return L;
+}
+
+// Arithmetic of one lean-kernel launch (flops, for the per-stage record): per
+// element-thread and step, the x interpolation of three new rows, the band
+// of the rank terms, the time integration of one element and the projection.
+static double lean_flops(st_handle *h) {
+  const double P = h->p, nq = h->nq;
+  const double R = h->desc.stabilization == ST_SU ? h->rank : 0;
+  const double per = 3 * nq * (P + 1) + R * (P + 1) * nq + (2 * P + 1) * nq +
+                     nq * nq * (4 * (P + 1) + 6) + nq * (P + 1);
+  return 2.0 * per * (double)h->nel[0] * (double)h->rows_x * (double)h->Nt;
+}
+
 // y = A x (Eq. lin_sys_A): Kronecker part C_m W_t (x) M_s + M_t (x) K_s by
 // banded passes, then the reaction + SU part (I (x) B_s^T) band (I (x) B_s)
 // by sum factorization in space and one banded product along time per
@@ -620,7 +691,10 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
     long long rows = 1;
     for (int k = 1; k < h->d; ++k) rows *= qd[k];
     float2 *Y2 = reinterpret_cast<float2 *>(P::W(h, ping));
-    {
+    if (h->lean) {
+      ProfScope ps(h, PROF_APPLY64, (2.0 * sz + 16.0) * (double)Nt * rows * nx, lean_flops(h));
+      ST_TRY(launch_xlean<float2>(s, lean_terms(h), Y2, cur2, h->Bq2[0], rows));
+    } else {
       ProfScope ps(h, PROF_APPLY64, sz * ((double)(p + 1) * h->NtQs + 2.0 * (double)Nt * rows * nx));
       launch_xband_fused<float2>(s, Y2, cur2, h->band32, h->band_lo, h->Bq2[0], h->nel[0], (int)Nt, rows, p,
                                  h->tc_err);
@@ -663,7 +737,12 @@ st_status apply_T(st_handle *h, const T *x, T *y) {
     long long rows = 1;
     for (int k = 1; k < h->d; ++k) rows *= qd[k];
     T *Y1 = P::W(h, ping);
-    {
+    if (h->lean) {
+      // the FP32 operator (the FP64 one takes the pair branch above)
+      ProfScope ps(h, PROF_QBAND, (2.0 * sz + 16.0) * (double)Nt * rows * nx, lean_flops(h));
+      ST_TRY(launch_xlean<float>(s, lean_terms(h), reinterpret_cast<float *>(Y1), reinterpret_cast<const float *>(cur),
+                                 h->Bq32[0], rows));
+    } else {
       ProfScope ps(h, sizeof(T) == 8 ? PROF_APPLY64 : PROF_QBAND, sz * ((double)(p + 1) * h->NtQs + 2.0 * (double)Nt * rows * nx));
       launch_xband_fused<T>(s, Y1, cur, h->band32, P::band_lo(h), P::Bq(h, 0), h->nel[0], (int)Nt, rows, p, h->tc_err);
     }
@@ -932,6 +1011,9 @@ static st_status setup_impl(st_handle *h) {
   h->Nt = z.Nt; h->nel_t = z.nel_t; h->Qt = z.Qt;
   h->Ns = z.Ns; h->Ndof = z.Ndof; h->Qs = z.Qs; h->Nel_s = z.Nel_s; h->NtQs = z.NtQs;
   h->m = z.m;
+  h->lean = z.lean;
+  h->rows_x = z.rows_x;
+  h->wcap = z.wcap;
   h->ldv = (z.Ndof + 63) / 64 * 64;
   h->rank_cap = z.cap;
   ST_TRY(host_setup(D, h->hs));
@@ -998,6 +1080,14 @@ static st_status setup_impl(st_handle *h) {
     ST_TRY(upload_vec<float2>(h, &h->bprod2, split(bp.data(), bp.size())));
   }
   ST_TRY(upload<double>(h, &h->wt, hs.tdir.wq));
+  {
+    std::vector<float2> w2(hs.tdir.wq.size());
+    for (size_t i = 0; i < w2.size(); ++i) {
+      const float hi = (float)hs.tdir.wq[i];
+      w2[i] = make_float2(hi, (float)(hs.tdir.wq[i] - (double)hi));
+    }
+    ST_TRY(upload_vec<float2>(h, &h->wt2, w2));
+  }
   ST_TRY(upload<double>(h, &h->xt, hs.tdir.xq));
   {
     // stimulus windows of each time quadrature point ([t0, t1), as in the
@@ -1037,8 +1127,15 @@ static st_status setup_impl(st_handle *h) {
   h->nxp = (h->n[0] + 3) / 4 * 4;
   h->Ns_pad = h->Ns / h->n[0] * h->nxp;
   h->lu32 = dalloc<float>(h, (size_t)h->Nt * h->B * h->Ns_pad, &e);
-  h->band32 = dalloc<float>(h, (size_t)(h->p + 1) * h->NtQs, &e);
-  h->band_lo = dalloc<float>(h, (size_t)(h->p + 1) * h->NtQs, &e);
+  if (!h->lean) {
+    h->band32 = dalloc<float>(h, (size_t)(h->p + 1) * h->NtQs, &e);
+    h->band_lo = dalloc<float>(h, (size_t)(h->p + 1) * h->NtQs, &e);
+  } else {
+    const size_t rn = (size_t)h->Nt * h->rows_x * h->n[0];
+    h->U1 = dalloc<float2>(h, rn, &e);
+    h->W1 = dalloc<float2>(h, rn, &e);
+    h->cfr = dalloc<double>(h, h->rank_cap, &e);
+  }
   h->f64 = dalloc<double>(h, h->Ndof, &e);
   h->emax = dalloc<unsigned long long>(h, (size_t)h->nel_t * h->Nel_s, &e);
   h->stats = dalloc<double>(h, 8, &e);
@@ -1056,16 +1153,20 @@ static st_status setup_impl(st_handle *h) {
   h->Tr = dalloc<double>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
   h->Tr2 = dalloc<float2>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
   for (int i = 0; i < 2; ++i) {
-    h->W64[i] = dalloc<double>(h, h->NtQs, &e);
-    h->W32[i] = dalloc<float>(h, h->NtQs, &e);
+    h->W64[i] = dalloc<double>(h, h->wcap, &e);
+    // the lean form's FP32 work buffers share the FP64 ones: the two operators
+    // run one after the other on the handle's stream and keep nothing there
+    h->W32[i] = h->lean ? reinterpret_cast<float *>(h->W64[i]) : dalloc<float>(h, h->wcap, &e);
   }
   for (int i = 0; i < 7; ++i) {
     h->K64[i] = dalloc<double>(h, h->Ndof, &e);
     h->K32[i] = dalloc<float>(h, h->Ndof, &e);
   }
-  h->U0 = dalloc<double>(h, h->NtQs, &e);
-  h->L0 = dalloc<double>(h, h->NtQs, &e);
-  h->Wq0 = dalloc<double>(h, h->NtQs, &e);
+  if (!h->lean) {
+    h->U0 = dalloc<double>(h, h->NtQs, &e);
+    h->L0 = dalloc<double>(h, h->NtQs, &e);
+    h->Wq0 = dalloc<double>(h, h->NtQs, &e);
+  }
   h->red = dalloc<double>(h, 4096 + 608 * (size_t)(2 * h->m + 56), &e);
   if (D.precision == ST_FP64) {
     h->V64 = dalloc<double>(h, (size_t)(h->m + 1) * h->ldv, &e);
@@ -1256,8 +1357,10 @@ st_status st_linsolve(st_handle *h, const double *b, double *x, st_stats *stats)
     return ST_OK;
   }
   int total = 0, outer = 0;
-  double rel = INFINITY;
+  double rel = INFINITY, rel_prev = INFINITY;
   st_status status = ST_ERR_NOT_CONVERGED;
+  if (D.precision == ST_MIXED && D.inner_op == ST_INNER_DF) h->inner_df = true;
+  if (D.precision == ST_MIXED && D.inner_op == ST_INNER_FP32) h->inner_df = false;
   while (true) {
     ST_TRY(apply_T<double>(h, x, h->t64a));
     launch_sub64(s, h->r64, b, h->t64a, N);
@@ -1265,6 +1368,12 @@ st_status st_linsolve(st_handle *h, const double *b, double *x, st_stats *stats)
     if (!std::isfinite(rn)) return ST_ERR_NAN;
     rel = rn / bn;
     if (rel <= D.rtol) { status = ST_OK; break; }
+    // a refinement step that reduced the true residual by less than a factor
+    // 20: the FP32 operator limits the inner correction; switch it to
+    // double-float (kept for the handle's later solves)
+    if (D.precision == ST_MIXED && D.inner_op == ST_INNER_AUTO && !h->inner_df && rel > rel_prev / 20.0)
+      h->inner_df = true;
+    rel_prev = rel;
     if (total >= D.max_it) break;
     int its = 0;
     double est = 0.0;

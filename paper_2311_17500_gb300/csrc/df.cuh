@@ -74,6 +74,10 @@ __device__ __forceinline__ df df_max_nonneg(df a, df b) {
 __device__ __forceinline__ float ct_fma(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ df ct_fma(df a, df b, df c) { return df_fma(a, b, c); }
 __device__ __forceinline__ float ct_add(float a, float b) { return a + b; }
+__device__ __forceinline__ float ct_mul(float a, float b) { return a * b; }
+__device__ __forceinline__ df ct_mul(df a, df b) { return df_mul(a, b); }
+__device__ __forceinline__ float ct_neg(float a) { return -a; }
+__device__ __forceinline__ df ct_neg(df a) { return df_neg(a); }
 __device__ __forceinline__ df ct_add(df a, df b) { return df_add(a, b); }
 __device__ __forceinline__ float ct_shfl_up(float v, int d) { return __shfl_up_sync(0xffffffffu, v, d); }
 __device__ __forceinline__ df ct_shfl_up(df v, int d) {

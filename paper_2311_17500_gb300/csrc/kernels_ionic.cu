@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstring>
 #include "st_internal.h"
 #include "df.cuh"
 
@@ -100,9 +101,18 @@ struct IonicArgs {
   long long Qs, Nel_s;
   int kind;                     // ST_PICARD: C_r, ST_NEWTON: C_J
   int want_stats;
-  float *band_hi, *band_lo;     // [k][it][q] as double-float pairs
+  float *band_hi, *band_lo;     // [k][it][q] as double-float pairs; null: no bands (lean form)
   unsigned long long *emax;     // [et][es]
   unsigned long long *stats;    // max|u|, max|d_t u|, max|R| (bit patterns)
+  // rows mode (lean form): the fields are interpolated along x here from
+  // their coefficients at the Gauss rows of the other axes, [N_t][rows][n_x]:
+  // U1 = u, W1 = w, L1 = the other axes' part of sum_l D_ll d_ll u (null in 1D)
+  int rows_mode;
+  const float2 *U1, *L1, *W1;
+  const float2 *tbx, *tb2x;     // x basis values and second derivatives [ex][g][a], pairs
+  double Dx;
+  int nx, Qx;
+  long long rows;
 };
 
 // |v| as the bit pattern of a non-negative double: the unsigned order of these
@@ -145,7 +155,40 @@ __global__ void __launch_bounds__(128, P <= 3 ? 4 : 2) ionic_tline_kernel(IonicA
     const df ws = df_from(sp.ws);
     const df zero = {0.f, 0.f};
     const bool newton = a.kind == ST_NEWTON;
+    const bool bands = a.band_hi != nullptr;
     const long long plane = (long long)a.Nt * a.Qs;
+    // rows mode: this point's x element and its basis values
+    const long long o = a.rows_mode ? q / a.Qx : 0;
+    const int gx = a.rows_mode ? (int)(q % a.Qx) : 0;
+    const int ex = gx / nq;
+    df bx[P + 1], b2x[P + 1];
+    if (a.rows_mode) {
+#pragma unroll
+      for (int j = 0; j <= P; ++j) {
+        bx[j] = df_from2(a.tbx[(size_t)gx * (P + 1) + j]);
+        b2x[j] = df_from2(a.tb2x[(size_t)gx * (P + 1) + j]);
+      }
+    }
+    const df Dx = df_from(a.Dx);
+    // u, the Laplacian term and w of coefficient row `row` at this point
+    auto fetch = [&](int row, df &fu, df &fl, df &fw) {
+      if (!a.rows_mode) {
+        const long long off = (long long)row * a.Qs + q;
+        fu = df_from2(a.U0[off]); fl = df_from2(a.L0[off]); fw = df_from2(a.W0[off]);
+        return;
+      }
+      const long long base = ((long long)row * a.rows + o) * a.nx + ex;
+      df su = zero, s2 = zero, sl = zero, sw = zero;
+#pragma unroll
+      for (int j = 0; j <= P; ++j) {
+        const df cu_j = df_from2(a.U1[base + j]);
+        su = df_fma(bx[j], cu_j, su);
+        s2 = df_fma(b2x[j], cu_j, s2);
+        if (a.L1) sl = df_fma(bx[j], df_from2(a.L1[base + j]), sl);
+        sw = df_fma(bx[j], df_from2(a.W1[base + j]), sw);
+      }
+      fu = su; fl = df_fma(Dx, s2, sl); fw = sw;
+    };
     df acc[P + 1][P + 1];
 #pragma unroll
     for (int r = 0; r <= P; ++r)
@@ -155,20 +198,12 @@ __global__ void __launch_bounds__(128, P <= 3 ? 4 : 2) ionic_tline_kernel(IonicA
     df cu[P + 1], cl[P + 1], cw[P + 1];
     cu[0] = cl[0] = cw[0] = zero;
 #pragma unroll
-    for (int j = 1; j <= P; ++j) {
-      const long long off = (long long)(j - 1) * a.Qs + q;
-      cu[j] = df_from2(a.U0[off]);
-      cl[j] = df_from2(a.L0[off]);
-      cw[j] = df_from2(a.W0[off]);
-    }
+    for (int j = 1; j <= P; ++j) fetch(j - 1, cu[j], cl[j], cw[j]);
     df mu_d = zero, mut_d = zero;
     for (int e = 0; e < a.nel_t; ++e) {
       // next row (e + P), requested before this element's work
-      float2 nu = make_float2(0.f, 0.f), nl = nu, nw = nu;
-      if (e + 1 < a.nel_t) {
-        const long long off = (long long)(e + P) * a.Qs + q;
-        nu = a.U0[off]; nl = a.L0[off]; nw = a.W0[off];
-      }
+      df nu = zero, nl = zero, nw = zero;
+      if (e + 1 < a.nel_t) fetch(e + P, nu, nl, nw);
       df rloc = zero;
 #pragma unroll
       for (int qt = 0; qt < nq; ++qt) {
@@ -206,20 +241,22 @@ __global__ void __launch_bounds__(128, P <= 3 ? 4 : 2) ionic_tline_kernel(IonicA
         rloc = df_max_nonneg(rloc, df_abs(R));
         mu_d = df_max_nonneg(mu_d, df_abs(u));
         mut_d = df_max_nonneg(mut_d, df_abs(ut));
-        const df wc = df_mul(ws, C);
-        const float2 *bp = a.bprod2 + ((size_t)e * nq + qt) * NPAIR;
-        int pr = 0;
+        if (bands) {
+          const df wc = df_mul(ws, C);
+          const float2 *bp = a.bprod2 + ((size_t)e * nq + qt) * NPAIR;
+          int pr = 0;
 #pragma unroll
-        for (int i = 0; i <= P; ++i)
+          for (int i = 0; i <= P; ++i)
 #pragma unroll
-          for (int k = 0; k <= P - i; ++k) { acc[i][k] = df_fma(wc, df_from2(__ldg(bp + pr)), acc[i][k]); ++pr; }
+            for (int k = 0; k <= P - i; ++k) { acc[i][k] = df_fma(wc, df_from2(__ldg(bp + pr)), acc[i][k]); ++pr; }
+        }
       }
       const unsigned long long rb = abs_bits(df_to(rloc));
       mr = mr > rb ? mr : rb;
       if (a.want_stats) atomicMax(&a.emax[(long long)e * a.Nel_s + sp.es], rb);
       // row e-1 is complete
       int row = e - 1;
-      if (row >= 0)
+      if (bands && row >= 0)
 #pragma unroll
         for (int k = 0; k <= P; ++k) {
           const long long bi = k * plane + (long long)row * a.Qs + q;
@@ -234,9 +271,9 @@ __global__ void __launch_bounds__(128, P <= 3 ? 4 : 2) ionic_tline_kernel(IonicA
       for (int k = 0; k <= P; ++k) acc[P][k] = zero;
 #pragma unroll
       for (int j = 0; j < P; ++j) { cu[j] = cu[j + 1]; cl[j] = cl[j + 1]; cw[j] = cw[j + 1]; }
-      cu[P] = df_from2(nu); cl[P] = df_from2(nl); cw[P] = df_from2(nw);
+      cu[P] = nu; cl[P] = nl; cw[P] = nw;
     }
-    for (int r = 0; r < P; ++r) {
+    for (int r = 0; bands && r < P; ++r) {
       int row = a.nel_t - 1 + r;
       if (row < a.Nt)
         for (int k = 0; k <= P; ++k) {
@@ -279,7 +316,9 @@ __global__ void __launch_bounds__(128, P <= 3 ? 4 : 2) ionic_tline_kernel(IonicA
 // Fq[it][q] = ws(q) sum over time Gauss points of wt f(x_q, t) b_it(t).
 template <int P>
 __global__ void source_tline_kernel(st_problem_desc D, GeomArgs g, const double *bt, const double *wt,
-                                    const double *xt, int Nt, int nel_t, long long Qs, double *Fq) {
+                                    const double *xt, int Nt, int nel_t, long long Qs, int r0, int nr, double *Fq) {
+  // rows r0 .. r0 + nr - 1 of Fq (row i at Fq[(i - r0) Qs + q]); row i takes
+  // the time elements i + 1 - P .. i + 1
   long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= Qs) return;
   const int nq = P + 1;
@@ -287,22 +326,26 @@ __global__ void source_tline_kernel(st_problem_desc D, GeomArgs g, const double 
   double acc[P + 1];
 #pragma unroll
   for (int r = 0; r <= P; ++r) acc[r] = 0.0;
-  for (int e = 0; e < nel_t; ++e) {
+  const int e_lo = max(0, r0 + 1 - P), e_hi = min(nel_t - 1, r0 + nr);
+  const int r1 = min(Nt, r0 + nr);
+  for (int e = e_lo; e <= e_hi; ++e) {
     for (int qt = 0; qt < nq; ++qt) {
       const double *b0 = bt + ((size_t)e * nq + qt) * (P + 1);
       double v = wt[e * nq + qt] * sp.ws * source_at(D, sp.x, xt[e * nq + qt]);
 #pragma unroll
       for (int j = 0; j <= P; ++j) acc[j] += v * b0[j];
     }
-    if (e - 1 >= 0) Fq[(long long)(e - 1) * Qs + q] = acc[0];
+    const int row = e - 1;
+    if (row >= r0 && row < r1) Fq[(long long)(row - r0) * Qs + q] = acc[0];
 #pragma unroll
     for (int r = 0; r < P; ++r) acc[r] = acc[r + 1];
     acc[P] = 0.0;
   }
-  for (int r = 0; r < P; ++r) {
-    int row = nel_t - 1 + r;
-    if (row < Nt) Fq[(long long)row * Qs + q] = acc[r];
-  }
+  if (e_hi == nel_t - 1)
+    for (int r = 0; r < P; ++r) {
+      const int row = e_hi + r;
+      if (row >= r0 && row < r1) Fq[(long long)(row - r0) * Qs + q] = acc[r];
+    }
 }
 
 // Support-extension maximum along one axis (Eq. suppext), separable over the
@@ -820,30 +863,34 @@ void spatial_to_qpts(st_handle *h, const float2 *x, int deriv_dir, float2 *dst, 
   }
 }
 
-}  // namespace
-
-st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bool want_stats) {
+// A field at the Gauss rows of the axes other than x, with x kept in
+// coefficients (the layout of the lean operator's rows, [N_t][rows][n_x]),
+// double-float: the axes d-1 .. 1 in turn (the order of the operator's own
+// forward passes); deriv_dir selects the axis taking the second derivative
+// (-1: none); the result is written to dst or added to it times coef.  The
+// intermediate of three dimensions uses the second work buffer.
+void rows_forward(st_handle *h, const float2 *x, int deriv_dir, float2 *dst, int accumulate, double coef) {
   cudaStream_t s = h->stream;
-  // fields at spatial Gauss points as double-float pairs: u, sum_l D_ll d_ll u, w
-  // (u and w split into pairs first; the FP64 field buffers hold the pairs)
-  float2 *u2 = reinterpret_cast<float2 *>(h->t64a), *w2 = reinterpret_cast<float2 *>(h->t64b);
-  st_count_launch(); d2df_kernel<<<grid_for(h->Ndof), 256, 0, s>>>(u2, u, h->Ndof);
-  st_count_launch(); d2df_kernel<<<grid_for(h->Ndof), 256, 0, s>>>(w2, w, h->Ndof);
-  float2 *U0 = reinterpret_cast<float2 *>(h->U0), *L0 = reinterpret_cast<float2 *>(h->L0);
-  float2 *W0 = reinterpret_cast<float2 *>(h->Wq0);
-  if (!fields_to_qpts_2d(h, u2, w2, U0, L0, W0)) {
-    spatial_to_qpts(h, u2, -1, U0, 0, 1.0);
-    for (int l = 0; l < h->d; ++l) spatial_to_qpts(h, u2, l, L0, l > 0 ? 1 : 0, h->desc.D[l]);
-    spatial_to_qpts(h, w2, -1, W0, 0, 1.0);
+  const float2 *cur = x;
+  for (int l = h->d - 1; l >= 1; --l) {
+    long long inner = 1, outer = h->Nt;
+    for (int m = 0; m < l; ++m) inner *= h->n[m];
+    for (int m = l + 1; m < h->d; ++m) outer *= h->Q[m];
+    const bool last = l == 1;
+    float2 *out = last ? dst : reinterpret_cast<float2 *>(h->W64[1]);
+    const float2 *tab = (l == deriv_dir) ? h->B2q2[l] : h->Bq2[l];
+    launch_interp_df(s, out, cur, tab, h->nel[l], h->p, inner, outer, last ? accumulate : 0, last ? coef : 1.0);
+    cur = out;
   }
-  if (want_stats) {
-    st_count_launch(); zero_ull_kernel<<<grid_for((long long)h->nel_t * h->Nel_s), 256, 0, s>>>(h->emax, (long long)h->nel_t * h->Nel_s);
-    st_count_launch(); zero_ull_kernel<<<1, 32, 0, s>>>((unsigned long long *)h->stats, 4);
-  }
+}
+
+// The arguments of the ionic kernel shared by both operator forms (no field
+// source, no bands, not in rows mode).
+IonicArgs ionic_args(st_handle *h, int kind, bool want_stats) {
   IonicArgs a;
+  std::memset(&a, 0, sizeof(a));
   a.D = h->desc;
   a.g = geom(h);
-  a.U0 = U0; a.L0 = L0; a.W0 = W0;
   a.bt = h->bt; a.xt = h->xt; a.bprod = h->bprod;
   a.bt2 = h->bt2; a.bprod2 = h->bprod2;
   a.tmask = h->tmask;
@@ -856,10 +903,17 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   a.Qs = h->Qs; a.Nel_s = h->Nel_s;
   a.kind = kind;
   a.want_stats = want_stats ? 1 : 0;
-  a.band_hi = h->band32;
-  a.band_lo = h->band_lo;
   a.emax = h->emax;
   a.stats = (unsigned long long *)h->stats;
+  return a;
+}
+
+st_status ionic_launch(st_handle *h, const IonicArgs &a) {
+  cudaStream_t s = h->stream;
+  if (a.want_stats) {
+    st_count_launch(); zero_ull_kernel<<<grid_for((long long)h->nel_t * h->Nel_s), 256, 0, s>>>(h->emax, (long long)h->nel_t * h->Nel_s);
+    st_count_launch(); zero_ull_kernel<<<1, 32, 0, s>>>((unsigned long long *)h->stats, 4);
+  }
   unsigned blocks = (unsigned)((h->Qs + 127) / 128);
   switch (h->p) {
     case 1: st_count_launch(); ionic_tline_kernel<1><<<blocks, 128, 0, s>>>(a); break;
@@ -869,6 +923,54 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;
+}
+
+// The lean form's linearization: u^k and w^k at the Gauss rows of the other
+// axes (the rows the operator reads), and, when the statistics are wanted,
+// the residual maxima of Eq. (theta_ce_u) from the same rows (the other axes'
+// Laplacian part in the first work buffer); no time bands.
+st_status ionic_rows(st_handle *h, const float2 *u2, const float2 *w2, int kind, bool want_stats) {
+  rows_forward(h, u2, -1, h->U1, 0, 1.0);
+  rows_forward(h, w2, -1, h->W1, 0, 1.0);
+  if (!want_stats) {
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+  }
+  float2 *L1 = reinterpret_cast<float2 *>(h->W64[0]);
+  for (int l = 1; l < h->d; ++l) rows_forward(h, u2, l, L1, l > 1 ? 1 : 0, h->desc.D[l]);
+  IonicArgs a = ionic_args(h, kind, want_stats);
+  a.rows_mode = 1;
+  a.U1 = h->U1; a.W1 = h->W1; a.L1 = h->d >= 2 ? L1 : nullptr;
+  a.tbx = h->Bq2[0]; a.tb2x = h->B2q2[0];
+  a.Dx = h->desc.D[0];
+  a.nx = h->n[0]; a.Qx = h->Q[0];
+  a.rows = h->rows_x;
+  return ionic_launch(h, a);
+}
+
+}  // namespace
+
+st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bool want_stats) {
+  cudaStream_t s = h->stream;
+  // fields at spatial Gauss points as double-float pairs: u, sum_l D_ll d_ll u, w
+  // (u and w split into pairs first; the FP64 field buffers hold the pairs)
+  float2 *u2 = reinterpret_cast<float2 *>(h->t64a), *w2 = reinterpret_cast<float2 *>(h->t64b);
+  st_count_launch(); d2df_kernel<<<grid_for(h->Ndof), 256, 0, s>>>(u2, u, h->Ndof);
+  st_count_launch(); d2df_kernel<<<grid_for(h->Ndof), 256, 0, s>>>(w2, w, h->Ndof);
+  h->lin_kind = kind;
+  if (h->lean) return ionic_rows(h, u2, w2, kind, want_stats);
+  float2 *U0 = reinterpret_cast<float2 *>(h->U0), *L0 = reinterpret_cast<float2 *>(h->L0);
+  float2 *W0 = reinterpret_cast<float2 *>(h->Wq0);
+  if (!fields_to_qpts_2d(h, u2, w2, U0, L0, W0)) {
+    spatial_to_qpts(h, u2, -1, U0, 0, 1.0);
+    for (int l = 0; l < h->d; ++l) spatial_to_qpts(h, u2, l, L0, l > 0 ? 1 : 0, h->desc.D[l]);
+    spatial_to_qpts(h, w2, -1, W0, 0, 1.0);
+  }
+  IonicArgs a = ionic_args(h, kind, want_stats);
+  a.U0 = U0; a.L0 = L0; a.W0 = W0;
+  a.band_hi = h->band32;
+  a.band_lo = h->band_lo;
+  return ionic_launch(h, a);
 }
 
 // C[m][c] = sum_k A[k][m] X[k][c] for the columns c0 <= c < min(c0 + 8, nc)
@@ -941,7 +1043,7 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
     // the grid holds several blocks per SM (partials in the first work buffer)
     const int ntile = (Nt + kGT - 1) / kGT, npair = ntile * (ntile + 1) / 2;
     int nsplit = (int)std::max<long long>(1, std::min<long long>((152LL * 6 + npair - 1) / npair, (h->Ns + 255) / 256));
-    while ((long long)nsplit * npair * kGT * kGT > h->NtQs && nsplit > 1) --nsplit;
+    while ((long long)nsplit * npair * kGT * kGT > h->wcap && nsplit > 1) --nsplit;
     const int kchunk = (int)((h->Ns + nsplit - 1) / nsplit);
     st_count_launch(); gram_df_kernel<<<dim3(npair, nsplit), 256, 0, s>>>(h->W64[0], h->theta, Nt, h->Ns, ntile, kchunk);
     st_count_launch(); gram_reduce_kernel<<<grid_for((long long)npair * kGT * kGT), 256, 0, s>>>(h->gram, h->W64[0], Nt, ntile, npair, nsplit);
@@ -988,6 +1090,12 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
   std::vector<double> sig(R);
   for (int r = 0; r < R; ++r) sig[r] = std::sqrt(std::max(lam[r], 0.0));
   ST_CUDA(cudaMemcpyAsync(h->sr, sig.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (h->lean) {
+    // scale of each SU rank term in the lean operator: C_m sigma_r
+    std::vector<double> cf(R);
+    for (int r = 0; r < R; ++r) cf[r] = D.C_m * sig[r];
+    ST_CUDA(cudaMemcpyAsync(h->cfr, cf.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+  }
   // V = Theta^T U_R diag(1/sigma): (N_s x R)
   for (int c0 = 0; c0 < R; c0 += 8) {
     st_count_launch();
@@ -1005,6 +1113,13 @@ st_status su_band_add(st_handle *h) {
   st_count_launch(); theta_t_kernel<<<grid_for((long long)h->Qt * R), 256, 0, s>>>(h->th_t, h->Ur, R, h->Qt, h->hat_i_t, h->hat_l_t);
   st_count_launch(); su_time_band_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tr, h->th_t, h->tauq, h->bt,
                                                                               h->wt, R, h->Nt, h->nel_t, p);
+  if (h->lean) {
+    // the lean operator reads the rank factors themselves: only the time
+    // bands, as double-float pairs
+    st_count_launch(); d2df_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tr2, h->Tr, (long long)R * (p + 1) * h->Nt);
+    ST_CUDA(cudaGetLastError());
+    return ST_OK;
+  }
   // Cq = C_m sigma_r ws theta_s (into the first work buffer, R x Q_s <= N_t x Q_s)
   double *Cq = h->W64[0];
   HatArgs hat;
@@ -1043,28 +1158,36 @@ st_status su_band_add(st_handle *h) {
 
 st_status source_assemble(st_handle *h) {
   cudaStream_t s = h->stream;
-  double *Fq = h->U0;   // [Nt][Qs]
+  // f at the spatial Gauss points of a block of time rows (all rows at once
+  // in the band form, whose field buffer holds them; blocks of rows that fit
+  // one work buffer in the lean form), then the spatial test functions
+  double *Fq = h->lean ? h->W64[0] : h->U0;
+  const long long cap = h->lean ? h->wcap : h->NtQs;
+  const int nr = (int)std::max<long long>(1, std::min<long long>(h->Nt, cap / h->Qs));
   unsigned blocks = (unsigned)((h->Qs + 127) / 128);
   GeomArgs g = geom(h);
-  switch (h->p) {
-    case 1: st_count_launch(); source_tline_kernel<1><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
-    case 2: st_count_launch(); source_tline_kernel<2><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
-    case 3: st_count_launch(); source_tline_kernel<3><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
-    default: st_count_launch(); source_tline_kernel<4><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, Fq); break;
-  }
-  // spatial test functions: Gauss points -> coefficients, last axis first
-  const double *cur = Fq;
   long long qd[3] = {h->Q[0], h->Q[1], h->Q[2]};
   long long nd[3] = {h->n[0], h->n[1], h->n[2]};
-  int ping = 0;
-  for (int l = h->d - 1; l >= 0; --l) {
-    long long inner = 1, outer = h->Nt;
-    for (int m = 0; m < l; ++m) inner *= qd[m];
-    for (int m = l + 1; m < h->d; ++m) outer *= nd[m];
-    double *out = (l == 0) ? h->f64 : h->W64[ping];
-    launch_interp_bwd<double>(s, out, cur, h->Bq[l], h->nel[l], h->p, h->nq, inner, outer, false);
-    cur = out;
-    ping ^= 1;
+  for (int r0 = 0; r0 < h->Nt; r0 += nr) {
+    const int rows = std::min(nr, h->Nt - r0);
+    switch (h->p) {
+      case 1: st_count_launch(); source_tline_kernel<1><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, r0, rows, Fq); break;
+      case 2: st_count_launch(); source_tline_kernel<2><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, r0, rows, Fq); break;
+      case 3: st_count_launch(); source_tline_kernel<3><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, r0, rows, Fq); break;
+      default: st_count_launch(); source_tline_kernel<4><<<blocks, 128, 0, s>>>(h->desc, g, h->bt, h->wt, h->xt, h->Nt, h->nel_t, h->Qs, r0, rows, Fq); break;
+    }
+    // spatial test functions: Gauss points -> coefficients, last axis first
+    const double *cur = Fq;
+    int ping = h->lean ? 1 : 0;   // the lean form's rows sit in the first work buffer
+    for (int l = h->d - 1; l >= 0; --l) {
+      long long inner = 1, outer = rows;
+      for (int m = 0; m < l; ++m) inner *= qd[m];
+      for (int m = l + 1; m < h->d; ++m) outer *= nd[m];
+      double *out = (l == 0) ? h->f64 + (long long)r0 * h->Ns : h->W64[ping];
+      launch_interp_bwd<double>(s, out, cur, h->Bq[l], h->nel[l], h->p, h->nq, inner, outer, false);
+      cur = out;
+      ping ^= 1;
+    }
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;

@@ -2409,6 +2409,13 @@ void launch_sub64(cudaStream_t s, double *r, const double *b, const double *ax, 
 void launch_d2f(cudaStream_t s, float *y, const double *x, double scale, long long n) {
   st_count_launch(); d2f_kernel<<<grid_for(n), kThreads, 0, s>>>(y, x, scale, n);
 }
+__global__ void f2d_kernel(double *__restrict__ y, const float *__restrict__ x, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+void launch_f2d(cudaStream_t s, double *y, const float *x, long long n) {
+  st_count_launch(); f2d_kernel<<<grid_for(n), 256, 0, s>>>(y, x, n);
+}
 void launch_f2d_axpy(cudaStream_t s, double *y, const float *x, double scale, long long n) {
   st_count_launch(); f2d_axpy_kernel<<<grid_for(n), kThreads, 0, s>>>(y, x, scale, n);
 }

@@ -89,6 +89,17 @@ struct st_handle {
   int nxp = 0;                // padded innermost axis
   float *lu32 = nullptr;
 
+  // operator form: time bands stored per spatial Gauss point (band form), or
+  // none (lean form: the reaction term is integrated from u^k, w^k in the
+  // apply and the SU term kept as its rank factors; see kernels_lean.cu)
+  bool lean = false;
+  float2 *U1 = nullptr, *W1 = nullptr;   // lean: u^k, w^k at the Gauss rows of the other axes, [N_t][rows][n_x] pairs
+  float2 *wt2 = nullptr;                 // time quadrature weights as double-float pairs
+  double *cfr = nullptr;                 // lean: scale C_m sigma_r of each SU rank
+  int lin_kind = ST_PICARD;              // linearization of the current operator
+  bool inner_df = false;                 // the mixed inner solve applies the operator in double-float
+  long long wcap = 0;                    // values per Gauss-point work buffer (W64 doubles, W32 floats)
+  long long rows_x = 1;                  // Gauss rows of the axes other than x: prod_{l>=1} Q_l
   // linearization: symmetric time band per spatial Gauss point, [k][it][q], k = 0..p
   // time bands per spatial Gauss point [k][it][q] as double-float pairs:
   // band32 = high parts (the FP32 operator), band_lo = low parts
@@ -237,6 +248,31 @@ void launch_interp_fwd_pairs(cudaStream_t s, float2 *out, const float2 *in, cons
 template <typename TO>
 void launch_interp_bwd_pairs(cudaStream_t s, TO *out, const float2 *in, const float2 *tab, int nel, int p,
                              long long inner, long long outer, bool accumulate);
+// Lean form of the reaction + SU part (kernels_lean.cu): everything the
+// kernel needs besides the x rows in and out.
+struct LeanTerms {
+  const float2 *U1 = nullptr, *W1 = nullptr;   // u^k, w^k rows (pairs); null without M_R
+  const float2 *bt = nullptr, *wt = nullptr;   // time basis [e][gt][a] and weights [e*nq+gt], pairs
+  const double *ws[3] = {};                    // spatial weights per direction
+  const int *hi[3] = {};                       // Greville hat data per 1D Gauss point
+  const double *hl[3] = {};
+  const double *V = nullptr, *cf = nullptr;    // rank factors [N_s][Rt] and scales [Rt]
+  const float2 *Tb = nullptr;                  // rank time bands [Rt][p+1][N_t], pairs
+  int Rt = 0;
+  int exact = 0, newton = 0;
+  double c1 = 0, c2 = 0, a = 0;
+  int d = 1, p = 1, nel = 1, Nt = 1, nel_t = 1;
+  int n[3] = {1, 1, 1}, Q[3] = {1, 1, 1};
+};
+// True when one block holds an x row of the lean kernel.
+bool xlean_feasible(int nel, int p);
+// Largest rank-term count the lean kernel takes (shared memory).
+int xlean_max_rank(int nel, int p, bool exact);
+// Y1 = (reaction + SU part along x and time) X1 for every Gauss row of the
+// other axes; T = float (FP32) or float2 (double-float pairs).
+template <typename T>
+st_status launch_xlean(cudaStream_t s, const LeanTerms &L, T *Y1, const T *X1, const T *tab, long long rows);
+LeanTerms lean_terms(st_handle *h);
 // Largest block (threads) of the fused x pass for this element size and degree.
 int xband_fused_limit(size_t elem, int p);
 template <typename T>
@@ -278,6 +314,7 @@ void launch_axpby64(cudaStream_t s, double *y, const double *x, double a, double
 void launch_sub64(cudaStream_t s, double *r, const double *b, const double *ax, long long n);
 void launch_d2f(cudaStream_t s, float *y, const double *x, double scale, long long n);
 void launch_f2d_axpy(cudaStream_t s, double *y, const float *x, double scale, long long n);
+void launch_f2d(cudaStream_t s, double *y, const float *x, long long n);
 void launch_absmax64(cudaStream_t s, double *out, const double *x, const double *y, long long n, double *scratch);
 void launch_norm2_64(cudaStream_t s, double *out, const double *x, long long n, double *scratch);
 void launch_band_to_f32(cudaStream_t s, float *out, const double *in, long long n);

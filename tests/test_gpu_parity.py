@@ -107,10 +107,15 @@ def test_rhs(P, c):
     s.close()
 
 
-@pytest.mark.parametrize("c", CASES, ids=IDS)
+# (case, operator form): the band form everywhere, the lean form where it applies (d >= 2)
+FORM_CASES = [(c, f) for c in CASES for f in ("bands", "lean") if f == "bands" or c["d"] >= 2]
+FORM_IDS = [f"d{c['d']}p{c['p']}-{f}" for c, f in FORM_CASES]
+
+
+@pytest.mark.parametrize("c,form", FORM_CASES, ids=FORM_IDS)
 @pytest.mark.parametrize("kind", ["picard", "newton"])
-def test_linearization_and_apply(P, c, kind):
-    desc = problem(c, nonlinear=kind)
+def test_linearization_and_apply(P, c, form, kind):
+    desc = problem(c, nonlinear=kind, operator_form=form)
     o = Oracle(desc)
     u, w = iterate(o, 2)
     A, info = o.linearization(u, w, kind)
@@ -135,12 +140,13 @@ def test_linearization_and_apply(P, c, kind):
     s.close()
 
 
-def test_lowrank_long_time(P):
+@pytest.mark.parametrize("form", ["bands", "lean"])
+def test_lowrank_long_time(P, form):
     """A Gram matrix larger than one batch of Lanczos steps (N_t = 61 against
     24), so the leading Ritz pairs must pass the residual test before the rank
     is taken: rank, Theta-hat and the FP64 operator as in the cases above."""
     c = dict(d=2, p=2, n_el=[8, 8], n_el_t=60)
-    desc = problem(c)
+    desc = problem(c, operator_form=form)
     o = Oracle(desc)
     u, w = iterate(o, 2)
     A, info = o.linearization(u, w, "picard")
@@ -155,13 +161,14 @@ def test_lowrank_long_time(P):
     s.close()
 
 
+@pytest.mark.parametrize("form", ["bands", "lean"])
 @pytest.mark.parametrize("kind", ["picard", "newton"])
-def test_apply_tiny_mesh(P, kind):
+def test_apply_tiny_mesh(P, form, kind):
     """A 2D mesh of 1 x 2 elements with p = 1 (6 coefficients per time slice, 3
     time functions): one 32-column strip far wider than the plane, time bands
     cut at both ends.  FP64 and FP32 operator as in the cases above."""
     c = dict(d=2, p=1, n_el=[1, 2], n_el_t=3)
-    desc = problem(c, nonlinear=kind)
+    desc = problem(c, nonlinear=kind, operator_form=form)
     o = Oracle(desc)
     u, w = iterate(o, 2)
     A, _ = o.linearization(u, w, kind)
@@ -210,10 +217,19 @@ def test_wupdate(P, c):
     s.close()
 
 
-@pytest.mark.parametrize("c", CASES[:5], ids=IDS[:5])
+SOLVE_CASES = [(c, f, i) for c in CASES[:5] for f, i in (("bands", "auto"), ("lean", "fp32"), ("lean", "df"))
+               if f == "bands" or c["d"] >= 2]
+SOLVE_IDS = [f"d{c['d']}p{c['p']}-{f}-{i}" for c, f, i in SOLVE_CASES]
+
+
+@pytest.mark.parametrize("c,form,inner", SOLVE_CASES, ids=SOLVE_IDS)
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_linsolve(P, c, precision):
-    desc = problem(c, precision=precision, rtol=1e-13 if precision == "fp64" else 1e-8, gmres_m=60)
+def test_linsolve(P, c, form, inner, precision):
+    """FP64 solves to 1e-13 against the oracle's direct solve (1e-10); mixed
+    solves, with the inner operator in FP32 or in double-float, to an oracle
+    residual of 1e-8."""
+    desc = problem(c, precision=precision, rtol=1e-13 if precision == "fp64" else 1e-8, gmres_m=60,
+                   operator_form=form, inner_op=inner)
     o = Oracle(desc)
     u, w = iterate(o, 2)
     A, _ = o.linearization(u, w)
@@ -235,11 +251,14 @@ def test_linsolve(P, c, precision):
     s.close()
 
 
-@pytest.mark.parametrize("c", CASES[:5], ids=IDS[:5])
+NL_CASES = [(c, f) for c in CASES[:5] for f in ("bands", "lean") if f == "bands" or c["d"] >= 2]
+
+
+@pytest.mark.parametrize("c,form", NL_CASES, ids=[f"d{c['d']}p{c['p']}-{f}" for c, f in NL_CASES])
 @pytest.mark.parametrize("kind", ["picard", "newton"])
-def test_nonlinear_iterations(P, c, kind):
+def test_nonlinear_iterations(P, c, form, kind):
     """Three nonlinear steps from u = w = 0 on both sides (FP64, tight inner solves)."""
-    desc = problem(c, nonlinear=kind, max_fp=3, delta=0.0, rtol=1e-13, gmres_m=80)
+    desc = problem(c, nonlinear=kind, max_fp=3, delta=0.0, rtol=1e-13, gmres_m=80, operator_form=form)
     o = Oracle(desc)
     u_ref, w_ref, _ = o.solve(max_fp=3)
     s = solver(P, desc)

@@ -37,7 +37,10 @@ SHAPES = ["3,16,16,16", "3,120,33,64", "2,194,33,64", "2,216,33,64", "2,150,33,6
           "2,255,32,16", "1,300,20,16", "4,200,20,16", "2,5,4,6", "3,4,5,5", "1,6,5,7", "4,6,5,7", "2,1,2,3",
           "2,8,8,512", "2,7,9", "3,40,20", "2,3,4,3,4", "3,8,8,8,16", "4,10,10,10,8", "1,20,20,20,8",
           "2,200,8,8,8", "3,16,16,16:fp64", "2,194,33,64:fp64:newton", "3,120,33,64:newton",
-          "2,8,8,8,16:fp64", "2,9,7,12:galerkin", "3,9,7,12:symmetric:wzero", "1,40,12:fp64"]
+          "2,8,8,8,16:fp64", "2,9,7,12:galerkin", "3,9,7,12:symmetric:wzero", "1,40,12:fp64",
+          # the band form where the lean one is the default, and the lean form at its widest x
+          "3,16,16,16:bands", "3,120,33,64:bands", "2,200,8,8,8:bands:fp64", "3,8,8,8,16:bands:newton",
+          "1,255,8,16:lean", "4,252,6,8:lean:fp64", "2,20,6,5,8:lean:newton"]
 
 
 def _have_tools():
@@ -172,7 +175,7 @@ def test_footprint_bounds_what_a_handle_allocates(audit_env):
 def test_audit_sees_a_missing_opt_in(audit_env):
     """With opt-ins ignored, the kernels that need more than 48 KB of dynamic
     shared memory are refused: the audit can see the failure it guards against."""
-    rows, log = run(audit_env, ["3,120,33,64", "2,194,33,64"], AUDIT_IGNORE_OPTIN="1")
+    rows, log = run(audit_env, ["3,120,33,64:bands", "2,194,33,64:bands"], AUDIT_IGNORE_OPTIN="1")
     assert sum(r["violations"] for r in rows) > 0
     assert "no opt-in" in log
     assert any(r["error"] and "pending since the launch at" in r["error"] for r in rows)

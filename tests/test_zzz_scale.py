@@ -18,6 +18,10 @@
       is bounded by the residual norm, which the solve brings below
       1e-8 ||f||.
   These checks use the Galerkin operator.
+* The largest workload (3D, p = 3, 96^3 x 192 elements), in the lean form:
+  f, both operators and the preconditioner on sampled rows.
+* Both operator forms (time bands stored per Gauss point, or the lean form)
+  on the 2D and 3D problems.
 * The 2D problem again with its SU term, at a smooth seeded linearization (an
   excitation front, workloads.wave_fields): the oracle evaluates the residual
   one time element at a time (oracle/streamed.py) and forms Theta-hat, its
@@ -118,11 +122,11 @@ def test_newton_workload_full_size():
     s.close()
 
 
-def sampled_rows_at_full_size(name):
+def sampled_rows_at_full_size(name, form="auto", solve=True, **over):
     torch = torch_cuda()
     P = library()
     desc = W.config(name)
-    desc.update(stabilization="galerkin", precision="mixed")
+    desc.update(stabilization="galerkin", precision="mixed", operator_form=form, **over)
     torch.cuda.empty_cache()
     free, _total = torch.cuda.mem_get_info()
     need = P.footprint(desc) + 8 * 8 * W.n_dofs(desc)   # the handle and the test's own vectors
@@ -152,6 +156,9 @@ def sampled_rows_at_full_size(name):
     s.precond(ptr(dr), ptr(dz), P.ST_FP64)
     SR.check_precond(st, desc, rows, inp, host(dz), SR.PRECOND_RESIDUAL_TOL)
     del dr, dz
+    if not solve:
+        s.close()
+        return
     dsol = empty(n)
     out = s.linsolve(ptr(f), ptr(dsol))
     assert out["rel_res"] <= 1e-8
@@ -159,12 +166,21 @@ def sampled_rows_at_full_size(name):
     s.close()
 
 
-def test_2d_workload_full_size_sampled_rows():
-    sampled_rows_at_full_size("c2_aniso_2d")
+@pytest.mark.parametrize("form", ["bands", "lean"])
+def test_2d_workload_full_size_sampled_rows(form):
+    sampled_rows_at_full_size("c2_aniso_2d", form)
 
 
-def test_3d_workload_full_size_sampled_rows():
-    sampled_rows_at_full_size("c3_cube_3d")
+@pytest.mark.parametrize("form", ["bands", "lean"])
+def test_3d_workload_full_size_sampled_rows(form):
+    sampled_rows_at_full_size("c3_cube_3d", form)
+
+
+def test_c5_workload_full_size_sampled_rows():
+    """The largest workload (3D, p = 3, 96^3 x 192 elements, 188 M unknowns),
+    which only the lean form fits on one GB300: f, both operators and the
+    preconditioner on sampled rows (the solve is timed by the benchmark)."""
+    sampled_rows_at_full_size("c5_cube_3d", "lean", solve=False, gmres_m=40)
 
 
 def test_2d_workload_full_size_su():
@@ -189,26 +205,28 @@ def test_2d_workload_full_size_su():
     fro = np.sqrt(np.sum(allsv ** 2))
     tail = np.sqrt(np.concatenate([np.cumsum((allsv ** 2)[::-1])[::-1], [0.0]]))
     assert R >= 2 and tail[R - 1] > (1 + 1e-4) * eps * fro and tail[R] < (1 - 1e-4) * eps * fro
-    s = P.Solver(desc, stream())
-    du, dw = dev(u), dev(w)
-    g = s.ionic(ptr(du), ptr(dw))
-    for key in ("u_max", "ut_max", "r_max", "den"):
-        assert abs(g[key] - info[key]) <= 1e-12 * info[key], (key, g[key], info[key])
-    assert g["rank"] == R
-    thg = np.array(s.get("theta_hat", n)).reshape(st.N_t, st.N_s)
-    assert np.abs(thg - th).max() <= 1e-12
-    assert rel(np.array(s.get("lowrank_s", R)), sv) <= 1e-10
     rows = SR.sample_rows(st, desc, seed=5)
     _, tau_q = tau_solve(st)
     terms = OR.picard_galerkin_terms(st, desc, u, w) + S.su_terms(st, desc, tau_q, U, sv, V)
     x = W.random_vector(n, seed=13)
     ref = OR.apply_rows(st, terms, rows, x)
-    dx, dy = dev(x), empty(n)
-    s.apply(ptr(dx), ptr(dy), P.ST_FP64)
-    y = host(dy)
-    assert np.abs(y[rows] - ref).max() <= 1e-12 * np.abs(y).max()
-    dx32, dy32 = dev(x, np.float32), empty(n, "float32")
-    s.apply(ptr(dx32), ptr(dy32), P.ST_MIXED)
-    y32 = host(dy32)
-    assert np.abs(y32[rows] - ref).max() <= 2e-5 * np.abs(y32).max()
-    s.close()
+    for form in ("bands", "lean"):
+        s = P.Solver(dict(desc, operator_form=form), stream())
+        du, dw = dev(u), dev(w)
+        g = s.ionic(ptr(du), ptr(dw))
+        for key in ("u_max", "ut_max", "r_max", "den"):
+            assert abs(g[key] - info[key]) <= 1e-12 * info[key], (form, key, g[key], info[key])
+        assert g["rank"] == R
+        thg = np.array(s.get("theta_hat", n)).reshape(st.N_t, st.N_s)
+        assert np.abs(thg - th).max() <= 1e-12
+        assert rel(np.array(s.get("lowrank_s", R)), sv) <= 1e-10
+        dx, dy = dev(x), empty(n)
+        s.apply(ptr(dx), ptr(dy), P.ST_FP64)
+        y = host(dy)
+        assert np.abs(y[rows] - ref).max() <= 1e-12 * np.abs(y).max(), form
+        dx32, dy32 = dev(x, np.float32), empty(n, "float32")
+        s.apply(ptr(dx32), ptr(dy32), P.ST_MIXED)
+        y32 = host(dy32)
+        assert np.abs(y32[rows] - ref).max() <= 2e-5 * np.abs(y32).max(), form
+        s.close()
+        del du, dw, dx, dy, dx32, dy32

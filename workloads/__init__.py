@@ -24,6 +24,10 @@ Problem description keys (all plain Python numbers / lists / strings):
   fix_w_zero      True: recovery variable held at zero (smooth 1D test, Sec. 4.1)
   precision       "fp64" | "mixed"
   gmres_m, rtol, max_it  Krylov restart length, relative residual target, cap
+  operator_form   "auto" | "bands" | "lean"   (how the device stores the
+                  reaction + SU part of the operator; results are the same)
+  inner_op        "auto" | "fp32" | "df"   (arithmetic of the operator inside
+                  the mixed mode's FP32 Krylov solve)
 """
 
 import copy
@@ -46,7 +50,7 @@ def base_desc(**over):
         source=dict(kind="zero"),
         stabilization="su", suppext="literal", eps_theta=0.1,
         nonlinear="picard", alpha=0.5, delta=1e-4, max_fp=60, fix_w_zero=False,
-        precision="fp64", gmres_m=100, rtol=1e-8, max_it=2000,
+        precision="fp64", gmres_m=100, rtol=1e-8, max_it=2000, operator_form="auto", inner_op="auto",
     )
     desc.update(PAPER_RM)
     for k, v in over.items():
@@ -85,6 +89,9 @@ def config(name, scale=None):
                    seeded corner stimulus (seed 2), Picard, FP64 (and mixed).
     c3_cube_3d     3D, p=2, 64^3 x 128 elements, D=1e-3 I, planar stimulus x<0.05,
                    mixed precision.
+    c5_cube_3d     3D, p=3, 96^3 x 192 elements (188,238,006 unknowns),
+                   D=diag(1e-3,5e-4,2.5e-4), two staggered stimuli ([0,0.1]^3 for
+                   t<1 and [0.9,1]^3 for 10<=t<11), mixed precision.
     heat_mms_2d    linear heat manufactured solution cos(pi x)cos(pi y)sin(t), T=1.
     e1_mms_1d      smooth 1D test of Sec. 4.1 (Omega=(0,1), T=1, D=1e-4).
 
@@ -109,6 +116,13 @@ def config(name, scale=None):
                          D=[1e-3, 1e-3, 1e-3], nonlinear="picard", precision="mixed",
                          source=dict(kind="stim", boxes=[stim_box([0, 0, 0], [0.05, 1, 1], 0.0, 1.0,
                                                                   DIMENSIONAL_STIM_AMP)]))
+        desc.update(DIMENSIONAL_RM)
+    elif name == "c5_cube_3d":
+        desc = base_desc(d=3, p=3, n_el=[96, 96, 96], n_el_t=192, T=50.0, C_m=1.0,
+                         D=[1e-3, 5e-4, 2.5e-4], nonlinear="picard", precision="mixed",
+                         source=dict(kind="stim", boxes=[
+                             stim_box([0, 0, 0], [0.1, 0.1, 0.1], 0.0, 1.0, DIMENSIONAL_STIM_AMP),
+                             stim_box([0.9, 0.9, 0.9], [1, 1, 1], 10.0, 11.0, DIMENSIONAL_STIM_AMP)]))
         desc.update(DIMENSIONAL_RM)
     elif name == "heat_mms_2d":
         desc = base_desc(d=2, p=2, n_el=[8, 8], n_el_t=8, T=1.0, C_m=1.0, D=[1e-3, 2.5e-4],
