@@ -14,7 +14,9 @@ Follows Sec. 3 of the paper:
     conductivity scaling D_ll on each direction (the unit-D form of the paper
     is available with unit_D=True);
   * a Newton variant on the u-equation (Jacobian coefficient C_J, w lagged,
-    theta frozen at the current iterate, no relaxation).
+    theta frozen at the current iterate, no relaxation);
+  * optionally (eps_reaction >= 0) the reaction coefficient in low rank:
+    its values at the Greville grid truncated like Theta-hat (reading A7).
 
 Linear systems are solved with scipy's sparse direct solver (SuperLU).
 
@@ -26,7 +28,7 @@ import scipy.sparse.linalg as spla
 
 from . import model
 from .spacetime import SpaceTime
-from .stabilization import tau_solve, theta_hat, low_rank, interpolate_at_gauss
+from .stabilization import tau_solve, theta_hat, low_rank, interpolate_at_gauss, greville_values
 
 
 class Oracle:
@@ -76,13 +78,29 @@ class Oracle:
             terms += st.su_terms(self.desc["C_m"], self.tau_q, theta_q)
         return st.assemble(terms)
 
+    def reaction_lowrank(self, u, w, kind):
+        """Low-rank reaction coefficient (reading A7, the SUPG variant's
+        low-rank C_r of Sec. 4.2 carried over to SU): the coefficient (C_r of
+        Eq. reaction, or C_J for Newton) of the splines' values at the Greville
+        grid, truncated like Theta-hat at the relative Frobenius tolerance
+        eps_reaction (Eq. tol), and its (d+1)-linear interpolant at the Gauss
+        points.  Returns (coefficient at the Gauss points, U, s, V)."""
+        d = self.desc
+        ug, wg = greville_values(self.st, u), greville_values(self.st, w)
+        C = model.jacobian_coef(d, ug, wg) if kind == "newton" else model.reaction_coef(d, ug, wg)
+        U, s, V = low_rank(C, d["eps_reaction"])
+        return interpolate_at_gauss(self.st, (U * s[None, :]) @ V.T), U, s, V
+
     def linearization(self, u, w, kind=None):
         """(A, ionic info) of one nonlinear step at (u, w)."""
         d = self.desc
         kind = d["nonlinear"] if kind is None else kind
         info = self.ionic(u, w)
         fl = info["fields"]
-        if kind == "newton":
+        if d.get("eps_reaction", -1.0) >= 0.0:
+            coef, Uc, sc, Vc = self.reaction_lowrank(u, w, kind)
+            info.update(Uc=Uc, sc=sc, Vc=Vc)
+        elif kind == "newton":
             coef = model.jacobian_coef(d, fl["u"], fl["w"])
         else:
             coef = model.reaction_coef(d, fl["u"], fl["w"])

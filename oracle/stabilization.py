@@ -9,6 +9,8 @@
 * The low-rank approximation U R V^T of Theta-hat at relative Frobenius
   tolerance eps (Eq. tol), and theta at the Gauss points as the
   (d+1)-linear interpolant on the Greville grid (Sec. 3.1).
+* The values of a spline at the Greville grid, from which the low-rank
+  reaction coefficient of reading A7 is formed the same way.
 
 Readings where the paper is silent: tau is the
 minimum-norm solution in the scaled coefficients c_k / h_t^(2k-1); the support
@@ -23,6 +25,7 @@ Test infrastructure only: nothing in the product path imports this package.
 import numpy as np
 
 from .bspline import bspline_all, open_uniform_knots
+from .bspline import greville as greville_param
 
 
 def tau_solve(st):
@@ -123,6 +126,23 @@ def low_rank(theta, eps):
     tail = np.sqrt(np.concatenate([np.cumsum((s ** 2)[::-1])[::-1], [0.0]]))  # tail[r] = ||s[r:]||
     R = next(r for r in range(1, len(s) + 1) if tail[r] <= eps * fro)
     return U[:, :R], s[:R], Vt[:R].T
+
+
+def greville_values(st, vec):
+    """Values of the space-time spline with coefficient vector `vec` at the
+    Greville grid (time: the Greville points of b_2 .. b_{n_t}, the functions of
+    X_t; space: all Greville points), as an (N_t, N_s) matrix: the
+    tensor-product spline evaluated with the 1D B-splines at those points."""
+    tdir = st.tdir
+    Gt = bspline_all(tdir.knots, st.p, greville_param(tdir.knots, st.p)[1:], 0)[:, 1:]   # (N_t, N_t)
+    X = vec.reshape([st.N_t] + st.n[::-1])                                             # (t, z, y, x)
+    X = np.tensordot(Gt, X, axes=(1, 0))
+    for pos in range(st.d):
+        l = st.d - 1 - pos
+        dr = st.sdirs[l]
+        G = bspline_all(dr.knots, st.p, greville_param(dr.knots, st.p), 0)             # (n_l, n_l)
+        X = np.moveaxis(np.tensordot(G, X, axes=(1, 1 + pos)), 0, 1 + pos)
+    return X.reshape(st.N_t, st.N_s)
 
 
 def hat_weights(grid, x):

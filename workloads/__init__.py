@@ -19,6 +19,8 @@ Problem description keys (all plain Python numbers / lists / strings):
   stabilization   "galerkin" | "su"
   suppext         "literal" | "symmetric"   (support-extension reading, see DESIGN)
   eps_theta       relative Frobenius tolerance of the low-rank theta (Sec. 3.1)
+  eps_reaction    < 0: exact reaction coefficient at the Gauss points; >= 0: its
+                  Greville-grid values in low rank at that tolerance
   nonlinear       "picard" (fixed point with relaxation) | "newton"
   alpha, delta, max_fp   relaxation, stopping tolerance, iteration cap
   fix_w_zero      True: recovery variable held at zero (smooth 1D test, Sec. 4.1)
@@ -48,7 +50,7 @@ def base_desc(**over):
     desc = dict(
         d=2, p=2, n_el=[4, 4], n_el_t=8, T=1.0, C_m=1.0, D=[1e-3, 1e-3],
         source=dict(kind="zero"),
-        stabilization="su", suppext="literal", eps_theta=0.1,
+        stabilization="su", suppext="literal", eps_theta=0.1, eps_reaction=-1.0,
         nonlinear="picard", alpha=0.5, delta=1e-4, max_fp=60, fix_w_zero=False,
         precision="fp64", gmres_m=100, rtol=1e-8, max_it=2000, operator_form="auto", inner_op="auto",
     )
