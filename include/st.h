@@ -118,6 +118,12 @@ typedef struct {
   int max_it;            /* cap on total inner GMRES iterations per linear solve */
   int operator_form;     /* ST_FORM_* */
   int inner_op;          /* ST_INNER_* (mixed mode) */
+  double eps_reaction;   /* < 0: the reaction coefficient of Eq. (reaction) (C_J for
+                          * Newton) exact at the Gauss points; >= 0: its values at
+                          * the Greville grid, truncated to low rank at this
+                          * relative Frobenius tolerance like Theta-hat (Eq. tol)
+                          * and interpolated (d+1)-linearly, the low-rank reaction
+                          * matrices of Sec. 4.2 */
 } st_problem_desc;
 
 typedef struct st_handle st_handle;
@@ -137,6 +143,7 @@ typedef struct {
   double den;            /* C_m (u_max / T + ut_max) */
   double r_max;          /* max |R| over the Gauss points */
   double theta_fro;      /* ||Theta-hat||_F */
+  int rank_reaction;     /* rank of the low-rank reaction coefficient (eps_reaction >= 0), else 0 */
 } st_ionic_info;
 
 /* Per-solve statistics. */
@@ -285,7 +292,8 @@ enum {
   ST_GET_LOWRANK_V = 3,  /* double[N_s * R]    row-major */
   ST_GET_TAU_Q = 4,      /* double[p * n_el_t * (p+1)]  tau_k at time Gauss points */
   ST_GET_FD_EIG = 5,     /* double[sum_l n_l]  generalized eigenvalues of (D_ll K_l, M_l) */
-  ST_GET_BANDS_1D = 6    /* double[(sum_l 2 n_l + 2 N_t) (2p+1)]: M_l, K_l per direction, M_t, W_t */
+  ST_GET_BANDS_1D = 6,   /* double[(sum_l 2 n_l + 2 N_t) (2p+1)]: M_l, K_l per direction, M_t, W_t */
+  ST_GET_REACTION_S = 7  /* double[rank_reaction]  singular values of the low-rank reaction coefficient */
 };
 st_status st_get(st_handle *h, int what, void *dst_host, size_t bytes);
 

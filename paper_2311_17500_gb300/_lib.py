@@ -23,7 +23,7 @@ ST_SUPPEXT = {"literal": 0, "symmetric": 1}
 ST_FORM = {"auto": 0, "bands": 1, "lean": 2}
 ST_INNER = {"auto": 0, "fp32": 1, "df": 2}
 ST_MAX_STIM = 8
-GET = dict(theta_hat=0, lowrank_s=1, lowrank_u=2, lowrank_v=3, tau_q=4, fd_eig=5, bands_1d=6)
+GET = dict(theta_hat=0, lowrank_s=1, lowrank_u=2, lowrank_v=3, tau_q=4, fd_eig=5, bands_1d=6, reaction_s=7)
 
 EXPORTS = ["st_footprint", "st_setup", "st_destroy", "st_error_string", "st_get_dims", "st_ionic",
            "st_linearize", "st_apply", "st_precond", "st_linsolve", "st_wupdate", "st_rhs", "st_solve",
@@ -47,7 +47,8 @@ class StProblemDesc(ctypes.Structure):
                 ("nonlinear", ctypes.c_int), ("alpha", ctypes.c_double), ("delta", ctypes.c_double),
                 ("max_fp", ctypes.c_int), ("fix_w_zero", ctypes.c_int), ("precision", ctypes.c_int),
                 ("gmres_m", ctypes.c_int), ("rtol", ctypes.c_double), ("max_it", ctypes.c_int),
-                ("operator_form", ctypes.c_int), ("inner_op", ctypes.c_int)]
+                ("operator_form", ctypes.c_int), ("inner_op", ctypes.c_int),
+                ("eps_reaction", ctypes.c_double)]
 
 
 class StDims(ctypes.Structure):
@@ -57,7 +58,8 @@ class StDims(ctypes.Structure):
 
 class StIonicInfo(ctypes.Structure):
     _fields_ = [("rank", ctypes.c_int), ("u_max", ctypes.c_double), ("ut_max", ctypes.c_double),
-                ("den", ctypes.c_double), ("r_max", ctypes.c_double), ("theta_fro", ctypes.c_double)]
+                ("den", ctypes.c_double), ("r_max", ctypes.c_double), ("theta_fro", ctypes.c_double),
+                ("rank_reaction", ctypes.c_int)]
 
 
 class StStats(ctypes.Structure):
@@ -153,6 +155,7 @@ def make_desc(desc):
     c.max_it = int(desc["max_it"])
     c.operator_form = ST_FORM[desc.get("operator_form", "auto")]
     c.inner_op = ST_INNER[desc.get("inner_op", "auto")]
+    c.eps_reaction = float(desc.get("eps_reaction", -1.0))
     return c
 
 

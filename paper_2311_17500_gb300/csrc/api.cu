@@ -48,6 +48,7 @@ st_status validate(const st_problem_desc *d) {
     return ST_ERR_ARG;
   if (d->operator_form < ST_FORM_AUTO || d->operator_form > ST_FORM_LEAN) return ST_ERR_ARG;
   if (d->inner_op < ST_INNER_AUTO || d->inner_op > ST_INNER_DF) return ST_ERR_ARG;
+  if (!(d->eps_reaction == d->eps_reaction)) return ST_ERR_ARG;   // NaN
   if (d->operator_form == ST_FORM_LEAN && !lean_applies(*d)) return ST_ERR_ARG;
   return ST_OK;
 }
@@ -107,6 +108,10 @@ Sizes plan(const st_problem_desc &D) {
   b += 2 * (std::max<size_t>(np, 2 * (size_t)z.Ndof) + 64) * f4;   // padded transform buffers
   if (D.precision == ST_FP64) b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * d8;
   else b += (size_t)(2 * z.m + 1) * (z.Ndof + 64) * f4;
+  if (D.eps_reaction >= 0.0) {                                     // low-rank reaction factors and bands
+    b += (size_t)z.cap * (z.Nt + z.Ns + 2 + z.Qt + (z.p + 1) * z.Nt) * d8 + (size_t)z.cap * (z.p + 1) * z.Nt * 8;
+    b += (size_t)(2 * z.nmax + z.Nt) * z.B * d8;
+  }
   b += (size_t)(608 * (2 * z.m + 56) + 4096) * d8;                 // reduction scratch
   b += 2 * (size_t)(2 * (z.m + 2) + 8) * d8 + 256;                 // Hessenberg column, DCGS2 coefficients, flags
   b += 64 * 1024;   // small tables: 1D data of tiny meshes (one element at least each), Gauss-point hats
@@ -573,6 +578,11 @@ LeanTerms lean_terms(st_handle *h) {
   L.cf = h->cfr;
   L.Tb = h->Tr2;
   L.newton = h->lin_kind == ST_NEWTON;
+  if (D.eps_reaction >= 0.0) {
+    // the reaction term as rank terms of its own (no Gauss-point evaluation)
+    L.exact = 0;
+    L.V2 = h->VrC; L.cf2 = h->cfc; L.Tb2 = h->Tc2; L.R2 = h->rankC;
+  }
   L.c1 = D.c1; L.c2 = D.c2; L.a = D.a;
   L.d = h->d; L.p = h->p; L.nel = h->nel[0]; L.Nt = h->Nt; L.nel_t = h->nel_t;
   return L;
@@ -583,9 +593,10 @@ LeanTerms lean_terms(st_handle *h) {
 // of the rank terms, the time integration of one element and the projection.
 static double lean_flops(st_handle *h) {
   const double P = h->p, nq = h->nq;
-  const double R = h->desc.stabilization == ST_SU ? h->rank : 0;
-  const double per = 3 * nq * (P + 1) + R * (P + 1) * nq + (2 * P + 1) * nq +
-                     nq * nq * (4 * (P + 1) + 6) + nq * (P + 1);
+  const bool exact = h->desc.eps_reaction < 0.0;
+  const double R = (h->desc.stabilization == ST_SU ? h->rank : 0) + (exact ? 0 : h->rankC);
+  const double per = (exact ? 3 : 1) * nq * (P + 1) + R * (P + 1) * nq + (2 * P + 1) * nq +
+                     (exact ? nq * nq * (4 * (P + 1) + 6) : 0) + nq * (P + 1);
   return 2.0 * per * (double)h->nel[0] * (double)h->rows_x * (double)h->Nt;
 }
 
@@ -1152,6 +1163,17 @@ static st_status setup_impl(st_handle *h) {
   h->th_t = dalloc<double>(h, (size_t)cap * h->Qt, &e);
   h->Tr = dalloc<double>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
   h->Tr2 = dalloc<float2>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
+  if (D.eps_reaction >= 0.0) {
+    for (int l = 0; l < h->d; ++l) ST_TRY(upload<double>(h, &h->Gsb[l], greville_band(hs.sdir[l], 0)));
+    ST_TRY(upload<double>(h, &h->Gtb, greville_band(hs.tdir, 1)));
+    h->UrC = dalloc<double>(h, (size_t)h->Nt * cap, &e);
+    h->srC = dalloc<double>(h, cap, &e);
+    h->cfc = dalloc<double>(h, cap, &e);
+    h->VrC = dalloc<double>(h, (size_t)h->Ns * cap, &e);
+    h->thC = dalloc<double>(h, (size_t)cap * h->Qt, &e);
+    h->Tc = dalloc<double>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
+    h->Tc2 = dalloc<float2>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
+  }
   for (int i = 0; i < 2; ++i) {
     h->W64[i] = dalloc<double>(h, h->wcap, &e);
     // the lean form's FP32 work buffers share the FP64 ones: the two operators
@@ -1287,6 +1309,8 @@ st_status st_linearize(st_handle *h, const double *u, const double *w, int kind,
     info->rank = h->rank;
     info->theta_fro = h->theta_fro;
   }
+  if (h->desc.eps_reaction >= 0.0) ST_TRY(reaction_lowrank(h, u, w, kind));
+  if (info) info->rank_reaction = h->desc.eps_reaction >= 0.0 ? h->rankC : 0;
   ST_TRY(su_band_add(h));   // also writes the FP32 copy of the bands
   ST_CUDA(cudaStreamSynchronize(h->stream));
   ST_CUDA(cudaGetLastError());
@@ -1504,6 +1528,7 @@ st_status st_get(st_handle *h, int what, void *dst, size_t bytes) {
     case ST_GET_LOWRANK_S: need = h->rank * sizeof(double); src = h->sr; break;
     case ST_GET_LOWRANK_U: need = (size_t)h->Nt * h->rank * sizeof(double); src = h->Ur; break;
     case ST_GET_LOWRANK_V: need = (size_t)h->Ns * h->rank * sizeof(double); src = h->Vr; break;
+    case ST_GET_REACTION_S: need = (size_t)h->rankC * sizeof(double); src = h->srC; if (!src) return ST_ERR_STATE; break;
     case ST_GET_TAU_Q: tmp = h->hs.tau_q; break;
     case ST_GET_FD_EIG: {
       size_t tot = 0;

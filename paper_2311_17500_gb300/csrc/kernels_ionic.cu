@@ -107,6 +107,7 @@ struct IonicArgs {
   // rows mode (lean form): the fields are interpolated along x here from
   // their coefficients at the Gauss rows of the other axes, [N_t][rows][n_x]:
   // U1 = u, W1 = w, L1 = the other axes' part of sum_l D_ll d_ll u (null in 1D)
+  int no_reaction_band;         // bands without the reaction term (it comes in low rank)
   int rows_mode;
   const float2 *U1, *L1, *W1;
   const float2 *tbx, *tb2x;     // x basis values and second derivatives [ex][g][a], pairs
@@ -242,7 +243,7 @@ __global__ void __launch_bounds__(128, P <= 3 ? 4 : 2) ionic_tline_kernel(IonicA
         mu_d = df_max_nonneg(mu_d, df_abs(u));
         mut_d = df_max_nonneg(mut_d, df_abs(ut));
         if (bands) {
-          const df wc = df_mul(ws, C);
+          const df wc = a.no_reaction_band ? zero : df_mul(ws, C);
           const float2 *bp = a.bprod2 + ((size_t)e * nq + qt) * NPAIR;
           int pr = 0;
 #pragma unroll
@@ -422,6 +423,45 @@ __global__ void su_time_band_kernel(double *__restrict__ Tr, const double *__res
       }
     }
     Tr[idx] = s;
+  }
+}
+
+// Time mass bands of the low-rank reaction ranks (the time factor of M_R in
+// low rank): Tc[r][k][it] = int rho_{t,r} b_it b_{it+k} dt, with rho_{t,r}
+// the linear interpolant of U[:, r] at the time Gauss points (rho[r][qt]).
+__global__ void mass_time_band_kernel(double *__restrict__ Tc, const double *__restrict__ rho,
+                                      const double *__restrict__ bt, const double *__restrict__ wt, int R, int Nt,
+                                      int nel_t, int p) {
+  int nq = p + 1;
+  int total = R * (p + 1) * Nt;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    int it = idx % Nt;
+    int k = (idx / Nt) % (p + 1);
+    int r = idx / (Nt * (p + 1));
+    double s = 0.0;
+    if (it + k < Nt) {
+      int e0 = max(0, it + k + 1 - p), e1 = min(nel_t - 1, it + 1);
+      for (int e = e0; e <= e1; ++e) {
+        int ai = it + 1 - e, ci = it + k + 1 - e;
+        for (int qt = 0; qt < nq; ++qt) {
+          const double *b0 = bt + ((size_t)e * nq + qt) * (p + 1);
+          s += wt[e * nq + qt] * rho[(long long)r * nel_t * nq + e * nq + qt] * b0[ai] * b0[ci];
+        }
+      }
+    }
+    Tc[idx] = s;
+  }
+}
+
+// The reaction coefficient (C_r of Eq. reaction, or C_J for Newton) of the
+// values u, w (FP64, elementwise).
+__global__ void reaction_coef_kernel(double *__restrict__ C, const double *__restrict__ u,
+                                     const double *__restrict__ w, double c1, double c2, double a, int newton,
+                                     long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double uu = u[i];
+    C[i] = newton ? c1 * ((3.0 * uu - 2.0 * (1.0 + a)) * uu + a) + c2 * w[i]
+                  : c1 * ((uu - (1.0 + a)) * uu + a) + c2 * w[i];
   }
 }
 
@@ -967,6 +1007,7 @@ st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bo
     spatial_to_qpts(h, w2, -1, W0, 0, 1.0);
   }
   IonicArgs a = ionic_args(h, kind, want_stats);
+  a.no_reaction_band = h->desc.eps_reaction >= 0.0 ? 1 : 0;
   a.U0 = U0; a.L0 = L0; a.W0 = W0;
   a.band_hi = h->band32;
   a.band_lo = h->band_lo;
@@ -994,6 +1035,71 @@ __global__ void skinny_atx_kernel(double *__restrict__ C, const double *__restri
 #pragma unroll
   for (int c = 0; c < 8; ++c)
     if (c < n) C[m * nc + c0 + c] = acc[c];
+}
+
+// Truncated SVD of the N_t x N_s matrix M (row-major, FP64) through its Gram
+// matrix (Eq. tol): the smallest rank R <= cap with
+// ||M - U diag(sigma) V^T||_F <= eps ||M||_F; U (N_t x R), sigma (R, device
+// and host), V = M^T U diag(1/sigma) (N_s x R).  R = 0 for M = 0.
+static st_status truncated_svd(st_handle *h, const double *M, double eps, int cap, double *Uo, double *so,
+                               double *Vo, int *R_out, double *fro_out, std::vector<double> &sig) {
+  cudaStream_t s = h->stream;
+  const int Nt = h->Nt;
+  {
+    // G = M M^T in double-float, upper-triangle tiles, K split so that the
+    // grid holds several blocks per SM (partials in the first work buffer)
+    const int ntile = (Nt + kGT - 1) / kGT, npair = ntile * (ntile + 1) / 2;
+    int nsplit = (int)std::max<long long>(1, std::min<long long>((152LL * 6 + npair - 1) / npair, (h->Ns + 255) / 256));
+    while ((long long)nsplit * npair * kGT * kGT > h->wcap && nsplit > 1) --nsplit;
+    const int kchunk = (int)((h->Ns + nsplit - 1) / nsplit);
+    st_count_launch(); gram_df_kernel<<<dim3(npair, nsplit), 256, 0, s>>>(h->W64[0], M, Nt, h->Ns, ntile, kchunk);
+    st_count_launch(); gram_reduce_kernel<<<grid_for((long long)npair * kGT * kGT), 256, 0, s>>>(h->gram, h->W64[0], Nt, ntile, npair, nsplit);
+  }
+  std::vector<double> G((size_t)Nt * Nt);
+  // trace = ||M||_F^2
+  ST_CUDA(cudaMemcpyAsync(G.data(), h->gram, G.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+  ST_CUDA(cudaStreamSynchronize(s));
+  double tr = 0.0;
+  for (int i = 0; i < Nt; ++i) tr += G[(size_t)i * Nt + i];
+  *fro_out = std::sqrt(tr);
+  *R_out = 0;
+  sig.clear();
+  if (!(tr > 0.0)) return std::isfinite(tr) ? ST_OK : ST_ERR_NAN;
+  // leading eigenpairs of G and the rank R: smallest R with
+  // ||M - U S V^T||_F^2 = tr - sum_{i<=R} lam_i <= eps^2 tr (Eq. tol)
+  std::vector<double> lam;
+  int R = 0;
+  st_status lz = gram_top_eigs(h, h->gram, Nt, tr, eps, cap, Uo, &R, lam);
+  if (lz == ST_ERR_NAN) return lz;
+  if (lz != ST_OK) {
+    // full decomposition (eigenvalues descending) when Lanczos did not settle
+    ST_TRY(sym_eig_desc(h, h->gram, Nt, h->evec, h->eval));
+    lam.assign(Nt, 0.0);
+    ST_CUDA(cudaMemcpyAsync(lam.data(), h->eval, Nt * sizeof(double), cudaMemcpyDeviceToHost, s));
+    ST_CUDA(cudaStreamSynchronize(s));
+    double kept = 0.0;
+    R = Nt;
+    for (int r = 1; r <= Nt; ++r) {
+      kept += std::max(lam[r - 1], 0.0);
+      if (tr - kept <= eps * eps * tr) { R = r; break; }
+    }
+    if (R > cap) R = cap;
+    // U_R (N_t x R) = first R columns of evec (evec[i][c], c sorted descending)
+    ST_CUDA(cudaMemcpy2DAsync(Uo, R * sizeof(double), h->evec, Nt * sizeof(double), R * sizeof(double), Nt,
+                              cudaMemcpyDeviceToDevice, s));
+  }
+  sig.assign(R, 0.0);
+  for (int r = 0; r < R; ++r) sig[r] = std::sqrt(std::max(lam[r], 0.0));
+  ST_CUDA(cudaMemcpyAsync(so, sig.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
+  // V = M^T U_R diag(1/sigma): (N_s x R)
+  for (int c0 = 0; c0 < R; c0 += 8) {
+    st_count_launch();
+    skinny_atx_kernel<<<(unsigned)((h->Ns + 127) / 128), 128, 0, s>>>(Vo, M, Uo, h->Ns, R, c0, Nt);
+  }
+  st_count_launch(); scale_cols_kernel<<<grid_for(h->Ns * R), 256, 0, s>>>(Vo, so, R, h->Ns);
+  *R_out = R;
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
 }
 
 st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
@@ -1036,91 +1142,32 @@ st_status theta_and_lowrank(st_handle *h, st_ionic_info *info) {
   }
   long long NtNs = h->Ndof;
   st_count_launch(); theta_kernel<<<grid_for(NtNs), 256, 0, s>>>(h->theta, cur, den, NtNs);
-  // Gram matrix G = Theta Theta^T (N_t x N_t, FP64)
-  int Nt = h->Nt;
-  {
-    // G = Theta Theta^T in double-float, upper-triangle tiles, K split so that
-    // the grid holds several blocks per SM (partials in the first work buffer)
-    const int ntile = (Nt + kGT - 1) / kGT, npair = ntile * (ntile + 1) / 2;
-    int nsplit = (int)std::max<long long>(1, std::min<long long>((152LL * 6 + npair - 1) / npair, (h->Ns + 255) / 256));
-    while ((long long)nsplit * npair * kGT * kGT > h->wcap && nsplit > 1) --nsplit;
-    const int kchunk = (int)((h->Ns + nsplit - 1) / nsplit);
-    st_count_launch(); gram_df_kernel<<<dim3(npair, nsplit), 256, 0, s>>>(h->W64[0], h->theta, Nt, h->Ns, ntile, kchunk);
-    st_count_launch(); gram_reduce_kernel<<<grid_for((long long)npair * kGT * kGT), 256, 0, s>>>(h->gram, h->W64[0], Nt, ntile, npair, nsplit);
-  }
-  std::vector<double> G((size_t)Nt * Nt);
-  // trace = ||Theta||_F^2
-  ST_CUDA(cudaMemcpyAsync(G.data(), h->gram, G.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
-  ST_CUDA(cudaStreamSynchronize(s));
-  double tr = 0.0;
-  for (int i = 0; i < Nt; ++i) tr += G[(size_t)i * Nt + i];
-  h->theta_fro = std::sqrt(tr);
-  if (info) info->theta_fro = h->theta_fro;
-  h->rank = 0;
-  if (!(tr > 0.0)) {
-    if (info) info->rank = 0;
-    return ST_OK;
-  }
-  // leading eigenpairs of G and the rank R: smallest R with
-  // ||Theta - U S V^T||_F^2 = tr - sum_{i<=R} lam_i <= eps^2 tr (Eq. tol)
-  double eps = D.eps_theta;
-  std::vector<double> lam;
+  std::vector<double> sig;
   int R = 0;
-  st_status lz = gram_top_eigs(h, h->gram, Nt, tr, eps, h->rank_cap, h->Ur, &R, lam);
-  if (lz == ST_ERR_NAN) return lz;
-  if (lz != ST_OK) {
-    // full decomposition (eigenvalues descending) when Lanczos did not settle
-    ST_TRY(sym_eig_desc(h, h->gram, Nt, h->evec, h->eval));
-    lam.assign(Nt, 0.0);
-    ST_CUDA(cudaMemcpyAsync(lam.data(), h->eval, Nt * sizeof(double), cudaMemcpyDeviceToHost, s));
-    ST_CUDA(cudaStreamSynchronize(s));
-    double kept = 0.0;
-    R = Nt;
-    for (int r = 1; r <= Nt; ++r) {
-      kept += std::max(lam[r - 1], 0.0);
-      if (tr - kept <= eps * eps * tr) { R = r; break; }
-    }
-    if (R > h->rank_cap) R = h->rank_cap;
-    // U_R (N_t x R) = first R columns of evec (evec[i][c], c sorted descending)
-    ST_CUDA(cudaMemcpy2DAsync(h->Ur, R * sizeof(double), h->evec, Nt * sizeof(double), R * sizeof(double), Nt,
-                              cudaMemcpyDeviceToDevice, s));
-  }
+  double fro = 0.0;
+  ST_TRY(truncated_svd(h, h->theta, D.eps_theta, h->rank_cap, h->Ur, h->sr, h->Vr, &R, &fro, sig));
+  h->theta_fro = fro;
   h->rank = R;
-  if (info) info->rank = R;
-  std::vector<double> sig(R);
-  for (int r = 0; r < R; ++r) sig[r] = std::sqrt(std::max(lam[r], 0.0));
-  ST_CUDA(cudaMemcpyAsync(h->sr, sig.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
-  if (h->lean) {
+  if (info) { info->theta_fro = fro; info->rank = R; }
+  if (h->lean && R > 0) {
     // scale of each SU rank term in the lean operator: C_m sigma_r
     std::vector<double> cf(R);
     for (int r = 0; r < R; ++r) cf[r] = D.C_m * sig[r];
     ST_CUDA(cudaMemcpyAsync(h->cfr, cf.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
   }
-  // V = Theta^T U_R diag(1/sigma): (N_s x R)
-  for (int c0 = 0; c0 < R; c0 += 8) {
-    st_count_launch();
-    skinny_atx_kernel<<<(unsigned)((h->Ns + 127) / 128), 128, 0, s>>>(h->Vr, h->theta, h->Ur, h->Ns, R, c0, Nt);
-  }
-  st_count_launch(); scale_cols_kernel<<<grid_for(h->Ns * R), 256, 0, s>>>(h->Vr, h->sr, R, h->Ns);
   ST_CUDA(cudaGetLastError());
   return ST_OK;
 }
 
-st_status su_band_add(st_handle *h) {
-  if (h->desc.stabilization != ST_SU || h->rank == 0) return ST_OK;   // the reaction band alone
+// Band form: band[(k,it)][q] += sum_r T[r][(k,it)] Cq[r][q], with the spatial
+// factors Cq[r][q] = scale sigma_r ws(q) phi_r(x_q) (phi_r the d-linear
+// interpolant of V[:, r] on the spatial Greville grid), 8 ranks per pass;
+// both factors split into double-float pairs first (Cq in the work buffers,
+// R Q_s <= N_t Q_s values).
+static st_status bands_add_ranks(st_handle *h, const double *V, const double *sig, double scale, const double *T,
+                                 float2 *T2, int R) {
   cudaStream_t s = h->stream;
-  int R = h->rank, p = h->p;
-  st_count_launch(); theta_t_kernel<<<grid_for((long long)h->Qt * R), 256, 0, s>>>(h->th_t, h->Ur, R, h->Qt, h->hat_i_t, h->hat_l_t);
-  st_count_launch(); su_time_band_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tr, h->th_t, h->tauq, h->bt,
-                                                                              h->wt, R, h->Nt, h->nel_t, p);
-  if (h->lean) {
-    // the lean operator reads the rank factors themselves: only the time
-    // bands, as double-float pairs
-    st_count_launch(); d2df_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tr2, h->Tr, (long long)R * (p + 1) * h->Nt);
-    ST_CUDA(cudaGetLastError());
-    return ST_OK;
-  }
-  // Cq = C_m sigma_r ws theta_s (into the first work buffer, R x Q_s <= N_t x Q_s)
+  const int p = h->p;
   double *Cq = h->W64[0];
   HatArgs hat;
   for (int l = 0; l < 3; ++l) {
@@ -1128,29 +1175,98 @@ st_status su_band_add(st_handle *h) {
     hat.lam[l] = h->hat_l_s[l];
     hat.n[l] = h->n[l];
   }
-  st_count_launch(); su_space_coef_kernel<<<grid_for(h->Qs * R), 256, 0, s>>>(Cq, h->Vr, h->sr, geom(h), hat, h->desc.C_m, R, h->Qs);
-  // band[(k,it)][q] += sum_r Tr[r][(k,it)] Cq[r][q], 16 ranks per pass, with
-  // both factors split into double-float pairs first (Cq into the second work
-  // buffer: R Q_s <= N_t Q_s pairs)
-  int Mrows = (p + 1) * h->Nt;
-  long long total = (long long)Mrows * h->Qs;
+  st_count_launch(); su_space_coef_kernel<<<grid_for(h->Qs * R), 256, 0, s>>>(Cq, V, sig, geom(h), hat, scale, R, h->Qs);
+  const int Mrows = (p + 1) * h->Nt;
   float2 *Cq2 = reinterpret_cast<float2 *>(h->W64[1]);
-  float2 *Tr2 = h->Tr2;
   st_count_launch(); d2df_kernel<<<grid_for((long long)R * h->Qs), 256, 0, s>>>(Cq2, Cq, (long long)R * h->Qs);
-  st_count_launch(); d2df_kernel<<<grid_for((long long)R * Mrows), 256, 0, s>>>(Tr2, h->Tr, (long long)R * Mrows);
+  st_count_launch(); d2df_kernel<<<grid_for((long long)R * Mrows), 256, 0, s>>>(T2, T, (long long)R * Mrows);
   // thread = 4 spatial points; about 8 blocks per SM in all
   const long long gx = (h->Qs + 1023) / 1024;
   const dim3 g2((unsigned)gx, (unsigned)std::max<long long>(1, std::min<long long>(Mrows, (152LL * 8 + gx - 1) / gx)));
-  (void)total;
   for (int r0 = 0; r0 < R; r0 += 8) {
     const int left = R - r0;
     if (left <= 2) {
-      st_count_launch(); su_band_update_kernel<2><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+      st_count_launch(); su_band_update_kernel<2><<<g2, 256, 0, s>>>(h->band32, h->band_lo, T2, Cq2, r0, R, Mrows, h->Qs);
     } else if (left <= 4) {
-      st_count_launch(); su_band_update_kernel<4><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+      st_count_launch(); su_band_update_kernel<4><<<g2, 256, 0, s>>>(h->band32, h->band_lo, T2, Cq2, r0, R, Mrows, h->Qs);
     } else {
-      st_count_launch(); su_band_update_kernel<8><<<g2, 256, 0, s>>>(h->band32, h->band_lo, Tr2, Cq2, r0, R, Mrows, h->Qs);
+      st_count_launch(); su_band_update_kernel<8><<<g2, 256, 0, s>>>(h->band32, h->band_lo, T2, Cq2, r0, R, Mrows, h->Qs);
     }
+  }
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status su_band_add(st_handle *h) {
+  cudaStream_t s = h->stream;
+  const int p = h->p;
+  const bool su = h->desc.stabilization == ST_SU && h->rank > 0;
+  if (su) {
+    const int R = h->rank;
+    st_count_launch(); theta_t_kernel<<<grid_for((long long)h->Qt * R), 256, 0, s>>>(h->th_t, h->Ur, R, h->Qt, h->hat_i_t, h->hat_l_t);
+    st_count_launch(); su_time_band_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tr, h->th_t, h->tauq, h->bt,
+                                                                                h->wt, R, h->Nt, h->nel_t, p);
+    if (h->lean) {
+      // the lean operator reads the rank factors themselves: only the time
+      // bands, as double-float pairs
+      st_count_launch(); d2df_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tr2, h->Tr, (long long)R * (p + 1) * h->Nt);
+    } else {
+      ST_TRY(bands_add_ranks(h, h->Vr, h->sr, h->desc.C_m, h->Tr, h->Tr2, R));
+    }
+  }
+  // the low-rank reaction (its time bands are ready): into the bands of the band form
+  if (!h->lean && h->desc.eps_reaction >= 0.0 && h->rankC > 0)
+    ST_TRY(bands_add_ranks(h, h->VrC, h->srC, 1.0, h->Tc, h->Tc2, h->rankC));
+  ST_CUDA(cudaGetLastError());
+  return ST_OK;
+}
+
+st_status reaction_lowrank(st_handle *h, const double *u, const double *w, int kind) {
+  cudaStream_t s = h->stream;
+  const st_problem_desc &D = h->desc;
+  // values at the Greville grid: one banded collocation pass per axis (x
+  // first, time last) into the Kronecker temporaries
+  auto greville = [&](const double *in, double *out) {
+    const double *cur = in;
+    const int naxes = h->d + 1;
+    int ping = 0;
+    for (int ax = 0; ax < naxes; ++ax) {
+      const bool time = ax == h->d;
+      const int n = time ? h->Nt : h->n[ax];
+      long long inner = 1, outer = 1;
+      if (time) {
+        inner = h->Ns;
+      } else {
+        for (int m = 0; m < ax; ++m) inner *= h->n[m];
+        outer = h->Nt;
+        for (int m = ax + 1; m < h->d; ++m) outer *= h->n[m];
+      }
+      double *dst = ax == naxes - 1 ? out : h->K64[ping];
+      const double *band = time ? h->Gtb : h->Gsb[ax];
+      const double *bands[1] = {band};
+      const double *ins[1] = {cur};
+      const double cf[1] = {1.0};
+      launch_band_pass<double>(s, dst, 1, bands, ins, cf, n, inner, outer, h->p, false);
+      cur = dst;
+      ping ^= 1;
+    }
+  };
+  double *Ug = h->K64[2], *Wg = h->K64[3], *Cg = h->K64[4];
+  greville(u, Ug);
+  greville(w, Wg);
+  st_count_launch(); reaction_coef_kernel<<<grid_for(h->Ndof), 256, 0, s>>>(Cg, Ug, Wg, D.c1, D.c2, D.a, kind == ST_NEWTON, h->Ndof);
+  std::vector<double> sig;
+  int R = 0;
+  double fro = 0.0;
+  ST_TRY(truncated_svd(h, Cg, D.eps_reaction, h->rank_cap, h->UrC, h->srC, h->VrC, &R, &fro, sig));
+  h->rankC = R;
+  if (R > 0) {
+    const int p = h->p;
+    st_count_launch(); theta_t_kernel<<<grid_for((long long)h->Qt * R), 256, 0, s>>>(h->thC, h->UrC, R, h->Qt, h->hat_i_t, h->hat_l_t);
+    st_count_launch(); mass_time_band_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tc, h->thC, h->bt, h->wt,
+                                                                                  R, h->Nt, h->nel_t, p);
+    st_count_launch(); d2df_kernel<<<grid_for((long long)R * (p + 1) * h->Nt), 256, 0, s>>>(h->Tc2, h->Tc, (long long)R * (p + 1) * h->Nt);
+    ST_CUDA(cudaMemcpyAsync(h->cfc, sig.data(), R * sizeof(double), cudaMemcpyHostToDevice, s));
   }
   ST_CUDA(cudaGetLastError());
   return ST_OK;

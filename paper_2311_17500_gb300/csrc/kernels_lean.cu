@@ -81,6 +81,9 @@ struct LeanArgs {
   const double *cf;             // scale of each rank term [Rt]
   const float2 *Tb;             // rank time bands [Rt][P+1][N_t], pairs
   int Rt;
+  const double *V2, *cf2;       // a second list of rank terms ([N_s][R2], [R2]; the low-rank reaction)
+  const float2 *Tb2;            // [R2][P+1][N_t]
+  int R2;
   int exact;                    // M_R from u^k, w^k at the Gauss points
   int newton;                   // C_J instead of C_r
   double c1, c2, a;
@@ -138,16 +141,20 @@ __global__ void __launch_bounds__(kLeanMaxThreads) xlean_kernel(LeanArgs<T> a) {
         wq[g] = ct_from<CT>(wqd);
         const int ix = owns ? a.hi[0][gx] : 0;
         const double lx = owns ? a.hl[0][gx] : 0.0;
-        for (int r = 0; r < a.Rt; ++r) {
+        for (int r = 0; r < a.Rt + a.R2; ++r) {
+          const bool second = r >= a.Rt;
+          const double *V = second ? a.V2 : a.V;
+          const int Rl = second ? a.R2 : a.Rt, rl = second ? r - a.Rt : r;
           double th = 0.0;
           for (int cz = 0; cz < ncz; ++cz)
             for (int cy = 0; cy < ncy; ++cy)
               for (int cx = 0; cx < 2; ++cx) {
                 const double wgt = (cx ? lx : 1.0 - lx) * (cy ? ly : 1.0 - ly) * (cz ? lz : 1.0 - lz);
                 const long long idx = (ix + cx) + (long long)a.n[0] * ((iy + cy) + (long long)a.n[1] * (iz + cz));
-                th += wgt * a.V[idx * a.Rt + r];
+                th += wgt * V[idx * Rl + rl];
               }
-          dsh[((size_t)r * nq + g) * nth + t] = ct_from<CT>(owns ? a.cf[r] * wqd * th : 0.0);
+          const double scale = second ? a.cf2[rl] : a.cf[rl];
+          dsh[((size_t)r * nq + g) * nth + t] = ct_from<CT>(owns ? scale * wqd * th : 0.0);
         }
       }
     }
@@ -246,17 +253,18 @@ __global__ void __launch_bounds__(kLeanMaxThreads) xlean_kernel(LeanArgs<T> a) {
       CT yq[nq];
 #pragma unroll
       for (int g = 0; g < nq; ++g) yq[g] = acc[0][g];
-      if (a.Rt > 0 && it >= 0) {
+      if (a.Rt + a.R2 > 0 && it >= 0) {
         // band of row it: b[k][g] = T_q(it, it + k) = sum_r d_r(q) Tb[r][k][it]
         CT b[P + 1][nq];
 #pragma unroll
         for (int k = 0; k <= P; ++k)
 #pragma unroll
           for (int g = 0; g < nq; ++g) b[k][g] = zero;
-        for (int r = 0; r < a.Rt; ++r) {
+        for (int r = 0; r < a.Rt + a.R2; ++r) {
+          const float2 *tb = r < a.Rt ? a.Tb + (size_t)r * (P + 1) * a.Nt : a.Tb2 + (size_t)(r - a.Rt) * (P + 1) * a.Nt;
           CT tk[P + 1];
 #pragma unroll
-          for (int k = 0; k <= P; ++k) tk[k] = from_pair<CT>(__ldg(a.Tb + ((size_t)r * (P + 1) + k) * a.Nt + it));
+          for (int k = 0; k <= P; ++k) tk[k] = from_pair<CT>(__ldg(tb + (size_t)k * a.Nt + it));
 #pragma unroll
           for (int g = 0; g < nq; ++g) {
             const CT dv = dsh[((size_t)r * nq + g) * nth + t];
@@ -389,6 +397,7 @@ st_status launch_xlean(cudaStream_t s, const LeanTerms &L, T *Y1, const T *X1, c
   a.bt = L.bt; a.wt = L.wt;
   for (int l = 0; l < 3; ++l) { a.ws[l] = L.ws[l]; a.hi[l] = L.hi[l]; a.hl[l] = L.hl[l]; a.n[l] = L.n[l]; a.Q[l] = L.Q[l]; }
   a.V = L.V; a.cf = L.cf; a.Tb = L.Tb; a.Rt = L.Rt;
+  a.V2 = L.V2; a.cf2 = L.cf2; a.Tb2 = L.Tb2; a.R2 = L.R2;
   a.exact = L.exact; a.newton = L.newton;
   a.c1 = L.c1; a.c2 = L.c2; a.a = L.a;
   a.d = L.d; a.nel = L.nel; a.Nt = L.Nt; a.nel_t = L.nel_t;
@@ -396,8 +405,8 @@ st_status launch_xlean(cudaStream_t s, const LeanTerms &L, T *Y1, const T *X1, c
   const int p = L.p;
   const int threads = xlean_threads(L.nel, p);
   if (threads > kLeanMaxThreads || rows < 1) return ST_ERR_ARG;
-  if (L.Rt > xlean_max_rank(L.nel, p, L.exact != 0)) return ST_ERR_CAPACITY;
-  const size_t smem = xlean_smem(L.nel, p, L.Rt, L.exact != 0, sizeof(T) == 8);
+  if (L.Rt + L.R2 > xlean_max_rank(L.nel, p, L.exact != 0)) return ST_ERR_CAPACITY;
+  const size_t smem = xlean_smem(L.nel, p, L.Rt + L.R2, L.exact != 0, sizeof(T) == 8);
   // time segments: enough blocks for about four per SM, each at least 4p steps
   const long long want = 152LL * 4;
   int nseg = (int)std::max<long long>(1, std::min<long long>((want + rows - 1) / rows, L.Nt / std::max(4 * p, 1)));

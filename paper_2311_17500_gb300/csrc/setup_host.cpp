@@ -143,6 +143,36 @@ void build_dir(Dir1D &dr, int n_el, int p, double scale, int kmax, int nq = 0) {
   }
 }
 
+}  // namespace
+
+// Collocation of the basis at its own Greville abscissae, banded (n x (2p+1)):
+// entry (i, j) = b_j(gamma_i), nonzero for |i - j| <= p since gamma_i lies in
+// the support of b_i.  `shift` = 1 drops the first function from rows and
+// columns (time: the functions of X_t at their Greville points).
+std::vector<double> greville_band(const Dir1D &dr, int shift) {
+  const int p = dr.p, B = 2 * p + 1, n = dr.n - shift;
+  std::vector<double> out((size_t)n * B, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const int f = i + shift;
+    double x = 0.0;
+    for (int j = 1; j <= p; ++j) x += dr.knots[f + j];
+    x = p > 0 ? x / p : 0.5 * (dr.knots[f] + dr.knots[f + 1]);
+    // span s with knots[s] <= x < knots[s+1] (the last span holds x = 1)
+    int s = p;
+    while (s + 1 < dr.n && dr.knots[s + 1] <= x) ++s;
+    double N[ST_MAXP + 1][ST_MAXP + 1];
+    local_values(dr.knots, s, p, x, N);
+    for (int r = 0; r <= p; ++r) {
+      const int j = s - p + r - shift;
+      if (j < 0 || j >= n) continue;
+      out[(size_t)i * B + (j - i + p)] = N[p][r];
+    }
+  }
+  return out;
+}
+
+namespace {
+
 // Banded Gram matrix sum_e sum_q w (d^ki b_i)(d^kj b_j) over the full basis;
 // `shift` removes the first function (time: X_t) when 1.  Row = index of the
 // function carrying derivative ki (test), column = kj (trial).

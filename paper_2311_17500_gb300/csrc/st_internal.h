@@ -40,6 +40,9 @@ struct HostSetup {
 st_status host_setup(const st_problem_desc &d, HostSetup &hs);
 // M_t and LU(W_t + b d_e M_t) alone, both N_t x (2p+1) banded.
 st_status host_time_bands(const st_problem_desc &d, std::vector<double> &Mt, std::vector<double> &wlu);
+// The basis of `dr` at its Greville abscissae, banded: (i, j) = b_j(gamma_i);
+// shift = 1 drops the first function (the time space X_t).
+std::vector<double> greville_band(const Dir1D &dr, int shift);
 // Banded LU without pivoting in place (n x (2p+1)); stores 1/u_ii on the diagonal.
 int band_lu_inplace(double *a, int n, int p);
 
@@ -122,6 +125,13 @@ struct st_handle {
   double *Tr = nullptr;     // SU time bands [r][k][it]
   int rank_cap = 0;
   double theta_fro = 0.0;
+  // low-rank reaction coefficient (eps_reaction >= 0): Greville collocation
+  // bands, the factors of the coefficient's Greville values, its time bands
+  double *Gsb[3] = {}, *Gtb = nullptr;   // [n][2p+1] per direction, time on X_t
+  int rankC = 0;
+  double *UrC = nullptr, *srC = nullptr, *VrC = nullptr, *cfc = nullptr;   // [Nt][R], [R], [Ns][R], [R]
+  double *thC = nullptr, *Tc = nullptr;  // rho_{t,r} at the time Gauss points [r][Qt]; bands [r][k][it]
+  float2 *Tc2 = nullptr;                 // the bands as double-float pairs
 
   // workspaces
   double *W64[2] = {};
@@ -259,6 +269,9 @@ struct LeanTerms {
   const double *V = nullptr, *cf = nullptr;    // rank factors [N_s][Rt] and scales [Rt]
   const float2 *Tb = nullptr;                  // rank time bands [Rt][p+1][N_t], pairs
   int Rt = 0;
+  const double *V2 = nullptr, *cf2 = nullptr;  // a second list of rank terms (the low-rank reaction)
+  const float2 *Tb2 = nullptr;
+  int R2 = 0;
   int exact = 0, newton = 0;
   double c1 = 0, c2 = 0, a = 0;
   int d = 1, p = 1, nel = 1, Nt = 1, nel_t = 1;
@@ -323,6 +336,9 @@ void launch_band_to_f32(cudaStream_t s, float *out, const double *in, long long 
 st_status ionic_run(st_handle *h, const double *u, const double *w, int kind, bool want_stats);
 st_status theta_and_lowrank(st_handle *h, st_ionic_info *info);
 st_status su_band_add(st_handle *h);
+// The low-rank reaction coefficient at (u, w) for the linearization `kind`
+// (eps_reaction >= 0): factors, time bands and scales.
+st_status reaction_lowrank(st_handle *h, const double *u, const double *w, int kind);
 st_status source_assemble(st_handle *h);
 st_status wupdate_run(st_handle *h, const double *u, double *w);
 // w-update with the time bands taken from host arrays and staged in the

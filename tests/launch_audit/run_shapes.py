@@ -26,7 +26,7 @@ from paper_2311_17500_gb300 import _lib as L  # noqa: E402
 def describe(base, shape):
     """SHAPE[:option...], options fp64 (FP64 GMRES), newton, galerkin, symmetric
     (support extension), wzero (w fixed at zero), bands / lean (operator form;
-    default: the library's choice)."""
+    default: the library's choice), lrreact (low-rank reaction coefficient)."""
     sizes, *opts = shape.split(":")
     v = [int(a) for a in sizes.split(",")]
     p, n_el, n_el_t = v[0], v[1:-1], v[-1]
@@ -48,6 +48,8 @@ def describe(base, shape):
             desc["fix_w_zero"] = True
         elif o in ("bands", "lean"):
             desc["operator_form"] = o
+        elif o == "lrreact":
+            desc["eps_reaction"] = 1e-3
         else:
             raise ValueError("unknown option " + o)
     return desc

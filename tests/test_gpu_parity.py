@@ -268,3 +268,44 @@ def test_nonlinear_iterations(P, c, form, kind):
     assert rel(host(u), u_ref) < 1e-10
     assert rel(host(w), w_ref) < 1e-10
     s.close()
+
+
+LR_CASES = [(c, f) for c in (CASES[0], CASES[2], CASES[3], CASES[4]) for f in ("bands", "lean")
+            if f == "bands" or c["d"] >= 2]
+
+
+@pytest.mark.parametrize("c,form", LR_CASES, ids=[f"d{c['d']}p{c['p']}-{f}" for c, f in LR_CASES])
+@pytest.mark.parametrize("kind", ["picard", "newton"])
+@pytest.mark.parametrize("eps", [1e-2, 1e-4])
+def test_lowrank_reaction(P, c, form, kind, eps):
+    """The low-rank reaction coefficient (reading A7): its rank and singular
+    values, and both operators, against the oracle's (the coefficient's
+    Greville values truncated at eps_reaction and interpolated)."""
+    from oracle import model
+    from oracle.stabilization import greville_values
+    desc = problem(c, nonlinear=kind, operator_form=form, eps_reaction=eps)
+    o = Oracle(desc)
+    u, w = iterate(o, 2)
+    A, info = o.linearization(u, w, kind)
+    sc = info["sc"]
+    R = len(sc)
+    # no tie at the cut
+    ug, wg = greville_values(o.st, u), greville_values(o.st, w)
+    C = model.jacobian_coef(desc, ug, wg) if kind == "newton" else model.reaction_coef(desc, ug, wg)
+    sv = np.linalg.svd(C, compute_uv=False)
+    fro = np.sqrt(np.sum(sv ** 2))
+    tail = np.sqrt(np.concatenate([np.cumsum((sv ** 2)[::-1])[::-1], [0.0]]))
+    assert tail[R - 1] > (1 + 1e-6) * eps * fro and tail[R] < (1 - 1e-6) * eps * fro
+    s = solver(P, desc)
+    du, dw = dev(u), dev(w)
+    ginfo = s.ionic(ptr(du), ptr(dw))
+    assert ginfo["rank_reaction"] == R
+    assert rel(np.array(s.get("reaction_s", R)), sc) < 1e-10
+    x = W.random_vector(o.st.N_dof, seed=5)
+    dx, dy = dev(x), empty(o.st.N_dof)
+    s.apply(ptr(dx), ptr(dy), P.ST_FP64)
+    assert rel(host(dy), A @ x) < 1e-12
+    dx32, dy32 = dev(x, np.float32), empty(o.st.N_dof, "float32")
+    s.apply(ptr(dx32), ptr(dy32), P.ST_MIXED)
+    assert rel(host(dy32), A @ x) < 2e-5
+    s.close()

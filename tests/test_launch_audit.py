@@ -40,7 +40,9 @@ SHAPES = ["3,16,16,16", "3,120,33,64", "2,194,33,64", "2,216,33,64", "2,150,33,6
           "2,8,8,8,16:fp64", "2,9,7,12:galerkin", "3,9,7,12:symmetric:wzero", "1,40,12:fp64",
           # the band form where the lean one is the default, and the lean form at its widest x
           "3,16,16,16:bands", "3,120,33,64:bands", "2,200,8,8,8:bands:fp64", "3,8,8,8,16:bands:newton",
-          "1,255,8,16:lean", "4,252,6,8:lean:fp64", "2,20,6,5,8:lean:newton"]
+          "1,255,8,16:lean", "4,252,6,8:lean:fp64", "2,20,6,5,8:lean:newton",
+          # the low-rank reaction coefficient in both forms
+          "2,9,7,12:lrreact", "3,8,8,8,16:bands:lrreact", "2,20,6,5,8:lean:lrreact:newton", "1,40,12:lrreact"]
 
 
 def _have_tools():
