@@ -124,6 +124,12 @@ typedef struct {
                           * relative Frobenius tolerance like Theta-hat (Eq. tol)
                           * and interpolated (d+1)-linearly, the low-rank reaction
                           * matrices of Sec. 4.2 */
+  const double *breaks[3];   /* per spatial direction: NULL for a uniform mesh, else
+                              * n_el[l] + 1 increasing breakpoints from 0 to 1 of the
+                              * open knot vector (maximal regularity, Sec. 2); read by
+                              * st_setup and st_footprint only (the caller keeps them) */
+  const double *breaks_t;    /* the same for time, parametric on [0, 1] (scaled by T);
+                              * e.g. knots clustered where the source switches (Sec. 4.2) */
 } st_problem_desc;
 
 typedef struct st_handle st_handle;

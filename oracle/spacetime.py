@@ -21,6 +21,15 @@ import scipy.sparse as sp
 from .bspline import Direction
 
 
+def open_knots(breaks, p):
+    """Open knot vector of maximal regularity on the breakpoints (None: uniform,
+    left to Direction): p+1 copies of each end, the interior breakpoints once."""
+    if breaks is None:
+        return None
+    b = np.asarray(breaks, dtype=float)
+    return np.concatenate([np.full(p, b[0]), b, np.full(p, b[-1])])
+
+
 def _spatial_table(dirs, kk):
     """Tensor-product table of the spatial basis on spatial elements.
 
@@ -90,8 +99,11 @@ class SpaceTime:
         self.p = desc["p"]
         p = self.p
         self.T = float(desc["T"])
-        self.sdirs = [Direction(ne, p, nq=nq, scale=1.0, max_deriv=2) for ne in desc["n_el"]]
-        self.tdir = Direction(desc["n_el_t"], p, nq=nq, scale=self.T, max_deriv=p)
+        breaks = desc.get("breaks") or [None] * self.d
+        self.sdirs = [Direction(ne, p, nq=nq, scale=1.0, max_deriv=2, knots=open_knots(breaks[l], p))
+                      for l, ne in enumerate(desc["n_el"])]
+        self.tdir = Direction(desc["n_el_t"], p, nq=nq, scale=self.T, max_deriv=p,
+                              knots=open_knots(desc.get("breaks_t"), p))
         self.n = [dr.n for dr in self.sdirs]
         self.N_s = int(np.prod(self.n))
         self.n_t = self.tdir.n

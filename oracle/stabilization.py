@@ -13,7 +13,9 @@
   reaction coefficient of reading A7 is formed the same way.
 
 Readings where the paper is silent: tau is the
-minimum-norm solution in the scaled coefficients c_k / h_t^(2k-1); the support
+minimum-norm solution in the scaled coefficients c_{k,m} / h_{k,m}^(2k-1), with
+h_{k,m} the largest element in the support of the m-th B-spline of tau_k (h_t
+on a uniform mesh); the support
 extension is taken literally with the underlying b-hat index in time; the
 L-infinity norms are maxima over Gauss points; Theta = 1 when the denominator
 vanishes with a non-zero residual and 0 when both vanish; the low-rank factors
@@ -24,7 +26,7 @@ Test infrastructure only: nothing in the product path imports this package.
 
 import numpy as np
 
-from .bspline import bspline_all, open_uniform_knots
+from .bspline import bspline_all
 from .bspline import greville as greville_param
 
 
@@ -40,13 +42,13 @@ def tau_solve(st):
     p = st.p
     td = st.tdir
     n_el = td.n_el
-    h_t = st.T * np.max(np.diff(td.br))
     xpar = td.xq_par.reshape(-1)
     w = td.wq.reshape(-1)
     B = [td.vals[k].reshape(-1, td.n)[:, 1:] for k in range(p + 1)]     # X_t basis, physical derivs
     beta = []
     for k in range(1, p + 1):
-        kn = open_uniform_knots(n_el, p - k)
+        # degree p-k on the breakpoints of the time mesh
+        kn = np.concatenate([np.full(p - k, td.br[0]), td.br, np.full(p - k, td.br[-1])])
         beta.append(bspline_all(kn, p - k, xpar, 0))                      # (nq_total, n_k)
     sizes = [bb.shape[1] for bb in beta]
     offs = np.concatenate([[0], np.cumsum(sizes)])
@@ -62,7 +64,15 @@ def tau_solve(st):
             rhs.append(-np.sum(w * B[1][:, j] * B[0][:, i]))
     C = np.array(rows)
     rhs = np.array(rhs)
-    scale = np.concatenate([np.full(sizes[k - 1], h_t ** (2 * k - 1)) for k in range(1, p + 1)])
+    # unknowns scaled by h^(2k-1), h the largest element in the support of the
+    # coefficient's B-spline (h_t itself on a uniform mesh)
+    hel = st.T * np.diff(td.br)
+    scale = []
+    for k in range(1, p + 1):
+        q = p - k
+        for m in range(sizes[k - 1]):
+            scale.append(hel[max(0, m - q):min(n_el - 1, m) + 1].max() ** (2 * k - 1))
+    scale = np.array(scale)
     y, *_ = np.linalg.lstsq(C * scale[None, :], rhs, rcond=None)
     c = y * scale
     coeffs = [c[offs[k - 1]:offs[k]] for k in range(1, p + 1)]

@@ -48,7 +48,8 @@ class StProblemDesc(ctypes.Structure):
                 ("max_fp", ctypes.c_int), ("fix_w_zero", ctypes.c_int), ("precision", ctypes.c_int),
                 ("gmres_m", ctypes.c_int), ("rtol", ctypes.c_double), ("max_it", ctypes.c_int),
                 ("operator_form", ctypes.c_int), ("inner_op", ctypes.c_int),
-                ("eps_reaction", ctypes.c_double)]
+                ("eps_reaction", ctypes.c_double),
+                ("breaks", ctypes.POINTER(ctypes.c_double) * 3), ("breaks_t", ctypes.POINTER(ctypes.c_double))]
 
 
 class StDims(ctypes.Structure):
@@ -156,6 +157,21 @@ def make_desc(desc):
     c.operator_form = ST_FORM[desc.get("operator_form", "auto")]
     c.inner_op = ST_INNER[desc.get("inner_op", "auto")]
     c.eps_reaction = float(desc.get("eps_reaction", -1.0))
+    # breakpoint arrays (None = uniform): the struct keeps the ctypes arrays alive
+    keep = []
+
+    def darr(vals):
+        a = (ctypes.c_double * len(vals))(*[float(v) for v in vals])
+        keep.append(a)
+        return ctypes.cast(a, ctypes.POINTER(ctypes.c_double))
+
+    breaks = desc.get("breaks") or [None] * c.d
+    for l in range(min(c.d, 3)):
+        if breaks[l] is not None:
+            c.breaks[l] = darr(breaks[l])
+    if desc.get("breaks_t") is not None:
+        c.breaks_t = darr(desc["breaks_t"])
+    c._keep = keep
     return c
 
 

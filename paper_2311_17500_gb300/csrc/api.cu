@@ -49,6 +49,16 @@ st_status validate(const st_problem_desc *d) {
   if (d->operator_form < ST_FORM_AUTO || d->operator_form > ST_FORM_LEAN) return ST_ERR_ARG;
   if (d->inner_op < ST_INNER_AUTO || d->inner_op > ST_INNER_DF) return ST_ERR_ARG;
   if (!(d->eps_reaction == d->eps_reaction)) return ST_ERR_ARG;   // NaN
+  auto breaks_ok = [](const double *b, int n_el) {
+    if (!b) return true;
+    if (!(b[0] == 0.0) || !(b[n_el] == 1.0)) return false;
+    for (int e = 0; e < n_el; ++e)
+      if (!(b[e + 1] > b[e])) return false;
+    return true;
+  };
+  for (int l = 0; l < d->d; ++l)
+    if (!breaks_ok(d->breaks[l], d->n_el[l])) return ST_ERR_ARG;
+  if (!breaks_ok(d->breaks_t, d->n_el_t)) return ST_ERR_ARG;
   if (d->operator_form == ST_FORM_LEAN && !lean_applies(*d)) return ST_ERR_ARG;
   return ST_OK;
 }
@@ -1270,6 +1280,10 @@ st_status st_setup(const st_problem_desc *desc, void *cuda_stream, st_handle **o
   cudaGetDevice(&h->dev);
   h->pooled = pools_supported(h->dev);
   st_status s = setup_impl(h);
+  // the breakpoint arrays belong to the caller: the handle keeps only the
+  // tables built from them
+  for (int l = 0; l < 3; ++l) h->desc.breaks[l] = nullptr;
+  h->desc.breaks_t = nullptr;
   if (s != ST_OK) {
     st_destroy(h);
     return s;

@@ -104,7 +104,10 @@ void local_derivs(const std::vector<double> &kn, int s, int p, double x, int kma
   }
 }
 
-void build_dir(Dir1D &dr, int n_el, int p, double scale, int kmax, int nq = 0) {
+// Open knot vector of maximal regularity on [0, 1] with the breakpoints
+// `breaks` (n_el + 1 increasing values from 0 to 1; null: uniform), the Gauss
+// rule of each span and the local basis derivatives 0..kmax there.
+void build_dir(Dir1D &dr, int n_el, int p, double scale, int kmax, int nq = 0, const double *breaks = nullptr) {
   dr.n_el = n_el;
   dr.p = p;
   dr.n = n_el + p;
@@ -113,7 +116,7 @@ void build_dir(Dir1D &dr, int n_el, int p, double scale, int kmax, int nq = 0) {
   dr.scale = scale;
   dr.knots.assign(dr.n + p + 1, 0.0);
   for (int i = 0; i <= p; ++i) dr.knots[dr.n + i] = 1.0;
-  for (int i = 1; i < n_el; ++i) dr.knots[p + i] = (double)i / n_el;
+  for (int i = 1; i < n_el; ++i) dr.knots[p + i] = breaks ? breaks[i] : (double)i / n_el;
   std::vector<double> gx, gw;
   gauss_legendre(dr.nq, gx, gw);
   dr.xq.assign((size_t)n_el * dr.nq, 0.0);
@@ -235,13 +238,23 @@ void chol_band_apply(const std::vector<double> &A, int n, int bw, std::vector<do
 bool tau_setup(const Dir1D &td, std::vector<double> &tau_q) {
   int p = td.p, n_el = td.n_el, nq = td.nq;
   int Nt = td.n - 1;
-  double h = 0.0;
-  for (int e = 0; e < n_el; ++e) h = std::max(h, (td.knots[e + p + 1] - td.knots[e + p]) * td.scale);
+  // unknowns scaled by h^(2k-1), h the largest element in the support of the
+  // unknown's B-spline (the mesh size itself on a uniform mesh)
+  std::vector<double> hel(n_el);
+  for (int e = 0; e < n_el; ++e) hel[e] = (td.knots[e + p + 1] - td.knots[e + p]) * td.scale;
+  auto hsc = [&](int k, int m) {   // m-th B-spline of degree p-k spans elements m-(p-k) .. m
+    double h = 0.0;
+    for (int e = std::max(0, m - (p - k)); e <= std::min(n_el - 1, m); ++e) h = std::max(h, hel[e]);
+    return std::pow(h, 2 * k - 1);
+  };
   // unknown spaces
   // unknown (k, m) of tau_k's m-th B-spline sits in column m*p + (k-1), so
   // that the columns a condition touches stay local and C C^T is banded
   std::vector<Dir1D> sp(p + 1);
-  for (int k = 1; k <= p; ++k) build_dir(sp[k], n_el, p - k, td.scale, 0, nq);   // at the time Gauss points
+  // on the breakpoints of the time mesh, evaluated at its Gauss points
+  std::vector<double> br(n_el + 1);
+  for (int e = 0; e <= n_el; ++e) br[e] = td.knots[e + p];
+  for (int k = 1; k <= p; ++k) build_dir(sp[k], n_el, p - k, td.scale, 0, nq, br.data());
   int nu = p * (n_el + p - 1);
   auto col = [p](int k, int m) { return m * p + (k - 1); };
   // conditions
@@ -261,9 +274,9 @@ bool tau_setup(const Dir1D &td, std::vector<double> &tau_q) {
           double w = td.wq[e * nq + q];
           r.rhs -= w * td.at(1, e, q, aj) * td.at(0, e, q, ai);
           for (int k = 1; k <= p; ++k) {
-            double prod = w * td.at(k, e, q, aj) * td.at(k, e, q, ai) * std::pow(h, 2 * k - 1);
+            double prod = w * td.at(k, e, q, aj) * td.at(k, e, q, ai);
             const Dir1D &s = sp[k];
-            for (int m = 0; m <= s.p; ++m) r.v[col(k, e + m)] += prod * s.at(0, e, q, m);
+            for (int m = 0; m <= s.p; ++m) r.v[col(k, e + m)] += prod * hsc(k, e + m) * s.at(0, e, q, m);
           }
         }
       }
@@ -312,12 +325,11 @@ bool tau_setup(const Dir1D &td, std::vector<double> &tau_q) {
   }
   tau_q.assign((size_t)p * n_el * nq, 0.0);
   for (int k = 1; k <= p; ++k) {
-    double sc = std::pow(h, 2 * k - 1);
     const Dir1D &s = sp[k];
     for (int e = 0; e < n_el; ++e)
       for (int q = 0; q < nq; ++q) {
         double v = 0.0;
-        for (int m = 0; m <= s.p; ++m) v += y[col(k, e + m)] * sc * s.at(0, e, q, m);
+        for (int m = 0; m <= s.p; ++m) v += y[col(k, e + m)] * hsc(k, e + m) * s.at(0, e, q, m);
         tau_q[((size_t)(k - 1) * n_el + e) * nq + q] = v;
       }
   }
@@ -362,11 +374,11 @@ st_status time_bands(const Dir1D &td, const st_problem_desc &d, std::vector<doub
 st_status host_setup(const st_problem_desc &d, HostSetup &hs) {
   int p = d.p;
   for (int l = 0; l < d.d; ++l) {
-    build_dir(hs.sdir[l], d.n_el[l], p, 1.0, std::min(2, p));
+    build_dir(hs.sdir[l], d.n_el[l], p, 1.0, std::min(2, p), 0, d.breaks[l]);
     hs.M[l] = band_matrix(hs.sdir[l], 0, 0, 0);
     hs.K[l] = band_matrix(hs.sdir[l], 1, 1, 0);
   }
-  build_dir(hs.tdir, d.n_el_t, p, d.T, p);
+  build_dir(hs.tdir, d.n_el_t, p, d.T, p, 0, d.breaks_t);
   if (!tau_setup(hs.tdir, hs.tau_q)) return ST_ERR_BREAKDOWN;
   return time_bands(hs.tdir, d, hs.Mt, hs.Wt, hs.wlu);
 }
@@ -375,7 +387,7 @@ st_status host_setup(const st_problem_desc &d, HostSetup &hs) {
 // handle-free w-update.
 st_status host_time_bands(const st_problem_desc &d, std::vector<double> &Mt, std::vector<double> &wlu) {
   Dir1D td;
-  build_dir(td, d.n_el_t, d.p, d.T, d.p);
+  build_dir(td, d.n_el_t, d.p, d.T, d.p, 0, d.breaks_t);
   std::vector<double> Wt;
   return time_bands(td, d, Mt, Wt, wlu);
 }

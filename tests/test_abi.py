@@ -43,7 +43,7 @@ def test_binding_struct_matches_header_field_order():
     names = []
     for f in fields:
         for part in f.split(","):
-            names.append(re.sub(r"\[.*\]", "", part).strip())
+            names.append(re.sub(r"\[.*\]", "", part).strip().lstrip("*").strip())
     assert names == [n for n, _ in StProblemDesc._fields_]
 
 

@@ -8,7 +8,9 @@
 * the rest state (zero source: u = w = 0 exactly, rank 0, no NaN);
 * the error statuses, made on the host: an iteration cap that is too small
   (ST_ERR_NOT_CONVERGED with the best iterate kept) and a NaN written into
-  an input vector (ST_ERR_NAN); the handle stays usable after both.
+  an input vector (ST_ERR_NAN); the handle stays usable after both;
+* non-uniform meshes: time knots clustered where the stimulus switches, a
+  graded spatial mesh, through every stage.
 """
 
 import numpy as np
@@ -232,4 +234,68 @@ def test_nan_input_is_reported(P):
     dx, dy = dev(xv), empty(n)
     s.apply(ptr(dx), ptr(dy), P.ST_FP64)
     assert rel(host(dy), A @ xv) < 1e-12
+    s.close()
+
+
+def nonuniform_problem(d, p, **over):
+    """Time knots clustered where the stimulus switches on and off (t = 0.2
+    and 1.5 of T = 8, Sec. 4.2) and a graded spatial mesh, 7 elements each way."""
+    c = dict(d=d, p=p, n_el=[7, 6, 5][:d], n_el_t=10)
+    desc = stim_problem(c, **over)
+    desc["breaks_t"] = W.clustered_breaks(10, [0.2, 1.5], p, T=desc["T"])
+    desc["breaks"] = [W.clustered_breaks(ne, [0.35], p) for ne in c["n_el"]]
+    return desc
+
+
+NU_CASES = [(d, p, f) for d, p in ((1, 2), (2, 3), (3, 2)) for f in ("bands", "lean") if f == "bands" or d >= 2]
+
+
+@pytest.mark.parametrize("d,p,form", NU_CASES, ids=[f"d{d}p{p}-{f}" for d, p, f in NU_CASES])
+def test_non_uniform_knots(P, d, p, form):
+    """Clustered time knots and graded spatial meshes through every stage: the
+    1D data and tau, the load vector, Theta-hat and both operators at an
+    iterate, the preconditioner, an FP64 linear solve, and three nonlinear
+    steps, against the oracle on the same breakpoints."""
+    import scipy.sparse.linalg as spla
+    desc = nonuniform_problem(d, p, operator_form=form, rtol=1e-13, gmres_m=80)
+    o = Oracle(desc)
+    st = o.st
+    s = P.Solver(desc, stream())
+    tau = np.array(s.get("tau_q", p * st.n_el_t * (p + 1)))
+    exp_tau = np.concatenate([t.ravel() for t in o.tau_q])
+    assert np.abs(tau - exp_tau).max() <= 1e-11 * max(1.0, np.abs(exp_tau).max())
+    f = empty(st.N_dof)
+    s.rhs(ptr(f))
+    assert rel(host(f), o.F) < 1e-13
+    u, w, hist = o.solve(max_fp=2, record=True)
+    u, w = hist[-1]["u"], hist[-1]["w"]
+    A, info = o.linearization(u, w)
+    du, dw = dev(u), dev(w)
+    g = s.ionic(ptr(du), ptr(dw))
+    th = np.array(s.get("theta_hat", st.N_dof)).reshape(st.N_t, st.N_s)
+    assert np.abs(th - info["theta_hat"]).max() < 1e-12
+    assert g["rank"] == len(info["s"])
+    x = W.random_vector(st.N_dof, seed=5)
+    dx, dy = dev(x), empty(st.N_dof)
+    s.apply(ptr(dx), ptr(dy), P.ST_FP64)
+    assert rel(host(dy), A @ x) < 1e-12
+    dx32, dy32 = dev(x, np.float32), empty(st.N_dof, "float32")
+    s.apply(ptr(dx32), ptr(dy32), P.ST_MIXED)
+    assert rel(host(dy32), A @ x) < 2e-5
+    r = W.random_vector(st.N_dof, seed=9)
+    dr, dz = dev(r), empty(st.N_dof)
+    s.precond(ptr(dr), ptr(dz), P.ST_FP64)
+    assert rel(host(dz), spla.spsolve(o.precond_matrix().tocsc(), r)) < 1e-10
+    sol = dev(u)
+    out = s.linsolve(ptr(f), ptr(sol))
+    assert out["rel_res"] <= 1e-13
+    assert rel(host(sol), spla.spsolve(A.tocsc(), o.F)) < 1e-10
+    s.close()
+    desc3 = dict(desc, max_fp=3, delta=0.0)
+    u_ref, w_ref, _ = Oracle(desc3).solve(max_fp=3)
+    s = P.Solver(desc3, stream())
+    u3, w3 = empty(st.N_dof), empty(st.N_dof)
+    st3 = s.solve(ptr(u3), ptr(w3), allow_unconverged=True)
+    assert st3["fp_iters"] == 3
+    assert rel(host(u3), u_ref) < 1e-10 and rel(host(w3), w_ref) < 1e-10
     s.close()

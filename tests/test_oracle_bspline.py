@@ -100,3 +100,20 @@ def test_mass_row_sums_and_stiffness_kernel(p):
     wq = st.tdir.wq.reshape(-1)
     col_b1 = (B0[:, 1:] * wq[:, None]).T @ B0[:, 0]
     assert np.abs(m["Mt"].sum(axis=1) + col_b1 - full[1:]).max() < 1e-14
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_non_uniform_knots_partition_of_unity_and_linear_precision(p):
+    """The same identities on clustered breakpoints (the non-uniform meshes the
+    boundary accepts), and mass rows summing to the support lengths / (p+1)."""
+    from oracle.spacetime import open_knots
+    br = W.clustered_breaks(11, [0.3, 0.7], p)
+    kn = open_knots(br, p)
+    x = np.linspace(0.0, 1.0, 101)
+    B = bspline_all(kn, p, x)
+    assert np.abs(B.sum(axis=1) - 1.0).max() < 1e-13
+    assert np.abs(B @ greville(kn, p) - x).max() < 1e-13
+    d = Direction(11, p, knots=kn)
+    M = (d.vals[0].reshape(-1, d.n) * d.wq.reshape(-1)[:, None]).T @ d.vals[0].reshape(-1, d.n)
+    supp = np.array([kn[i + p + 1] - kn[i] for i in range(d.n)])
+    assert np.abs(M.sum(axis=1) - supp / (p + 1)).max() < 1e-14

@@ -12,9 +12,10 @@ import workloads as W
 
 
 @pytest.mark.parametrize("p", [1, 2, 3])
-@pytest.mark.parametrize("n_el_t", [2, 4, 9])
-def test_tau_makes_time_block_lower_triangular(p, n_el_t):
-    st = SpaceTime(W.base_desc(d=1, p=p, n_el=[2], n_el_t=n_el_t, T=3.0))
+@pytest.mark.parametrize("n_el_t,clustered", [(2, False), (4, False), (9, False), (9, True), (16, True)])
+def test_tau_makes_time_block_lower_triangular(p, n_el_t, clustered):
+    breaks_t = W.clustered_breaks(n_el_t, [0.5], p, T=3.0) if clustered else None
+    st = SpaceTime(W.base_desc(d=1, p=p, n_el=[2], n_el_t=n_el_t, T=3.0, breaks_t=breaks_t))
     _, tau_q = tau_solve(st)
     m = st.matrices_1d()
     td = st.tdir

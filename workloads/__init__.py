@@ -26,6 +26,9 @@ Problem description keys (all plain Python numbers / lists / strings):
   fix_w_zero      True: recovery variable held at zero (smooth 1D test, Sec. 4.1)
   precision       "fp64" | "mixed"
   gmres_m, rtol, max_it  Krylov restart length, relative residual target, cap
+  breaks, breaks_t  None (uniform) or the n_el + 1 increasing breakpoints from 0 to
+                  1 of each spatial direction (a list of d lists or None) and of
+                  time (parametric, scaled by T)
   operator_form   "auto" | "bands" | "lean"   (how the device stores the
                   reaction + SU part of the operator; results are the same)
   inner_op        "auto" | "fp32" | "df"   (arithmetic of the operator inside
@@ -172,6 +175,32 @@ def wave_fields(desc, seed=7, speed=0.03, width=0.05):
     u = 0.5 * (1.0 + np.tanh((speed * t - r) / width))
     w = 0.3 * 0.5 * (1.0 + np.tanh((speed * (t - 5.0) - r) / width))
     return u.reshape(-1), w.reshape(-1)
+
+
+def clustered_breaks(n_el, centers, p, T=1.0, spread=0.125):
+    """Breakpoints on [0, 1] (parametric; physical times are T times these):
+    p + 1 of them clustered at spacing spread / n_el around each physical time
+    in `centers`, the rest spread almost uniformly over the gaps between the
+    clusters and the ends, in proportion to the gap lengths (the time knots
+    clustered where the source switches on and off, same number of elements,
+    Sec. 4.2).  Plain arithmetic on a list of numbers."""
+    h = 1.0 / n_el
+    fixed = [0.0, 1.0]
+    for c in centers:
+        x = c / T
+        fixed += [x + (k - p / 2.0) * spread * h for k in range(p + 1)]
+    fixed = sorted(fixed)
+    left = n_el + 1 - len(fixed)
+    gaps = np.diff(fixed)
+    share = gaps / gaps.sum() * left
+    count = np.floor(share).astype(int)
+    for i in np.argsort(-(share - count))[:left - count.sum()]:
+        count[i] += 1
+    out = list(fixed)
+    for i, m in enumerate(count):
+        a, b = fixed[i], fixed[i + 1]
+        out += [a + (b - a) * (k + 1) / (m + 1) for k in range(m)]
+    return sorted(float(v) for v in out)
 
 
 def random_vector(n, seed, lo=-1.0, hi=1.0):
