@@ -66,7 +66,8 @@ enum { ST_SUPPEXT_LITERAL = 0, ST_SUPPEXT_SYMMETRIC = 1 };
  *                 space-time Gauss points from u^k, w^k inside the apply and the
  *                 SU term of Eq. (tildeS) is kept as its rank-R factors
  *                 (requires d >= 2 and n_el[0] + p <= 256);
- *  ST_FORM_AUTO:  the lean form where it applies, else the band form. */
+ *  ST_FORM_AUTO:  the band form, faster per apply, unless its footprint
+ *                 exceeds 160 GiB and the lean form applies. */
 enum { ST_FORM_AUTO = 0, ST_FORM_BANDS = 1, ST_FORM_LEAN = 2 };
 /* operator of the inner FP32 Krylov solve of the mixed mode (the Krylov
  * vectors and the preconditioner stay FP32):
@@ -78,10 +79,26 @@ enum { ST_FORM_AUTO = 0, ST_FORM_BANDS = 1, ST_FORM_LEAN = 2 };
  *                 (the B-spline mass matrices of d+1 directions), the inner
  *                 correction then carries a relative error near kappa(A) u_32
  *                 and the FP64 refinement contracts slowly;
- *  ST_INNER_AUTO: FP32 first; from the first refinement step that reduces
- *                 the true residual by less than a factor 20, double-float for
- *                 the rest of the handle's life. */
+ *  ST_INNER_AUTO: FP32 first; double-float for the rest of the handle's life
+ *                 from a refinement step that stagnates with the FP64
+ *                 preconditioner already in use (see ST_PRECOND_AUTO). */
 enum { ST_INNER_AUTO = 0, ST_INNER_FP32 = 1, ST_INNER_DF = 2 };
+/* arithmetic of the preconditioner inside the FP32 Krylov solve (mixed mode):
+ *  ST_PRECOND_TF32: spatial transforms on the tensor cores (tcgen05, TF32
+ *                   inputs, FP32 accumulation) where every n_l <= 256 and the
+ *                   once-per-process self-test passed, else on CUDA cores;
+ *  ST_PRECOND_FP32: transforms on CUDA cores in FP32;
+ *  ST_PRECOND_FP64: the FP64 preconditioner, its input and output rounded to
+ *                   FP32;
+ *  ST_PRECOND_AUTO: TF32 for d <= 2 and FP64 for d = 3, and FP64 from the
+ *                   first refinement step on that stagnates (an inner cycle
+ *                   that ends without reaching its tolerance, or a step that
+ *                   reduces the true residual by less than a factor 20).
+ * The error of a rounded preconditioner is amplified by the conditioning of
+ * its time solves: a TF32 forward error near 2^-11 left the FGMRES residual of
+ * the 3D workload near 1e-7 after 600 iterations, FP32 needed 270 to 385
+ * iterations to 1e-8 and FP64 30 (GB300 measurement). */
+enum { ST_PRECOND_AUTO = 0, ST_PRECOND_TF32 = 1, ST_PRECOND_FP32 = 2, ST_PRECOND_FP64 = 3 };
 
 #define ST_MAX_STIM 8
 
@@ -130,6 +147,7 @@ typedef struct {
                               * st_setup and st_footprint only (the caller keeps them) */
   const double *breaks_t;    /* the same for time, parametric on [0, 1] (scaled by T);
                               * e.g. knots clustered where the source switches (Sec. 4.2) */
+  int precond_arith;         /* ST_PRECOND_* (mixed mode) */
 } st_problem_desc;
 
 typedef struct st_handle st_handle;
@@ -299,7 +317,10 @@ enum {
   ST_GET_TAU_Q = 4,      /* double[p * n_el_t * (p+1)]  tau_k at time Gauss points */
   ST_GET_FD_EIG = 5,     /* double[sum_l n_l]  generalized eigenvalues of (D_ll K_l, M_l) */
   ST_GET_BANDS_1D = 6,   /* double[(sum_l 2 n_l + 2 N_t) (2p+1)]: M_l, K_l per direction, M_t, W_t */
-  ST_GET_REACTION_S = 7  /* double[rank_reaction]  singular values of the low-rank reaction coefficient */
+  ST_GET_REACTION_S = 7, /* double[rank_reaction]  singular values of the low-rank reaction coefficient */
+  ST_GET_REACTION_U = 8, /* double[N_t * rank_reaction]  its time factors, row-major */
+  ST_GET_REACTION_V = 9, /* double[N_s * rank_reaction]  its space factors, row-major */
+  ST_GET_REACTION_TB = 10 /* double[rank_reaction * (p+1) * N_t]  its time mass bands [r][k][it] */
 };
 st_status st_get(st_handle *h, int what, void *dst_host, size_t bytes);
 

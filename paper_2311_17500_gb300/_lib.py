@@ -22,8 +22,10 @@ ST_FP64, ST_MIXED = 0, 1
 ST_SUPPEXT = {"literal": 0, "symmetric": 1}
 ST_FORM = {"auto": 0, "bands": 1, "lean": 2}
 ST_INNER = {"auto": 0, "fp32": 1, "df": 2}
+ST_PRECOND = {"auto": 0, "tf32": 1, "fp32": 2, "fp64": 3}
 ST_MAX_STIM = 8
-GET = dict(theta_hat=0, lowrank_s=1, lowrank_u=2, lowrank_v=3, tau_q=4, fd_eig=5, bands_1d=6, reaction_s=7)
+GET = dict(theta_hat=0, lowrank_s=1, lowrank_u=2, lowrank_v=3, tau_q=4, fd_eig=5, bands_1d=6, reaction_s=7,
+           reaction_u=8, reaction_v=9, reaction_tb=10)
 
 EXPORTS = ["st_footprint", "st_setup", "st_destroy", "st_error_string", "st_get_dims", "st_ionic",
            "st_linearize", "st_apply", "st_precond", "st_linsolve", "st_wupdate", "st_rhs", "st_solve",
@@ -49,7 +51,8 @@ class StProblemDesc(ctypes.Structure):
                 ("gmres_m", ctypes.c_int), ("rtol", ctypes.c_double), ("max_it", ctypes.c_int),
                 ("operator_form", ctypes.c_int), ("inner_op", ctypes.c_int),
                 ("eps_reaction", ctypes.c_double),
-                ("breaks", ctypes.POINTER(ctypes.c_double) * 3), ("breaks_t", ctypes.POINTER(ctypes.c_double))]
+                ("breaks", ctypes.POINTER(ctypes.c_double) * 3), ("breaks_t", ctypes.POINTER(ctypes.c_double)),
+                ("precond_arith", ctypes.c_int)]
 
 
 class StDims(ctypes.Structure):
@@ -172,6 +175,7 @@ def make_desc(desc):
     if desc.get("breaks_t") is not None:
         c.breaks_t = darr(desc["breaks_t"])
     c._keep = keep
+    c.precond_arith = ST_PRECOND[desc.get("precond_arith", "auto")]
     return c
 
 

@@ -23,11 +23,17 @@ struct Sizes {
   int m, nmax, cap;
   bool lean;
   long long rows_x, wcap;
+  long long gpart;   // values of a separate Gram partial-sum buffer (0: the first work buffer holds them)
   size_t bytes;
 };
 
 // The lean operator form applies to d >= 2 with an x row in one block.
 bool lean_applies(const st_problem_desc &D) { return D.d >= 2 && xlean_feasible(D.n_el[0], D.p); }
+
+// Device bytes above which ST_FORM_AUTO takes the lean form.
+constexpr size_t kBandFormLimit = (size_t)160 << 30;
+
+Sizes plan(const st_problem_desc &D);
 
 st_status validate(const st_problem_desc *d) {
   if (!d) return ST_ERR_ARG;
@@ -49,6 +55,7 @@ st_status validate(const st_problem_desc *d) {
   if (d->operator_form < ST_FORM_AUTO || d->operator_form > ST_FORM_LEAN) return ST_ERR_ARG;
   if (d->inner_op < ST_INNER_AUTO || d->inner_op > ST_INNER_DF) return ST_ERR_ARG;
   if (!(d->eps_reaction == d->eps_reaction)) return ST_ERR_ARG;   // NaN
+  if (d->precond_arith < ST_PRECOND_AUTO || d->precond_arith > ST_PRECOND_FP64) return ST_ERR_ARG;
   auto breaks_ok = [](const double *b, int n_el) {
     if (!b) return true;
     if (!(b[0] == 0.0) || !(b[n_el] == 1.0)) return false;
@@ -81,13 +88,29 @@ Sizes plan(const st_problem_desc &D) {
   z.nmax = z.Nt;
   for (int l = 0; l < D.d; ++l) z.nmax = std::max(z.nmax, z.n[l]);
   z.cap = (int)std::min<long long>(z.Nt, z.Ns);
-  z.lean = D.operator_form == ST_FORM_LEAN || (D.operator_form == ST_FORM_AUTO && lean_applies(D));
+  // automatic form: the band form, faster per apply wherever it fits (C2:
+  // 0.30 against 1.23 ms, C3: 5.1 against 16 ms per FP32 apply on GB300),
+  // unless its footprint exceeds kBandFormLimit and the lean form applies
+  z.lean = D.operator_form == ST_FORM_LEAN;
+  if (D.operator_form == ST_FORM_AUTO && lean_applies(D)) {
+    st_problem_desc b = D;
+    b.operator_form = ST_FORM_BANDS;
+    z.lean = plan(b).bytes > kBandFormLimit;
+  }
   z.rows_x = 1;
   for (int l = 1; l < D.d; ++l) z.rows_x *= z.Q[l];
   // values per Gauss-point work buffer: every spatial Gauss point of every time
   // row in the band form; in the lean form the Gauss rows of the other axes
   // with x in coefficients (the largest array of the apply), at least N_dof
   z.wcap = z.lean ? std::max<long long>((long long)z.Nt * z.rows_x * z.n[0], z.Ndof) : z.NtQs;
+  // the Gram matrix of the low-rank steps sums 64 x 64 tiles of partial sums,
+  // at least one per upper-triangle tile pair: small problems need more room
+  // than their work buffer
+  {
+    const long long nt = (z.Nt + kGramTile - 1) / kGramTile;
+    const long long need = nt * (nt + 1) / 2 * kGramTile * kGramTile;
+    z.gpart = need > z.wcap ? need : 0;
+  }
   size_t b = 0;
   size_t d8 = sizeof(double), f4 = sizeof(float);
   // 1D data (generous)
@@ -122,6 +145,7 @@ Sizes plan(const st_problem_desc &D) {
     b += (size_t)z.cap * (z.Nt + z.Ns + 2 + z.Qt + (z.p + 1) * z.Nt) * d8 + (size_t)z.cap * (z.p + 1) * z.Nt * 8;
     b += (size_t)(2 * z.nmax + z.Nt) * z.B * d8;
   }
+  b += (size_t)z.gpart * d8;                                       // Gram partial sums (small problems)
   b += (size_t)(608 * (2 * z.m + 56) + 4096) * d8;                 // reduction scratch
   b += 2 * (size_t)(2 * (z.m + 2) + 8) * d8 + 256;                 // Hessenberg column, DCGS2 coefficients, flags
   b += 64 * 1024;   // small tables: 1D data of tiny meshes (one element at least each), Gauss-point hats
@@ -228,6 +252,19 @@ template <> st_status inner_apply<float>(st_handle *h, const float *z, float *w)
   return ST_OK;
 }
 
+// The preconditioner inside a Krylov cycle: FP64 in the FP64 cycle; in the
+// FP32 cycle the FP32 (TF32) one, or the FP64 one on the FP32 vectors
+// (converted around it) when the handle's inner solve needs the accuracy.
+template <typename T> st_status inner_precond(st_handle *h, const T *v, T *z);
+template <> st_status inner_precond<double>(st_handle *h, const double *v, double *z) { return precond_T<double>(h, v, z); }
+template <> st_status inner_precond<float>(st_handle *h, const float *v, float *z) {
+  if (!h->pre64) return precond_T<float>(h, v, z);
+  launch_f2d(h->stream, h->r64, v, h->Ndof);
+  ST_TRY(precond_T<double>(h, h->r64, h->t64b));
+  launch_d2f(h->stream, z, h->t64b, 1.0, h->Ndof);
+  return ST_OK;
+}
+
 template <typename T>
 st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int *its, double *est) {
   cudaStream_t s = h->stream;
@@ -293,7 +330,7 @@ st_status gmres_cycle(st_handle *h, const T *b, T *d, double tol, int maxit, int
   const size_t slot = (size_t)nhh + 1;   // coefficients, then the tensor-core error flag
   auto launch_iter = [&](int jj) -> st_status {
     T *uj = V + (long long)jj * ld, *w = V + (long long)(jj + 1) * ld, *zj = Z + (long long)jj * ld;
-    ST_TRY(precond_T<T>(h, uj, zj));
+    ST_TRY(inner_precond<T>(h, uj, zj));
     ST_TRY(inner_apply<T>(h, zj, w));
     {
       // delayed CGS2: one dot pass of [V_0..V_{j-1}, u_j, w] against (u_j, w),
@@ -1035,6 +1072,7 @@ static st_status setup_impl(st_handle *h) {
   h->lean = z.lean;
   h->rows_x = z.rows_x;
   h->wcap = z.wcap;
+  h->gpart_cap = z.gpart;
   h->ldv = (z.Ndof + 63) / 64 * 64;
   h->rank_cap = z.cap;
   ST_TRY(host_setup(D, h->hs));
@@ -1184,6 +1222,7 @@ static st_status setup_impl(st_handle *h) {
     h->Tc = dalloc<double>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
     h->Tc2 = dalloc<float2>(h, (size_t)cap * (h->p + 1) * h->Nt, &e);
   }
+  if (h->gpart_cap > 0) h->gpart = dalloc<double>(h, h->gpart_cap, &e);
   for (int i = 0; i < 2; ++i) {
     h->W64[i] = dalloc<double>(h, h->wcap, &e);
     // the lean form's FP32 work buffers share the FP64 ones: the two operators
@@ -1241,7 +1280,8 @@ static st_status setup_impl(st_handle *h) {
     // zero-padded FP32 copies of U_l^T and U_l for the tensor-core transforms
     bool fits = true;
     for (int l = 0; l < h->d; ++l) fits = fits && h->n[l] <= 256;
-    if (fits && tc_state(h->stream, nullptr) == 1) {
+    const bool want_tc = D.precond_arith == ST_PRECOND_TF32 || (D.precond_arith == ST_PRECOND_AUTO && h->d <= 2);
+    if (fits && want_tc && tc_state(h->stream, nullptr) == 1) {
       for (int l = 0; l < h->d; ++l) {
         int n = h->n[l];
         h->Npad[l] = (n + 15) / 16 * 16;
@@ -1399,6 +1439,9 @@ st_status st_linsolve(st_handle *h, const double *b, double *x, st_stats *stats)
   st_status status = ST_ERR_NOT_CONVERGED;
   if (D.precision == ST_MIXED && D.inner_op == ST_INNER_DF) h->inner_df = true;
   if (D.precision == ST_MIXED && D.inner_op == ST_INNER_FP32) h->inner_df = false;
+  if (D.precision == ST_MIXED && D.precond_arith == ST_PRECOND_FP64) h->pre64 = true;
+  if (D.precision == ST_MIXED && D.precond_arith == ST_PRECOND_AUTO && h->d >= 3) h->pre64 = true;
+  bool stalled = false;   // the last inner cycle ended without reaching its tolerance
   while (true) {
     ST_TRY(apply_T<double>(h, x, h->t64a));
     launch_sub64(s, h->r64, b, h->t64a, N);
@@ -1406,11 +1449,14 @@ st_status st_linsolve(st_handle *h, const double *b, double *x, st_stats *stats)
     if (!std::isfinite(rn)) return ST_ERR_NAN;
     rel = rn / bn;
     if (rel <= D.rtol) { status = ST_OK; break; }
-    // a refinement step that reduced the true residual by less than a factor
-    // 20: the FP32 operator limits the inner correction; switch it to
-    // double-float (kept for the handle's later solves)
-    if (D.precision == ST_MIXED && D.inner_op == ST_INNER_AUTO && !h->inner_df && rel > rel_prev / 20.0)
-      h->inner_df = true;
+    // a refinement step that stagnated (its inner cycle ended short of its
+    // tolerance, or the true residual fell by less than a factor 20): first
+    // the FP64 preconditioner, then the double-float operator (both kept for
+    // the handle's later solves)
+    if (D.precision == ST_MIXED && (stalled || rel > rel_prev / 20.0)) {
+      if (D.precond_arith == ST_PRECOND_AUTO && !h->pre64) h->pre64 = true;
+      else if (D.inner_op == ST_INNER_AUTO && !h->inner_df) h->inner_df = true;
+    }
     rel_prev = rel;
     if (total >= D.max_it) break;
     int its = 0;
@@ -1425,6 +1471,7 @@ st_status st_linsolve(st_handle *h, const double *b, double *x, st_stats *stats)
       launch_d2f(s, h->r32, h->r64, 1.0 / rn, N);
       double tin = std::max(0.5 * tol_in, 1e-6);
       ST_TRY(gmres_cycle<float>(h, h->r32, h->d32, tin, maxit, &its, &est));
+      stalled = its >= maxit && est > tin;
       launch_f2d_axpy(s, x, h->d32, rn, N);
     }
     total += its;
@@ -1543,6 +1590,10 @@ st_status st_get(st_handle *h, int what, void *dst, size_t bytes) {
     case ST_GET_LOWRANK_U: need = (size_t)h->Nt * h->rank * sizeof(double); src = h->Ur; break;
     case ST_GET_LOWRANK_V: need = (size_t)h->Ns * h->rank * sizeof(double); src = h->Vr; break;
     case ST_GET_REACTION_S: need = (size_t)h->rankC * sizeof(double); src = h->srC; if (!src) return ST_ERR_STATE; break;
+    case ST_GET_REACTION_U: need = (size_t)h->Nt * h->rankC * sizeof(double); src = h->UrC; if (!src) return ST_ERR_STATE; break;
+    case ST_GET_REACTION_V: need = (size_t)h->Ns * h->rankC * sizeof(double); src = h->VrC; if (!src) return ST_ERR_STATE; break;
+    case ST_GET_REACTION_TB:
+      need = (size_t)h->rankC * (h->p + 1) * h->Nt * sizeof(double); src = h->Tc; if (!src) return ST_ERR_STATE; break;
     case ST_GET_TAU_Q: tmp = h->hs.tau_q; break;
     case ST_GET_FD_EIG: {
       size_t tot = 0;

@@ -647,7 +647,7 @@ __global__ void __launch_bounds__(256) su_band_update_kernel(float *__restrict__
 // each block stages 64 x 32 slices of the two row panels as double-float pairs
 // and accumulates 4 x 4 outputs per thread; part[split][tile][64][64] holds
 // the chunk sums as FP64.
-constexpr int kGT = 64, kGK = 32;
+constexpr int kGT = kGramTile, kGK = 32;
 
 __global__ void __launch_bounds__(256) gram_df_kernel(double *__restrict__ part, const double *__restrict__ Th, int n,
                                                       long long K, int ntile, int kchunk) {
@@ -1047,13 +1047,18 @@ static st_status truncated_svd(st_handle *h, const double *M, double eps, int ca
   const int Nt = h->Nt;
   {
     // G = M M^T in double-float, upper-triangle tiles, K split so that the
-    // grid holds several blocks per SM (partials in the first work buffer)
+    // grid holds several blocks per SM; the partials go to the first work
+    // buffer, or to the handle's own buffer where that one is too small for a
+    // single split (set-up sizes it for exactly that)
     const int ntile = (Nt + kGT - 1) / kGT, npair = ntile * (ntile + 1) / 2;
+    double *part = h->gpart ? h->gpart : h->W64[0];
+    const long long cap = h->gpart ? h->gpart_cap : h->wcap;
+    if ((long long)npair * kGT * kGT > cap) return ST_ERR_STATE;  // set-up sizes the buffer: not reached
     int nsplit = (int)std::max<long long>(1, std::min<long long>((152LL * 6 + npair - 1) / npair, (h->Ns + 255) / 256));
-    while ((long long)nsplit * npair * kGT * kGT > h->wcap && nsplit > 1) --nsplit;
+    while ((long long)nsplit * npair * kGT * kGT > cap && nsplit > 1) --nsplit;
     const int kchunk = (int)((h->Ns + nsplit - 1) / nsplit);
-    st_count_launch(); gram_df_kernel<<<dim3(npair, nsplit), 256, 0, s>>>(h->W64[0], M, Nt, h->Ns, ntile, kchunk);
-    st_count_launch(); gram_reduce_kernel<<<grid_for((long long)npair * kGT * kGT), 256, 0, s>>>(h->gram, h->W64[0], Nt, ntile, npair, nsplit);
+    st_count_launch(); gram_df_kernel<<<dim3(npair, nsplit), 256, 0, s>>>(part, M, Nt, h->Ns, ntile, kchunk);
+    st_count_launch(); gram_reduce_kernel<<<grid_for((long long)npair * kGT * kGT), 256, 0, s>>>(h->gram, part, Nt, ntile, npair, nsplit);
   }
   std::vector<double> G((size_t)Nt * Nt);
   // trace = ||M||_F^2

@@ -302,12 +302,14 @@ bool tau_setup(const Dir1D &td, std::vector<double> &tau_q) {
         G[(size_t)a * nr + b] = s;
         G[(size_t)b * nr + a] = s;
       }
-    // Cholesky of C C^T once; y = C^T z, then two refinement steps on the
-    // residual rhs - C y (the normal equations square the condition number)
+    // Cholesky of C C^T once; y = C^T z, then refinement steps on the
+    // residual rhs - C y (the normal equations square the condition number,
+    // which graded time meshes raise further); every update stays in the
+    // range of C^T, so y tends to the minimum-norm solution
     std::vector<double> z(nr), res(nr);
     for (int a = 0; a < nr; ++a) z[a] = rows[a].rhs;
     if (!chol_band_factor(G, nr, bw)) return false;
-    for (int pass = 0; pass < 3; ++pass) {
+    for (int pass = 0; pass < 6; ++pass) {
       if (pass == 0) {
         for (int a = 0; a < nr; ++a) res[a] = rows[a].rhs;
       } else {

@@ -10,6 +10,8 @@
 
 #define ST_MAXP 4
 #define ST_MAXB (2 * ST_MAXP + 1)
+// tile edge of the Gram matrix kernel of the low-rank steps
+constexpr int kGramTile = 64;
 
 // ---------------------------------------------------------------- host 1D data
 // One parametric direction (space, or time with `scale` = T).  Tables are per
@@ -101,7 +103,10 @@ struct st_handle {
   double *cfr = nullptr;                 // lean: scale C_m sigma_r of each SU rank
   int lin_kind = ST_PICARD;              // linearization of the current operator
   bool inner_df = false;                 // the mixed inner solve applies the operator in double-float
+  bool pre64 = false;                    // the mixed inner solve applies the FP64 preconditioner
   long long wcap = 0;                    // values per Gauss-point work buffer (W64 doubles, W32 floats)
+  double *gpart = nullptr;               // Gram partial sums when the first work buffer is too small
+  long long gpart_cap = 0;
   long long rows_x = 1;                  // Gauss rows of the axes other than x: prod_{l>=1} Q_l
   // linearization: symmetric time band per spatial Gauss point, [k][it][q], k = 0..p
   // time bands per spatial Gauss point [k][it][q] as double-float pairs:

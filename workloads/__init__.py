@@ -33,6 +33,8 @@ Problem description keys (all plain Python numbers / lists / strings):
                   reaction + SU part of the operator; results are the same)
   inner_op        "auto" | "fp32" | "df"   (arithmetic of the operator inside
                   the mixed mode's FP32 Krylov solve)
+  precond_arith   "auto" | "tf32" | "fp32" | "fp64"   (the preconditioner inside
+                  the mixed mode's FP32 Krylov solve)
 """
 
 import copy
@@ -55,7 +57,7 @@ def base_desc(**over):
         source=dict(kind="zero"),
         stabilization="su", suppext="literal", eps_theta=0.1, eps_reaction=-1.0,
         nonlinear="picard", alpha=0.5, delta=1e-4, max_fp=60, fix_w_zero=False,
-        precision="fp64", gmres_m=100, rtol=1e-8, max_it=2000, operator_form="auto", inner_op="auto",
+        precision="fp64", gmres_m=100, rtol=1e-8, max_it=2000, operator_form="auto", inner_op="auto", precond_arith="auto",
     )
     desc.update(PAPER_RM)
     for k, v in over.items():
@@ -181,7 +183,8 @@ def clustered_breaks(n_el, centers, p, T=1.0, spread=0.125):
     """Breakpoints on [0, 1] (parametric; physical times are T times these):
     p + 1 of them clustered at spacing spread / n_el around each physical time
     in `centers`, the rest spread almost uniformly over the gaps between the
-    clusters and the ends, in proportion to the gap lengths (the time knots
+    clusters and the ends, in proportion to the gap lengths; cluster points
+    outside (0, 1) are dropped (the time knots
     clustered where the source switches on and off, same number of elements,
     Sec. 4.2).  Plain arithmetic on a list of numbers."""
     h = 1.0 / n_el
@@ -189,7 +192,8 @@ def clustered_breaks(n_el, centers, p, T=1.0, spread=0.125):
     for c in centers:
         x = c / T
         fixed += [x + (k - p / 2.0) * spread * h for k in range(p + 1)]
-    fixed = sorted(fixed)
+    # cluster points must lie strictly inside (0, 1), once each
+    fixed = sorted(set(v for v in fixed if 0.0 < v < 1.0) | {0.0, 1.0})
     left = n_el + 1 - len(fixed)
     gaps = np.diff(fixed)
     share = gaps / gaps.sum() * left
@@ -201,6 +205,12 @@ def clustered_breaks(n_el, centers, p, T=1.0, spread=0.125):
         a, b = fixed[i], fixed[i + 1]
         out += [a + (b - a) * (k + 1) / (m + 1) for k in range(m)]
     return sorted(float(v) for v in out)
+
+
+def graded_breaks(n_el, power=1.3):
+    """Breakpoints (i / n_el)^power on [0, 1]: elements growing smoothly from
+    0 to 1 (plain arithmetic on a list of numbers)."""
+    return [float((i / n_el) ** power) for i in range(n_el + 1)]
 
 
 def random_vector(n, seed, lo=-1.0, hi=1.0):
