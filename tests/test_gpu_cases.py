@@ -258,7 +258,9 @@ def test_non_uniform_knots(P, d, p, form):
     iterate, the preconditioner, an FP64 linear solve, and three nonlinear
     steps, against the oracle on the same breakpoints."""
     import scipy.sparse.linalg as spla
-    desc = nonuniform_problem(d, p, operator_form=form, rtol=1e-13, gmres_m=80)
+    # eps ||A|| ||x|| / ||F|| is about 7e-13 for the p = 3 graded mesh: a
+    # 1e-13 residual target sits on the rounding floor there
+    desc = nonuniform_problem(d, p, operator_form=form, rtol=1e-12, gmres_m=80)
     o = Oracle(desc)
     st = o.st
     s = P.Solver(desc, stream())
@@ -291,7 +293,7 @@ def test_non_uniform_knots(P, d, p, form):
     assert rel(host(dz), spla.spsolve(o.precond_matrix().tocsc(), r)) < 1e-10
     sol = dev(u)
     out = s.linsolve(ptr(f), ptr(sol))
-    assert out["rel_res"] <= 1e-13
+    assert out["rel_res"] <= 1e-12
     assert rel(host(sol), spla.spsolve(A.tocsc(), o.F)) < 1e-10
     s.close()
     desc3 = dict(desc, max_fp=3, delta=0.0)
