@@ -73,15 +73,15 @@ enum { ST_FORM_AUTO = 0, ST_FORM_BANDS = 1, ST_FORM_LEAN = 2 };
  * vectors and the preconditioner stay FP32):
  *  ST_INNER_FP32: the operator in FP32 arithmetic;
  *  ST_INNER_DF:   the operator in double-float arithmetic (FP64 accuracy on the
- *                 FP32 pipes), its input and output rounded to FP32.  An FP32
- *                 operator has rounding errors of the size of the mass-matrix
- *                 terms it sums; when the space-time system is ill conditioned
- *                 (the B-spline mass matrices of d+1 directions), the inner
- *                 correction then carries a relative error near kappa(A) u_32
- *                 and the FP64 refinement contracts slowly;
+ *                 FP32 pipes), its input and output rounded to FP32;
  *  ST_INNER_AUTO: FP32 first; double-float for the rest of the handle's life
- *                 from a refinement step that stagnates with the FP64
- *                 preconditioner already in use (see ST_PRECOND_AUTO). */
+ *                 from a refinement step that fails with the FP64
+ *                 preconditioner already in use (see ST_PRECOND_AUTO).
+ * Either way an inner cycle cannot push the true residual of its correction d
+ * below about u_32 ||A|| ||d|| / ||b|| (d is stored in FP32): on the 3D
+ * 64^3 x 128 workload that level is near 4e-5 for every operator and
+ * preconditioner choice.  Each FP32 cycle ends when it gets there (see
+ * st_linsolve) and the FP64 refinement takes over. */
 enum { ST_INNER_AUTO = 0, ST_INNER_FP32 = 1, ST_INNER_DF = 2 };
 /* arithmetic of the preconditioner inside the FP32 Krylov solve (mixed mode):
  *  ST_PRECOND_TF32: spatial transforms on the tensor cores (tcgen05, TF32
@@ -90,14 +90,12 @@ enum { ST_INNER_AUTO = 0, ST_INNER_FP32 = 1, ST_INNER_DF = 2 };
  *  ST_PRECOND_FP32: transforms on CUDA cores in FP32;
  *  ST_PRECOND_FP64: the FP64 preconditioner, its input and output rounded to
  *                   FP32;
- *  ST_PRECOND_AUTO: TF32 for d <= 2 and FP64 for d = 3, and FP64 from the
- *                   first refinement step on that stagnates (an inner cycle
- *                   that ends without reaching its tolerance, or a step that
- *                   reduces the true residual by less than a factor 20).
- * The error of a rounded preconditioner is amplified by the conditioning of
- * its time solves: a TF32 forward error near 2^-11 left the FGMRES residual of
- * the 3D workload near 1e-7 after 600 iterations, FP32 needed 270 to 385
- * iterations to 1e-8 and FP64 30 (GB300 measurement). */
+ *  ST_PRECOND_AUTO: TF32 for d <= 2 and FP32 for d = 3, and FP64 from the
+ *                   first refinement step on that fails (one that reduces the
+ *                   true residual by less than a factor 2).
+ * On the 3D workload FP32 and FP64 preconditioners give the same residual
+ * after the same number of iterations, the FP64 one at 4x the cost of an
+ * iteration; TF32 needs about 1.5x the iterations of FP32 (GB300 measurement). */
 enum { ST_PRECOND_AUTO = 0, ST_PRECOND_TF32 = 1, ST_PRECOND_FP32 = 2, ST_PRECOND_FP64 = 3 };
 
 #define ST_MAX_STIM 8
@@ -250,7 +248,11 @@ st_status st_precond(st_handle *h, int prec, const void *r_dev, void *z_dev);
  * refinement around FP32 flexible GMRES (the FP32 preconditioner uses TF32
  * tensor cores, so it is kept as Z = M^{-1} V).  Arnoldi uses classical
  * Gram-Schmidt with one delayed reorthogonalization (two passes over the
- * basis per step) and FP64-accumulated inner products.
+ * basis per step) and FP64-accumulated inner products.  An FP32 cycle ends at
+ * its tolerance, or where its iterate stops improving: when its Arnoldi
+ * residual estimate first drops below 1e-3, 1e-4, ..., and every 10 columns
+ * after that, it forms its iterate (one extra operator application) and ends
+ * if the true residual is above twice the estimate.
  * ST_ERR_NOT_CONVERGED after desc.max_it inner iterations (x holds the best
  * iterate). */
 st_status st_linsolve(st_handle *h, const double *b_dev, double *x_dev, st_stats *stats);
