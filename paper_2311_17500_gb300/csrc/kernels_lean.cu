@@ -25,7 +25,10 @@
 // Layout and work split follow the fused x pass of the band form: X1, Y1 are
 // [N_t][rows][n_x], the x coefficients of every Gauss row of the other axes;
 // one block per (row, time segment), one thread per x element (its p+1
-// Gauss points) plus p threads for the trailing coefficients.  The block
+// Gauss points), the block rounded up to whole warps.  Thread e writes
+// coefficient e of each output row; the thread of the last element also
+// writes the p coefficients after it (a block of n_el + p threads would
+// spend a whole warp on those p values when n_el is a multiple of 32).  The block
 // sweeps its time segment with register windows of the rows it .. it+p of X,
 // U and W at its Gauss points (new rows arrive through a cp.async ring in
 // shared memory); at step it it
@@ -101,13 +104,16 @@ __global__ void __launch_bounds__(kLeanMaxThreads) xlean_kernel(LeanArgs<T> a) {
   extern __shared__ __align__(16) unsigned char lean_raw[];
   const int nth = blockDim.x;
   const bool exact = a.exact != 0;
-  T *xr = reinterpret_cast<T *>(lean_raw);                                    // [S][nth]
-  float2 *ur = reinterpret_cast<float2 *>(lean_raw + (size_t)S * nth * sizeof(T));   // [S][nth]
-  float2 *wr = ur + (exact ? (size_t)S * nth : 0);                            // [S][nth]
-  CT *dsh = reinterpret_cast<CT *>(wr + (exact ? (size_t)S * nth : 0));       // [Rt][nq][nth]
   const int nx = a.nel + P;
+  const int rs = max(nth, (nx + 3) / 4 * 4);   // ring row stride: all n_x coefficients of a row
+  T *xr = reinterpret_cast<T *>(lean_raw);                                    // [S][rs]
+  float2 *ur = reinterpret_cast<float2 *>(lean_raw + (size_t)S * rs * sizeof(T));    // [S][rs]
+  float2 *wr = ur + (exact ? (size_t)S * rs : 0);                             // [S][rs]
+  CT *dsh = reinterpret_cast<CT *>(wr + (exact ? (size_t)S * rs : 0));        // [Rt][nq][nth]
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const bool owns = t < a.nel;
+  const bool last = t == a.nel - 1;            // also writes coefficients n_el .. n_el + P - 1
+  const int tail_warp = (a.nel - 1) >> 5;
   const CT zero = ct_zero<CT>();
   CT wv[nq][P + 1];
 #pragma unroll
@@ -202,12 +208,14 @@ __global__ void __launch_bounds__(kLeanMaxThreads) xlean_kernel(LeanArgs<T> a) {
     // step it reads row it + P from ring slot (it - it0) % S
     auto issue = [&](int it) {
       const int row = it + P;
-      if (it < t1 && t < nx && row < a.Nt) {
+      if (it < t1 && row < a.Nt) {
         const int sl = (it - it0) % S;
-        lean_cp_async<(int)sizeof(T)>(xr + (size_t)sl * nth + t, xrow + (long long)row * planeX + t);
-        if (exact) {
-          lean_cp_async<8>(ur + (size_t)sl * nth + t, urow + (long long)row * planeX + t);
-          lean_cp_async<8>(wr + (size_t)sl * nth + t, wrow2 + (long long)row * planeX + t);
+        for (int cx = t; cx < nx; cx += nth) {
+          lean_cp_async<(int)sizeof(T)>(xr + (size_t)sl * rs + cx, xrow + (long long)row * planeX + cx);
+          if (exact) {
+            lean_cp_async<8>(ur + (size_t)sl * rs + cx, urow + (long long)row * planeX + cx);
+            lean_cp_async<8>(wr + (size_t)sl * rs + cx, wrow2 + (long long)row * planeX + cx);
+          }
         }
       }
       lean_commit();
@@ -215,6 +223,9 @@ __global__ void __launch_bounds__(kLeanMaxThreads) xlean_kernel(LeanArgs<T> a) {
 #pragma unroll
     for (int u = 0; u < S - 1; ++u) issue(it0 + u);
     CT pend = zero;   // this thread's output of the previous step before its cross-warp part
+    CT tail[P];       // the last element's thread: coefficients n_el - 1 + m, m = 1 .. P, likewise
+#pragma unroll
+    for (int m = 0; m < P; ++m) tail[m] = zero;
     auto flush = [&](int itf) {
       const int pp = itf & 1;
       if (lane < P && warp > 0) {
@@ -222,7 +233,21 @@ __global__ void __launch_bounds__(kLeanMaxThreads) xlean_kernel(LeanArgs<T> a) {
         for (int k = 1; k <= P; ++k)
           if (k > lane) pend = ct_add(pend, xch[pp][warp - 1][k - 1][lane + P - k]);
       }
-      if (t < nx) ct_store(yrow + (long long)itf * planeX + t, pend);
+      if (owns) ct_store(yrow + (long long)itf * planeX + t, pend);
+      if (last) {
+        // coefficient n_el - 1 + m takes c[k] of element n_el - 1 - (k - m), k >= m;
+        // those in the previous warp are in its exchange slots
+#pragma unroll
+        for (int m = 1; m <= P; ++m) {
+          CT v = tail[m - 1];
+          if (warp > 0) {
+#pragma unroll
+            for (int k = m + 1; k <= P; ++k)
+              if (k - m > lane) v = ct_add(v, xch[pp][warp - 1][k - 1][lane - (k - m) + P]);
+          }
+          ct_store(yrow + (long long)itf * planeX + a.nel - 1 + m, v);
+        }
+      }
     };
     for (int it = it0; it < t1; ++it) {
       lean_wait<S - 2>();
@@ -239,14 +264,14 @@ __global__ void __launch_bounds__(kLeanMaxThreads) xlean_kernel(LeanArgs<T> a) {
         const bool ok = owns && it + P < a.Nt;
         CT c[P + 1];
 #pragma unroll
-        for (int j = 0; j <= P; ++j) c[j] = ok ? ct_from<CT>(xr[(size_t)sl * nth + t + j]) : zero;
+        for (int j = 0; j <= P; ++j) c[j] = ok ? ct_from<CT>(xr[(size_t)sl * rs + t + j]) : zero;
         interp(c, xw[P]);
         if (exact) {
 #pragma unroll
-          for (int j = 0; j <= P; ++j) c[j] = ok ? from_pair<CT>(ur[(size_t)sl * nth + t + j]) : zero;
+          for (int j = 0; j <= P; ++j) c[j] = ok ? from_pair<CT>(ur[(size_t)sl * rs + t + j]) : zero;
           interp(c, uw[P]);
 #pragma unroll
-          for (int j = 0; j <= P; ++j) c[j] = ok ? from_pair<CT>(wr[(size_t)sl * nth + t + j]) : zero;
+          for (int j = 0; j <= P; ++j) c[j] = ok ? from_pair<CT>(wr[(size_t)sl * rs + t + j]) : zero;
           interp(c, ww[P]);
         }
       }
@@ -332,6 +357,18 @@ __global__ void __launch_bounds__(kLeanMaxThreads) xlean_kernel(LeanArgs<T> a) {
         CT v = ct_shfl_up(c[k], k);
         if (lane >= k) out = ct_add(out, v);
       }
+      if (warp == tail_warp) {   // warp-uniform: the shuffles below need the whole warp
+#pragma unroll
+        for (int m = 1; m <= P; ++m) {
+          CT v = c[m];
+#pragma unroll
+          for (int k = m + 1; k <= P; ++k) {
+            CT sv = ct_shfl_up(c[k], k - m);
+            if (lane >= k - m) v = ct_add(v, sv);
+          }
+          tail[m - 1] = v;
+        }
+      }
       if (lane >= 32 - P) {
 #pragma unroll
         for (int k = 1; k <= P; ++k) xch[it & 1][warp][k - 1][lane - (32 - P)] = c[k];
@@ -370,14 +407,15 @@ st_status launch_p(cudaStream_t s, const LeanArgs<T> &a, int threads, size_t sme
 
 }  // namespace
 
-int xlean_threads(int nel, int p) { return (nel + p + 31) / 32 * 32; }
+int xlean_threads(int nel, int p) { (void)p; return (nel + 31) / 32 * 32; }
 
 bool xlean_feasible(int nel, int p) { return xlean_threads(nel, p) <= kLeanMaxThreads; }
 
 size_t xlean_smem(int nel, int p, int rank, bool exact, bool pairs) {
   const size_t nth = (size_t)xlean_threads(nel, p);
+  const size_t rs = std::max(nth, (size_t)(nel + p + 3) / 4 * 4);   // ring row stride, as in the kernel
   const size_t elem = pairs ? 8 : 4;
-  return (size_t)kLeanRing * nth * (elem + (exact ? 16 : 0)) + (size_t)rank * (p + 1) * nth * elem;
+  return (size_t)kLeanRing * rs * (elem + (exact ? 16 : 0)) + (size_t)rank * (p + 1) * nth * elem;
 }
 
 int xlean_max_rank(int nel, int p, bool exact) {

@@ -140,6 +140,37 @@ def test_linearization_and_apply(P, c, form, kind):
     s.close()
 
 
+# x extents that put the last element of the lean kernel's row in lanes
+# 0 .. p-2 of a warp (33, 34 with p = 3) or last in a warp (64 with p = 2)
+TAIL_CASES = [dict(d=2, p=3, n_el=[33, 2], n_el_t=4), dict(d=2, p=3, n_el=[34, 2], n_el_t=4),
+              dict(d=2, p=2, n_el=[64, 2], n_el_t=4)]
+
+
+@pytest.mark.parametrize("c", TAIL_CASES, ids=[f"p{c['p']}-nx{c['n_el'][0]}" for c in TAIL_CASES])
+def test_lean_trailing_coefficients(P, c):
+    """The lean form gives each x element one thread, and the thread of the
+    last element also writes the p coefficients after it, taking the
+    contributions of the elements before it from the previous warp's exchange
+    slots when they sit there: both operators against the assembled matrix."""
+    desc = problem(c, operator_form="lean")
+    o = Oracle(desc)
+    u, w = iterate(o, 2)
+    A, info = o.linearization(u, w, "picard")
+    s = solver(P, desc)
+    du, dw = dev(u), dev(w)
+    ginfo = s.ionic(ptr(du), ptr(dw))
+    assert ginfo["rank"] == len(info["s"])
+    x = W.random_vector(o.st.N_dof, seed=5)
+    ref = A @ x
+    dx, dy = dev(x), empty(o.st.N_dof)
+    s.apply(ptr(dx), ptr(dy), P.ST_FP64)
+    assert rel(host(dy), ref) < 1e-12
+    dx32, dy32 = dev(x, np.float32), empty(o.st.N_dof, "float32")
+    s.apply(ptr(dx32), ptr(dy32), P.ST_MIXED)
+    assert rel(host(dy32), ref) < 2e-5
+    s.close()
+
+
 @pytest.mark.parametrize("form", ["bands", "lean"])
 def test_lowrank_long_time(P, form):
     """A Gram matrix larger than one batch of Lanczos steps (N_t = 61 against
