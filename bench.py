@@ -6,23 +6,27 @@ Sec. 3.1 (ionic quadrature, Theta-hat, low rank, reaction + SU bands, the
 preconditioned GMRES solve of A u = f to true relative residual 1e-8, the
 w-update, relaxation and the stopping norm), starting every step from the
 same saved iterate k = 2.  The default workload is the largest configuration
-that fits one GB300: the 3D cube (p = 2, 64^3 spatial x 128 time elements,
-37,086,984 unknowns, mixed precision); --workload c2_aniso_2d selects the 2D
-anisotropic one (p = 3, 128 x 128 x 256 elements, 4,427,538 unknowns).  The
-set-up (1D data, eigendecompositions, LU factors) runs once per problem and
-is reported apart.
+(3D cube, p = 3, 96^3 spatial x 192 time elements, 188,238,006 unknowns,
+mixed precision, the lean operator form that fits it in one GB300);
+--workload c3_cube_3d selects the 3D p = 2, 64^3 x 128 one and c2_aniso_2d
+the 2D anisotropic one (p = 3, 128 x 128 x 256 elements).  The set-up (1D
+data, eigendecompositions, LU factors) runs once per problem and is reported
+apart.
 
 Output: one JSON line (rank 0).  `value` is unknowns per second of the mixed
 FP32/FP64 path with inputs resident on the device; `fp64` gives the FP64 path
 on the same step; `e2e` measures the same step through the C ABI from pinned
-host buffers, copies included; `roofline` reports the FP32 operator apply
-(the hot kernel group of every GMRES iteration) against the measured HBM
-bandwidth, counting the method's algorithmic bytes (x in, y out, u^k and w^k
-in: 16 bytes per unknown), with every stage's time and bandwidth beside it;
+host buffers, copies included; `roofline` reports the dominant kernel: in
+the lean form the reaction + SU kernel, bound by FP32 arithmetic (the
+reaction integrated at every space-time Gauss point), against the FP32 peak
+derived from the SM count and clock; in the band form the fused band kernel
+against the measured HBM bandwidth.  The whole FP32 apply against 16 bytes
+per unknown (x in, y out, u^k and w^k in) is given beside it.  `linear_solve`
+times one solve at the frozen linearization in both precisions;
 `cpu_baseline` times the CPU oracle on a bounded sample of the same workload.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                       [--workload c3_cube_3d|c2_aniso_2d]
+                       [--workload c5_cube_3d|c3_cube_3d|c2_aniso_2d]
 """
 
 import argparse
@@ -37,10 +41,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "c5_cube_3d"
-# DRAM bytes (read + write) of one FP32 operator apply (all of its kernels)
-# from an ncu capture of the same build, per workload; absent until captured,
-# and removed whenever one of those kernels changes.
-TRAFFIC_PER_APPLY = {}
+# DRAM bytes (read + write) of the dominant kernel per unit of its work (one
+# coefficient of one Gauss row at one time row) from an ncu capture of the
+# same kernel on a smaller case of the same form and degree, scaled to a
+# full launch by the units it processes; absent until captured, and removed
+# whenever that kernel changes.
+TRAFFIC_PER_UNIT = {"c5_cube_3d": 23.67}   # xlean_kernel<float,3>, 32^3 x 64 lean case: 895.8 MB / 37.85 M units
 # bounded CPU samples of each workload (same physics, fewer elements): the
 # cpu_baseline of our line (one step, about 10 s of oracle work) and each step
 # of the reference arm (a few seconds, so that its whole run stays short)
@@ -59,15 +65,21 @@ APPLY_BYTES_PER_DOF = 16.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(CPU_SAMPLES))
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=1)
-    ap.add_argument("--scale", default=None, help="nx,ny,nt element counts (smaller case, e.g. for profiling)")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="FP64 fixed-point steps beside the mixed ones (default 1; 0 on the 96^3 x 192 workload, "
+                         "whose FP64 linear solve alone takes minutes)")
+    ap.add_argument("--profiled-steps", type=int, default=1, help="steps repeated with per-stage events")
+    ap.add_argument("--scale", default=None,
+                    help="element counts n_el..., n_el_t (a smaller case of the same physics, e.g. for profiling)")
+    ap.add_argument("--form", default=None, choices=["auto", "bands", "lean"],
+                    help="operator form (default: the workload's, auto)")
     ap.add_argument("--serve", action="store_true",
                     help="the serving stream instead of the single workload (latency p50/p99, DoF/s)")
     ap.add_argument("--requests", type=int, default=256, help="--serve: requests in the stream")
@@ -75,8 +87,9 @@ def parse():
                     help="--serve: Poisson arrival rate (requests/s); 0 = 0.8 x the measured saturated rate")
     ap.add_argument("--slots", type=int, default=8, help="--serve: requests in flight at most")
     ap.add_argument("--serve-log", default=None, help="--serve: write one JSON line per request to this file")
-    ap.add_argument("--serve-requests", type=int, default=64,
-                    help="requests of the short serving pass in the default run (0: none)")
+    ap.add_argument("--serve-requests", type=int, default=None,
+                    help="requests of the short serving pass in the default run (0: none; default 64, "
+                         "0 on the 96^3 x 192 workload)")
     return ap.parse_args()
 
 
@@ -85,8 +98,8 @@ def measured_peaks():
     if os.path.exists(path):
         with open(path) as fh:
             d = json.load(fh)
-        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured"
-    return 6800.0, 1900.0, "fallback"
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, 1900.0, "fallback", 2070.0
 
 
 class Clocks:
@@ -245,10 +258,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def time_linear_solve(solver, u2, w2, stream, reps):
+def time_linear_solve(solver, u2, w2, stream, reps, warm=1):
     """Time of one linear solve to relative residual 1e-8 (st_linsolve) with
     the linearization frozen at the saved iterate (u2, w2) and x0 = u2; the
-    right-hand side is f.  Mean of `reps` solves after one untimed solve."""
+    right-hand side is f.  Mean of `reps` solves after `warm` untimed ones."""
     import torch
     n = u2.numel()
     f = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -257,7 +270,7 @@ def time_linear_solve(solver, u2, w2, stream, reps):
     solver.linearize(u2.data_ptr(), w2.data_ptr(), "picard")
     out = None
     times = []
-    for k in range(reps + 1):
+    for k in range(reps + warm):
         x.copy_(u2)
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
@@ -265,7 +278,7 @@ def time_linear_solve(solver, u2, w2, stream, reps):
         out = solver.linsolve(f.data_ptr(), x.data_ptr(), allow_unconverged=True)
         ev1.record(stream)
         ev1.synchronize()
-        if k > 0:
+        if k >= warm:
             times.append(ev0.elapsed_time(ev1))
     ms = sum(times) / len(times)
     return {"ms": ms, "dof_per_s": n / (ms / 1000.0), "gmres_iters": out["gmres_iters"],
@@ -299,6 +312,8 @@ def run_ours(args):
         vals = [int(v) for v in args.scale.split(",")]
         desc["n_el"] = vals[:-1]
         desc["n_el_t"] = vals[-1]
+    if args.form:
+        desc["operator_form"] = args.form
     desc["max_fp"] = 1
     desc["rtol"] = 1e-8
     desc["gmres_m"] = 150
@@ -324,9 +339,13 @@ def run_ours(args):
         s.desc_m = d["gmres_m"]
         return s, time.perf_counter() - t0
 
+    big = WORKLOAD == "c5_cube_3d"
+    fp64_steps = args.fp64_steps if args.fp64_steps is not None else (0 if big else 1)
+    serve_requests = args.serve_requests if args.serve_requests is not None else (0 if big else 64)
     s, setup_s = make("mixed")
     s_m = s.desc_m
-    s_form = "lean" if W.config(WORKLOAD)["d"] >= 2 else "bands"
+    s_form = {1: "bands", 2: "lean"}.get(s.dims["operator_form"], "?")
+    s_tc = bool(s.dims["precond_tc"])
     N = s.dims["N_dof"]
     u = torch.zeros(N, dtype=torch.float64, device="cuda")
     w = torch.zeros_like(u)
@@ -365,7 +384,7 @@ def run_ours(args):
     # (their recording costs a few percent, so they stay out of the headline)
     s.profile(True)
     ptimes = []
-    for _ in range(min(args.steps, 3)):
+    for _ in range(max(1, args.profiled_steps)):
         ms, _ = step(s)
         ptimes.append(ms)
     barrier()
@@ -375,34 +394,54 @@ def run_ours(args):
     ms_step, value = whole_job(ms_local, N, dist, "cuda")
     st_last = stats[-1]
 
-    # roofline of the FP32 operator apply, the kernel group every GMRES
-    # iteration runs (stages kron + interp + qband; one qband launch per
-    # apply): the method's algorithmic bytes (APPLY_BYTES_PER_DOF per
-    # unknown) over the event-timed duration of those stages.  The bytes the
-    # kernels actually stream (stored time bands at the spatial Gauss points,
-    # sum-factorization intermediates) are reported beside it as `streamed`.
-    hbm, bf16, src = peaks
-    applies = max(prof["qband"]["launches"], 1)
-    t_apply = sum(prof[k]["ms"] for k in ("kron", "interp", "qband")) / applies
+    # roofline of the dominant kernel (stage qband: one launch per FP32
+    # apply), from the profiled steps' per-stage CUDA events on the solver's
+    # stream.  Lean form: the reaction at every space-time Gauss point and the
+    # SU rank terms, counted as the flops of its sum-factorized quadrature,
+    # against the FP32 peak (SMs x 128 lanes x 2 flop per FMA x the maximum SM
+    # clock).  Band form: the fused band kernel against the measured HBM
+    # bandwidth, its bytes being the stored time bands and the x rows.
+    hbm, bf16, src, sm_max = peaks
+    q = prof["qband"]
+    nl = max(q["launches"], 1)
+    t_launch = q["ms"] / nl
+    units = q["bytes"] / nl / 24.0   # lean: x, y FP32 and u^k, w^k pairs per unit
+    tpu = TRAFFIC_PER_UNIT.get(WORKLOAD) if args.scale is None else None
+    if s_form == "lean":
+        flops = q["flops"] / nl
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+        achieved = flops / (t_launch / 1000.0) / 1e12 if t_launch > 0 else 0.0
+        roof = {"bound": "alu", "kernel": "xlean_kernel<float,%d> (stage qband)" % desc["p"],
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": tpu * units if tpu else None,
+                "algorithmic_flops_per_launch": flops,
+                "flops_rule": "per (Gauss row, x element, time row): x, u^k, w^k at the p+1 x Gauss points; "
+                              "at the (p+1)^2 space-time points of the next time element C(u,w) x and its test "
+                              "against p+1 time functions; the R rank bands; the x projection",
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flop per FMA x {sm_max:g} MHz",
+                "algorithmic_bytes_per_launch": q["bytes"] / nl,
+                "hbm_gbs": q["bytes"] / nl / (t_launch / 1000.0) / 1e9 if t_launch > 0 else None}
+    else:
+        achieved = q["bytes"] / nl / (t_launch / 1000.0) / 1e9 if t_launch > 0 else 0.0
+        roof = {"bound": "hbm", "kernel": "xband_fused_kernel<float,%d> (stage qband)" % desc["p"],
+                "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "algorithmic_bytes_per_launch": q["bytes"] / nl,
+                "bytes_rule": "stored time bands (p+1 per spatial Gauss point and time row) + x rows in and out",
+                "peak_source": src}
+    t_apply = sum(prof[k]["ms"] for k in ("kron", "interp", "qband")) / nl
     alg = APPLY_BYTES_PER_DOF * N
-    achieved = alg / (t_apply / 1000.0) / 1e9 if t_apply > 0 else 0.0
-    streamed = sum(prof[k]["bytes"] for k in ("kron", "interp", "qband")) / applies
-    traffic = TRAFFIC_PER_APPLY.get(WORKLOAD) if args.scale is None else None
-    roof = {"bound": "hbm", "kernel": "FP32 operator apply (kron + interp + xband_fused; stages kron, interp, qband)",
-            "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": traffic, "algorithmic_bytes_per_launch": alg,
-            "algorithmic_bytes_rule": f"{APPLY_BYTES_PER_DOF:g} B per unknown: x in, y out, u^k and w^k in (FP32)",
-            "apply_ms": t_apply, "applies": applies,
-            "streamed_bytes_per_apply": streamed,
-            "streamed_over_algorithmic": streamed / alg,
-            "peak_source": src,
-            "share_of_step": t_apply * applies / sum(ptimes),
-            "profiled_ms_per_step": sum(ptimes) / len(ptimes),
-            "stages_ms_per_step": {k: v["ms"] / len(ptimes) for k, v in prof.items()},
-            "stages_gbs": {k: (v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] > 0 and v["bytes"] > 0 else None)
-                           for k, v in prof.items()}}
+    roof.update({"launch_ms": t_launch, "launches": nl, "share_of_step": q["ms"] / sum(ptimes),
+                 "apply_hbm_view": {"ms": t_apply, "algorithmic_bytes": alg,
+                                    "gbs": alg / (t_apply / 1000.0) / 1e9 if t_apply > 0 else None,
+                                    "frac_of_hbm": alg / (t_apply / 1000.0) / 1e9 / hbm if t_apply > 0 else None,
+                                    "rule": f"whole FP32 apply, {APPLY_BYTES_PER_DOF:g} B per unknown: x in, "
+                                            "y out, u^k and w^k in"},
+                 "profiled_ms_per_step": sum(ptimes) / len(ptimes),
+                 "stages_ms_per_step": {k: v["ms"] / len(ptimes) for k, v in prof.items()},
+                 "stages_gbs": {k: (v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] > 0 and v["bytes"] > 0 else None)
+                                for k, v in prof.items()}})
 
-    # e2e: pinned host inputs, copies inside the timed region
+    # e2e: pinned host buffers, copies inside the timed region
     e2e = None
     if not args.no_e2e:
         hu = u2.cpu().pin_memory()
@@ -410,7 +449,7 @@ def run_ours(args):
         ou = torch.empty_like(hu).pin_memory()
         ow = torch.empty_like(hw).pin_memory()
         e_ms = []
-        for k in range(2):
+        for k in range(1 if big else 2):
             ev0 = torch.cuda.Event(enable_timing=True)
             ev1 = torch.cuda.Event(enable_timing=True)
             ev0.record(stream)
@@ -428,7 +467,7 @@ def run_ours(args):
     # the linear solve alone, mixed and FP64, at the same frozen linearization
     linear = {}
     try:
-        linear["mixed"] = time_linear_solve(s, u2, w2, stream, 2)
+        linear["mixed"] = time_linear_solve(s, u2, w2, stream, 1 if big else 2, warm=0 if big else 1)
     except Exception as e:  # noqa: BLE001 (reported in the line, never fatal)
         linear["mixed"] = {"error": f"{type(e).__name__}: {e}"}
     s.close()
@@ -436,18 +475,22 @@ def run_ours(args):
     fp64 = None
     if not args.no_fp64:
         s64, setup64 = make("fp64")
-        u.copy_(u2); w.copy_(w2)
-        step(s64)                                   # warm-up
-        f_ms = []
-        f_st = None
-        for _ in range(max(1, args.fp64_steps)):
-            ms, f_st = step(s64)
-            f_ms.append(ms)
-        fm = sum(f_ms) / len(f_ms)
-        fp64 = {"value": N / (fm / 1000.0), "ms_per_step": fm, "gmres_iters": f_st["gmres_iters"],
-                "rel_res": f_st["rel_res"], "setup_s": setup64, "speedup_mixed_vs_fp64": fm / ms_step}
+        fp64 = {"setup_s": setup64, "gmres_m": s64.desc_m}
+        if fp64_steps > 0:
+            u.copy_(u2); w.copy_(w2)
+            step(s64)                                   # warm-up
+            f_ms = []
+            f_st = None
+            for _ in range(fp64_steps):
+                ms, f_st = step(s64)
+                f_ms.append(ms)
+            fm = sum(f_ms) / len(f_ms)
+            fp64.update({"value": N / (fm / 1000.0), "ms_per_step": fm, "gmres_iters": f_st["gmres_iters"],
+                         "rel_res": f_st["rel_res"], "speedup_mixed_vs_fp64": fm / ms_step})
         try:
-            linear["fp64"] = time_linear_solve(s64, u2, w2, stream, 1)
+            # with no FP64 step before it the solve is timed cold: its own first
+            # FP64 residual is the warm-up of the FP64 kernels
+            linear["fp64"] = time_linear_solve(s64, u2, w2, stream, 1, warm=0 if fp64_steps == 0 else 1)
             if "ms" in linear.get("mixed", {}):
                 linear["speedup_mixed_vs_fp64"] = linear["fp64"]["ms"] / linear["mixed"]["ms"]
         except Exception as e:  # noqa: BLE001
@@ -455,11 +498,11 @@ def run_ours(args):
         s64.close()
 
     serving = None
-    if ws == 1 and args.serve_requests > 0:
+    if ws == 1 and serve_requests > 0:
         # the serving stream, shortened: latency percentiles beside the step
         # throughput; a failure here is reported in the line, never fatal
         try:
-            f = serving_pass(args.serve_requests, 0.0, args.slots, local, clocks=False)
+            f = serving_pass(serve_requests, 0.0, args.slots, local, clocks=False)
             serving = {k: f[k] for k in ("value", "unit", "latency_ms", "queue_ms", "service_ms_mean", "requests",
                                          "done", "failed", "rejected", "errors", "config")}
         except Exception as e:  # noqa: BLE001
@@ -478,7 +521,10 @@ def run_ours(args):
         "config": {"workload": workload_name(desc),
                    "N_dof": N, "precision": f"mixed: FP32 inner GMRES({s_m}) + FP64 refinement",
                    "operator_form": s_form, "gmres_m": s_m,
-                   "l2": "inputs larger than L2 (vectors of %.0f MB FP32 and the stored time bands)" % (4 * N / 1e6),
+                   "preconditioner": ("TF32 tensor-core (tcgen05) FD transforms" if s_tc
+                                      else "FP32 CUDA-core FD transforms"),
+                   "l2": "inputs larger than L2 (vectors of %.0f MB FP32; %s)" % (
+                       4 * N / 1e6, "the Gauss-row arrays of x, u^k, w^k" if s_form == "lean" else "the stored time bands"),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "setup_s": setup_s},
         "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},

@@ -155,6 +155,9 @@ typedef struct {
   long long N_s, N_t, N_dof;
   long long Q_s;         /* spatial Gauss points: prod n_el[l] (p+1) */
   int n[3];              /* spatial basis functions per direction */
+  int operator_form;     /* ST_FORM_BANDS or ST_FORM_LEAN: the form set-up chose */
+  int precond_tc;        /* 1: the FP32 preconditioner's spatial transforms run on
+                          * the tensor cores (tcgen05, TF32), 0: on CUDA cores */
 } st_dims;
 
 /* Output of st_ionic (Eq. theta_ce_u and Eq. tol). */

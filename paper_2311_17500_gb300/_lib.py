@@ -57,7 +57,8 @@ class StProblemDesc(ctypes.Structure):
 
 class StDims(ctypes.Structure):
     _fields_ = [("N_s", ctypes.c_longlong), ("N_t", ctypes.c_longlong), ("N_dof", ctypes.c_longlong),
-                ("Q_s", ctypes.c_longlong), ("n", ctypes.c_int * 3)]
+                ("Q_s", ctypes.c_longlong), ("n", ctypes.c_int * 3), ("operator_form", ctypes.c_int),
+                ("precond_tc", ctypes.c_int)]
 
 
 class StIonicInfo(ctypes.Structure):

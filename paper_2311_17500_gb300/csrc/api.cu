@@ -1100,6 +1100,8 @@ st_status st_get_dims(const st_handle *h, st_dims *out) {
   if (!h || !out) return ST_ERR_ARG;
   out->N_s = h->Ns; out->N_t = h->Nt; out->N_dof = h->Ndof; out->Q_s = h->Qs;
   for (int l = 0; l < 3; ++l) out->n[l] = h->n[l];
+  out->operator_form = h->lean ? ST_FORM_LEAN : ST_FORM_BANDS;
+  out->precond_tc = h->use_tc ? 1 : 0;
   return ST_OK;
 }
 
