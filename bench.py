@@ -611,6 +611,9 @@ def serving_pass(n_requests, rate, slots, local, clocks=True, log_path=None):
                 d = desc_of(reqs[r["id"]])
                 print(f"request {r['id']} ({d['p']}, {d['n_el']}, {d['n_el_t']}): {r['error']}", file=sys.stderr)
     iters = [r["result"]["stats"]["total_gmres"] for r in recs if r["status"] == "done"]
+    # requests whose FP32 preconditioner ran on CUDA cores (an axis wider than
+    # the tensor-core transform takes, n_l > 256)
+    no_tc = sum(1 for r in recs if r["status"] == "done" and r["result"].get("precond_tc") is False)
     if log_path:
         # one JSON line per request: its shape, its times and how it ended
         with open(log_path, "w") as f:
@@ -620,6 +623,8 @@ def serving_pass(n_requests, rate, slots, local, clocks=True, log_path=None):
                                     "n_dof": W.n_dofs(d), "arrival_s": r["arrival"], "admitted_s": r["admitted"],
                                     "done_s": r["done"], "status": r["status"], "retries": r["retries"],
                                     "gmres": (r["result"] or {}).get("stats", {}).get("total_gmres"),
+                                    "operator_form": (r["result"] or {}).get("operator_form"),
+                                    "precond_tc": (r["result"] or {}).get("precond_tc"),
                                     "error": r["error"]}) + "\n")
     fields = {
         "value": out.get("dof_per_s"), "unit": "DoF/s",
@@ -630,6 +635,7 @@ def serving_pass(n_requests, rate, slots, local, clocks=True, log_path=None):
         "makespan_s": out.get("makespan_s"),
         "requests": out["requests"], "done": out["done"], "failed": out["failed"], "rejected": out["rejected"],
         "retries": sum(r["retries"] for r in recs),
+        "cuda_core_preconditioner": no_tc,
         "errors": dict(sorted(errors.items(), key=lambda kv: -kv[1])[:5]),
         "failed_shapes": [[desc_of(reqs[r["id"]])["p"]] + desc_of(reqs[r["id"]])["n_el"] +
                           [desc_of(reqs[r["id"]])["n_el_t"]] for r in recs if r["status"] == "failed"][:12],

@@ -182,7 +182,9 @@ def gpu_runner(desc_of, keep_solution=False, device=None):
     """Runs one request: st_setup and st_solve (u = w = 0 initially) on a
     private stream of `device` (default: the current device when the runner
     is made; worker threads do not inherit it); returns the solver
-    statistics (and u, w on the host when `keep_solution`)."""
+    statistics, the operator form set-up chose and whether the FP32
+    preconditioner's transforms ran on the tensor cores (and u, w on the host
+    when `keep_solution`)."""
     import torch
     from . import _lib as L
     dev = torch.cuda.current_device() if device is None else int(device)
@@ -199,9 +201,11 @@ def gpu_runner(desc_of, keep_solution=False, device=None):
             try:
                 st = s.solve(u.data_ptr(), w.data_ptr(), allow_unconverged=True)
                 stream.synchronize()
+                form = {1: "bands", 2: "lean"}.get(s.dims["operator_form"], "?")
+                tc = bool(s.dims["precond_tc"])
             finally:
                 s.close()
-            out = dict(stats=st, n_dof=n)
+            out = dict(stats=st, n_dof=n, operator_form=form, precond_tc=tc)
             if keep_solution:
                 out["u"] = u.cpu().numpy()
                 out["w"] = w.cpu().numpy()
