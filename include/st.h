@@ -90,14 +90,15 @@ enum { ST_INNER_AUTO = 0, ST_INNER_FP32 = 1, ST_INNER_DF = 2 };
  *  ST_PRECOND_FP32: transforms on CUDA cores in FP32;
  *  ST_PRECOND_FP64: the FP64 preconditioner, its input and output rounded to
  *                   FP32;
- *  ST_PRECOND_AUTO: TF32, and FP64 from the first refinement step on that
- *                   fails (one that reduces the true residual by less than a
- *                   factor 2).
+ *  ST_PRECOND_AUTO: TF32 for d <= 2 and FP32 for d = 3, and FP64 from the
+ *                   first refinement step on that fails (one that reduces the
+ *                   true residual by less than a factor 2).
  * On the 3D workloads FP32 and FP64 preconditioners give the same residual
  * after the same number of iterations, the FP64 one at 4x the cost of an
- * iteration.  TF32 converges a little more slowly per iteration but costs
- * less: its solves were 17 % (64^3 x 128) and 5 % (96^3 x 192) faster than
- * FP32 ones (GB300 measurement). */
+ * iteration.  TF32 converges a little more slowly per iteration; on the
+ * 64^3 x 128 workload it let a refinement step fail, after which the handle
+ * ran the FP64 preconditioner and double-float operator at 4x the cost of
+ * an FP64 solve (GB300 measurement).  Explicit TF32 stays available. */
 enum { ST_PRECOND_AUTO = 0, ST_PRECOND_TF32 = 1, ST_PRECOND_FP32 = 2, ST_PRECOND_FP64 = 3 };
 
 #define ST_MAX_STIM 8

@@ -1324,7 +1324,7 @@ static st_status setup_impl(st_handle *h) {
     // zero-padded FP32 copies of U_l^T and U_l for the tensor-core transforms
     bool fits = true;
     for (int l = 0; l < h->d; ++l) fits = fits && h->n[l] <= 256;
-    const bool want_tc = D.precond_arith == ST_PRECOND_TF32 || D.precond_arith == ST_PRECOND_AUTO;
+    const bool want_tc = D.precond_arith == ST_PRECOND_TF32 || (D.precond_arith == ST_PRECOND_AUTO && h->d <= 2);
     if (fits && want_tc && tc_state(h->stream, nullptr) == 1) {
       for (int l = 0; l < h->d; ++l) {
         int n = h->n[l];
