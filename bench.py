@@ -69,7 +69,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(CPU_SAMPLES))
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison step")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the FP64 comparison (it is skipped by default under torchrun with more than one "
+                         "rank on the 96^3 x 192 workload, where it holds every GPU for minutes; --fp64 forces it)")
+    ap.add_argument("--fp64", action="store_true", help="run the FP64 comparison whatever the rank count")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=None,
@@ -473,7 +476,9 @@ def run_ours(args):
     s.close()
 
     fp64 = None
-    if not args.no_fp64:
+    # replicas repeat the same FP64 solve; on the largest workload it takes
+    # minutes, so a multi-rank run leaves it out unless asked for
+    if not args.no_fp64 and (args.fp64 or ws == 1 or not big):
         s64, setup64 = make("fp64")
         fp64 = {"setup_s": setup64, "gmres_m": s64.desc_m}
         if fp64_steps > 0:
