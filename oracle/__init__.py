@@ -15,6 +15,11 @@ tolerance, convergence rates against closed-form solutions and the spatially
 uniform ODE limit.  Parity is unpinned for the full nonlinear Spline-Upwind
 wave runs, which only the oracle itself defines.
 
+`supg` holds the comparison method of Sec. 4.2 (C^0 time splines, SUPG and
+shock capturing), pinned by exact reproduction of a solution in its discrete
+space and by its convergence rate; its constants h/(2p+1) and c h^2/4 are
+the paper's definitions and are parity unpinned.
+
 For problems too large to assemble, `rows` evaluates selected rows of the
 operators and of the load vector over the supports of their test functions.
 That uses the same tables and Gauss rule as the assembly, and the rows equal

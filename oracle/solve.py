@@ -16,7 +16,10 @@ Follows Sec. 3 of the paper:
   * a Newton variant on the u-equation (Jacobian coefficient C_J, w lagged,
     theta frozen at the current iterate, no relaxation);
   * optionally (eps_reaction >= 0) the reaction coefficient in low rank:
-    its values at the Greville grid truncated like Theta-hat (reading A7).
+    its values at the Greville grid truncated like Theta-hat (reading A7);
+  * the comparison method of Sec. 4.2 (stabilization = "supg_sc", on C^0
+    time splines): SUPG plus shock capturing in place of the SU term, with
+    the f part of SUPG on the right-hand side (oracle/supg.py).
 
 Linear systems are solved with scipy's sparse direct solver (SuperLU).
 
@@ -27,6 +30,7 @@ import numpy as np
 import scipy.sparse.linalg as spla
 
 from . import model
+from . import supg
 from .spacetime import SpaceTime
 from .stabilization import tau_solve, theta_hat, low_rank, interpolate_at_gauss, greville_values
 
@@ -36,11 +40,15 @@ class Oracle:
         self.desc = desc
         self.st = SpaceTime(desc)
         st = self.st
-        self.tau_coeffs, self.tau_q = tau_solve(st)
+        self.supg = desc["stabilization"] == "supg_sc"
+        # tau belongs to SU, whose splines are C^(p-1) in time
+        self.tau_coeffs, self.tau_q = (None, None) if self.supg else tau_solve(st)
         tq = st.time_points()[:, None, :, None]
         xs = [x[None, :, None, :] for x in st.xs]
         self.f_q = model.source(desc, xs, tq) * np.ones((st.n_el_t, st.N_el_s, st.nq_t, st.nq_s))
         self.F = st.load(self.f_q)
+        if self.supg:
+            self.F = self.F + supg.supg_load(st, self.f_q)
         self.lin_terms = st.linear_terms(desc["C_m"], desc["D"])
 
     # ------------------------------------------------------------ pieces
@@ -69,14 +77,29 @@ class Oracle:
         return dict(fields=fl, R=R, theta_hat=th, U=U, s=s, V=V, theta_lr=approx,
                     theta_q=theta_q, **info)
 
-    def operator(self, coef_q, theta_q=None):
+    def operator(self, coef_q, theta_q=None, sc_q=None):
         """Assembled A with reaction coefficient coef_q at the Gauss points and,
-        for SU, theta at the Gauss points."""
+        for SU, theta at the Gauss points; for SUPG + shock capturing, the
+        SUPG terms with the same reaction coefficient and the shock-capturing
+        coefficient sc_q."""
         st = self.st
+        d = self.desc
         terms = list(self.lin_terms) + st.mass_terms(coef_q)
-        if self.desc["stabilization"] == "su" and theta_q is not None:
-            terms += st.su_terms(self.desc["C_m"], self.tau_q, theta_q)
+        if d["stabilization"] == "su" and theta_q is not None:
+            terms += st.su_terms(d["C_m"], self.tau_q, theta_q)
+        if self.supg:
+            terms += supg.supg_terms(st, d["C_m"], d["D"], coef_q)
+            if sc_q is not None:
+                terms += supg.sc_terms(st, sc_q, d.get("sc_c", 1.0))
         return st.assemble(terms)
+
+    def supg_ionic(self, u, w):
+        """Fields, residual and shock-capturing coefficient at (u, w)."""
+        d = self.desc
+        fl = self.fields(u, w)
+        R = self.residual_q(fl)
+        sc_q, den = supg.sc_coefficient(R, fl["u"], fl["ut"], d["C_m"], self.st.T)
+        return dict(fields=fl, R=R, sc_q=sc_q, den=den, s=np.zeros(0))
 
     def reaction_lowrank(self, u, w, kind):
         """Low-rank reaction coefficient (reading A7, the SUPG variant's
@@ -95,6 +118,13 @@ class Oracle:
         """(A, ionic info) of one nonlinear step at (u, w)."""
         d = self.desc
         kind = d["nonlinear"] if kind is None else kind
+        if self.supg:
+            if kind != "picard" or d.get("eps_reaction", -1.0) >= 0.0:
+                raise NotImplementedError("SUPG + shock capturing: fixed point with the exact reaction only")
+            info = self.supg_ionic(u, w)
+            coef = model.reaction_coef(d, info["fields"]["u"], info["fields"]["w"])
+            info["coef_q"] = coef
+            return self.operator(coef, sc_q=info["sc_q"]), info
         info = self.ionic(u, w)
         fl = info["fields"]
         if d.get("eps_reaction", -1.0) >= 0.0:

@@ -2,8 +2,10 @@
 direct loop over (d+1)-dimensional elements with Gauss quadrature.
 
 Discrete space (Sec. 2): tensor-product B-splines of degree p in each of the d
-spatial directions and in time, maximal regularity, the first time function
-b_1 removed to impose the zero initial condition, so N_t = n_t - 1 and
+spatial directions and in time, maximal regularity (or C^0 in time with
+time_continuity = "c0", the space of the comparison method of Sec. 4.2), the
+first time function b_1 removed to impose the zero initial condition, so
+N_t = n_t - 1 and
 N_dof = N_s * N_t.  Unknowns are ordered colexicographically: x fastest, then
 y, z, and time slowest, i.e. index = i_t * N_s + i_s with
 i_s = i_x + n_x (i_y + n_y i_z).
@@ -28,6 +30,15 @@ def open_knots(breaks, p):
         return None
     b = np.asarray(breaks, dtype=float)
     return np.concatenate([np.full(p, b[0]), b, np.full(p, b[-1])])
+
+
+def c0_time_knots(n_el_t, p, breaks=None):
+    """Knot vector on [0, 1] of degree p and continuity C^0 (the time space of
+    the comparison method of Sec. 4.2): p+1 copies of each end, every interior
+    breakpoint p times; uniform breakpoints unless given."""
+    b = np.linspace(0.0, 1.0, n_el_t + 1) if breaks is None else np.asarray(breaks, dtype=float)
+    inner = np.repeat(b[1:-1], p)
+    return np.concatenate([np.full(p + 1, b[0]), inner, np.full(p + 1, b[-1])])
 
 
 def _spatial_table(dirs, kk):
@@ -102,8 +113,11 @@ class SpaceTime:
         breaks = desc.get("breaks") or [None] * self.d
         self.sdirs = [Direction(ne, p, nq=nq, scale=1.0, max_deriv=2, knots=open_knots(breaks[l], p))
                       for l, ne in enumerate(desc["n_el"])]
-        self.tdir = Direction(desc["n_el_t"], p, nq=nq, scale=self.T, max_deriv=p,
-                              knots=open_knots(desc.get("breaks_t"), p))
+        if desc.get("time_continuity", "max") == "c0":
+            tknots = c0_time_knots(desc["n_el_t"], p, desc.get("breaks_t"))
+        else:
+            tknots = open_knots(desc.get("breaks_t"), p)
+        self.tdir = Direction(desc["n_el_t"], p, nq=nq, scale=self.T, max_deriv=p, knots=tknots)
         self.n = [dr.n for dr in self.sdirs]
         self.N_s = int(np.prod(self.n))
         self.n_t = self.tdir.n
