@@ -88,9 +88,10 @@ Sizes plan(const st_problem_desc &D) {
   z.nmax = z.Nt;
   for (int l = 0; l < D.d; ++l) z.nmax = std::max(z.nmax, z.n[l]);
   z.cap = (int)std::min<long long>(z.Nt, z.Ns);
-  // automatic form: the band form, faster per apply wherever it fits (C2:
-  // 0.30 against 1.23 ms, C3: 5.1 against 16 ms per FP32 apply on GB300),
-  // unless its footprint exceeds kBandFormLimit and the lean form applies
+  // automatic form: the band form, faster per apply wherever it fits (FP32
+  // apply on GB300: 0.30 against 1.23 ms on the 2D p = 3, 128^2 x 256 mesh,
+  // 5.1 against 16 ms on the 3D p = 2, 64^3 x 128 one), unless its footprint
+  // exceeds kBandFormLimit and the lean form applies
   z.lean = D.operator_form == ST_FORM_LEAN;
   if (D.operator_form == ST_FORM_AUTO && lean_applies(D)) {
     st_problem_desc b = D;
